@@ -1,0 +1,389 @@
+"""Pins of the FP64 oracle against what the mathematics fixes (CPU only, no GPU).
+
+Each test checks the oracle against something other than itself: a library routine, a
+closed form, an exact identity, an invariance of the S-matrix, or an independent brute-force
+calculation (oracle/fullcolour.py, written from the standard Feynman rules with explicit SU(3)
+matrices).  The workflow pinned here is the paper's random numbers -> momenta -> matrix
+element per event (arXiv 2210.11122, Sec. 1, Fig. 1; Sec. 2).
+"""
+import ctypes
+import ctypes.util
+import math
+import os
+from fractions import Fraction
+from itertools import permutations
+
+import numpy as np
+import pytest
+
+SQRTS, MT, AS = 1500.0, 173.0, 0.118
+
+
+# ----------------------------------------------------------------------------------------
+# Philox4x32-10
+# ----------------------------------------------------------------------------------------
+def _curand():
+    cands = [ctypes.util.find_library("curand"), "/usr/local/cuda/lib64/libcurand.so", "libcurand.so.10"]
+    for c in cands:
+        if not c:
+            continue
+        try:
+            return ctypes.CDLL(c)
+        except OSError:
+            continue
+    return None
+
+
+@pytest.mark.parametrize("seed", [0, 1, 0x123456789ABCDEF, 2**64 - 1])
+def test_philox_matches_curand_host_generator(orc, seed):
+    """cuRAND's host-side PHILOX4_32_10 generator (library code run on the CPU) emits, for seed s,
+    word 4i+j = Philox4x32-10(counter (0, 0, i, 0), key (s_lo, s_hi))[j]."""
+    L = _curand()
+    if L is None:
+        pytest.skip("libcurand not available")
+    gen = ctypes.c_void_p()
+    assert L.curandCreateGeneratorHost(ctypes.byref(gen), 161) == 0  # CURAND_RNG_PSEUDO_PHILOX4_32_10
+    try:
+        assert L.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
+        n = 4096
+        out = np.zeros(n, dtype=np.uint32)
+        assert L.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(n)) == 0
+    finally:
+        L.curandDestroyGenerator(gen)
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    ref = np.concatenate([orc.philox([0, 0, i, 0], key) for i in range(n // 4)])
+    assert np.array_equal(out, ref)
+
+
+def test_event_uniform_mapping(orc):
+    """u = (x + 0.5) 2^-32 from counter {e_lo, e_hi, j, 0}, key {seed_lo, seed_hi}."""
+    seed, e = 0xDEADBEEF12345678, (7 << 32) + 11
+    for j in range(5):
+        x = orc.philox([e & 0xFFFFFFFF, e >> 32, j, 0], [seed & 0xFFFFFFFF, seed >> 32])
+        u = orc.uniforms(seed, e, j)
+        assert np.array_equal(u, (x.astype(np.float64) + 0.5) * 2.0**-32)
+        assert np.all((u > 0) & (u < 1))
+
+
+# ----------------------------------------------------------------------------------------
+# RAMBO
+# ----------------------------------------------------------------------------------------
+def mdot(a, b):
+    return a[..., 0] * b[..., 0] - a[..., 1] * b[..., 1] - a[..., 2] * b[..., 2] - a[..., 3] * b[..., 3]
+
+
+@pytest.mark.parametrize("ng", [0, 1, 2, 3])
+def test_rambo_conservation_and_mass_shell(orc, ng):
+    mom, w, st = orc.events(ng, 10 + ng, 2000)
+    assert np.all(st == 0)
+    fin = mom[:, 2:, :].sum(axis=1)
+    assert np.max(np.abs(fin - np.array([SQRTS, 0, 0, 0]))) <= 1e-12 * SQRTS
+    ini = mom[:, 0, :] + mom[:, 1, :]
+    assert np.max(np.abs(ini - np.array([SQRTS, 0, 0, 0]))) == 0.0
+    for i in (2, 3):
+        m2 = mdot(mom[:, i], mom[:, i])
+        assert np.max(np.abs(m2 / MT**2 - 1.0)) <= 1e-10
+    for i in range(4, 4 + ng):
+        m2 = mdot(mom[:, i], mom[:, i])
+        assert np.max(np.abs(m2)) <= 1e-12 * SQRTS**2
+    assert np.all(mom[:, 2:, 0] > 0)
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+def test_rambo_massless_weight_is_flat_volume(orc, n):
+    """Massless n-body phase-space volume (2pi)^(4-3n) (pi/2)^(n-1) s^(n-2) / ((n-1)!(n-2)!)."""
+    rng = np.random.default_rng(n)
+    vol = (2 * math.pi) ** (4 - 3 * n) * (math.pi / 2) ** (n - 1) * SQRTS ** (2 * (n - 2)) / (
+        math.factorial(n - 1) * math.factorial(n - 2))
+    for _ in range(20):
+        u = rng.uniform(0.01, 0.99, size=(n, 4))
+        p, w, st = orc.rambo(np.zeros(n), u, SQRTS)
+        assert st == 0
+        assert abs(w / vol - 1) < 1e-13
+        assert np.max(np.abs(mdot(p, p))) < 1e-10 * SQRTS**2
+
+
+def test_rambo_two_body_massive_weight(orc):
+    """Two-body phase space with equal masses: beta / (8 pi), beta = sqrt(1 - 4 m^2 / s)."""
+    mom, w, st = orc.events(0, 3, 100)
+    beta = math.sqrt(1 - 4 * MT**2 / SQRTS**2)
+    assert np.max(np.abs(w / (beta / (8 * math.pi)) - 1)) < 1e-12
+
+
+def test_rambo_three_body_massive_volume(orc):
+    """Mean massive RAMBO weight = 3-body phase-space volume, computed independently as the Dalitz-plot
+    area / (16 s (2pi)^3) (PDG kinematics), for t tbar g at sqrt(s) = 1500."""
+    from scipy.integrate import quad
+    s = SQRTS**2
+    m1 = m2 = MT
+    m3 = 0.0
+
+    def m23_range(m12sq):
+        # PDG: E2*, E3* in the (12) rest frame
+        m12 = math.sqrt(m12sq)
+        e2 = (m12sq - m1**2 + m2**2) / (2 * m12)
+        e3 = (s - m12sq - m3**2) / (2 * m12)
+        p2 = math.sqrt(max(e2**2 - m2**2, 0))
+        p3 = math.sqrt(max(e3**2 - m3**2, 0))
+        return (e2 + e3) ** 2 - (p2 + p3) ** 2, (e2 + e3) ** 2 - (p2 - p3) ** 2
+
+    area, _ = quad(lambda x: m23_range(x)[1] - m23_range(x)[0], (m1 + m2) ** 2, (SQRTS - m3) ** 2,
+                   epsabs=0, epsrel=1e-12, limit=200)
+    vol = area / (16 * s * (2 * math.pi) ** 3)
+    _, w, st = orc.events(1, 99, 200000)
+    assert np.all(st == 0)
+    mean, err = w.mean(), w.std() / math.sqrt(len(w))
+    assert abs(mean - vol) < 5 * err
+    assert err / vol < 3e-3
+
+
+# ----------------------------------------------------------------------------------------
+# matrix element: closed form, brute force, invariances
+# ----------------------------------------------------------------------------------------
+def test_ggtt_closed_form(orc):
+    from oracle.closed_form import ggtt_me
+    mom, _, _ = orc.events(0, 1, 512)
+    me = orc.me_batch(0, mom)
+    ref = ggtt_me(mom, MT, AS)
+    # gauge cancellations between the three diagrams amplify rounding to ~1e-13 at worst
+    assert np.max(np.abs(me / ref - 1)) < 1e-12
+    assert np.median(np.abs(me / ref - 1)) < 1e-14
+
+
+def test_ggtt_closed_form_massless_limit(orc):
+    from oracle.closed_form import ggtt_me
+    mom, _, st = orc.events(0, 2, 256, mt=0.0)
+    assert np.all(st == 0)
+    me = orc.me_batch(0, mom, mt=0.0)
+    ref = ggtt_me(mom, 0.0, AS)
+    # The closed form assumes exactly on-shell momenta; RAMBO's FP64 momenta are off shell by
+    # ~1e-13 E^2, which near-collinear events (small 2 p1.p4) amplify to a few 1e-12.
+    assert np.max(np.abs(me / ref - 1)) < 2e-11
+    assert np.median(np.abs(me / ref - 1)) < 1e-14
+
+
+@pytest.mark.parametrize("ng,nev,hels", [(0, 2, None), (1, 1, None), (2, 1, [0, 21, 42, 63])])
+def test_full_colour_brute_force(orc, ng, nev, hels):
+    """Colour-ordered recursion x exact colour matrix == explicit SU(3) sum over all Feynman diagrams."""
+    from oracle import fullcolour as fc
+    mom, _, _ = orc.events(ng, 40 + ng, nev)
+    for e in range(nev):
+        mh = orc.me_hel(ng, mom[e])
+        hs = range(len(mh)) if hels is None else hels
+        for h in hs:
+            ref = fc.helicity_me(ng, mom[e], h, MT, AS)
+            assert abs(mh[h] - ref) <= 1e-12 * mh.max()
+            if ref > 1e-10 * mh.max():
+                assert abs(mh[h] / ref - 1) < 1e-11
+
+
+@pytest.mark.parametrize("ng", [0, 1, 2, 3])
+def test_gauge_invariance(orc, ng):
+    """epsilon_g -> k_g for any one gluon makes every colour-ordered amplitude vanish."""
+    mom, _, _ = orc.events(ng, 50 + ng, 1)
+    _, J = orc.me_hel(ng, mom[0], want_jamps=True)
+    scale = np.abs(J).max()
+    for g in range(ng + 2):
+        _, Jg = orc.me_hel(ng, mom[0], gauge_gluon=g, want_jamps=True)
+        assert np.abs(Jg).max() <= 1e-10 * scale
+
+
+def _boost_rotate(p, seed):
+    rng = np.random.default_rng(seed)
+    q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    if np.linalg.det(q) < 0:
+        q[:, 0] *= -1
+    out = p.copy()
+    out[..., 1:] = p[..., 1:] @ q.T
+    beta = rng.uniform(-0.4, 0.4, size=3)
+    b2 = beta @ beta
+    g = 1 / math.sqrt(1 - b2)
+    E, v = out[..., 0].copy(), out[..., 1:].copy()
+    bp = v @ beta
+    out[..., 0] = g * (E + bp)
+    out[..., 1:] = v + ((g - 1) * bp / b2)[..., None] * beta + (g * E)[..., None] * beta
+    return out
+
+
+@pytest.mark.parametrize("ng", [0, 1, 2, 3])
+def test_lorentz_invariance(orc, ng):
+    mom, _, _ = orc.events(ng, 60 + ng, 2)
+    for e in range(2):
+        a = orc.me_hel(ng, mom[e]).sum()
+        b = orc.me_hel(ng, _boost_rotate(mom[e], e)).sum()
+        assert abs(b / a - 1) < 1e-12
+
+
+@pytest.mark.parametrize("ng", [0, 1, 2, 3])
+def test_beam_swap_and_gluon_permutation(orc, ng):
+    mom, _, _ = orc.events(ng, 70 + ng, 1)
+    p = mom[0]
+    a = orc.me_hel(ng, p).sum()
+    ps = p.copy()
+    ps[[0, 1]] = ps[[1, 0]]
+    ps[:, 3] *= -1
+    assert abs(orc.me_hel(ng, ps).sum() / a - 1) < 1e-12
+    fin = list(range(4, 4 + ng))
+    for perm in list(permutations(fin))[1:3]:
+        pp = p.copy()
+        pp[fin] = p[list(perm)]
+        assert abs(orc.me_hel(ng, pp).sum() / a - 1) < 1e-12
+
+
+@pytest.mark.parametrize("ng", [1, 2])
+def test_parity(orc, ng):
+    """QCD conserves parity: |M_h(p)|^2 = |M_{-h}(P p)|^2 with P: p -> -p (3-momenta)."""
+    mom, _, _ = orc.events(ng, 80 + ng, 1)
+    p = mom[0]
+    pp = p.copy()
+    pp[:, 1:] *= -1
+    a = orc.me_hel(ng, p)
+    b = orc.me_hel(ng, pp)
+    nh = len(a)
+    flipped = np.array([b[(nh - 1) ^ h] for h in range(nh)])
+    assert np.max(np.abs(a - flipped)) <= 1e-12 * a.max()
+
+
+def test_ggtt_helicity_zeros(orc):
+    """gg -> t tbar: equal physical gluon helicities (J_z = 0) produce equal-helicity top pairs only;
+    the four configurations with lambda_1 = lambda_2 and lambda_t != lambda_tbar vanish."""
+    mom, _, _ = orc.events(0, 5, 16)
+    for e in range(16):
+        mh = orc.me_hel(0, mom[e])
+        zero = [h for h in range(16) if ((h >> 3) & 1) == ((h >> 2) & 1) and ((h >> 1) & 1) != (h & 1)]
+        assert zero == [1, 2, 13, 14]
+        for h in range(16):
+            if h in zero:
+                assert mh[h] <= 1e-25 * mh.sum()
+            else:
+                assert mh[h] > 1e-8 * mh.sum()
+
+
+def test_fullcolour_wavefunctions_are_helicity_eigenstates():
+    """The brute-force wavefunctions carry the physical helicities they are labelled with:
+    (Sigma.p^) u = lam u, (Sigma.p^) v = -lam v, (S.k^) eps = lam eps, plus the Dirac equations."""
+    from oracle import fullcolour as fc
+    rng = np.random.default_rng(3)
+    sig = fc._S[1:]
+    for _ in range(10):
+        d = rng.normal(size=3)
+        d /= np.linalg.norm(d)
+        pabs = rng.uniform(10, 700)
+        p = np.concatenate([[math.sqrt(pabs**2 + MT**2)], pabs * d])
+        Sig = sum(d[i] * np.kron(np.eye(2), sig[i]) for i in range(3))
+        pslash = np.einsum("m,mst->st", fc.METRIC @ p, fc.GAMMA)
+        for lam in (1, -1):
+            u = fc.spinor_u(p, MT, lam)
+            v = fc.spinor_v(p, MT, lam)
+            assert np.allclose(Sig @ u, lam * u, atol=1e-9 * np.abs(u).max())
+            assert np.allclose(Sig @ v, -lam * v, atol=1e-9 * np.abs(v).max())
+            assert np.allclose((pslash - MT * np.eye(4)) @ u, 0, atol=1e-9 * pabs * np.abs(u).max())
+            assert np.allclose((pslash + MT * np.eye(4)) @ v, 0, atol=1e-9 * pabs * np.abs(v).max())
+            k = np.concatenate([[pabs], pabs * d])
+            e = fc.polarisation(k, lam)
+            S = [np.array([[0, 0, 0], [0, 0, -1j], [0, 1j, 0]]), np.array([[0, 0, 1j], [0, 0, 0], [-1j, 0, 0]]),
+                 np.array([[0, -1j, 0], [1j, 0, 0], [0, 0, 0]])]
+            Sk = sum(d[i] * S[i] for i in range(3))
+            assert np.allclose(Sk @ e[1:], lam * e[1:], atol=1e-12)
+            assert abs(fc.METRIC @ k @ e) < 1e-9 * pabs
+            assert abs(e @ fc.METRIC @ e.conj() + 1) < 1e-12
+
+
+def test_diagram_counts():
+    """All tree diagrams of g g -> t tbar + n g: 3, 16, 123, 1240 (the process set of the paper)."""
+    from oracle import fullcolour as fc
+    golden = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "process_sizes.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                ng, nd, nh, nc = map(int, line.split())
+                golden[ng] = (nd, nh, nc)
+    for ng, (nd, nh, nc) in golden.items():
+        assert fc.count_diagrams(ng + 2) == nd
+        assert 1 << (ng + 4) == nh
+        assert math.factorial(ng + 2) == nc
+
+
+# ----------------------------------------------------------------------------------------
+# colour matrix
+# ----------------------------------------------------------------------------------------
+def _numeric_colour_rows(k, rows):
+    from oracle import fullcolour as fc
+    perms = list(permutations(range(k)))
+    # (T^sigma)_{ij} for every assignment of adjoint indices: shape [8]*k + [3,3]
+    def word(sig):
+        out = None
+        for pos, g in enumerate(sig):
+            # T^{a_g} with a_g on axis g
+            shp = [1] * k + [3, 3]
+            shp[g] = 8
+            t = fc.T.reshape(shp)
+            out = t if out is None else np.einsum("...ij,...jk->...ik", out, t)
+        return np.broadcast_to(out, (8,) * k + (3, 3))
+    W = {s: word(s) for s in perms}
+    res = {}
+    for r in rows:
+        s = perms[r]
+        res[r] = np.array([np.sum(W[s] * W[t].conj()).real for t in perms])
+    return res
+
+
+@pytest.mark.parametrize("k,rows", [(2, [0, 1]), (3, list(range(6))), (4, [0, 7, 23]), (5, [0, 77])])
+def test_colour_matrix_exact_vs_gell_mann(k, rows):
+    from oracle import colour
+    C = colour.colour_matrix_exact(k)
+    num = _numeric_colour_rows(k, rows)
+    for r, vals in num.items():
+        exact = np.array([float(x) for x in C[r]])
+        assert np.max(np.abs(vals - exact)) < 1e-12 * np.abs(exact).max()
+
+
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_colour_matrix_structure(k):
+    """Diagonal N C_F^k; symmetric; positive definite; ggtt = (1/3)[[16,-2],[-2,16]]."""
+    from oracle import colour
+    C = colour.colour_matrix_exact(k)
+    n = len(C)
+    diag = 3 * Fraction(4, 3) ** k
+    for i in range(n):
+        assert C[i][i] == diag
+        for j in range(i):
+            assert C[i][j] == C[j][i]
+    ev = np.linalg.eigvalsh(colour.colour_matrix(k))
+    assert ev.min() > 0
+    if k == 2:
+        assert C == ((Fraction(16, 3), Fraction(-2, 3)), (Fraction(-2, 3), Fraction(16, 3)))
+
+
+# ----------------------------------------------------------------------------------------
+# helicity filter and flop counter
+# ----------------------------------------------------------------------------------------
+@pytest.mark.parametrize("ng,nwarm", [(0, 1024), (1, 1024), (2, 256), (3, 64)])
+def test_helicity_filter_gap(orc, ng, nwarm):
+    """Rejected and accepted max-ratios are at least six decades apart around tau = 1e-9, so the
+    mask cannot depend on FP rounding order."""
+    mom, _, _ = orc.events(ng, 1 + ng, nwarm)
+    mask, ratio = orc.hel_mask(ng, mom, nthreads=os.cpu_count() or 1)
+    acc = ratio[ratio > 1e-9]
+    rej = ratio[ratio <= 1e-9]
+    # accepted ratios sit >= 2 decades above tau, rejected ones (exact zeros up to rounding)
+    # >= 6 decades below it
+    assert acc.min() > 1e-7
+    if len(rej):
+        assert rej.max() < 1e-15
+        assert acc.min() / rej.max() > 1e6
+    expect_good = 12 if ng == 0 else 1 << (ng + 4)
+    assert len(acc) == expect_good
+    bits = sum(bin(int(w)).count("1") for w in mask)
+    assert bits == expect_good
+
+
+@pytest.mark.parametrize("ng", [0, 1, 2])
+def test_flop_counter_colour_part(orc, ng):
+    """The colour sum costs exactly 4 ncol^2 + 4 ncol flops per helicity."""
+    mom, _, _ = orc.events(ng, 1, 1)
+    c = orc.flops(ng, mom[0])
+    ncol = math.factorial(ng + 2)
+    nh = 1 << (ng + 4)
+    assert c["colour"]["add"] + c["colour"]["mul"] == nh * (4 * ncol * ncol + 4 * ncol)
+    assert c["amp"]["add"] + c["amp"]["mul"] > 0
