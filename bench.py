@@ -1,0 +1,314 @@
+#!/usr/bin/env python
+"""Throughput benchmark: matrix elements per second on one or more GB300s.
+
+Metric (the paper's N_events / t_MEs, arXiv 2210.11122 Sec. 2, Tables 1-2): MEs/s of the whole
+random numbers -> momenta -> ME path.  One step = one pass of every stage over one batch:
+Philox4x32-10 + massive RAMBO (mg_rambo_range), the helicity filter on the batch's first 1,024
+events (mg_hel_filter), and the FP64 matrix elements of every event (mg_sigmakin).
+
+Default workload: g g -> t tbar g, 524,288 events per GPU, sqrt(s) = 1500 GeV, m_t = 173 GeV,
+alpha_s = 0.118, Philox seed 2.  Under torchrun every rank processes its own disjoint range of
+the seed's event stream (weak scaling, no collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--process ggttg] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the host cores on a
+bounded sample of the same workload.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "ggtt": dict(ng=0, nevt=16384, seed=1),
+    "ggttg": dict(ng=1, nevt=524288, seed=2),
+    "ggttgg": dict(ng=2, nevt=262144, seed=3),
+    "ggttggg": dict(ng=3, nevt=65536, seed=4),
+}
+LABEL = {"ggtt": "gg->ttbar", "ggttg": "gg->ttbar g", "ggttgg": "gg->ttbar gg", "ggttggg": "gg->ttbar ggg"}
+SQRTS, MT, ALPHAS = 1500.0, 173.0, 0.118
+L2_FLUSH_BYTES = 256 << 20
+METRIC = "MEs/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--process", default="ggttg", choices=sorted(WORKLOADS))
+    ap.add_argument("--nevt", type=int, default=0, help="events per GPU (default: the workload's)")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def config_of(args, nevt, extra=None):
+    w = WORKLOADS[args.process]
+    c = {"workload": "%s LO QCD, %d events/GPU, sqrt(s)=1500 GeV, m_t=173 GeV, alpha_s=0.118, Philox seed %d"
+                     % (LABEL[args.process], nevt, w["seed"]),
+         "process": args.process, "events_per_gpu": nevt, "seed": w["seed"],
+         "step": "philox+rambo -> helicity filter (1024 warm-up events) -> FP64 matrix elements",
+         "l2": "256 MB memset between timed steps, outside the per-step CUDA events"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+# ------------------------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline and the reference arm)
+# ------------------------------------------------------------------------------------------
+def oracle_rate(ng, seed, nevt, target_s=15.0):
+    """Events/s of the FP64 oracle's ME on all host cores, over a bounded sample of the workload."""
+    import oracle
+    cores = os.cpu_count() or 1
+    probe = 200 if ng < 2 else (40 if ng == 2 else 8)
+    mom, _, _ = oracle.events(ng, seed, probe * cores)
+    t = time.perf_counter()
+    oracle.me_batch(ng, mom, nthreads=cores)
+    rate = probe * cores / (time.perf_counter() - t)
+    n = int(max(cores, min(nevt, rate * target_s)))
+    mom, _, _ = oracle.events(ng, seed, n)
+    t = time.perf_counter()
+    oracle.me_batch(ng, mom, nthreads=cores)
+    dt = time.perf_counter() - t
+    return n / dt, cores, n, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = WORKLOADS[args.process]
+    nevt = args.nevt or w["nevt"]
+    import oracle
+    oracle.build()
+    cores = os.cpu_count() or 1
+    # each step: a bounded sample of the workload, sized so the whole run stays within minutes
+    _, _, nsamp, dt = oracle_rate(w["ng"], w["seed"], nevt, target_s=min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    mom, _, _ = oracle.events(w["ng"], w["seed"], nsamp)
+    for _ in range(args.warmup):
+        oracle.me_batch(w["ng"], mom[: max(1, nsamp // 8)], nthreads=cores)
+    times = []
+    for _ in range(args.steps):
+        t = time.perf_counter()
+        oracle.me_batch(w["ng"], mom, nthreads=cores)
+        times.append(time.perf_counter() - t)
+    ms = 1e3 * statistics.mean(times)
+    value = nsamp / (ms * 1e-3)
+    sample = "first %d events of the workload's Philox stream per step (of %d), ME only" % (nsamp, nevt)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MEs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args, nevt, {"reference": "FP64 CPU oracle (oracle/me_oracle.cpp) on the host cores"}),
+            "cpu_baseline": {"value": value, "unit": "MEs/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "MEs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2210_11122_gb300 import build as mgbuild
+    mgbuild.build()
+    import paper_2210_11122_gb300 as mg
+
+    w = WORKLOADS[args.process]
+    ng, seed = w["ng"], w["seed"]
+    nevt = args.nevt or w["nevt"]
+    e0 = rank * nevt
+    stream = torch.cuda.Stream()
+    ctx = mg.Context(ng, mt=MT, alphas=ALPHAS)
+    mom = torch.zeros(ctx.mom_count(nevt), dtype=torch.float64, device="cuda")
+    me = torch.zeros(nevt, dtype=torch.float64, device="cuda")
+    me32 = torch.zeros(nevt, dtype=torch.float64, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    nwarm = min(nevt, 1024)
+
+    def step(precision, ev):
+        ev[0].record(stream)
+        ctx.rambo_range(seed, e0, nevt, SQRTS, mom, stream=stream)
+        ctx.hel_filter(mom, nwarm, stream=stream)
+        ev[1].record(stream)
+        ctx.sigmakin(mom, nevt, me if precision == mg.MG_FP64 else me32, precision, stream=stream)
+        ev[2].record(stream)
+
+    def timed(precision, steps, warmup):
+        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                step(precision, [torch.cuda.Event(enable_timing=True) for _ in range(3)])
+                flush.zero_()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for k in range(steps):
+                step(precision, evs[k])
+                flush.zero_()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        wall = time.perf_counter() - t0
+        step_ms = [e[0].elapsed_time(e[2]) for e in evs]
+        me_ms = [e[1].elapsed_time(e[2]) for e in evs]
+        return statistics.mean(step_ms), statistics.mean(me_ms), wall
+
+    if ctx.check(stream) != 0:
+        raise RuntimeError("RAMBO did not converge")
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms_step, ms_me, wall = timed(mg.MG_FP64, args.steps, max(3, args.warmup))
+    clk = clocks.stop()
+    nbad = ctx.check(stream)
+    if world > 1:
+        t = torch.tensor([ms_step, ms_me], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step, ms_me = t.tolist()
+    value = world * nevt / (ms_step * 1e-3)
+
+    # FP32-amplitude variant of the same step
+    ms32, ms32_me, _ = timed(mg.MG_FP32_AMP, max(3, args.steps // 2), 3)
+    torch.cuda.synchronize()
+    a, b = me.double().cpu(), me32.double().cpu()
+    rel = ((b / a) - 1).abs()
+    fp32 = {"value": world * nevt / (ms32 * 1e-3), "ms_per_step": ms32, "me_kernel_ms": ms32_me,
+            "rel_err_vs_fp64": {"max": float(rel.max()), "p99": float(rel.quantile(0.99)) if rel.numel() <= 1 << 24 else None,
+                                "median": float(rel.median())}}
+
+    # end to end through the host-buffer entry point (pinned momenta in, MEs out, copies timed)
+    host_mom = mom.cpu().pin_memory()
+    host_me = torch.zeros(nevt, dtype=torch.float64).pin_memory()
+    ne2e = max(3, args.steps // 2)
+    for _ in range(2):
+        ctx.sigmakin_host(host_mom, nevt, host_me, mg.MG_FP64, stream=stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(ne2e):
+        ctx.sigmakin_host(host_mom, nevt, host_me, mg.MG_FP64, stream=stream)
+    e2e_s = (time.perf_counter() - t0) / ne2e
+    e2e = {"value": world * nevt / e2e_s, "unit": "MEs/s", "h2d_bytes_per_step": int(host_mom.numel() * 8),
+           "d2h_bytes_per_step": int(nevt * 8),
+           "api": "mg_sigmakin_host: pinned AoSoA momenta -> device -> FP64 MEs -> host"}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel (the FP64 matrix-element kernel, ALU bound on the FP64 pipe)
+    mask, ngood = ctx.hel_mask()
+    amp_f, col_f = mg.flops_per_helicity(ng)
+    flops = (amp_f + col_f) * ngood * nevt
+    peak = mg.measure_fma_peak(fp32=False, iters=2048)
+    achieved = flops / (ms_me * 1e-3)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": "k_me_helicity<%d,double> + k_hel_sum (mg_sigmakin)" % (ng + 2),
+                "flops_per_event": (amp_f + col_f) * ngood,
+                "peak_source": "measured FP64 DFMA-chain microbenchmark (mg_measure_fma_peak) on this GPU"}
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        rate, cores, n, dt = oracle_rate(ng, seed, nevt)
+        cpu = {"value": rate, "unit": "MEs/s", "cores": cores, "kind": "oracle",
+               "sample": "first %d events of the workload (of %d), FP64 ME only, %.1f s on %d threads"
+                         % (n, nevt, dt, cores)}
+
+    launches_per_step = 1 + 3 + 2   # rambo; filter (ME, sum, mask); sigmakin (ME, sum)
+    line = {"metric": METRIC, "value": value, "unit": "MEs/s", "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_of(args, nevt, {"parallelism": "dp%d (disjoint event ranges)" % world}),
+            "me_kernel_ms": ms_me, "wall_s": wall, "nonconverged_events": nbad, "good_helicities": ngood,
+            "fp32_amp": fp32, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "gpu_launches": launches_per_step * args.steps}
+    print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

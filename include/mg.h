@@ -1,0 +1,163 @@
+/*
+ * mg.h -- C ABI of the GB300 (sm_103a) engine for per-event tree-level QCD matrix elements of
+ *         g g -> t tbar + n_g gluons, n_g = 0..3.
+ *
+ * The workflow follows arXiv 2210.11122 (Sec. 1, Fig. 1): random numbers -> phase-space
+ * momenta -> matrix element (ME) per event, all on the GPU (the "standalone" application of
+ * Sec. 1).  The ME is the per-event hot path of Sec. 2 (the paper's gg -> t tbar gg kernel uses
+ * every one of the 255 registers of a thread) and its throughput is counted as
+ * N_events / t_MEs (Sec. 2, Tables 1-2).  The paper prints no formulas; the physics below is the
+ * textbook one (HELAS wavefunctions, Feynman-gauge QCD vertices, colour decomposition of
+ * Mangano-Parke) with the conventions stated here.
+ *
+ * Conventions shared by every entry point
+ *   - metric (+,-,-,-); momenta (E, px, py, pz) in GeV, FP64;
+ *   - particle order g1, g2, t, tbar, g3, ..., g(2+n_g); npar = 4 + n_g;
+ *     incoming p1 = (sqrt(s)/2)(1,0,0,1), p2 = (sqrt(s)/2)(1,0,0,-1);
+ *   - helicity index h = sum_i bit_i 2^(npar-1-i), bit_i = 1 for physical helicity +1,
+ *     particle 0 (g1) is the most significant bit; nhel = 2^npar;
+ *   - ME = (1/256) (1/n_g!) sum_{good h} sum_colours |M_h|^2: averaged over the helicities and
+ *     colours of the two incoming gluons, divided by n_g! for identical final-state gluons;
+ *   - alpha_s fixed (default 0.118), m_t = 173, top width 0 unless set.
+ *
+ * Momentum layout ("AoSoA", V = 32 events per page): element (event e, particle i, component mu)
+ * sits at  mom[((e / 32) * npar + i) * 4 * 32 + mu * 32 + (e % 32)].  A buffer for nevt events
+ * holds mg_mom_count(process, nevt) doubles (nevt rounded up to a multiple of 32); pages are
+ * 8-byte aligned doubles, every warp-wide access is one 256-byte line.
+ *
+ * Ownership and errors
+ *   - The caller owns every buffer passed in (device buffers are raw cudaMalloc/torch pointers);
+ *     the library never frees caller memory.  A context owns only its own state (helicity mask,
+ *     colour matrix, couplings, scratch).
+ *   - Calls taking a stream are asynchronous and stream-ordered (stream = cudaStream_t, NULL =
+ *     legacy default stream).  Argument errors are returned synchronously; launch errors return
+ *     MG_ECUDA; device-side conditions (RAMBO non-convergence) are recorded in the context and
+ *     reported by mg_check() after the stream has drained.  No C++ exception crosses the ABI.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef MG_H
+#define MG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MG_OK = 0,
+  MG_EINVAL = 1,   /* invalid argument (null pointer, bad size, sqrt(s) <= sum of masses, ...) */
+  MG_ENOMEM = 2,   /* device or host allocation failed */
+  MG_ECUDA = 3,    /* a CUDA call failed (launch error, no device, ...) */
+  MG_ENOCONV = 4,  /* RAMBO massive rescaling did not converge for some event */
+  MG_EAGAIN = 5,   /* not ready yet (serving) */
+  MG_ETIMEOUT = 6, /* a bounded wait expired */
+  MG_EBUSY = 7,    /* resource busy (serving admission) */
+  MG_ENOTSUP = 8   /* valid request that this build does not implement */
+} mg_status;
+
+typedef enum { MG_GG_TT = 0, MG_GG_TTG = 1, MG_GG_TTGG = 2, MG_GG_TTGGG = 3 } mg_process;
+
+/* Arithmetic of mg_sigmakin.  MG_FP64 is plain FP64 throughout (per-event relative error
+ * vs an FP64 reference <= 1e-12).  MG_FP32_AMP computes the amplitudes in FP32 with FP64 kept for
+ * momenta, the top wavefunctions and the helicity sum. */
+typedef enum { MG_FP64 = 0, MG_FP32_AMP = 1, MG_FP64_TCCOLOR = 2, MG_MIXED = 3 } mg_precision;
+
+typedef struct {
+  double mt;        /* top mass [GeV], default 173 */
+  double wt;        /* top width [GeV], default 0 */
+  double alphas;    /* strong coupling, default 0.118 */
+  int hel_warmup;   /* events used by the helicity filter, default 1024 */
+  double hel_tau;   /* helicity h is kept iff max_e |M_h|^2 / sum_h' |M_h'|^2 > hel_tau, default 1e-9 */
+} mg_params;
+
+typedef struct mg_ctx mg_ctx;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* mg_strerror(mg_status s);
+
+/* Fill *p with the defaults listed in mg_params. */
+void mg_default_params(mg_params* p);
+
+/* Sizes of a process: npar, nhel, ncol (colour flows = (n_g+2)!), number of Feynman diagrams.
+ * Any output pointer may be NULL.  Host only. */
+mg_status mg_process_info(mg_process proc, int* npar, int* nhel, int* ncol, int* ndiagrams);
+
+/* Number of doubles of an AoSoA momentum buffer for nevt events (nevt rounded up to 32). */
+int64_t mg_mom_count(mg_process proc, int64_t nevt);
+
+/* Exact colour matrix C = num / den (C(sigma,tau) = Tr(T^sigma (T^tau)^dagger), colour flows in
+ * the lexicographic order of the gluon permutations; Mangano-Parke colour decomposition).
+ * num receives ncol*ncol int64 values, *den the common denominator.  Host only, no GPU needed. */
+mg_status mg_colour_matrix(mg_process proc, int64_t* num, int64_t* den);
+
+/* Create a context on the current CUDA device: uploads couplings, colour matrix and helicity
+ * tables.  params may be NULL (defaults).  *out receives the context. */
+mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out);
+
+/* Release a context and its device memory (synchronises the device first).  NULL is a no-op. */
+void mg_destroy(mg_ctx* ctx);
+
+/* Philox4x32-10 words (Salmon et al. SC'11) for nevt events and nfinal final-state particles:
+ * words[(e * nfinal + j) * 4 + w] = Philox4x32-10(counter {e_lo, e_hi, j, 0}, key {seed_lo, seed_hi})[w].
+ * words_dev holds 4 * nevt * nfinal uint32 on the device, 16-byte aligned. */
+mg_status mg_philox(uint64_t seed, int64_t nevt, int nfinal, uint32_t* words_dev, void* stream);
+
+/* Random numbers -> momenta (Sec. 1, Fig. 1 of the paper): per event e and final particle j the
+ * four uniforms u_w = (x_w + 0.5) 2^-32 of the Philox words above drive massive RAMBO
+ * (Kleiss-Stirling-Ellis): massless momenta, then the Newton solve for the rescaling xi,
+ * stopped at |f| <= 1e-14 sqrt(s) (<= 50 steps).  Writes AoSoA FP64 momenta of all npar particles
+ * (incoming beams included) and, if wgt_dev is not NULL, the phase-space weight per event.
+ * sqrt(s) <= 2 m_t -> MG_EINVAL.  Events that fail to converge are counted in the context
+ * (see mg_check). */
+mg_status mg_rambo(mg_ctx* ctx, uint64_t seed, int64_t nevt, double sqrts, double* mom_dev, double* wgt_dev,
+                   void* stream);
+
+/* The same for the events e0 .. e0+nevt-1 of the seed's stream (Philox counters start at e0):
+ * event e0+i is written at position i of mom_dev / wgt_dev.  Disjoint ranges on several GPUs
+ * reproduce the single-GPU sample exactly. */
+mg_status mg_rambo_range(mg_ctx* ctx, uint64_t seed, int64_t e0, int64_t nevt, double sqrts, double* mom_dev,
+                         double* wgt_dev, void* stream);
+
+/* Helicity filter: recompute the context's helicity mask from the first min(nevt, hel_warmup)
+ * events of mom_dev (AoSoA).  good(h) <=> max_e |M_h|^2 / sum_h' |M_h'|^2 > hel_tau, evaluated in
+ * FP64.  Stream-ordered; the mask is used by every later mg_sigmakin on this context. */
+mg_status mg_hel_filter(mg_ctx* ctx, const double* mom_dev, int64_t nevt, void* stream);
+
+/* Matrix elements: me_dev[e] = ME of event e of mom_dev (AoSoA), e < nevt.  If no helicity mask
+ * has been computed yet, the first call runs mg_hel_filter on its own first events.  precision
+ * selects the arithmetic (MG_ENOTSUP if not built). */
+mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_precision precision, double* me_dev,
+                      void* stream);
+
+/* The same, through host buffers: copies mom_host (AoSoA, mg_mom_count doubles) to the device,
+ * computes, and copies the MEs back to me_host; returns after the results are in me_host.
+ * Device staging buffers are owned by the context and grown on demand. */
+mg_status mg_sigmakin_host(mg_ctx* ctx, const double* mom_host, int64_t nevt, mg_precision precision,
+                           double* me_host, void* stream);
+
+/* Copy the current helicity mask (ceil(nhel/32) words, bit h of word h/32) to mask_host and the
+ * number of good helicities to *ngood.  Synchronises the context's last stream. */
+mg_status mg_hel_mask(mg_ctx* ctx, uint32_t* mask_host, int* ngood);
+
+/* Wait for the context's work on stream and report device-side conditions: MG_ENOCONV if any
+ * event since the last mg_check failed to converge in RAMBO (the count goes to *nbad if not
+ * NULL), MG_ECUDA on an asynchronous CUDA error, else MG_OK.  Clears the condition. */
+mg_status mg_check(mg_ctx* ctx, void* stream, int64_t* nbad);
+
+/* Floating-point operation counts of one event's ME in this engine's algorithm, per good
+ * helicity: fp64[0] = amplitude part (wavefunctions, currents, jamps), fp64[1] = colour sum
+ * (4 ncol^2 + 4 ncol).  FMA counts 2.  Host only. */
+mg_status mg_flops_per_helicity(mg_process proc, double* amp_flops, double* colour_flops);
+
+/* Diagnostic: FMA throughput of the current device, the ALU roofline denominator of the
+ * matrix-element kernels.  Runs 8 independent FMA chains per thread (iters x 16 FMAs each) over
+ * 8 blocks of 256 threads per SM and returns the measured rate in flop/s (an FMA counts 2) for
+ * FP64 (fp32 = 0) or FP32 (fp32 = 1).  Synchronous; 1 <= iters <= 2^20. */
+mg_status mg_measure_fma_peak(int fp32, int iters, double* flops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MG_H */

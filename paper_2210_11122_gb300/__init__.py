@@ -1,0 +1,253 @@
+"""GB300 (sm_103a) engine for per-event tree-level QCD matrix elements of g g -> t tbar + n gluons.
+
+Thin Python binding over the C ABI of include/mg.h (libmg.so, built by build.py): argument
+marshalling only -- every step of the random numbers -> momenta -> matrix element path (arXiv
+2210.11122, Sec. 1, Fig. 1 and Sec. 2) runs in the library's CUDA kernels.  Device buffers are
+torch CUDA tensors (or raw device pointers as ints); streams are torch.cuda.Stream objects, raw
+cudaStream_t ints, or None for torch's current stream.  There is no CPU fallback: if libmg.so is
+missing every call raises.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+MG_GG_TT, MG_GG_TTG, MG_GG_TTGG, MG_GG_TTGGG = 0, 1, 2, 3
+PROCESSES = {"ggtt": 0, "ggttg": 1, "ggttgg": 2, "ggttggg": 3}
+MG_FP64, MG_FP32_AMP, MG_FP64_TCCOLOR, MG_MIXED = 0, 1, 2, 3
+PAGE = 32
+
+STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "MG_ENOCONV", 5: "MG_EAGAIN",
+          6: "MG_ETIMEOUT", 7: "MG_EBUSY", 8: "MG_ENOTSUP"}
+
+
+class MGError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__("%s: %s (%s)" % (what, STATUS.get(status, status), _strerror(status)))
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("mt", ctypes.c_double), ("wt", ctypes.c_double), ("alphas", ctypes.c_double),
+                ("hel_warmup", ctypes.c_int), ("hel_tau", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libmg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libmg.so is not built (run paper_2210_11122_gb300.build.build(); needs nvcc)")
+    L = ctypes.CDLL(_build.LIB)
+    vp, i64, u64, dbl, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double, ctypes.c_int
+    P = ctypes.POINTER
+    L.mg_strerror.argtypes = [i32]
+    L.mg_strerror.restype = ctypes.c_char_p
+    L.mg_default_params.argtypes = [P(Params)]
+    L.mg_default_params.restype = None
+    L.mg_process_info.argtypes = [i32, P(i32), P(i32), P(i32), P(i32)]
+    L.mg_mom_count.argtypes = [i32, i64]
+    L.mg_mom_count.restype = i64
+    L.mg_colour_matrix.argtypes = [i32, P(ctypes.c_int64), P(ctypes.c_int64)]
+    L.mg_create.argtypes = [i32, P(Params), P(vp)]
+    L.mg_destroy.argtypes = [vp]
+    L.mg_destroy.restype = None
+    L.mg_philox.argtypes = [u64, i64, i32, vp, vp]
+    L.mg_rambo.argtypes = [vp, u64, i64, dbl, vp, vp, vp]
+    L.mg_rambo_range.argtypes = [vp, u64, i64, i64, dbl, vp, vp, vp]
+    L.mg_measure_fma_peak.argtypes = [i32, i32, P(dbl)]
+    L.mg_hel_filter.argtypes = [vp, vp, i64, vp]
+    L.mg_sigmakin.argtypes = [vp, vp, i64, i32, vp, vp]
+    L.mg_sigmakin_host.argtypes = [vp, vp, i64, i32, vp, vp]
+    L.mg_hel_mask.argtypes = [vp, P(ctypes.c_uint32), P(i32)]
+    L.mg_check.argtypes = [vp, vp, P(ctypes.c_int64)]
+    L.mg_flops_per_helicity.argtypes = [i32, P(dbl), P(dbl)]
+    for name in ("mg_process_info", "mg_colour_matrix", "mg_create", "mg_philox", "mg_rambo", "mg_rambo_range",
+                 "mg_measure_fma_peak", "mg_hel_filter",
+                 "mg_sigmakin", "mg_sigmakin_host", "mg_hel_mask", "mg_check", "mg_flops_per_helicity"):
+        getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+def _strerror(s):
+    try:
+        return lib().mg_strerror(s).decode()
+    except Exception:
+        return "?"
+
+
+def _check(status, what):
+    if status != 0:
+        raise MGError(status, what)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError("expected a tensor, ndarray or raw pointer, got %r" % type(x))
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _proc(p):
+    return PROCESSES[p] if isinstance(p, str) else int(p)
+
+
+# ------------------------------------------------------------------------------------------
+# host-only queries
+# ------------------------------------------------------------------------------------------
+def default_params():
+    p = Params()
+    lib().mg_default_params(ctypes.byref(p))
+    return p
+
+
+def process_info(process):
+    a, b, c, d = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().mg_process_info(_proc(process), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
+           "mg_process_info")
+    return {"npar": a.value, "nhel": b.value, "ncol": c.value, "ndiagrams": d.value}
+
+
+def mom_count(process, nevt):
+    return int(lib().mg_mom_count(_proc(process), nevt))
+
+
+def colour_matrix(process):
+    """Exact colour matrix as (int64 numerators [ncol, ncol], common denominator)."""
+    n = process_info(process)["ncol"]
+    num = np.zeros((n, n), dtype=np.int64)
+    den = ctypes.c_int64()
+    _check(lib().mg_colour_matrix(_proc(process), num.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                  ctypes.byref(den)), "mg_colour_matrix")
+    return num, den.value
+
+
+def flops_per_helicity(process):
+    a, c = ctypes.c_double(), ctypes.c_double()
+    _check(lib().mg_flops_per_helicity(_proc(process), ctypes.byref(a), ctypes.byref(c)), "mg_flops_per_helicity")
+    return a.value, c.value
+
+
+# ------------------------------------------------------------------------------------------
+# layout helpers (pure index permutations of the AoSoA layout in mg.h)
+# ------------------------------------------------------------------------------------------
+def to_aosoa(mom):
+    """[nevt, npar, 4] -> flat AoSoA array of mom_count doubles (zero padded to 32 events)."""
+    mom = np.asarray(mom, dtype=np.float64)
+    nevt, npar, _ = mom.shape
+    npage = (nevt + PAGE - 1) // PAGE
+    buf = np.zeros((npage * PAGE, npar, 4))
+    buf[:nevt] = mom
+    return np.ascontiguousarray(buf.reshape(npage, PAGE, npar, 4).transpose(0, 2, 3, 1)).reshape(-1)
+
+
+def from_aosoa(buf, nevt, npar):
+    buf = np.asarray(buf, dtype=np.float64)
+    npage = (nevt + PAGE - 1) // PAGE
+    a = buf[: npage * npar * 4 * PAGE].reshape(npage, npar, 4, PAGE).transpose(0, 3, 1, 2).reshape(-1, npar, 4)
+    return a[:nevt]
+
+
+def measure_fma_peak(fp32=False, iters=4096):
+    """Measured FMA throughput of the current device in flop/s (FMA = 2 flops)."""
+    r = ctypes.c_double()
+    _check(lib().mg_measure_fma_peak(1 if fp32 else 0, iters, ctypes.byref(r)), "mg_measure_fma_peak")
+    return r.value
+
+
+def philox(seed, nevt, nfinal, words, stream=None):
+    _check(lib().mg_philox(seed, nevt, nfinal, _ptr(words), _stream(stream)), "mg_philox")
+
+
+# ------------------------------------------------------------------------------------------
+# contexts
+# ------------------------------------------------------------------------------------------
+class Context:
+    """One process on the current CUDA device (mg_create / mg_destroy)."""
+
+    def __init__(self, process, mt=173.0, wt=0.0, alphas=0.118, hel_warmup=1024, hel_tau=1e-9):
+        self.process = _proc(process)
+        info = process_info(self.process)
+        self.npar, self.nhel, self.ncol = info["npar"], info["nhel"], info["ncol"]
+        self.ng = self.npar - 4
+        p = Params(mt, wt, alphas, hel_warmup, hel_tau)
+        h = ctypes.c_void_p()
+        _check(lib().mg_create(self.process, ctypes.byref(p), ctypes.byref(h)), "mg_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def mom_count(self, nevt):
+        return mom_count(self.process, nevt)
+
+    def rambo(self, seed, nevt, sqrts, mom, wgt=None, stream=None):
+        _check(lib().mg_rambo(self._h, seed, nevt, sqrts, _ptr(mom), _ptr(wgt), _stream(stream)), "mg_rambo")
+
+    def rambo_range(self, seed, e0, nevt, sqrts, mom, wgt=None, stream=None):
+        _check(lib().mg_rambo_range(self._h, seed, e0, nevt, sqrts, _ptr(mom), _ptr(wgt), _stream(stream)),
+               "mg_rambo_range")
+
+    def hel_filter(self, mom, nevt, stream=None):
+        _check(lib().mg_hel_filter(self._h, _ptr(mom), nevt, _stream(stream)), "mg_hel_filter")
+
+    def sigmakin(self, mom, nevt, me, precision=MG_FP64, stream=None):
+        _check(lib().mg_sigmakin(self._h, _ptr(mom), nevt, precision, _ptr(me), _stream(stream)), "mg_sigmakin")
+
+    def sigmakin_host(self, mom_host, nevt, me_host, precision=MG_FP64, stream=None):
+        _check(lib().mg_sigmakin_host(self._h, _ptr(mom_host), nevt, precision, _ptr(me_host), _stream(stream)),
+               "mg_sigmakin_host")
+
+    def hel_mask(self):
+        nw = (self.nhel + 31) // 32
+        m = (ctypes.c_uint32 * nw)()
+        n = ctypes.c_int()
+        _check(lib().mg_hel_mask(self._h, m, ctypes.byref(n)), "mg_hel_mask")
+        return np.array(list(m), dtype=np.uint32), n.value
+
+    def check(self, stream=None):
+        """Returns the number of RAMBO events that failed to converge since the last check."""
+        n = ctypes.c_int64()
+        s = lib().mg_check(self._h, _stream(stream), ctypes.byref(n))
+        if s not in (0, 4):
+            _check(s, "mg_check")
+        return n.value

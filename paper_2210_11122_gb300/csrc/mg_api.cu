@@ -1,0 +1,369 @@
+// mg_api.cu -- the C ABI of include/mg.h: contexts, argument checks, launches, error handling.
+//
+// Host runtime for the paper's workflow (Sec. 1, Fig. 1): random numbers -> momenta -> matrix
+// elements, every step a kernel on the current CUDA device, stream-ordered and asynchronous.
+// No C++ exception crosses the ABI; every entry point returns an mg_status.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "mg_internal.h"
+#include "mg_kernels.h"
+
+struct mg_ctx {
+  mg_process proc;
+  int K, npar, nhel, ncol, ng;
+  mg_params prm;
+  mg::Tables* d_tab = nullptr;
+  double* d_ctri = nullptr;   // packed upper triangle of the integer colour matrix, off-diagonal doubled
+  int64_t colour_den = 1;
+  uint32_t* d_mask = nullptr;
+  int* d_good = nullptr;      // good helicity list
+  int* d_ngood = nullptr;
+  int* d_allhel = nullptr;    // 0..nhel-1
+  int* d_nhel = nullptr;      // nhel
+  unsigned long long* d_nbad = nullptr;
+  double* d_part = nullptr;   // per-(helicity, event) colour sums
+  int64_t part_cap = 0;
+  double* d_tot = nullptr;    // per-event helicity sums of the filter
+  int64_t tot_cap = 0;
+  double* d_mom_stage = nullptr;
+  double* d_me_stage = nullptr;
+  int64_t stage_cap = 0;
+  bool mask_ready = false;
+  cudaStream_t last = nullptr;
+  double flops_amp = 0, flops_col = 0;
+};
+
+namespace {
+
+const double kPi = 3.14159265358979323846;
+
+#define MG_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return MG_ECUDA;             \
+  } while (0)
+
+bool valid_proc(mg_process p) { return p >= MG_GG_TT && p <= MG_GG_TTGGG; }
+
+int64_t pad32(int64_t n) { return (n + mg::kPage - 1) / mg::kPage * mg::kPage; }
+
+mg_status grow(double** buf, int64_t* cap, int64_t need) {
+  if (need <= *cap) return MG_OK;
+  if (*buf) cudaFree(*buf);
+  *buf = nullptr;
+  *cap = 0;
+  if (cudaMalloc(buf, static_cast<size_t>(need) * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    return MG_ENOMEM;
+  }
+  *cap = need;
+  return MG_OK;
+}
+
+// Flop model of k_me_helicity for one helicity (FMA counted as 2): mirrors the arithmetic of the
+// kernel operation by operation (complex multiply 6, complex add 2, complex dot 30, ...).
+void flop_model(const mg::Tables& t, double* amp, double* col) {
+  const int K = t.K, nsub = 1 << K;
+  double f = 0;
+  f += 30.0 * nsub;                          // subset momenta, gluon and quark propagator factors
+  f += 120.0 + 40.0 * K;                     // external wavefunctions
+  for (int s = K; s < t.nseq; ++s) f += 166.0 * t.seq_nv3[s] + 202.0 * t.seq_nv4[s] + 24.0;
+  f += 80.0;                                 // Jq
+  f += 94.0 * t.nseq;                        // X and D
+  for (int i = 0; i < t.nfull; ++i) f += 118.0 * t.full_nv3[i] + 116.0 * t.full_nv4[i] + 10.0;
+  for (int c = 0; c < t.ncol; ++c) {
+    for (int m = t.lcp[c] + 1; m < K; ++m) f += 86.0 + 72.0 * m;
+    f += 32.0 * (K - 1);
+  }
+  *amp = f;
+  *col = 5.0 * t.ncol * (t.ncol + 1) / 2.0 + t.ncol;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* mg_strerror(mg_status s) {
+  switch (s) {
+    case MG_OK: return "ok";
+    case MG_EINVAL: return "invalid argument";
+    case MG_ENOMEM: return "out of memory";
+    case MG_ECUDA: return "CUDA error";
+    case MG_ENOCONV: return "RAMBO did not converge";
+    case MG_EAGAIN: return "not ready";
+    case MG_ETIMEOUT: return "timed out";
+    case MG_EBUSY: return "busy";
+    case MG_ENOTSUP: return "not supported";
+  }
+  return "unknown status";
+}
+
+void mg_default_params(mg_params* p) {
+  if (!p) return;
+  p->mt = 173.0;
+  p->wt = 0.0;
+  p->alphas = 0.118;
+  p->hel_warmup = 1024;
+  p->hel_tau = 1e-9;
+}
+
+mg_status mg_process_info(mg_process proc, int* npar, int* nhel, int* ncol, int* ndiagrams) {
+  if (!valid_proc(proc)) return MG_EINVAL;
+  static const int nd[4] = {3, 16, 123, 1240};
+  int K = mg::gluons_of(proc);
+  if (npar) *npar = K + 2;
+  if (nhel) *nhel = 1 << (K + 2);
+  if (ncol) *ncol = mg::factorial(K);
+  if (ndiagrams) *ndiagrams = nd[proc];
+  return MG_OK;
+}
+
+int64_t mg_mom_count(mg_process proc, int64_t nevt) {
+  if (!valid_proc(proc) || nevt < 0) return -1;
+  return pad32(nevt) * mg::npar_of(proc) * 4;
+}
+
+mg_status mg_colour_matrix(mg_process proc, int64_t* num, int64_t* den) {
+  if (!valid_proc(proc) || !num || !den) return MG_EINVAL;
+  std::vector<int64_t> v;
+  int64_t d;
+  try {
+    mg::colour_matrix_exact(mg::gluons_of(proc), v, d);
+  } catch (...) {
+    return MG_ENOMEM;
+  }
+  std::memcpy(num, v.data(), v.size() * sizeof(int64_t));
+  *den = d;
+  return MG_OK;
+}
+
+mg_status mg_flops_per_helicity(mg_process proc, double* amp_flops, double* colour_flops) {
+  if (!valid_proc(proc)) return MG_EINVAL;
+  mg::Tables* t = new (std::nothrow) mg::Tables;
+  if (!t) return MG_ENOMEM;
+  mg::build_tables(mg::gluons_of(proc), *t);
+  double a, c;
+  flop_model(*t, &a, &c);
+  delete t;
+  if (amp_flops) *amp_flops = a;
+  if (colour_flops) *colour_flops = c;
+  return MG_OK;
+}
+
+void mg_destroy(mg_ctx* ctx) {
+  if (!ctx) return;
+  cudaDeviceSynchronize();
+  cudaFree(ctx->d_tab);
+  cudaFree(ctx->d_ctri);
+  cudaFree(ctx->d_mask);
+  cudaFree(ctx->d_good);
+  cudaFree(ctx->d_ngood);
+  cudaFree(ctx->d_allhel);
+  cudaFree(ctx->d_nhel);
+  cudaFree(ctx->d_nbad);
+  cudaFree(ctx->d_part);
+  cudaFree(ctx->d_tot);
+  cudaFree(ctx->d_mom_stage);
+  cudaFree(ctx->d_me_stage);
+  delete ctx;
+}
+
+mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
+  if (!out) return MG_EINVAL;
+  *out = nullptr;
+  if (!valid_proc(proc)) return MG_EINVAL;
+  mg_params prm;
+  mg_default_params(&prm);
+  if (params) prm = *params;
+  if (!(prm.mt >= 0.0) || !(prm.wt >= 0.0) || !(prm.alphas > 0.0) || prm.hel_warmup < 1 || !(prm.hel_tau >= 0.0))
+    return MG_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) { cudaGetLastError(); return MG_ECUDA; }
+  mg_ctx* c = new (std::nothrow) mg_ctx;
+  if (!c) return MG_ENOMEM;
+  c->proc = proc;
+  c->K = mg::gluons_of(proc);
+  c->ng = c->K - 2;
+  c->npar = c->K + 2;
+  c->nhel = 1 << c->npar;
+  c->ncol = mg::factorial(c->K);
+  c->prm = prm;
+  mg_status st = MG_OK;
+  do {
+    mg::Tables* t = new (std::nothrow) mg::Tables;
+    if (!t) { st = MG_ENOMEM; break; }
+    mg::build_tables(c->K, *t);
+    flop_model(*t, &c->flops_amp, &c->flops_col);
+    cudaError_t e = cudaMalloc(&c->d_tab, sizeof(mg::Tables));
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_tab, t, sizeof(mg::Tables), cudaMemcpyHostToDevice);
+    delete t;
+    if (e != cudaSuccess) { st = MG_ECUDA; break; }
+    std::vector<int64_t> num;
+    mg::colour_matrix_exact(c->K, num, c->colour_den);
+    std::vector<double> tri;
+    for (int a = 0; a < c->ncol; ++a)
+      for (int b = a; b < c->ncol; ++b)
+        tri.push_back(static_cast<double>(num[static_cast<size_t>(a) * c->ncol + b]) * (a == b ? 1.0 : 2.0));
+    e = cudaMalloc(&c->d_ctri, tri.size() * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_ctri, tri.data(), tri.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { st = MG_ECUDA; break; }
+    std::vector<int> all(c->nhel);
+    for (int h = 0; h < c->nhel; ++h) all[h] = h;
+    if (cudaMalloc(&c->d_mask, 4 * sizeof(uint32_t)) != cudaSuccess || cudaMalloc(&c->d_good, 128 * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->d_ngood, sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_allhel, c->nhel * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->d_nhel, sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_nbad, sizeof(unsigned long long)) != cudaSuccess) {
+      st = MG_ENOMEM;
+      break;
+    }
+    if (cudaMemcpy(c->d_allhel, all.data(), c->nhel * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_nhel, &c->nhel, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(c->d_nbad, 0, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMemset(c->d_mask, 0, 4 * sizeof(uint32_t)) != cudaSuccess ||
+        cudaMemset(c->d_ngood, 0, sizeof(int)) != cudaSuccess) {
+      st = MG_ECUDA;
+      break;
+    }
+  } while (false);
+  if (st != MG_OK) {
+    cudaGetLastError();
+    mg_destroy(c);
+    return st;
+  }
+  *out = c;
+  return MG_OK;
+}
+
+mg_status mg_philox(uint64_t seed, int64_t nevt, int nfinal, uint32_t* words_dev, void* stream) {
+  if (nevt < 0 || nfinal < 1 || nfinal > 64 || (nevt > 0 && !words_dev)) return MG_EINVAL;
+  if (reinterpret_cast<uintptr_t>(words_dev) & 15u) return MG_EINVAL;
+  if (nevt == 0) return MG_OK;
+  MG_CUDA(mg::launch_philox(seed, nevt, nfinal, words_dev, static_cast<cudaStream_t>(stream)));
+  return MG_OK;
+}
+
+mg_status mg_rambo(mg_ctx* ctx, uint64_t seed, int64_t nevt, double sqrts, double* mom_dev, double* wgt_dev,
+                   void* stream) {
+  return mg_rambo_range(ctx, seed, 0, nevt, sqrts, mom_dev, wgt_dev, stream);
+}
+
+mg_status mg_rambo_range(mg_ctx* ctx, uint64_t seed, int64_t e0, int64_t nevt, double sqrts, double* mom_dev,
+                         double* wgt_dev, void* stream) {
+  if (!ctx || nevt < 0 || e0 < 0 || (nevt > 0 && !mom_dev)) return MG_EINVAL;
+  if (!(sqrts > 2.0 * ctx->prm.mt) || !std::isfinite(sqrts)) return MG_EINVAL;
+  if (nevt == 0) return MG_OK;
+  const int n = ctx->K;   // final-state particles
+  double w0 = std::pow(2.0 * kPi, 4 - 3 * n) * std::pow(kPi / 2.0, n - 1) * std::pow(sqrts * sqrts, n - 2) /
+              (mg::factorial(n - 1) * static_cast<double>(mg::factorial(n - 2)));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ctx->last = st;
+  MG_CUDA(mg::launch_rambo(ctx->K, seed, e0, nevt, sqrts, ctx->prm.mt, w0, mom_dev, wgt_dev, ctx->d_nbad, st));
+  return MG_OK;
+}
+
+static mg::MeConst me_const(const mg_ctx* ctx) {
+  mg::MeConst c;
+  c.gs = std::sqrt(4.0 * kPi * ctx->prm.alphas);
+  c.mt = ctx->prm.mt;
+  c.wt = ctx->prm.wt;
+  c.colour_scale = c.gs * c.gs / static_cast<double>(ctx->colour_den);
+  return c;
+}
+
+mg_status mg_hel_filter(mg_ctx* ctx, const double* mom_dev, int64_t nevt, void* stream) {
+  if (!ctx || nevt < 1 || !mom_dev) return MG_EINVAL;
+  const int64_t w = nevt < ctx->prm.hel_warmup ? nevt : ctx->prm.hel_warmup;
+  const int64_t stride = pad32(w);
+  mg_status s = grow(&ctx->d_part, &ctx->part_cap, stride * ctx->nhel);
+  if (s != MG_OK) return s;
+  s = grow(&ctx->d_tot, &ctx->tot_cap, stride);
+  if (s != MG_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  ctx->last = st;
+  const mg::MeConst cst = me_const(ctx);
+  MG_CUDA(mg::launch_me_helicity(ctx->K, false, mom_dev, w, ctx->d_tab, ctx->d_allhel, ctx->nhel, ctx->d_nhel,
+                                 ctx->d_ctri, cst, ctx->d_part, stride, st));
+  MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_nhel, w, stride, 1.0, ctx->d_tot, st));
+  MG_CUDA(mg::launch_hel_mask(ctx->d_part, ctx->d_tot, ctx->nhel, w, stride, ctx->prm.hel_tau, ctx->d_mask,
+                              ctx->d_good, ctx->d_ngood, st));
+  ctx->mask_ready = true;
+  return MG_OK;
+}
+
+mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_precision precision, double* me_dev,
+                      void* stream) {
+  if (!ctx || nevt < 0 || (nevt > 0 && (!mom_dev || !me_dev))) return MG_EINVAL;
+  if (precision != MG_FP64 && precision != MG_FP32_AMP) {
+    if (precision == MG_FP64_TCCOLOR || precision == MG_MIXED) return MG_ENOTSUP;
+    return MG_EINVAL;
+  }
+  if (nevt == 0) return MG_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!ctx->mask_ready) {
+    mg_status s = mg_hel_filter(ctx, mom_dev, nevt, stream);
+    if (s != MG_OK) return s;
+  }
+  const int64_t stride = pad32(nevt);
+  mg_status s = grow(&ctx->d_part, &ctx->part_cap, stride * ctx->nhel);
+  if (s != MG_OK) return s;
+  ctx->last = st;
+  const mg::MeConst cst = me_const(ctx);
+  const double norm = 1.0 / (256.0 * mg::factorial(ctx->ng));
+  MG_CUDA(mg::launch_me_helicity(ctx->K, precision == MG_FP32_AMP, mom_dev, nevt, ctx->d_tab, ctx->d_good, ctx->nhel,
+                                 ctx->d_ngood, ctx->d_ctri, cst, ctx->d_part, stride, st));
+  MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_ngood, nevt, stride, norm, me_dev, st));
+  return MG_OK;
+}
+
+mg_status mg_sigmakin_host(mg_ctx* ctx, const double* mom_host, int64_t nevt, mg_precision precision,
+                           double* me_host, void* stream) {
+  if (!ctx || nevt < 0 || (nevt > 0 && (!mom_host || !me_host))) return MG_EINVAL;
+  if (nevt == 0) return MG_OK;
+  const int64_t nmom = mg_mom_count(ctx->proc, nevt);
+  if (ctx->stage_cap < nmom + pad32(nevt)) {
+    if (ctx->d_mom_stage) cudaFree(ctx->d_mom_stage);
+    if (ctx->d_me_stage) cudaFree(ctx->d_me_stage);
+    ctx->d_mom_stage = ctx->d_me_stage = nullptr;
+    ctx->stage_cap = 0;
+    if (cudaMalloc(&ctx->d_mom_stage, nmom * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&ctx->d_me_stage, pad32(nevt) * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      return MG_ENOMEM;
+    }
+    ctx->stage_cap = nmom + pad32(nevt);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  MG_CUDA(cudaMemcpyAsync(ctx->d_mom_stage, mom_host, nmom * sizeof(double), cudaMemcpyHostToDevice, st));
+  mg_status s = mg_sigmakin(ctx, ctx->d_mom_stage, nevt, precision, ctx->d_me_stage, stream);
+  if (s != MG_OK) return s;
+  MG_CUDA(cudaMemcpyAsync(me_host, ctx->d_me_stage, nevt * sizeof(double), cudaMemcpyDeviceToHost, st));
+  MG_CUDA(cudaStreamSynchronize(st));
+  return MG_OK;
+}
+
+mg_status mg_hel_mask(mg_ctx* ctx, uint32_t* mask_host, int* ngood) {
+  if (!ctx || !mask_host || !ngood) return MG_EINVAL;
+  MG_CUDA(cudaStreamSynchronize(ctx->last));
+  const int nw = (ctx->nhel + 31) / 32;
+  MG_CUDA(cudaMemcpy(mask_host, ctx->d_mask, nw * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  MG_CUDA(cudaMemcpy(ngood, ctx->d_ngood, sizeof(int), cudaMemcpyDeviceToHost));
+  return MG_OK;
+}
+
+mg_status mg_check(mg_ctx* ctx, void* stream, int64_t* nbad) {
+  if (!ctx) return MG_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(st) != cudaSuccess) { cudaGetLastError(); return MG_ECUDA; }
+  unsigned long long n = 0;
+  MG_CUDA(cudaMemcpy(&n, ctx->d_nbad, sizeof(n), cudaMemcpyDeviceToHost));
+  MG_CUDA(cudaMemset(ctx->d_nbad, 0, sizeof(n)));
+  if (nbad) *nbad = static_cast<int64_t>(n);
+  return n ? MG_ENOCONV : MG_OK;
+}
+
+}  // extern "C"

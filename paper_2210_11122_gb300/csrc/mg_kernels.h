@@ -1,0 +1,31 @@
+// mg_kernels.h -- launch wrappers of the engine's device kernels (host-callable).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mg_internal.h"
+
+namespace mg {
+
+constexpr int kMeThreads = 128;
+
+struct MeConst {
+  double gs;            // strong coupling g_s = sqrt(4 pi alpha_s)
+  double mt, wt;        // top mass and width
+  double colour_scale;  // g_s^2 / colour-matrix denominator
+};
+
+cudaError_t launch_philox(uint64_t seed, int64_t nevt, int nfinal, uint32_t* words, cudaStream_t st);
+cudaError_t launch_rambo(int K, uint64_t seed, int64_t e0, int64_t nevt, double sqrts, double mt, double w0,
+                         double* mom, double* wgt, unsigned long long* nbad, cudaStream_t st);
+// out[slot * stride + e] = colour-summed |M_h|^2 of event e for helicity hels[slot]
+// (slots >= *nslot exit at once, so the helicity count can stay on the device)
+cudaError_t launch_me_helicity(int K, bool fp32, const double* mom, int64_t nevt, const Tables* tab, const int* hels,
+                               int maxslot, const int* nslot, const double* ctri, const MeConst& cst, double* out,
+                               int64_t stride, cudaStream_t st);
+cudaError_t launch_hel_sum(const double* part, const int* nslot, int64_t nevt, int64_t stride, double norm,
+                           double* me, cudaStream_t st);
+cudaError_t launch_hel_mask(const double* part, const double* tot, int nhel, int64_t nevt, int64_t stride, double tau,
+                            uint32_t* mask, int* good, int* ngood, cudaStream_t st);
+
+}  // namespace mg

@@ -1,0 +1,103 @@
+"""C ABI checks that need no GPU: the library loads, exports every entry point that
+include/mg.h declares, and its host-only logic (colour matrix, sizes, layout, argument
+validation) is right.  No compute call is made here."""
+import ctypes
+import os
+import re
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="session")
+def mg():
+    import paper_2210_11122_gb300 as m
+    from paper_2210_11122_gb300 import build
+    build.build()
+    return m
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "mg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mg_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_declares_the_boundary():
+    syms = declared_symbols()
+    for name in ("mg_create", "mg_destroy", "mg_rambo", "mg_sigmakin", "mg_hel_mask", "mg_philox", "mg_strerror"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(mg):
+    L = ctypes.CDLL(mg.library_path())
+    missing = [s for s in declared_symbols() if not hasattr(L, s)]
+    assert not missing, missing
+
+
+def test_strerror_and_defaults(mg):
+    for s in range(9):
+        assert mg.lib().mg_strerror(s)
+    p = mg.default_params()
+    assert (p.mt, p.wt, p.alphas, p.hel_warmup, p.hel_tau) == (173.0, 0.0, 0.118, 1024, 1e-9)
+
+
+def test_process_info(mg):
+    for name, (npar, nhel, ncol, nd) in {"ggtt": (4, 16, 2, 3), "ggttg": (5, 32, 6, 16), "ggttgg": (6, 64, 24, 123),
+                                         "ggttggg": (7, 128, 120, 1240)}.items():
+        assert mg.process_info(name) == {"npar": npar, "nhel": nhel, "ncol": ncol, "ndiagrams": nd}
+    with pytest.raises(mg.MGError):
+        mg.process_info(7)
+
+
+def test_mom_count_pads_to_pages(mg):
+    assert mg.mom_count("ggtt", 0) == 0
+    assert mg.mom_count("ggtt", 1) == 32 * 4 * 4
+    assert mg.mom_count("ggttggg", 33) == 64 * 7 * 4
+    assert mg.mom_count("ggtt", -1) == -1
+
+
+@pytest.mark.parametrize("proc,k", [("ggtt", 2), ("ggttg", 3), ("ggttgg", 4), ("ggttggg", 5)])
+def test_colour_matrix_matches_oracle(mg, proc, k):
+    """The library's U(N)-loop-counting colour matrix equals the oracle's Fierz reduction exactly."""
+    from oracle import colour
+    num, den = mg.colour_matrix(proc)
+    ex = colour.colour_matrix_exact(k)
+    n = len(ex)
+    assert num.shape == (n, n)
+    for a in range(n):
+        for b in range(n):
+            assert Fraction(int(num[a, b]), den) == ex[a][b]
+
+
+def test_aosoa_roundtrip(mg):
+    rng = np.random.default_rng(0)
+    for nevt in (1, 31, 32, 33, 100):
+        m = rng.normal(size=(nevt, 5, 4))
+        buf = mg.to_aosoa(m)
+        assert buf.size == mg.mom_count("ggttg", nevt)
+        assert np.array_equal(mg.from_aosoa(buf, nevt, 5), m)
+        # element (e, i, mu) at ((e/32) npar + i) 4 32 + mu 32 + e%32
+        e, i, mu = nevt - 1, 3, 2
+        assert buf[((e // 32) * 5 + i) * 128 + mu * 32 + e % 32] == m[e, i, mu]
+
+
+def test_flop_model(mg):
+    for proc in ("ggtt", "ggttg", "ggttgg", "ggttggg"):
+        amp, col = mg.flops_per_helicity(proc)
+        n = mg.process_info(proc)["ncol"]
+        assert amp > 0
+        assert col == 5.0 * n * (n + 1) / 2 + n
+
+
+def test_invalid_arguments_rejected_without_gpu(mg):
+    L = mg.lib()
+    assert L.mg_rambo(None, 1, 10, 1500.0, None, None, None) == 1
+    assert L.mg_sigmakin(None, None, 10, 0, None, None) == 1
+    assert L.mg_hel_mask(None, None, None) == 1
+    assert L.mg_philox(1, -1, 2, None, None) == 1
+    assert L.mg_create(9, None, ctypes.byref(ctypes.c_void_p())) == 1
+    assert L.mg_create(0, None, None) == 1
