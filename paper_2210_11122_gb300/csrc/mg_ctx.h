@@ -1,0 +1,33 @@
+// mg_ctx.h -- layout of a context (struct mg_ctx of include/mg.h), shared by the engine's own
+// translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mg_internal.h"
+
+struct mg_ctx {
+  mg_process proc;
+  int K, npar, nhel, ncol, ng;
+  mg_params prm;
+  mg::Tables* d_tab = nullptr;
+  double* d_ctri = nullptr;   // packed upper triangle of the integer colour matrix, off-diagonal doubled
+  int64_t colour_den = 1;
+  uint32_t* d_mask = nullptr;
+  int* d_good = nullptr;      // good helicity list
+  int* d_ngood = nullptr;
+  int* d_allhel = nullptr;    // 0..nhel-1
+  int* d_nhel = nullptr;      // nhel
+  unsigned long long* d_nbad = nullptr;
+  double* d_part = nullptr;   // per-(helicity, event) colour sums
+  int64_t part_cap = 0;
+  double* d_tot = nullptr;    // per-event helicity sums of the filter
+  int64_t tot_cap = 0;
+  double* d_mom_stage = nullptr;
+  double* d_me_stage = nullptr;
+  int64_t stage_cap = 0;
+  bool mask_ready = false;
+  cudaStream_t last = nullptr;
+  double flops_amp = 0, flops_col = 0;
+};
+
