@@ -150,6 +150,24 @@ mg_status mg_check(mg_ctx* ctx, void* stream, int64_t* nbad);
  * (4 ncol^2 + 4 ncol).  FMA counts 2.  Host only. */
 mg_status mg_flops_per_helicity(mg_process proc, double* amp_flops, double* colour_flops);
 
+/* FP64 matrix elements exactly as mg_sigmakin(..., MG_FP64, ...), for callers that must not have
+ * the library allocate device memory during the call (an application that hands the engine a
+ * fixed memory budget, or whose own pooling allocator must remain the only one): this entry point
+ * calls no cudaMalloc/cudaFree and no allocating routine.  The paper has no counterpart; it is an
+ * integration aid of this library.
+ *   - Scratch: a fixed 16 MiB array in device global memory (2^21 doubles), part of the library
+ *     image, so every GPU that loads the library holds it until the process exits.  A call needs
+ *     nhel * ceil(nevt/32)*32 <= 2^21, i.e. nevt <= 131072 (gg->tt), 65536 (gg->ttg),
+ *     32768 (gg->ttgg), 16384 (gg->ttggg); larger batches return MG_EINVAL: split them.
+ *   - The context must already hold a helicity mask (mg_hel_filter, or one earlier mg_sigmakin),
+ *     else MG_EINVAL.
+ *   - All calls on a device share the one scratch array (it keeps the last call's contents; every
+ *     element a call reads is written by that call first).  Calls whose work can overlap on the
+ *     GPU (different streams without ordering, several host threads) race on it: serialise them.
+ *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress with
+ *     that device current); make that first call before any stream capture. */
+mg_status mg_sigmakin_noalloc(mg_ctx* ctx, const double* mom_dev, int64_t nevt, double* me_dev, void* stream);
+
 /* Diagnostic: FMA throughput of the current device, the ALU roofline denominator of the
  * matrix-element kernels.  Runs 8 independent FMA chains per thread (iters x 16 FMAs each) over
  * 8 blocks of 256 threads per SM and returns the measured rate in flop/s (an FMA counts 2) for

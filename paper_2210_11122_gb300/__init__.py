@@ -69,12 +69,13 @@ def lib():
     L.mg_hel_filter.argtypes = [vp, vp, i64, vp]
     L.mg_sigmakin.argtypes = [vp, vp, i64, i32, vp, vp]
     L.mg_sigmakin_host.argtypes = [vp, vp, i64, i32, vp, vp]
+    L.mg_sigmakin_noalloc.argtypes = [vp, vp, i64, vp, vp]
     L.mg_hel_mask.argtypes = [vp, P(ctypes.c_uint32), P(i32)]
     L.mg_check.argtypes = [vp, vp, P(ctypes.c_int64)]
     L.mg_flops_per_helicity.argtypes = [i32, P(dbl), P(dbl)]
     for name in ("mg_process_info", "mg_colour_matrix", "mg_create", "mg_philox", "mg_rambo", "mg_rambo_range",
                  "mg_measure_fma_peak", "mg_hel_filter",
-                 "mg_sigmakin", "mg_sigmakin_host", "mg_hel_mask", "mg_check", "mg_flops_per_helicity"):
+                 "mg_sigmakin", "mg_sigmakin_host", "mg_sigmakin_noalloc", "mg_hel_mask", "mg_check", "mg_flops_per_helicity"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -236,6 +237,10 @@ class Context:
     def sigmakin_host(self, mom_host, nevt, me_host, precision=MG_FP64, stream=None):
         _check(lib().mg_sigmakin_host(self._h, _ptr(mom_host), nevt, precision, _ptr(me_host), _stream(stream)),
                "mg_sigmakin_host")
+
+    def sigmakin_noalloc(self, mom, nevt, me, stream=None):
+        """FP64 MEs without any device allocation (fixed 16 MiB library scratch; see mg.h)."""
+        _check(lib().mg_sigmakin_noalloc(self._h, _ptr(mom), nevt, _ptr(me), _stream(stream)), "mg_sigmakin_noalloc")
 
     def hel_mask(self):
         nw = (self.nhel + 31) // 32
