@@ -52,6 +52,24 @@ def parse():
     return ap.parse_args()
 
 
+def profiled_traffic(kernel_file, profile_md, nevt):
+    """DRAM bytes of one launch scaled from a committed ncu summary, or None when the kernel source
+    has changed since the counters were taken."""
+    import hashlib
+    try:
+        sha = hashlib.sha256(open(kernel_file, "rb").read()).hexdigest()[:16]
+        fields = {}
+        for line in open(profile_md):
+            if ":" in line and line.split(":")[0].strip() in ("source_sha256_16", "traffic_bytes_per_event"):
+                k, v = line.split(":", 1)
+                fields[k.strip()] = v.split()[0]
+        if fields.get("source_sha256_16") != sha:
+            return None
+        return float(fields["traffic_bytes_per_event"]) * nevt
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def config_of(args, nevt, extra=None):
     w = WORKLOADS[args.process]
     c = {"workload": "%s LO QCD, %d events/GPU, sqrt(s)=1500 GeV, m_t=173 GeV, alpha_s=0.118, Philox seed %d"
@@ -275,8 +293,10 @@ def run_ours(args):
     flops = (amp_f + col_f) * ngood * nevt
     peak = mg.measure_fma_peak(fp32=False, iters=2048)
     achieved = flops / (ms_me * 1e-3)
+    traffic = profiled_traffic(os.path.join(ROOT, "paper_2210_11122_gb300", "csrc", "mg_me.cu"),
+                               os.path.join(ROOT, "profiles", "k_me_helicity_fp64_%s_65536.md" % args.process), nevt)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_me_helicity<%d,double> + k_hel_sum (mg_sigmakin)" % (ng + 2),
                 "flops_per_event": (amp_f + col_f) * ngood,
                 "peak_source": "measured FP64 DFMA-chain microbenchmark (mg_measure_fma_peak) on this GPU"}
