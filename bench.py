@@ -289,16 +289,16 @@ def run_ours(args):
 
     # roofline of the dominant kernel (the FP64 matrix-element kernel, ALU bound on the FP64 pipe)
     mask, ngood = ctx.hel_mask()
-    amp_f, col_f = mg.flops_per_helicity(ng)
-    flops = (amp_f + col_f) * ngood * nevt
+    amp_f, col_f = mg.flops_per_event(ng, mask)
+    flops = (amp_f + col_f) * nevt
     peak = mg.measure_fma_peak(fp32=False, iters=2048)
     achieved = flops / (ms_me * 1e-3)
-    traffic = profiled_traffic(os.path.join(ROOT, "paper_2210_11122_gb300", "csrc", "mg_me.cu"),
-                               os.path.join(ROOT, "profiles", "k_me_helicity_fp64_%s_65536.md" % args.process), nevt)
+    traffic = profiled_traffic(os.path.join(ROOT, "paper_2210_11122_gb300", "csrc", "mg_me2.cu"),
+                               os.path.join(ROOT, "profiles", "k_me_gluonhel_fp64_%s_65536.md" % args.process), nevt)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_me_helicity<%d,double> + k_hel_sum (mg_sigmakin)" % (ng + 2),
-                "flops_per_event": (amp_f + col_f) * ngood,
+                "kernel": "k_me_gluonhel<%d,double> + k_hel_sum (mg_sigmakin)" % (ng + 2),
+                "flops_per_event": amp_f + col_f,
                 "peak_source": "measured FP64 DFMA-chain microbenchmark (mg_measure_fma_peak) on this GPU"}
 
     cpu = None

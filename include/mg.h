@@ -145,10 +145,11 @@ mg_status mg_hel_mask(mg_ctx* ctx, uint32_t* mask_host, int* ngood);
  * NULL), MG_ECUDA on an asynchronous CUDA error, else MG_OK.  Clears the condition. */
 mg_status mg_check(mg_ctx* ctx, void* stream, int64_t* nbad);
 
-/* Floating-point operation counts of one event's ME in this engine's algorithm, per good
- * helicity: fp64[0] = amplitude part (wavefunctions, currents, jamps), fp64[1] = colour sum
- * (4 ncol^2 + 4 ncol).  FMA counts 2.  Host only. */
-mg_status mg_flops_per_helicity(mg_process proc, double* amp_flops, double* colour_flops);
+/* Floating-point operations of one event's FP64 matrix element in this engine's algorithm (the
+ * roofline numerator): *amp_flops for wavefunctions, currents and jamps, *colour_flops for the colour
+ * sums (4 ncol(ncol+1)/2 + 4 ncol per good helicity), counting an FMA as 2.  mask (ceil(nhel/32)
+ * words, as returned by mg_hel_mask) selects the good helicities; NULL = all.  Host only. */
+mg_status mg_flops_per_event(mg_process proc, const uint32_t* mask, double* amp_flops, double* colour_flops);
 
 /* FP64 matrix elements exactly as mg_sigmakin(..., MG_FP64, ...), for callers that must not have
  * the library allocate device memory during the call (an application that hands the engine a

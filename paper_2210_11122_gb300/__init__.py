@@ -72,10 +72,10 @@ def lib():
     L.mg_sigmakin_noalloc.argtypes = [vp, vp, i64, vp, vp]
     L.mg_hel_mask.argtypes = [vp, P(ctypes.c_uint32), P(i32)]
     L.mg_check.argtypes = [vp, vp, P(ctypes.c_int64)]
-    L.mg_flops_per_helicity.argtypes = [i32, P(dbl), P(dbl)]
+    L.mg_flops_per_event.argtypes = [i32, P(ctypes.c_uint32), P(dbl), P(dbl)]
     for name in ("mg_process_info", "mg_colour_matrix", "mg_create", "mg_philox", "mg_rambo", "mg_rambo_range",
                  "mg_measure_fma_peak", "mg_hel_filter",
-                 "mg_sigmakin", "mg_sigmakin_host", "mg_sigmakin_noalloc", "mg_hel_mask", "mg_check", "mg_flops_per_helicity"):
+                 "mg_sigmakin", "mg_sigmakin_host", "mg_sigmakin_noalloc", "mg_hel_mask", "mg_check", "mg_flops_per_event"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -148,9 +148,13 @@ def colour_matrix(process):
     return num, den.value
 
 
-def flops_per_helicity(process):
+def flops_per_event(process, mask=None):
+    """(amplitude flops, colour-sum flops) of one event's FP64 ME for the given helicity mask."""
     a, c = ctypes.c_double(), ctypes.c_double()
-    _check(lib().mg_flops_per_helicity(_proc(process), ctypes.byref(a), ctypes.byref(c)), "mg_flops_per_helicity")
+    m = None
+    if mask is not None:
+        m = (ctypes.c_uint32 * len(mask))(*[int(x) for x in mask])
+    _check(lib().mg_flops_per_event(_proc(process), m, ctypes.byref(a), ctypes.byref(c)), "mg_flops_per_event")
     return a.value, c.value
 
 

@@ -42,23 +42,44 @@ mg_status grow(double** buf, int64_t* cap, int64_t need) {
   return MG_OK;
 }
 
-// Flop model of k_me_helicity for one helicity (FMA counted as 2): mirrors the arithmetic of the
-// kernel operation by operation (complex multiply 6, complex add 2, complex dot 30, ...).
-void flop_model(const mg::Tables& t, double* amp, double* col) {
-  const int K = t.K, nsub = 1 << K;
-  double f = 0;
-  f += 30.0 * nsub;                          // subset momenta, gluon and quark propagator factors
-  f += 120.0 + 40.0 * K;                     // external wavefunctions
-  for (int s = K; s < t.nseq; ++s) f += 166.0 * t.seq_nv3[s] + 202.0 * t.seq_nv4[s] + 24.0;
-  f += 80.0;                                 // Jq
-  f += 94.0 * t.nseq;                        // X and D
-  for (int i = 0; i < t.nfull; ++i) f += 118.0 * t.full_nv3[i] + 116.0 * t.full_nv4[i] + 10.0;
+// Flop model of the matrix-element kernel of mg_me2.cu for one event (FMA counted as 2 flops, a
+// complex multiply-add as 8): mirrors the kernel operation by operation.  One thread per gluon-
+// helicity combination with a good helicity; per thread the gluon currents once, (gamma.J) v per
+// antitop helicity, a depth-first walk of the quark-line prefixes per top helicity, the jamps and
+// the colour sum per good helicity.  mask == NULL means every helicity is good.
+void flop_model(const mg::Tables& t, const uint32_t* mask, double* amp, double* col) {
+  const int K = t.K, nsub = 1 << K, npar = K + 2;
+  const double v3 = 158.0, v4 = 192.0, row_gamma = 72.0, row_prop = 56.0, gamma_col = 64.0, sdot = 32.0,
+               mdot = 30.0;
+  double per_thread = 25.0 * nsub + 30.0 * K + 100.0;              // subsets, gluon and antitop wavefunctions
+  for (int s = K; s < t.nseq; ++s) per_thread += v3 * t.seq_nv3[s] + v4 * t.seq_nv4[s] + 8.0;
+  for (int f = 0; f < t.nfull; ++f) per_thread += v3 * t.full_nv3[f] + v4 * t.full_nv4[f] + 8.0;
+  per_thread += 2.0 * gamma_col * t.nseq;
+  double walk = 50.0 + 2.0 * 72.0;                                 // ubar, two quark currents
   for (int c = 0; c < t.ncol; ++c) {
-    for (int m = t.lcp[c] + 1; m < K; ++m) f += 86.0 + 72.0 * m;
-    f += 32.0 * (K - 1);
+    for (int m = t.lcp[c] + 1; m < K; ++m) walk += row_gamma * m + row_prop;
+    walk += 2.0 * (mdot + sdot * (K - 1));                         // jamps of both antitop helicities
   }
-  *amp = f;
-  *col = 5.0 * t.ncol * (t.ncol + 1) / 2.0 + t.ncol;
+  const double colour = 4.0 * t.ncol * (t.ncol + 1) / 2.0 + 4.0 * t.ncol;
+  double a = 0, c = 0;
+  for (int gc = 0; gc < nsub; ++gc) {
+    int hb = 0;
+    for (int g = 0; g < K; ++g)
+      if ((gc >> g) & 1) hb |= 1 << (npar - 1 - (g < 2 ? g : g + 2));
+    int good[4], any = 0;
+    for (int k = 0; k < 4; ++k) {
+      const int h = hb | ((k >> 1) << (npar - 3)) | ((k & 1) << (npar - 4));   // k = 2*top + antitop
+      good[k] = mask ? static_cast<int>((mask[h >> 5] >> (h & 31)) & 1u) : 1;
+      any |= good[k];
+    }
+    if (!any) continue;
+    a += per_thread;
+    for (int top = 0; top < 2; ++top)
+      if (good[2 * top] || good[2 * top + 1]) a += walk;
+    for (int k = 0; k < 4; ++k) c += good[k] ? colour : 0.0;
+  }
+  *amp = a;
+  *col = c;
 }
 
 }  // namespace
@@ -119,13 +140,13 @@ mg_status mg_colour_matrix(mg_process proc, int64_t* num, int64_t* den) {
   return MG_OK;
 }
 
-mg_status mg_flops_per_helicity(mg_process proc, double* amp_flops, double* colour_flops) {
+mg_status mg_flops_per_event(mg_process proc, const uint32_t* mask, double* amp_flops, double* colour_flops) {
   if (!valid_proc(proc)) return MG_EINVAL;
   mg::Tables* t = new (std::nothrow) mg::Tables;
   if (!t) return MG_ENOMEM;
   mg::build_tables(mg::gluons_of(proc), *t);
   double a, c;
-  flop_model(*t, &a, &c);
+  flop_model(*t, mask, &a, &c);
   delete t;
   if (amp_flops) *amp_flops = a;
   if (colour_flops) *colour_flops = c;
@@ -142,6 +163,10 @@ void mg_destroy(mg_ctx* ctx) {
   cudaFree(ctx->d_ngood);
   cudaFree(ctx->d_allhel);
   cudaFree(ctx->d_nhel);
+  cudaFree(ctx->d_gslots);
+  cudaFree(ctx->d_ngslots);
+  cudaFree(ctx->d_allg);
+  cudaFree(ctx->d_nallg);
   cudaFree(ctx->d_nbad);
   cudaFree(ctx->d_part);
   cudaFree(ctx->d_tot);
@@ -175,7 +200,6 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
     mg::Tables* t = new (std::nothrow) mg::Tables;
     if (!t) { st = MG_ENOMEM; break; }
     mg::build_tables(c->K, *t);
-    flop_model(*t, &c->flops_amp, &c->flops_col);
     cudaError_t e = cudaMalloc(&c->d_tab, sizeof(mg::Tables));
     if (e == cudaSuccess) e = cudaMemcpy(c->d_tab, t, sizeof(mg::Tables), cudaMemcpyHostToDevice);
     delete t;
@@ -195,6 +219,18 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
         cudaMalloc(&c->d_ngood, sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_allhel, c->nhel * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&c->d_nhel, sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_nbad, sizeof(unsigned long long)) != cudaSuccess) {
       st = MG_ENOMEM;
+      break;
+    }
+    const int ng2 = 1 << c->K;
+    if (cudaMalloc(&c->d_gslots, 32 * sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_ngslots, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->d_allg, 32 * sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_nallg, sizeof(int)) != cudaSuccess) {
+      st = MG_ENOMEM;
+      break;
+    }
+    if (cudaMemcpy(c->d_allg, all.data(), ng2 * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(c->d_nallg, &ng2, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(c->d_ngslots, 0, sizeof(int)) != cudaSuccess) {
+      st = MG_ECUDA;
       break;
     }
     if (cudaMemcpy(c->d_allhel, all.data(), c->nhel * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -262,11 +298,17 @@ mg_status mg_hel_filter(mg_ctx* ctx, const double* mom_dev, int64_t nevt, void* 
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   ctx->last = st;
   const mg::MeConst cst = me_const(ctx);
-  MG_CUDA(mg::launch_me_helicity(ctx->K, false, mom_dev, w, ctx->d_tab, ctx->d_allhel, ctx->nhel, ctx->d_nhel,
-                                 ctx->d_ctri, cst, ctx->d_part, stride, st));
+  if (ctx->prm.wt == 0.0) {
+    MG_CUDA(mg::launch_me_gluonhel(ctx->K, false, true, mom_dev, w, ctx->d_tab, ctx->d_allg, 1 << ctx->K, ctx->d_nallg,
+                                   ctx->d_mask, ctx->d_ctri, cst, ctx->d_part, stride, st));
+  } else {
+    MG_CUDA(mg::launch_me_helicity(ctx->K, false, mom_dev, w, ctx->d_tab, ctx->d_allhel, ctx->nhel, ctx->d_nhel,
+                                   ctx->d_ctri, cst, ctx->d_part, stride, st));
+  }
   MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_nhel, w, stride, 1.0, ctx->d_tot, st));
   MG_CUDA(mg::launch_hel_mask(ctx->d_part, ctx->d_tot, ctx->nhel, w, stride, ctx->prm.hel_tau, ctx->d_mask,
                               ctx->d_good, ctx->d_ngood, st));
+  MG_CUDA(mg::launch_gluon_slots(ctx->d_mask, ctx->K, ctx->d_gslots, ctx->d_ngslots, st));
   ctx->mask_ready = true;
   return MG_OK;
 }
@@ -290,9 +332,15 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
   ctx->last = st;
   const mg::MeConst cst = me_const(ctx);
   const double norm = 1.0 / (256.0 * mg::factorial(ctx->ng));
-  MG_CUDA(mg::launch_me_helicity(ctx->K, precision == MG_FP32_AMP, mom_dev, nevt, ctx->d_tab, ctx->d_good, ctx->nhel,
-                                 ctx->d_ngood, ctx->d_ctri, cst, ctx->d_part, stride, st));
-  MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_ngood, nevt, stride, norm, me_dev, st));
+  if (ctx->prm.wt == 0.0) {
+    MG_CUDA(mg::launch_me_gluonhel(ctx->K, precision == MG_FP32_AMP, false, mom_dev, nevt, ctx->d_tab, ctx->d_gslots,
+                                   1 << ctx->K, ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, cst, ctx->d_part, stride, st));
+    MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_ngslots, nevt, stride, norm, me_dev, st));
+  } else {
+    MG_CUDA(mg::launch_me_helicity(ctx->K, precision == MG_FP32_AMP, mom_dev, nevt, ctx->d_tab, ctx->d_good, ctx->nhel,
+                                   ctx->d_ngood, ctx->d_ctri, cst, ctx->d_part, stride, st));
+    MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_ngood, nevt, stride, norm, me_dev, st));
+  }
   return MG_OK;
 }
 

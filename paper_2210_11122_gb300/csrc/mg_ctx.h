@@ -18,6 +18,10 @@ struct mg_ctx {
   int* d_ngood = nullptr;
   int* d_allhel = nullptr;    // 0..nhel-1
   int* d_nhel = nullptr;      // nhel
+  int* d_gslots = nullptr;    // gluon-helicity combinations with a good helicity
+  int* d_ngslots = nullptr;
+  int* d_allg = nullptr;      // 0..2^K-1
+  int* d_nallg = nullptr;     // 2^K
   unsigned long long* d_nbad = nullptr;
   double* d_part = nullptr;   // per-(helicity, event) colour sums
   int64_t part_cap = 0;
@@ -28,6 +32,5 @@ struct mg_ctx {
   int64_t stage_cap = 0;
   bool mask_ready = false;
   cudaStream_t last = nullptr;
-  double flops_amp = 0, flops_col = 0;
 };
 

@@ -23,6 +23,12 @@ cudaError_t launch_rambo(int K, uint64_t seed, int64_t e0, int64_t nevt, double 
 cudaError_t launch_me_helicity(int K, bool fp32, const double* mom, int64_t nevt, const Tables* tab, const int* hels,
                                int maxslot, const int* nslot, const double* ctri, const MeConst& cst, double* out,
                                int64_t stride, cudaStream_t st);
+// One thread per (event, gluon-helicity combination gslots[slot]); per_hel: out[h * stride + e] for every
+// helicity h of the combination, else out[slot * stride + e] = sum over its good helicities.  Zero top width.
+cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom, int64_t nevt, const Tables* tab,
+                               const int* gslots, int maxslot, const int* nslot, const uint32_t* mask,
+                               const double* ctri, const MeConst& cst, double* out, int64_t stride, cudaStream_t st);
+cudaError_t launch_gluon_slots(const uint32_t* mask, int K, int* gslots, int* n, cudaStream_t st);
 cudaError_t launch_hel_sum(const double* part, const int* nslot, int64_t nevt, int64_t stride, double norm,
                            double* me, cudaStream_t st);
 cudaError_t launch_hel_mask(const double* part, const double* tot, int nhel, int64_t nevt, int64_t stride, double tau,

@@ -70,9 +70,16 @@ extern "C" mg_status mg_sigmakin_noalloc(mg_ctx* ctx, const double* mom_dev, int
   cst.colour_scale = cst.gs * cst.gs / static_cast<double>(ctx->colour_den);
   const double norm = 1.0 / (256.0 * mg::factorial(ctx->ng));
   // every element the sum kernel reads (good slots x events) is written first: nothing to clear
-  if (mg::launch_me_helicity(ctx->K, false, mom_dev, nevt, ctx->d_tab, ctx->d_good, ctx->nhel, ctx->d_ngood,
-                             ctx->d_ctri, cst, scratch, stride, st) != cudaSuccess)
-    return MG_ECUDA;
-  if (mg::launch_hel_sum(scratch, ctx->d_ngood, nevt, stride, norm, me_dev, st) != cudaSuccess) return MG_ECUDA;
+  if (ctx->prm.wt == 0.0) {
+    if (mg::launch_me_gluonhel(ctx->K, false, false, mom_dev, nevt, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
+                               ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, cst, scratch, stride, st) != cudaSuccess)
+      return MG_ECUDA;
+    if (mg::launch_hel_sum(scratch, ctx->d_ngslots, nevt, stride, norm, me_dev, st) != cudaSuccess) return MG_ECUDA;
+  } else {
+    if (mg::launch_me_helicity(ctx->K, false, mom_dev, nevt, ctx->d_tab, ctx->d_good, ctx->nhel, ctx->d_ngood,
+                               ctx->d_ctri, cst, scratch, stride, st) != cudaSuccess)
+      return MG_ECUDA;
+    if (mg::launch_hel_sum(scratch, ctx->d_ngood, nevt, stride, norm, me_dev, st) != cudaSuccess) return MG_ECUDA;
+  }
   return MG_OK;
 }

@@ -87,10 +87,16 @@ def test_aosoa_roundtrip(mg):
 
 def test_flop_model(mg):
     for proc in ("ggtt", "ggttg", "ggttgg", "ggttggg"):
-        amp, col = mg.flops_per_helicity(proc)
-        n = mg.process_info(proc)["ncol"]
+        info = mg.process_info(proc)
+        n, nh = info["ncol"], info["nhel"]
+        amp, col = mg.flops_per_event(proc)
         assert amp > 0
-        assert col == 5.0 * n * (n + 1) / 2 + n
+        assert col == nh * (4.0 * n * (n + 1) / 2 + 4 * n)
+        # a mask with fewer good helicities costs less
+        mask = np.zeros((nh + 31) // 32, dtype=np.uint32)
+        mask[0] = 1
+        amp1, col1 = mg.flops_per_event(proc, mask)
+        assert col1 == 4.0 * n * (n + 1) / 2 + 4 * n and 0 < amp1 < amp
 
 
 def test_invalid_arguments_rejected_without_gpu(mg):
