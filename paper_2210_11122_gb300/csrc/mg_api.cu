@@ -170,6 +170,7 @@ void mg_destroy(mg_ctx* ctx) {
   cudaFree(ctx->d_nbad);
   cudaFree(ctx->d_part);
   cudaFree(ctx->d_tot);
+  cudaFree(ctx->d_prep);
   cudaFree(ctx->d_mom_stage);
   cudaFree(ctx->d_me_stage);
   delete ctx;
@@ -299,8 +300,8 @@ mg_status mg_hel_filter(mg_ctx* ctx, const double* mom_dev, int64_t nevt, void* 
   ctx->last = st;
   const mg::MeConst cst = me_const(ctx);
   if (ctx->prm.wt == 0.0) {
-    MG_CUDA(mg::launch_me_gluonhel(ctx->K, false, true, mom_dev, w, ctx->d_tab, ctx->d_allg, 1 << ctx->K, ctx->d_nallg,
-                                   ctx->d_mask, ctx->d_ctri, cst, ctx->d_part, stride, st));
+    MG_CUDA(mg::launch_me_gluonhel(ctx->K, false, true, mom_dev, nullptr, w, ctx->d_tab, ctx->d_allg, 1 << ctx->K,
+                                   ctx->d_nallg, ctx->d_mask, ctx->d_ctri, cst, ctx->d_part, stride, st));
   } else {
     MG_CUDA(mg::launch_me_helicity(ctx->K, false, mom_dev, w, ctx->d_tab, ctx->d_allhel, ctx->nhel, ctx->d_nhel,
                                    ctx->d_ctri, cst, ctx->d_part, stride, st));
@@ -333,7 +334,10 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
   const mg::MeConst cst = me_const(ctx);
   const double norm = 1.0 / (256.0 * mg::factorial(ctx->ng));
   if (ctx->prm.wt == 0.0) {
-    MG_CUDA(mg::launch_me_gluonhel(ctx->K, precision == MG_FP32_AMP, false, mom_dev, nevt, ctx->d_tab, ctx->d_gslots,
+    const bool fp32 = precision == MG_FP32_AMP;
+    s = grow(&ctx->d_prep, &ctx->prep_cap, stride * mg::event_record_bytes(ctx->K, fp32) / 8 + 1);
+    if (s != MG_OK) return s;
+    MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_dev, ctx->d_prep, nevt, ctx->d_tab, ctx->d_gslots,
                                    1 << ctx->K, ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, cst, ctx->d_part, stride, st));
     MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_ngslots, nevt, stride, norm, me_dev, st));
   } else {

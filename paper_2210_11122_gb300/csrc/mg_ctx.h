@@ -26,6 +26,8 @@ struct mg_ctx {
   double* d_part = nullptr;   // per-(helicity, event) colour sums
   int64_t part_cap = 0;
   double* d_tot = nullptr;    // per-event helicity sums of the filter
+  double* d_prep = nullptr;   // per-event records (momenta sums, propagators, wavefunctions)
+  int64_t prep_cap = 0;       // in doubles
   int64_t tot_cap = 0;
   double* d_mom_stage = nullptr;
   double* d_me_stage = nullptr;

@@ -25,9 +25,13 @@ cudaError_t launch_me_helicity(int K, bool fp32, const double* mom, int64_t nevt
                                int64_t stride, cudaStream_t st);
 // One thread per (event, gluon-helicity combination gslots[slot]); per_hel: out[h * stride + e] for every
 // helicity h of the combination, else out[slot * stride + e] = sum over its good helicities.  Zero top width.
-cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom, int64_t nevt, const Tables* tab,
-                               const int* gslots, int maxslot, const int* nslot, const uint32_t* mask,
-                               const double* ctri, const MeConst& cst, double* out, int64_t stride, cudaStream_t st);
+// prep: NULL (every thread computes its event's momenta sums, propagators and wavefunctions) or a
+// buffer of ceil(nevt/32)*32 * event_record_bytes(K, fp32) bytes that a per-event kernel fills first.
+cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom, void* prep, int64_t nevt,
+                               const Tables* tab, const int* gslots, int maxslot, const int* nslot,
+                               const uint32_t* mask, const double* ctri, const MeConst& cst, double* out,
+                               int64_t stride, cudaStream_t st);
+int64_t event_record_bytes(int K, bool fp32);
 cudaError_t launch_gluon_slots(const uint32_t* mask, int K, int* gslots, int* n, cudaStream_t st);
 cudaError_t launch_hel_sum(const double* part, const int* nslot, int64_t nevt, int64_t stride, double norm,
                            double* me, cudaStream_t st);

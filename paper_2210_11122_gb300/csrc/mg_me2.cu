@@ -230,9 +230,107 @@ __device__ __forceinline__ T colour_sum(const cx<T>* A, const double* __restrict
   return sum;
 }
 
-template <int K, class T, bool PER_HEL>
+// ---- per-event data shared by every helicity of an event (FP64 arithmetic, stored as T) ----
+// Layout of one event's record (NITEM values of T): PT[S][4] (incoming gluon momentum of subset S),
+// gprop[S] (-g/P_S^2), qc[S][5] (quark propagator coefficients), eps[g][hel][4] complex,
+// ubar[hel][4] complex, v[hel][4] complex.
+template <int K> struct EvLayout {
+  static constexpr int NSUB = 1 << K;
+  static constexpr int PT = 0, GP = 4 * NSUB, QC = 5 * NSUB, EPS = 10 * NSUB, UB = EPS + 16 * K, VV = UB + 16;
+  static constexpr int NITEM = VV + 16;
+};
+
+template <int K, class T>
+__device__ __forceinline__ void event_data(const double (*p)[4], const MeConst& cst, T (*PT)[4], T* gprop, T (*qc)[5],
+                                           cx<T> (*eps)[2][4], cx<T> (*ub)[4], cx<T> (*vv)[4]) {
+  constexpr int NSUB = 1 << K;
+  double Pst[NSUB][4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) Pst[0][m] = 0.0;
+#pragma unroll
+  for (int S = 1; S < NSUB; ++S) {
+    const int g = __ffs(S) - 1;
+    const int part = g < 2 ? g : g + 2;
+    const double sg = g < 2 ? 1.0 : -1.0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) Pst[S][m] = Pst[S & (S - 1)][m] + sg * p[part][m];
+  }
+#pragma unroll
+  for (int S = 0; S < NSUB; ++S) {
+    const double* P = Pst[S];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) PT[S][m] = static_cast<T>(P[m]);
+    const double p2 = P[0] * P[0] - P[1] * P[1] - P[2] * P[2] - P[3] * P[3];
+    gprop[S] = static_cast<T>((S & (S - 1)) ? -cst.gs / p2 : 0.0);   // includes one power of g
+    const double Q0 = p[2][0] - P[0], Q1 = p[2][1] - P[1], Q2 = p[2][2] - P[2], Q3 = p[2][3] - P[3];
+    const double f = -cst.gs / (Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3 - cst.mt * cst.mt);
+    qc[S][0] = static_cast<T>((Q0 + Q3) * f);
+    qc[S][1] = static_cast<T>((Q0 - Q3) * f);
+    qc[S][2] = static_cast<T>(Q1 * f);
+    qc[S][3] = static_cast<T>(Q2 * f);
+    qc[S][4] = static_cast<T>(cst.mt * f);
+  }
+#pragma unroll
+  for (int g = 0; g < K; ++g) {
+    const int part = g < 2 ? g : g + 2;
+    gluon_eps<T>(p[part], -1, g >= 2, eps[g][0]);
+    gluon_eps<T>(p[part], 1, g >= 2, eps[g][1]);
+  }
+  top_ubar<T>(p[2], cst.mt, -1, ub[0]);
+  top_ubar<T>(p[2], cst.mt, 1, ub[1]);
+  top_v<T>(p[3], cst.mt, -1, vv[0]);
+  top_v<T>(p[3], cst.mt, 1, vv[1]);
+}
+
+// One thread per event: the event's record, AoSoA (page of 32 events, value-major within a page).
+template <int K, class T>
+__global__ void __launch_bounds__(128) k_event_prep(const double* __restrict__ mom, int64_t nevt, MeConst cst,
+                                                    T* __restrict__ rec) {
+  constexpr int npar = K + 2, NSUB = 1 << K;
+  using L = EvLayout<K>;
+  const int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (e >= nevt) return;
+  double p[npar][4];
+  const double* base = mom + (e / kPage) * npar * 4 * kPage + (e % kPage);
+#pragma unroll
+  for (int i = 0; i < npar; ++i)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) p[i][m] = __ldg(base + (i * 4 + m) * kPage);
+  T PT[NSUB][4], gprop[NSUB], qc[NSUB][5];
+  cx<T> eps[K][2][4], ub[2][4], vv[2][4];
+  event_data<K, T>(p, cst, PT, gprop, qc, eps, ub, vv);
+  T* out = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
+#pragma unroll
+  for (int S = 0; S < NSUB; ++S) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) out[(L::PT + 4 * S + m) * kPage] = PT[S][m];
+    out[(L::GP + S) * kPage] = gprop[S];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) out[(L::QC + 5 * S + c) * kPage] = qc[S][c];
+  }
+#pragma unroll
+  for (int g = 0; g < K; ++g)
+#pragma unroll
+    for (int l = 0; l < 2; ++l)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        out[(L::EPS + ((g * 2 + l) * 4 + m) * 2) * kPage] = eps[g][l][m].r;
+        out[(L::EPS + ((g * 2 + l) * 4 + m) * 2 + 1) * kPage] = eps[g][l][m].i;
+      }
+#pragma unroll
+  for (int l = 0; l < 2; ++l)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      out[(L::UB + (l * 4 + a) * 2) * kPage] = ub[l][a].r;
+      out[(L::UB + (l * 4 + a) * 2 + 1) * kPage] = ub[l][a].i;
+      out[(L::VV + (l * 4 + a) * 2) * kPage] = vv[l][a].r;
+      out[(L::VV + (l * 4 + a) * 2 + 1) * kPage] = vv[l][a].i;
+    }
+}
+
+template <int K, class T, bool PER_HEL, bool PREP>
 __global__ void __launch_bounds__(kMeThreads)
-k_me_gluonhel(const double* __restrict__ mom, int64_t nevt, const Tables* __restrict__ tab,
+k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab,
               const int* __restrict__ gslots, const int* __restrict__ nslot_dev, const uint32_t* __restrict__ mask,
               const double* __restrict__ ctri, MeConst cst, double* __restrict__ out, int64_t stride) {
   constexpr int npar = K + 2;
@@ -245,56 +343,54 @@ k_me_gluonhel(const double* __restrict__ mom, int64_t nevt, const Tables* __rest
   if (e >= nevt || slot >= *nslot_dev) return;
   const int gc = gslots[slot];   // bit g = helicity (+1) of gluon g
 
-  double p[npar][4];
-  {
+  const T gs = static_cast<T>(cst.gs);
+  T PT[NSUB][4];
+  T gprop[NSUB];
+  T qc[NSUB][5];
+  cx<T> J[NSEQ][4];
+  cx<T> ub[2][4], vv[2][4];
+  if (PREP) {
+    using L = EvLayout<K>;
+    const T* in = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
+#pragma unroll
+    for (int S = 0; S < NSUB; ++S) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) PT[S][m] = __ldg(in + (L::PT + 4 * S + m) * kPage);
+      gprop[S] = __ldg(in + (L::GP + S) * kPage);
+#pragma unroll
+      for (int c = 0; c < 5; ++c) qc[S][c] = __ldg(in + (L::QC + 5 * S + c) * kPage);
+    }
+#pragma unroll
+    for (int g = 0; g < K; ++g) {
+      const int l = (gc >> g) & 1;
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        J[g][m] = {__ldg(in + (L::EPS + ((g * 2 + l) * 4 + m) * 2) * kPage),
+                   __ldg(in + (L::EPS + ((g * 2 + l) * 4 + m) * 2 + 1) * kPage)};
+    }
+#pragma unroll
+    for (int l = 0; l < 2; ++l)
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        ub[l][a] = {__ldg(in + (L::UB + (l * 4 + a) * 2) * kPage), __ldg(in + (L::UB + (l * 4 + a) * 2 + 1) * kPage)};
+        vv[l][a] = {__ldg(in + (L::VV + (l * 4 + a) * 2) * kPage), __ldg(in + (L::VV + (l * 4 + a) * 2 + 1) * kPage)};
+      }
+  } else {
+    double p[npar][4];
     const double* base = mom + (e / kPage) * npar * 4 * kPage + (e % kPage);
 #pragma unroll
     for (int i = 0; i < npar; ++i)
 #pragma unroll
       for (int m = 0; m < 4; ++m) p[i][m] = __ldg(base + (i * 4 + m) * kPage);
-  }
-  const T gs = static_cast<T>(cst.gs);
-
-  // ---- subset momenta, gluon propagators -1/P^2, quark propagator coefficients ----
-  T PT[NSUB][4];
-  T gprop[NSUB];
-  T qc[NSUB][5];
-  {
-    double P[4] = {0, 0, 0, 0};
-    double Pst[NSUB][4];
+    cx<T> eps[K][2][4];
+    event_data<K, T>(p, cst, PT, gprop, qc, eps, ub, vv);
 #pragma unroll
-    for (int m = 0; m < 4; ++m) Pst[0][m] = 0.0;
+    for (int g = 0; g < K; ++g)
 #pragma unroll
-    for (int S = 1; S < NSUB; ++S) {
-      const int g = __ffs(S) - 1;
-      const int part = g < 2 ? g : g + 2;
-      const double sg = g < 2 ? 1.0 : -1.0;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) Pst[S][m] = Pst[S & (S - 1)][m] + sg * p[part][m];
-    }
-#pragma unroll
-    for (int S = 0; S < NSUB; ++S) {
-#pragma unroll
-      for (int m = 0; m < 4; ++m) { P[m] = Pst[S][m]; PT[S][m] = static_cast<T>(P[m]); }
-      const double p2 = P[0] * P[0] - P[1] * P[1] - P[2] * P[2] - P[3] * P[3];
-      gprop[S] = static_cast<T>((S & (S - 1)) ? -cst.gs / p2 : 0.0);   // includes one power of g
-      const double Q0 = p[2][0] - P[0], Q1 = p[2][1] - P[1], Q2 = p[2][2] - P[2], Q3 = p[2][3] - P[3];
-      const double f = -cst.gs / (Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3 - cst.mt * cst.mt);
-      qc[S][0] = static_cast<T>((Q0 + Q3) * f);
-      qc[S][1] = static_cast<T>((Q0 - Q3) * f);
-      qc[S][2] = static_cast<T>(Q1 * f);
-      qc[S][3] = static_cast<T>(Q2 * f);
-      qc[S][4] = static_cast<T>(cst.mt * f);
-    }
+      for (int m = 0; m < 4; ++m) J[g][m] = eps[g][(gc >> g) & 1][m];
   }
 
   // ---- gluon currents (helicities of gc) ----
-  cx<T> J[NSEQ][4];
-#pragma unroll
-  for (int g = 0; g < K; ++g) {
-    const int part = g < 2 ? g : g + 2;
-    gluon_eps<T>(p[part], ((gc >> g) & 1) ? 1 : -1, g >= 2, J[g]);
-  }
   for (int s = K; s < NSEQ; ++s) {
     cx<T> acc[4] = {};
     const int n3 = tab->seq_nv3[s];
@@ -334,12 +430,9 @@ k_me_gluonhel(const double* __restrict__ mom, int64_t nevt, const Tables* __rest
 
   // ---- antitop spinors and (gamma.J) v for both antitop helicities ----
   cx<T> X[2][NSEQ][4];
-  cx<T> vv[2][4];
 #pragma unroll
-  for (int b = 0; b < 2; ++b) {
-    top_v<T>(p[3], cst.mt, b ? 1 : -1, vv[b]);
+  for (int b = 0; b < 2; ++b)
     for (int s = 0; s < NSEQ; ++s) gamma_col(J[s], vv[b], X[b][s]);
-  }
 
   // helicity index of (gc, top helicity a, antitop helicity b)
   int hbase = 0;
@@ -355,7 +448,8 @@ k_me_gluonhel(const double* __restrict__ mom, int64_t nevt, const Tables* __rest
     const bool good1 = PER_HEL || ((mask[h1 >> 5] >> (h1 & 31)) & 1u);
     if (!good0 && !good1) continue;
     cx<T> stk[K][4];
-    top_ubar<T>(p[2], cst.mt, a ? 1 : -1, stk[0]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) stk[0][q] = ub[a][q];
     cx<T> Jq[2][4];
     quark_current(stk[0], vv[0], Jq[0]);
     quark_current(stk[0], vv[1], Jq[1]);
@@ -424,28 +518,48 @@ cudaError_t launch_gluon_slots(const uint32_t* mask, int K, int* gslots, int* n,
 }
 
 template <int K, class T, bool PER_HEL>
-static cudaError_t launch_v2(const double* mom, int64_t nevt, const Tables* tab, const int* gslots, int maxslot,
-                             const int* nslot, const uint32_t* mask, const double* ctri, const MeConst& cst,
-                             double* out, int64_t stride, cudaStream_t st) {
+static cudaError_t launch_v2(const double* mom, void* prep, int64_t nevt, const Tables* tab, const int* gslots,
+                             int maxslot, const int* nslot, const uint32_t* mask, const double* ctri,
+                             const MeConst& cst, double* out, int64_t stride, cudaStream_t st) {
   dim3 grid(static_cast<unsigned>((nevt + kMeThreads - 1) / kMeThreads), static_cast<unsigned>(maxslot));
   if (grid.x == 0 || grid.y == 0) return cudaSuccess;
-  v2::k_me_gluonhel<K, T, PER_HEL><<<grid, kMeThreads, 0, st>>>(mom, nevt, tab, gslots, nslot, mask, ctri, cst, out,
-                                                                 stride);
+  if (prep && !PER_HEL) {
+    T* rec = static_cast<T*>(prep);
+    v2::k_event_prep<K, T><<<static_cast<unsigned>((nevt + 127) / 128), 128, 0, st>>>(mom, nevt, cst, rec);
+    v2::k_me_gluonhel<K, T, PER_HEL, true><<<grid, kMeThreads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot, mask,
+                                                                         ctri, cst, out, stride);
+  } else {
+    v2::k_me_gluonhel<K, T, PER_HEL, false><<<grid, kMeThreads, 0, st>>>(mom, nullptr, nevt, tab, gslots, nslot,
+                                                                          mask, ctri, cst, out, stride);
+  }
   return cudaGetLastError();
 }
 
-cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom, int64_t nevt, const Tables* tab,
-                               const int* gslots, int maxslot, const int* nslot, const uint32_t* mask,
-                               const double* ctri, const MeConst& cst, double* out, int64_t stride, cudaStream_t st) {
+int64_t event_record_bytes(int K, bool fp32) {
+  int nitem = 0;
+  switch (K) {
+    case 2: nitem = v2::EvLayout<2>::NITEM; break;
+    case 3: nitem = v2::EvLayout<3>::NITEM; break;
+    case 4: nitem = v2::EvLayout<4>::NITEM; break;
+    case 5: nitem = v2::EvLayout<5>::NITEM; break;
+    default: return 0;
+  }
+  return static_cast<int64_t>(nitem) * (fp32 ? 4 : 8);
+}
+
+cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom, void* prep, int64_t nevt,
+                               const Tables* tab, const int* gslots, int maxslot, const int* nslot,
+                               const uint32_t* mask, const double* ctri, const MeConst& cst, double* out,
+                               int64_t stride, cudaStream_t st) {
 #define MG_V2_CASE(KK)                                                                                              \
   case KK:                                                                                                          \
-    if (per_hel) return fp32 ? launch_v2<KK, float, true>(mom, nevt, tab, gslots, maxslot, nslot, mask, ctri, cst,  \
+    if (per_hel) return fp32 ? launch_v2<KK, float, true>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri, cst,  \
                                                           out, stride, st)                                          \
-                             : launch_v2<KK, double, true>(mom, nevt, tab, gslots, maxslot, nslot, mask, ctri, cst, \
+                             : launch_v2<KK, double, true>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri, cst, \
                                                            out, stride, st);                                        \
-    return fp32 ? launch_v2<KK, float, false>(mom, nevt, tab, gslots, maxslot, nslot, mask, ctri, cst, out, stride, \
+    return fp32 ? launch_v2<KK, float, false>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri, cst, out, stride, \
                                               st)                                                                   \
-                : launch_v2<KK, double, false>(mom, nevt, tab, gslots, maxslot, nslot, mask, ctri, cst, out, stride,\
+                : launch_v2<KK, double, false>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri, cst, out, stride,\
                                                st);
   switch (K) {
     MG_V2_CASE(2)
