@@ -258,14 +258,17 @@ def run_ours(args):
         ms_step, ms_me = t.tolist()
     value = world * nevt / (ms_step * 1e-3)
 
-    # FP32-amplitude variant of the same step
-    ms32, ms32_me, _ = timed(mg.MG_FP32_AMP, max(3, args.steps // 2), 3)
-    torch.cuda.synchronize()
-    a, b = me.double().cpu(), me32.double().cpu()
-    rel = ((b / a) - 1).abs()
-    fp32 = {"value": world * nevt / (ms32 * 1e-3), "ms_per_step": ms32, "me_kernel_ms": ms32_me,
-            "rel_err_vs_fp64": {"max": float(rel.max()), "p99": float(rel.quantile(0.99)) if rel.numel() <= 1 << 24 else None,
-                                "median": float(rel.median())}}
+    # the other arithmetic modes on the same step: FP32 amplitudes; FP64 or FP32 amplitudes with the
+    # colour sum on the tensor cores
+    ref64 = me.double().cpu()
+    variants = {}
+    for name, prec in (("fp32_amp", mg.MG_FP32_AMP), ("fp64_tccolor", mg.MG_FP64_TCCOLOR), ("mixed", mg.MG_MIXED)):
+        msv, msv_me, _ = timed(prec, max(3, args.steps // 2), 3)
+        torch.cuda.synchronize()
+        rel = ((me32.double().cpu() / ref64) - 1).abs()
+        variants[name] = {"value": world * nevt / (msv * 1e-3), "ms_per_step": msv, "me_kernel_ms": msv_me,
+                          "rel_err_vs_fp64": {"max": float(rel.max()), "p99": float(rel.quantile(0.99)),
+                                              "median": float(rel.median())}}
 
     # end to end through the host-buffer entry point (pinned momenta in, MEs out, copies timed)
     host_mom = mom.cpu().pin_memory()
@@ -314,7 +317,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(args, nevt, {"parallelism": "dp%d (disjoint event ranges)" % world}),
             "me_kernel_ms": ms_me, "wall_s": wall, "nonconverged_events": nbad, "good_helicities": ngood,
-            "fp32_amp": fp32, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "modes": variants, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": launches_per_step * args.steps}
     print(json.dumps(line))
     ctx.close()

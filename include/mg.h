@@ -58,9 +58,15 @@ typedef enum {
 
 typedef enum { MG_GG_TT = 0, MG_GG_TTG = 1, MG_GG_TTGG = 2, MG_GG_TTGGG = 3 } mg_process;
 
-/* Arithmetic of mg_sigmakin.  MG_FP64 is plain FP64 throughout (per-event relative error
- * vs an FP64 reference <= 1e-12).  MG_FP32_AMP computes the amplitudes in FP32 with FP64 kept for
- * momenta, the top wavefunctions and the helicity sum. */
+/* Arithmetic of mg_sigmakin.
+ *   MG_FP64         plain FP64 throughout (per-event relative error vs an FP64 reference <= 1e-12);
+ *   MG_FP32_AMP     amplitudes and colour sum in FP32; FP64 kept for momenta, propagator
+ *                   denominators, the top wavefunctions and the helicity sum;
+ *   MG_FP64_TCCOLOR FP64 amplitudes; colour sum A^dagger C A on the tensor cores: the integer colour
+ *                   matrix exact in FP16, every jamp row scaled by a power of two and split hi + lo
+ *                   in FP16, FP32 accumulation (~1e-7 relative per helicity);
+ *   MG_MIXED        FP32 amplitudes + the tensor-core colour sum.
+ * The tensor-core modes need zero top width (MG_ENOTSUP otherwise). */
 typedef enum { MG_FP64 = 0, MG_FP32_AMP = 1, MG_FP64_TCCOLOR = 2, MG_MIXED = 3 } mg_precision;
 
 typedef struct {

@@ -166,6 +166,9 @@ void mg_destroy(mg_ctx* ctx) {
   cudaFree(ctx->d_gslots);
   cudaFree(ctx->d_ngslots);
   cudaFree(ctx->d_allg);
+  cudaFree(ctx->d_nrows);
+  cudaFree(ctx->d_cmat);
+  cudaFree(ctx->d_jamps);
   cudaFree(ctx->d_nallg);
   cudaFree(ctx->d_nbad);
   cudaFree(ctx->d_part);
@@ -223,6 +226,16 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
       break;
     }
     const int ng2 = 1 << c->K;
+    {
+      std::vector<uint16_t> halves(mg::colour_tc_cmat_halves(c->ncol));
+      mg::colour_tc_pack(c->ncol, num.data(), halves.data());
+      if (cudaMalloc(&c->d_cmat, halves.size() * sizeof(uint16_t)) != cudaSuccess ||
+          cudaMemcpy(c->d_cmat, halves.data(), halves.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMalloc(&c->d_nrows, sizeof(int)) != cudaSuccess || cudaMemset(c->d_nrows, 0, sizeof(int)) != cudaSuccess) {
+        st = MG_ENOMEM;
+        break;
+      }
+    }
     if (cudaMalloc(&c->d_gslots, 32 * sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_ngslots, sizeof(int)) != cudaSuccess ||
         cudaMalloc(&c->d_allg, 32 * sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_nallg, sizeof(int)) != cudaSuccess) {
       st = MG_ENOMEM;
@@ -309,7 +322,7 @@ mg_status mg_hel_filter(mg_ctx* ctx, const double* mom_dev, int64_t nevt, void* 
   MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_nhel, w, stride, 1.0, ctx->d_tot, st));
   MG_CUDA(mg::launch_hel_mask(ctx->d_part, ctx->d_tot, ctx->nhel, w, stride, ctx->prm.hel_tau, ctx->d_mask,
                               ctx->d_good, ctx->d_ngood, st));
-  MG_CUDA(mg::launch_gluon_slots(ctx->d_mask, ctx->K, ctx->d_gslots, ctx->d_ngslots, st));
+  MG_CUDA(mg::launch_gluon_slots(ctx->d_mask, ctx->K, ctx->d_gslots, ctx->d_ngslots, ctx->d_nrows, st));
   ctx->mask_ready = true;
   return MG_OK;
 }
@@ -317,10 +330,10 @@ mg_status mg_hel_filter(mg_ctx* ctx, const double* mom_dev, int64_t nevt, void* 
 mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_precision precision, double* me_dev,
                       void* stream) {
   if (!ctx || nevt < 0 || (nevt > 0 && (!mom_dev || !me_dev))) return MG_EINVAL;
-  if (precision != MG_FP64 && precision != MG_FP32_AMP) {
-    if (precision == MG_FP64_TCCOLOR || precision == MG_MIXED) return MG_ENOTSUP;
+  if (precision != MG_FP64 && precision != MG_FP32_AMP && precision != MG_FP64_TCCOLOR && precision != MG_MIXED)
     return MG_EINVAL;
-  }
+  const bool tc = precision == MG_FP64_TCCOLOR || precision == MG_MIXED;
+  if (tc && ctx->prm.wt != 0.0) return MG_ENOTSUP;   // the tensor-core colour path has zero top width
   if (nevt == 0) return MG_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!ctx->mask_ready) {
@@ -333,7 +346,39 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
   ctx->last = st;
   const mg::MeConst cst = me_const(ctx);
   const double norm = 1.0 / (256.0 * mg::factorial(ctx->ng));
-  if (ctx->prm.wt == 0.0) {
+  if (tc) {
+    // amplitudes -> FP32 jamps -> tensor-core colour sums, in chunks of whole pages that keep the jamp
+    // buffer within 4 GiB
+    const bool fp32 = precision == MG_MIXED;
+    const int64_t per_event = static_cast<int64_t>(ctx->nhel) * ctx->ncol;   // float2 per event
+    int64_t chunk = (int64_t(1) << 29) / per_event;                          // 2^29 float2 = 4 GiB
+    chunk = chunk / mg::kPage * mg::kPage;
+    if (chunk < mg::kPage) chunk = mg::kPage;
+    if (chunk > stride) chunk = stride;
+    if (ctx->jamp_cap < chunk * per_event) {
+      if (ctx->d_jamps) cudaFree(ctx->d_jamps);
+      ctx->d_jamps = nullptr;
+      ctx->jamp_cap = 0;
+      if (cudaMalloc(&ctx->d_jamps, static_cast<size_t>(chunk * per_event) * sizeof(float2)) != cudaSuccess) {
+        cudaGetLastError();
+        return MG_ENOMEM;
+      }
+      ctx->jamp_cap = chunk * per_event;
+    }
+    s = grow(&ctx->d_prep, &ctx->prep_cap, chunk * mg::event_record_bytes(ctx->K, fp32) / 8 + 1);
+    if (s != MG_OK) return s;
+    for (int64_t e0 = 0; e0 < nevt; e0 += chunk) {
+      const int64_t n = nevt - e0 < chunk ? nevt - e0 : chunk;
+      const int64_t cst_stride = pad32(n);
+      const double* mom_c = mom_dev + (e0 / mg::kPage) * ctx->npar * 4 * mg::kPage;
+      MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_c, ctx->d_prep, n, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
+                                     ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, cst, ctx->d_part, cst_stride, st,
+                                     ctx->d_jamps));
+      MG_CUDA(mg::launch_colour_tc(ctx->ncol, ctx->d_jamps, n, ctx->nhel, ctx->d_nrows, ctx->d_cmat, cst.colour_scale,
+                                   ctx->d_part, cst_stride, st));
+      MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_nrows, n, cst_stride, norm, me_dev + e0, st));
+    }
+  } else if (ctx->prm.wt == 0.0) {
     const bool fp32 = precision == MG_FP32_AMP;
     s = grow(&ctx->d_prep, &ctx->prep_cap, stride * mg::event_record_bytes(ctx->K, fp32) / 8 + 1);
     if (s != MG_OK) return s;

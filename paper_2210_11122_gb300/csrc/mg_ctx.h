@@ -20,6 +20,10 @@ struct mg_ctx {
   int* d_nhel = nullptr;      // nhel
   int* d_gslots = nullptr;    // gluon-helicity combinations with a good helicity
   int* d_ngslots = nullptr;
+  int* d_nrows = nullptr;     // 4 * (number of gluon combinations): jamp rows per event
+  void* d_cmat = nullptr;     // colour matrix numerators as the packed FP16 tensor-core operand
+  float2* d_jamps = nullptr;  // FP32 jamps of the tensor-core colour path
+  int64_t jamp_cap = 0;       // in float2
   int* d_allg = nullptr;      // 0..2^K-1
   int* d_nallg = nullptr;     // 2^K
   unsigned long long* d_nbad = nullptr;

@@ -30,9 +30,16 @@ cudaError_t launch_me_helicity(int K, bool fp32, const double* mom, int64_t nevt
 cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom, void* prep, int64_t nevt,
                                const Tables* tab, const int* gslots, int maxslot, const int* nslot,
                                const uint32_t* mask, const double* ctri, const MeConst& cst, double* out,
-                               int64_t stride, cudaStream_t st);
+                               int64_t stride, cudaStream_t st, float2* jout = nullptr);
 int64_t event_record_bytes(int K, bool fp32);
-cudaError_t launch_gluon_slots(const uint32_t* mask, int K, int* gslots, int* n, cudaStream_t st);
+
+// Tensor-core colour sum (mg_colour_tc.cu): out[r * stride + e] = scale * (Re A^T C Re A + Im A^T C Im A)
+// for the jamp rows jamps[(e * rows_alloc + r) * ncol ...], r < *nrows.
+int colour_tc_cmat_halves(int ncol);
+void colour_tc_pack(int ncol, const int64_t* num, uint16_t* out_halves);
+cudaError_t launch_colour_tc(int ncol, const float2* jamps, int64_t nevt, int rows_alloc, const int* nrows,
+                             const void* cmat, double scale, double* out, int64_t stride, cudaStream_t st);
+cudaError_t launch_gluon_slots(const uint32_t* mask, int K, int* gslots, int* n, int* nrows, cudaStream_t st);
 cudaError_t launch_hel_sum(const double* part, const int* nslot, int64_t nevt, int64_t stride, double norm,
                            double* me, cudaStream_t st);
 cudaError_t launch_hel_mask(const double* part, const double* tot, int nhel, int64_t nevt, int64_t stride, double tau,

@@ -328,11 +328,15 @@ __global__ void __launch_bounds__(128) k_event_prep(const double* __restrict__ m
     }
 }
 
-template <int K, class T, bool PER_HEL, bool PREP>
+// JOUT: instead of colour sums, write the jamps of every helicity of the slot as FP32 complex
+// numbers to jout[((e * 4 * 2^K) + slot * 4 + 2 * top + antitop) * ncol + sigma] (zeros for helicities
+// outside the mask), for the tensor-core colour sum.
+template <int K, class T, bool PER_HEL, bool PREP, bool JOUT>
 __global__ void __launch_bounds__(kMeThreads)
 k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab,
               const int* __restrict__ gslots, const int* __restrict__ nslot_dev, const uint32_t* __restrict__ mask,
-              const double* __restrict__ ctri, MeConst cst, double* __restrict__ out, int64_t stride) {
+              const double* __restrict__ ctri, MeConst cst, double* __restrict__ out, int64_t stride,
+              float2* __restrict__ jout) {
   constexpr int npar = K + 2;
   constexpr int NSEQ = Sizes<K>::nseq;
   constexpr int NCOL = Sizes<K>::ncol;
@@ -446,7 +450,13 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
     const int h0 = hbase | (a ? bit_t : 0), h1 = h0 | bit_tb;
     const bool good0 = PER_HEL || ((mask[h0 >> 5] >> (h0 & 31)) & 1u);
     const bool good1 = PER_HEL || ((mask[h1 >> 5] >> (h1 & 31)) & 1u);
-    if (!good0 && !good1) continue;
+    if (!good0 && !good1) {
+      if (JOUT) {
+        float2* row = jout + (e * (4 << K) + slot * 4 + 2 * a) * NCOL;
+        for (int c = 0; c < 2 * NCOL; ++c) row[c] = make_float2(0.f, 0.f);
+      }
+      continue;
+    }
     cx<T> stk[K][4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) stk[0][q] = ub[a][q];
@@ -478,6 +488,16 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
         A[b][c] = amp;
       }
     }
+    if (JOUT) {
+#pragma unroll
+      for (int b = 0; b < 2; ++b) {
+        const bool good = b ? good1 : good0;
+        float2* row = jout + (e * (4 << K) + slot * 4 + 2 * a + b) * NCOL;
+        for (int c = 0; c < NCOL; ++c)
+          row[c] = good ? make_float2(static_cast<float>(A[b][c].r), static_cast<float>(A[b][c].i)) : make_float2(0.f, 0.f);
+      }
+      continue;
+    }
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
       const int h = b ? h1 : h0;
@@ -488,11 +508,12 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
       else total += v;
     }
   }
-  if (!PER_HEL) out[slot * stride + e] = total;
+  if (!PER_HEL && !JOUT) out[slot * stride + e] = total;
 }
 
 // Gluon-helicity combinations with at least one good helicity (fixed ascending order).
-__global__ void k_gluon_slots(const uint32_t* __restrict__ mask, int K, int* __restrict__ gslots, int* __restrict__ n) {
+__global__ void k_gluon_slots(const uint32_t* __restrict__ mask, int K, int* __restrict__ gslots, int* __restrict__ n,
+                              int* __restrict__ nrows) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int npar = K + 2;
   int cnt = 0;
@@ -508,29 +529,34 @@ __global__ void k_gluon_slots(const uint32_t* __restrict__ mask, int K, int* __r
     if (any) gslots[cnt++] = gc;
   }
   *n = cnt;
+  *nrows = 4 * cnt;
 }
 
 }  // namespace v2
 
-cudaError_t launch_gluon_slots(const uint32_t* mask, int K, int* gslots, int* n, cudaStream_t st) {
-  v2::k_gluon_slots<<<1, 32, 0, st>>>(mask, K, gslots, n);
+cudaError_t launch_gluon_slots(const uint32_t* mask, int K, int* gslots, int* n, int* nrows, cudaStream_t st) {
+  v2::k_gluon_slots<<<1, 32, 0, st>>>(mask, K, gslots, n, nrows);
   return cudaGetLastError();
 }
 
 template <int K, class T, bool PER_HEL>
 static cudaError_t launch_v2(const double* mom, void* prep, int64_t nevt, const Tables* tab, const int* gslots,
                              int maxslot, const int* nslot, const uint32_t* mask, const double* ctri,
-                             const MeConst& cst, double* out, int64_t stride, cudaStream_t st) {
+                             const MeConst& cst, double* out, int64_t stride, float2* jout, cudaStream_t st) {
   dim3 grid(static_cast<unsigned>((nevt + kMeThreads - 1) / kMeThreads), static_cast<unsigned>(maxslot));
   if (grid.x == 0 || grid.y == 0) return cudaSuccess;
   if (prep && !PER_HEL) {
     T* rec = static_cast<T*>(prep);
     v2::k_event_prep<K, T><<<static_cast<unsigned>((nevt + 127) / 128), 128, 0, st>>>(mom, nevt, cst, rec);
-    v2::k_me_gluonhel<K, T, PER_HEL, true><<<grid, kMeThreads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot, mask,
-                                                                         ctri, cst, out, stride);
+    if (jout)
+      v2::k_me_gluonhel<K, T, false, true, true><<<grid, kMeThreads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot, mask,
+                                                                             ctri, cst, out, stride, jout);
+    else
+      v2::k_me_gluonhel<K, T, false, true, false><<<grid, kMeThreads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot,
+                                                                              mask, ctri, cst, out, stride, nullptr);
   } else {
-    v2::k_me_gluonhel<K, T, PER_HEL, false><<<grid, kMeThreads, 0, st>>>(mom, nullptr, nevt, tab, gslots, nslot,
-                                                                          mask, ctri, cst, out, stride);
+    v2::k_me_gluonhel<K, T, PER_HEL, false, false><<<grid, kMeThreads, 0, st>>>(mom, nullptr, nevt, tab, gslots, nslot,
+                                                                                 mask, ctri, cst, out, stride, nullptr);
   }
   return cudaGetLastError();
 }
@@ -550,17 +576,17 @@ int64_t event_record_bytes(int K, bool fp32) {
 cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom, void* prep, int64_t nevt,
                                const Tables* tab, const int* gslots, int maxslot, const int* nslot,
                                const uint32_t* mask, const double* ctri, const MeConst& cst, double* out,
-                               int64_t stride, cudaStream_t st) {
+                               int64_t stride, cudaStream_t st, float2* jout) {
 #define MG_V2_CASE(KK)                                                                                              \
   case KK:                                                                                                          \
     if (per_hel) return fp32 ? launch_v2<KK, float, true>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri, cst,  \
-                                                          out, stride, st)                                          \
+                                                          out, stride, jout, st)                                          \
                              : launch_v2<KK, double, true>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri, cst, \
-                                                           out, stride, st);                                        \
+                                                           out, stride, jout, st);                                        \
     return fp32 ? launch_v2<KK, float, false>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri, cst, out, stride, \
-                                              st)                                                                   \
+                                              jout, st)                                                                   \
                 : launch_v2<KK, double, false>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri, cst, out, stride,\
-                                               st);
+                                               jout, st);
   switch (K) {
     MG_V2_CASE(2)
     MG_V2_CASE(3)
