@@ -158,6 +158,7 @@ void mg_destroy(mg_ctx* ctx) {
   cudaDeviceSynchronize();
   cudaFree(ctx->d_tab);
   cudaFree(ctx->d_ctri);
+  cudaFree(ctx->d_ctri_f);
   cudaFree(ctx->d_mask);
   cudaFree(ctx->d_good);
   cudaFree(ctx->d_ngood);
@@ -216,6 +217,9 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
         tri.push_back(static_cast<double>(num[static_cast<size_t>(a) * c->ncol + b]) * (a == b ? 1.0 : 2.0));
     e = cudaMalloc(&c->d_ctri, tri.size() * sizeof(double));
     if (e == cudaSuccess) e = cudaMemcpy(c->d_ctri, tri.data(), tri.size() * sizeof(double), cudaMemcpyHostToDevice);
+    std::vector<float> trif(tri.begin(), tri.end());
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_ctri_f, trif.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_ctri_f, trif.data(), trif.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) { st = MG_ECUDA; break; }
     std::vector<int> all(c->nhel);
     for (int h = 0; h < c->nhel; ++h) all[h] = h;
@@ -314,7 +318,7 @@ mg_status mg_hel_filter(mg_ctx* ctx, const double* mom_dev, int64_t nevt, void* 
   const mg::MeConst cst = me_const(ctx);
   if (ctx->prm.wt == 0.0) {
     MG_CUDA(mg::launch_me_gluonhel(ctx->K, false, true, mom_dev, nullptr, w, ctx->d_tab, ctx->d_allg, 1 << ctx->K,
-                                   ctx->d_nallg, ctx->d_mask, ctx->d_ctri, cst, ctx->d_part, stride, st));
+                                   ctx->d_nallg, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, stride, st));
   } else {
     MG_CUDA(mg::launch_me_helicity(ctx->K, false, mom_dev, w, ctx->d_tab, ctx->d_allhel, ctx->nhel, ctx->d_nhel,
                                    ctx->d_ctri, cst, ctx->d_part, stride, st));
@@ -372,7 +376,7 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
       const int64_t cst_stride = pad32(n);
       const double* mom_c = mom_dev + (e0 / mg::kPage) * ctx->npar * 4 * mg::kPage;
       MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_c, ctx->d_prep, n, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
-                                     ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, cst, ctx->d_part, cst_stride, st,
+                                     ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, cst_stride, st,
                                      ctx->d_jamps));
       MG_CUDA(mg::launch_colour_tc(ctx->ncol, ctx->d_jamps, n, ctx->nhel, ctx->d_nrows, ctx->d_cmat, cst.colour_scale,
                                    ctx->d_part, cst_stride, st));
@@ -383,7 +387,7 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
     s = grow(&ctx->d_prep, &ctx->prep_cap, stride * mg::event_record_bytes(ctx->K, fp32) / 8 + 1);
     if (s != MG_OK) return s;
     MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_dev, ctx->d_prep, nevt, ctx->d_tab, ctx->d_gslots,
-                                   1 << ctx->K, ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, cst, ctx->d_part, stride, st));
+                                   1 << ctx->K, ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, stride, st));
     MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_ngslots, nevt, stride, norm, me_dev, st));
   } else {
     MG_CUDA(mg::launch_me_helicity(ctx->K, precision == MG_FP32_AMP, mom_dev, nevt, ctx->d_tab, ctx->d_good, ctx->nhel,

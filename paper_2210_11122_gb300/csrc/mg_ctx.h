@@ -12,6 +12,7 @@ struct mg_ctx {
   mg_params prm;
   mg::Tables* d_tab = nullptr;
   double* d_ctri = nullptr;   // packed upper triangle of the integer colour matrix, off-diagonal doubled
+  float* d_ctri_f = nullptr;  // the same in FP32 (exact: integers < 2^24)
   int64_t colour_den = 1;
   uint32_t* d_mask = nullptr;
   int* d_good = nullptr;      // good helicity list

@@ -29,8 +29,8 @@ cudaError_t launch_me_helicity(int K, bool fp32, const double* mom, int64_t nevt
 // buffer of ceil(nevt/32)*32 * event_record_bytes(K, fp32) bytes that a per-event kernel fills first.
 cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom, void* prep, int64_t nevt,
                                const Tables* tab, const int* gslots, int maxslot, const int* nslot,
-                               const uint32_t* mask, const double* ctri, const MeConst& cst, double* out,
-                               int64_t stride, cudaStream_t st, float2* jout = nullptr);
+                               const uint32_t* mask, const double* ctri64, const float* ctri32, const MeConst& cst,
+                               double* out, int64_t stride, cudaStream_t st, float2* jout = nullptr);
 int64_t event_record_bytes(int K, bool fp32);
 
 // Tensor-core colour sum (mg_colour_tc.cu): out[r * stride + e] = scale * (Re A^T C Re A + Im A^T C Im A)

@@ -214,13 +214,13 @@ template <class T> __device__ __forceinline__ void quark_current(const cx<T>* u,
 
 // colour sum of one helicity: sum_a A_a^* (sum_b Ctri_ab A_b), packed upper triangle
 template <int NCOL, class T>
-__device__ __forceinline__ T colour_sum(const cx<T>* A, const double* __restrict__ ctri) {
+__device__ __forceinline__ T colour_sum(const cx<T>* A, const T* __restrict__ ctri) {
   T sum = 0;
   int idx = 0;
   for (int a = 0; a < NCOL; ++a) {
     T wr = 0, wi = 0;
     for (int b = a; b < NCOL; ++b, ++idx) {
-      const T c = static_cast<T>(__ldg(ctri + idx));
+      const T c = __ldg(ctri + idx);
       wr = fma(c, A[b].r, wr);
       wi = fma(c, A[b].i, wi);
     }
@@ -335,7 +335,7 @@ template <int K, class T, bool PER_HEL, bool PREP, bool JOUT>
 __global__ void __launch_bounds__(kMeThreads)
 k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab,
               const int* __restrict__ gslots, const int* __restrict__ nslot_dev, const uint32_t* __restrict__ mask,
-              const double* __restrict__ ctri, MeConst cst, double* __restrict__ out, int64_t stride,
+              const T* __restrict__ ctri, MeConst cst, double* __restrict__ out, int64_t stride,
               float2* __restrict__ jout) {
   constexpr int npar = K + 2;
   constexpr int NSEQ = Sizes<K>::nseq;
@@ -541,8 +541,9 @@ cudaError_t launch_gluon_slots(const uint32_t* mask, int K, int* gslots, int* n,
 
 template <int K, class T, bool PER_HEL>
 static cudaError_t launch_v2(const double* mom, void* prep, int64_t nevt, const Tables* tab, const int* gslots,
-                             int maxslot, const int* nslot, const uint32_t* mask, const double* ctri,
+                             int maxslot, const int* nslot, const uint32_t* mask, const void* ctri_any,
                              const MeConst& cst, double* out, int64_t stride, float2* jout, cudaStream_t st) {
+  const T* ctri = static_cast<const T*>(ctri_any);
   dim3 grid(static_cast<unsigned>((nevt + kMeThreads - 1) / kMeThreads), static_cast<unsigned>(maxslot));
   if (grid.x == 0 || grid.y == 0) return cudaSuccess;
   if (prep && !PER_HEL) {
@@ -575,17 +576,17 @@ int64_t event_record_bytes(int K, bool fp32) {
 
 cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom, void* prep, int64_t nevt,
                                const Tables* tab, const int* gslots, int maxslot, const int* nslot,
-                               const uint32_t* mask, const double* ctri, const MeConst& cst, double* out,
-                               int64_t stride, cudaStream_t st, float2* jout) {
+                               const uint32_t* mask, const double* ctri64, const float* ctri32, const MeConst& cst,
+                               double* out, int64_t stride, cudaStream_t st, float2* jout) {
 #define MG_V2_CASE(KK)                                                                                              \
   case KK:                                                                                                          \
-    if (per_hel) return fp32 ? launch_v2<KK, float, true>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri, cst,  \
+    if (per_hel) return fp32 ? launch_v2<KK, float, true>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri32, cst,  \
                                                           out, stride, jout, st)                                          \
-                             : launch_v2<KK, double, true>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri, cst, \
+                             : launch_v2<KK, double, true>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri64, cst, \
                                                            out, stride, jout, st);                                        \
-    return fp32 ? launch_v2<KK, float, false>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri, cst, out, stride, \
+    return fp32 ? launch_v2<KK, float, false>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri32, cst, out, stride, \
                                               jout, st)                                                                   \
-                : launch_v2<KK, double, false>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri, cst, out, stride,\
+                : launch_v2<KK, double, false>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri64, cst, out, stride,\
                                                jout, st);
   switch (K) {
     MG_V2_CASE(2)

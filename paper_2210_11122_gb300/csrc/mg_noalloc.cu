@@ -72,7 +72,7 @@ extern "C" mg_status mg_sigmakin_noalloc(mg_ctx* ctx, const double* mom_dev, int
   // every element the sum kernel reads (good slots x events) is written first: nothing to clear
   if (ctx->prm.wt == 0.0) {
     if (mg::launch_me_gluonhel(ctx->K, false, false, mom_dev, nullptr, nevt, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
-                               ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, cst, scratch, stride, st) != cudaSuccess)
+                               ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, scratch, stride, st) != cudaSuccess)
       return MG_ECUDA;
     if (mg::launch_hel_sum(scratch, ctx->d_ngslots, nevt, stride, norm, me_dev, st) != cudaSuccess) return MG_ECUDA;
   } else {
