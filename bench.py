@@ -49,6 +49,10 @@ def parse():
     ap.add_argument("--nevt", type=int, default=0, help="events per GPU (default: the workload's)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve", action="store_true", help="serving workload: request trace, p50/p99 latency")
+    ap.add_argument("--requests", type=int, default=2000)
+    ap.add_argument("--serve-precision", default="fp64", choices=["fp64", "fp32_amp", "fp64_tccolor", "mixed"])
+    ap.add_argument("--slots", type=int, default=8)
     return ap.parse_args()
 
 
@@ -326,8 +330,84 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------------------------------------------------
+# serving workload
+# ------------------------------------------------------------------------------------------
+def serve_trace(mg, torch, n):
+    """Request r: Philox4x32-10 words of counter {r, 0, 0, 0}, key {0x5E12E, 0} (the engine's own
+    generator): process with probabilities 0.4/0.3/0.2/0.1, nevt log-uniform in [32, 65536] rounded
+    up to a multiple of 32, seed = r, exponential inter-arrival variate."""
+    import numpy as np
+    w = torch.zeros(n * 4, dtype=torch.int32, device="cuda")
+    mg.philox(0x5E12E, n, 1, w)
+    torch.cuda.synchronize()
+    u = (w.cpu().numpy().view(np.uint32).reshape(n, 4).astype(np.float64) + 0.5) * 2.0**-32
+    proc = np.searchsorted(np.cumsum([0.4, 0.3, 0.2, 0.1]), u[:, 0], side="right").clip(0, 3)
+    nevt = np.floor(np.exp(np.log(32) + u[:, 1] * (np.log(65536) - np.log(32)))).astype(np.int64)
+    nevt = ((nevt + 31) // 32) * 32
+    expo = -np.log(u[:, 2])
+    return proc, nevt, expo
+
+
+def run_trace(mg, srv, proc, nevt, expo, rate):
+    """rate None: closed loop (all submitted at t=0); else Poisson arrivals at `rate` requests/s."""
+    import numpy as np
+    t0 = time.perf_counter()
+    tickets = []
+    arrival = 0.0
+    for r in range(len(proc)):
+        if rate:
+            arrival += expo[r] / rate
+            dt = t0 + arrival - time.perf_counter()
+            if dt > 0:
+                time.sleep(dt)
+        tickets.append(srv.submit(int(proc[r]), r, int(nevt[r])))
+    lat = np.array([srv.wait(t)[1] for t in tickets])
+    span = time.perf_counter() - t0
+    return span, lat
+
+
+def run_serve(args):
+    import numpy as np
+    import torch
+    from paper_2210_11122_gb300 import build as mgbuild
+    mgbuild.build()
+    import paper_2210_11122_gb300 as mg
+    prec = {"fp64": mg.MG_FP64, "fp32_amp": mg.MG_FP32_AMP, "fp64_tccolor": mg.MG_FP64_TCCOLOR,
+            "mixed": mg.MG_MIXED}[args.serve_precision]
+    proc, nevt, expo = serve_trace(mg, torch, args.requests)
+    total = int(nevt.sum())
+    out = {}
+    for label, slots, precision in (("served", args.slots, prec), ("one_at_a_time_fp64", 1, mg.MG_FP64)):
+        with mg.Server(slots=slots, precision=precision) as srv:
+            w = [srv.submit(p, 10**9 + p, 2048) for p in range(4)]       # warm-up
+            for t in w:
+                srv.wait(t)
+            span, _ = run_trace(mg, srv, proc, nevt, expo, None)
+            cap = len(proc) / span
+            span2, lat = run_trace(mg, srv, proc, nevt, expo, 0.8 * cap)
+            out[label] = {"slots": slots, "capacity_req_per_s": cap, "closed_loop_MEs_per_s": total / span,
+                          "open_loop_rate_req_per_s": 0.8 * cap, "open_loop_MEs_per_s": total / span2,
+                          "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                          "peak": srv.stats()}
+    s, o = out["served"], out["one_at_a_time_fp64"]
+    line = {"metric": "served MEs/s (closed loop) and p50/p99 latency at 80% of capacity", "value":
+            s["closed_loop_MEs_per_s"], "unit": "MEs/s", "n_gpus": 1, "higher_is_better": True,
+            "dtype": args.serve_precision, "data": "synthetic",
+            "config": {"workload": "serving mix: %d requests, gg->tt/ttg/ttgg/ttggg with p=0.4/0.3/0.2/0.1, nevt "
+                                   "log-uniform in [32, 65536] (multiple of 32), seed = request id, Poisson "
+                                   "arrivals at 80%% of measured capacity, HBM admission cap 64 GiB" % args.requests,
+                       "requests": args.requests, "events": total},
+            "served": s, "one_at_a_time_fp64": o,
+            "speedup_closed_loop": s["closed_loop_MEs_per_s"] / o["closed_loop_MEs_per_s"]}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
+    if args.serve:
+        return run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -175,6 +175,53 @@ mg_status mg_flops_per_event(mg_process proc, const uint32_t* mask, double* amp_
  *     that device current); make that first call before any stream capture. */
 mg_status mg_sigmakin_noalloc(mg_ctx* ctx, const double* mom_dev, int64_t nevt, double* me_dev, void* stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Serving: continuous batching of matrix-element requests (no counterpart in the paper, which runs
+ * one batch at a time; the paper's Sec. 4 notes that 8k-event batches underfill a GPU).
+ * A request (process, seed, nevt) returns the MEs of events 0..nevt-1 of the seed's Philox stream
+ * (mg_rambo_range + mg_hel_filter on the request's own first events + mg_sigmakin).  A scheduler
+ * thread admits queued requests in FIFO order when a slot is free and the sum of the in-flight
+ * requests' device footprints (mg_serve_footprint) stays within hbm_cap_bytes; each slot is a CUDA
+ * stream with its own pre-reserved contexts and buffers, so admitted requests run concurrently on
+ * the GPU and serving itself allocates no device memory.  A request's result does not depend on
+ * what else is in flight.  The server is thread-safe; results are returned through host memory.
+ * --------------------------------------------------------------------------------------------- */
+typedef struct {
+  int slots;               /* requests in flight at once (CUDA streams), 1..64, default 8 */
+  int64_t max_nevt;        /* events per launch; larger requests run in consecutive chunks; default 65536 */
+  int64_t hbm_cap_bytes;   /* admission cap on the in-flight device footprint, default 64 GiB */
+  mg_precision precision;  /* arithmetic of every request, default MG_FP64 */
+  double sqrts;            /* collision energy [GeV], default 1500 */
+  mg_params params;        /* physics parameters, default mg_default_params */
+} mg_serve_cfg;
+
+typedef struct mg_server mg_server;
+
+void mg_serve_default_cfg(mg_serve_cfg* cfg);
+
+/* Device bytes a request of nevt events holds while in flight (momenta, MEs, scratch); host only. */
+int64_t mg_serve_footprint(mg_process proc, int64_t nevt, mg_precision precision);
+
+/* Create a server on the current device (allocates every slot up front).  cfg may be NULL. */
+mg_status mg_serve_create(const mg_serve_cfg* cfg, mg_server** out);
+
+/* Queue a request; *ticket identifies it.  Returns at once. */
+mg_status mg_serve_submit(mg_server* srv, mg_process proc, uint64_t seed, int64_t nevt, uint64_t* ticket);
+
+/* Non-blocking: *done = 0 while in flight; once done, *done = 1, the nevt MEs are copied to
+ * me_out_host (if not NULL), *latency_ms (if not NULL) receives completion - submission time, the
+ * request is released and its status returned (MG_ENOCONV if RAMBO failed for some event). */
+mg_status mg_serve_poll(mg_server* srv, uint64_t ticket, double* me_out_host, int* done, double* latency_ms);
+
+/* Blocking version with a timeout: MG_ETIMEOUT (request kept) if not done within timeout_ms. */
+mg_status mg_serve_wait(mg_server* srv, uint64_t ticket, double* me_out_host, int64_t timeout_ms, double* latency_ms);
+
+/* Counters since creation: completed requests, their events, peak in-flight footprint and count. */
+mg_status mg_serve_stats(mg_server* srv, int64_t* completed, int64_t* events, int64_t* peak_bytes, int* peak_inflight);
+
+/* Drain the queue, stop the scheduler and free everything (unpolled results are dropped). */
+void mg_serve_destroy(mg_server* srv);
+
 /* Diagnostic: FMA throughput of the current device, the ALU roofline denominator of the
  * matrix-element kernels.  Runs 8 independent FMA chains per thread (iters x 16 FMAs each) over
  * 8 blocks of 256 threads per SM and returns the measured rate in flop/s (an FMA counts 2) for

@@ -34,6 +34,11 @@ class Params(ctypes.Structure):
                 ("hel_warmup", ctypes.c_int), ("hel_tau", ctypes.c_double)]
 
 
+class ServeCfg(ctypes.Structure):
+    _fields_ = [("slots", ctypes.c_int), ("max_nevt", ctypes.c_int64), ("hbm_cap_bytes", ctypes.c_int64),
+                ("precision", ctypes.c_int), ("sqrts", ctypes.c_double), ("params", Params)]
+
+
 _lib = None
 
 
@@ -73,6 +78,19 @@ def lib():
     L.mg_hel_mask.argtypes = [vp, P(ctypes.c_uint32), P(i32)]
     L.mg_check.argtypes = [vp, vp, P(ctypes.c_int64)]
     L.mg_flops_per_event.argtypes = [i32, P(ctypes.c_uint32), P(dbl), P(dbl)]
+    L.mg_serve_default_cfg.argtypes = [P(ServeCfg)]
+    L.mg_serve_default_cfg.restype = None
+    L.mg_serve_footprint.argtypes = [i32, i64, i32]
+    L.mg_serve_footprint.restype = i64
+    L.mg_serve_create.argtypes = [P(ServeCfg), P(vp)]
+    L.mg_serve_submit.argtypes = [vp, i32, u64, i64, P(ctypes.c_uint64)]
+    L.mg_serve_poll.argtypes = [vp, ctypes.c_uint64, vp, P(i32), P(dbl)]
+    L.mg_serve_wait.argtypes = [vp, ctypes.c_uint64, vp, i64, P(dbl)]
+    L.mg_serve_stats.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64), P(i32)]
+    L.mg_serve_destroy.argtypes = [vp]
+    L.mg_serve_destroy.restype = None
+    for name in ("mg_serve_create", "mg_serve_submit", "mg_serve_poll", "mg_serve_wait", "mg_serve_stats"):
+        getattr(L, name).restype = i32
     for name in ("mg_process_info", "mg_colour_matrix", "mg_create", "mg_philox", "mg_rambo", "mg_rambo_range",
                  "mg_measure_fma_peak", "mg_hel_filter",
                  "mg_sigmakin", "mg_sigmakin_host", "mg_sigmakin_noalloc", "mg_hel_mask", "mg_check", "mg_flops_per_event"):
@@ -260,3 +278,75 @@ class Context:
         if s not in (0, 4):
             _check(s, "mg_check")
         return n.value
+
+
+# ------------------------------------------------------------------------------------------
+# serving
+# ------------------------------------------------------------------------------------------
+def serve_footprint(process, nevt, precision=MG_FP64):
+    return int(lib().mg_serve_footprint(_proc(process), nevt, precision))
+
+
+class Server:
+    """Continuous-batching request server (mg_serve_*)."""
+
+    def __init__(self, slots=8, max_nevt=65536, hbm_cap_bytes=64 << 30, precision=MG_FP64, sqrts=1500.0,
+                 mt=173.0, wt=0.0, alphas=0.118, hel_warmup=1024, hel_tau=1e-9):
+        c = ServeCfg()
+        lib().mg_serve_default_cfg(ctypes.byref(c))
+        c.slots, c.max_nevt, c.hbm_cap_bytes, c.precision, c.sqrts = slots, max_nevt, hbm_cap_bytes, precision, sqrts
+        c.params = Params(mt, wt, alphas, hel_warmup, hel_tau)
+        h = ctypes.c_void_p()
+        _check(lib().mg_serve_create(ctypes.byref(c), ctypes.byref(h)), "mg_serve_create")
+        self._h = h
+        self._nevt = {}
+
+    def submit(self, process, seed, nevt):
+        t = ctypes.c_uint64()
+        _check(lib().mg_serve_submit(self._h, _proc(process), seed, nevt, ctypes.byref(t)), "mg_serve_submit")
+        self._nevt[t.value] = nevt
+        return t.value
+
+    def poll(self, ticket):
+        """None while in flight, else (me ndarray, latency_ms)."""
+        out = np.empty(self._nevt[ticket])
+        done, lat = ctypes.c_int(), ctypes.c_double()
+        s = lib().mg_serve_poll(self._h, ticket, out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(done), ctypes.byref(lat))
+        if s == 0 and not done.value:
+            return None
+        del self._nevt[ticket]
+        _check(s, "mg_serve_poll")
+        return out, lat.value
+
+    def wait(self, ticket, timeout_ms=600000):
+        out = np.empty(self._nevt[ticket])
+        lat = ctypes.c_double()
+        s = lib().mg_serve_wait(self._h, ticket, out.ctypes.data_as(ctypes.c_void_p), timeout_ms, ctypes.byref(lat))
+        if s == 6:
+            raise MGError(s, "mg_serve_wait")
+        del self._nevt[ticket]
+        _check(s, "mg_serve_wait")
+        return out, lat.value
+
+    def stats(self):
+        a, b, c, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()
+        _check(lib().mg_serve_stats(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), ctypes.byref(d)),
+               "mg_serve_stats")
+        return {"completed": a.value, "events": b.value, "peak_bytes": c.value, "peak_inflight": d.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mg_serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

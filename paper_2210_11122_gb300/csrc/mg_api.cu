@@ -84,6 +84,53 @@ void flop_model(const mg::Tables& t, const uint32_t* mask, double* amp, double* 
 
 }  // namespace
 
+namespace mg {
+
+// Grow every scratch buffer of ctx so that mg_hel_filter and mg_sigmakin(precision) on up to nevt
+// events allocate nothing (used by the serving loop, which must not synchronise the device).
+mg_status ctx_reserve(mg_ctx* ctx, int64_t nevt, mg_precision precision) {
+  if (!ctx || nevt < 1) return MG_EINVAL;
+  const int64_t stride = pad32(nevt);
+  const int64_t wstride = pad32(nevt < ctx->prm.hel_warmup ? nevt : ctx->prm.hel_warmup);
+  mg_status s = grow(&ctx->d_part, &ctx->part_cap, (stride > wstride ? stride : wstride) * ctx->nhel);
+  if (s == MG_OK) s = grow(&ctx->d_tot, &ctx->tot_cap, wstride);
+  const bool fp32 = precision == MG_FP32_AMP || precision == MG_MIXED;
+  const bool tc = precision == MG_FP64_TCCOLOR || precision == MG_MIXED;
+  int64_t chunk = stride;
+  if (tc) {
+    const int64_t per_event = static_cast<int64_t>(ctx->nhel) * ctx->ncol;
+    chunk = (int64_t(1) << 29) / per_event / kPage * kPage;
+    if (chunk < kPage) chunk = kPage;
+    if (chunk > stride) chunk = stride;
+    if (s == MG_OK && ctx->jamp_cap < chunk * per_event) {
+      if (ctx->d_jamps) cudaFree(ctx->d_jamps);
+      ctx->d_jamps = nullptr;
+      ctx->jamp_cap = 0;
+      if (cudaMalloc(&ctx->d_jamps, static_cast<size_t>(chunk * per_event) * sizeof(float2)) != cudaSuccess) {
+        cudaGetLastError();
+        return MG_ENOMEM;
+      }
+      ctx->jamp_cap = chunk * per_event;
+    }
+  }
+  if (s == MG_OK) s = grow(&ctx->d_prep, &ctx->prep_cap, chunk * event_record_bytes(ctx->K, fp32) / 8 + 1);
+  return s;
+}
+
+// Device bytes one sigmakin call of nevt events touches (momenta, MEs, scratch): the serving
+// loop's admission footprint.
+int64_t footprint_bytes(mg_process proc, int64_t nevt, mg_precision precision) {
+  const int K = gluons_of(proc), npar = K + 2, nhel = 1 << npar, ncol = factorial(K);
+  const int64_t stride = pad32(nevt);
+  const bool fp32 = precision == MG_FP32_AMP || precision == MG_MIXED;
+  const bool tc = precision == MG_FP64_TCCOLOR || precision == MG_MIXED;
+  int64_t b = stride * npar * 4 * 8 + stride * 8 + stride * nhel * 8 + stride * event_record_bytes(K, fp32);
+  if (tc) b += stride * nhel * ncol * 8;
+  return b;
+}
+
+}  // namespace mg
+
 extern "C" {
 
 const char* mg_strerror(mg_status s) {

@@ -41,3 +41,8 @@ struct mg_ctx {
   cudaStream_t last = nullptr;
 };
 
+
+namespace mg {
+mg_status ctx_reserve(mg_ctx* ctx, int64_t nevt, mg_precision precision);
+int64_t footprint_bytes(mg_process proc, int64_t nevt, mg_precision precision);
+}  // namespace mg

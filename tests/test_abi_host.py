@@ -107,3 +107,18 @@ def test_invalid_arguments_rejected_without_gpu(mg):
     assert L.mg_philox(1, -1, 2, None, None) == 1
     assert L.mg_create(9, None, ctypes.byref(ctypes.c_void_p())) == 1
     assert L.mg_create(0, None, None) == 1
+
+
+def test_serve_footprint_host(mg):
+    """Admission footprint of a request: momenta + MEs + per-helicity partial sums + per-event records
+    (+ FP32 jamps for the tensor-core colour modes)."""
+    for proc in ("ggtt", "ggttg", "ggttgg", "ggttggg"):
+        info = mg.process_info(proc)
+        npar, nhel, ncol = info["npar"], info["nhel"], info["ncol"]
+        f64 = mg.serve_footprint(proc, 100, mg.MG_FP64)
+        n = 128
+        assert f64 > n * (npar * 4 * 8 + 8 + nhel * 8)
+        ftc = mg.serve_footprint(proc, 100, mg.MG_FP64_TCCOLOR)
+        assert ftc - f64 == n * nhel * ncol * 8
+        assert mg.serve_footprint(proc, 1000, mg.MG_FP64) > f64
+    assert mg.serve_footprint(9, 10, 0) == -1
