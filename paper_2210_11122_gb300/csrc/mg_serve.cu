@@ -11,7 +11,12 @@
 //     hbm_cap_bytes; otherwise the request waits in FIFO order;
 //   * the slots' streams run concurrently, so small requests overlap with each other and with large
 //     ones on the GPU; completion is detected with events and the results staged through pinned
-//     memory.
+//     memory;
+//   * half of the slots own high-priority streams and take the "small" requests (estimated work,
+//     events x flops per event of the process, below one full 65,536-event g g -> t tbar g batch),
+//     so their thread blocks are dispatched ahead of a large request's pending blocks; large
+//     requests use the low-priority slots; a small request may pass a large one that waits for a
+//     slot.
 // A request's result depends only on (process, seed, nevt): its helicity mask is computed from its
 // own first events and every kernel sums in a fixed order, so a request gives the same bits alone
 // and in any mix.  Requests larger than max_nevt run as consecutive chunks on one slot.
@@ -35,6 +40,7 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 struct Request {
+  bool small = true;
   uint64_t ticket;
   mg_process proc;
   uint64_t seed;
@@ -48,6 +54,7 @@ struct Request {
 };
 
 struct Slot {
+  bool high = false;
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
   mg_ctx* ctx[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -136,15 +143,19 @@ void worker_loop(mg_server* srv) {
       srv->events += r->nevt;
       srv->cv_done.notify_all();
     }
-    // admission, FIFO
-    while (!srv->queue.empty()) {
-      Request* r = srv->queue.front();
+    // admission: FIFO within each class; small requests take high-priority slots first and may
+    // pass a large request that is waiting for a low-priority slot
+    for (auto it = srv->queue.begin(); it != srv->queue.end();) {
+      Request* r = *it;
       Slot* free_slot = nullptr;
       for (Slot& s : srv->slots)
-        if (!s.req) { free_slot = &s; break; }
-      if (!free_slot) break;
+        if (!s.req && s.high == r->small) { free_slot = &s; break; }
+      if (!free_slot && r->small)
+        for (Slot& s : srv->slots)
+          if (!s.req) { free_slot = &s; break; }
+      if (!free_slot) { ++it; continue; }
       if (srv->inflight > 0 && srv->inflight_bytes + r->footprint > srv->cfg.hbm_cap_bytes) break;
-      srv->queue.pop_front();
+      it = srv->queue.erase(it);
       free_slot->req = r;
       srv->inflight++;
       srv->inflight_bytes += r->footprint;
@@ -222,8 +233,12 @@ mg_status mg_serve_create(const mg_serve_cfg* cfg_in, mg_server** out) {
   srv->slots.resize(cfg.slots);
   mg_status st = MG_OK;
   const int64_t nmax = srv->cfg.max_nevt;
-  for (Slot& s : srv->slots) {
-    if (cudaStreamCreateWithFlags(&s.stream, cudaStreamNonBlocking) != cudaSuccess ||
+  int prio_low = 0, prio_high = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) { cudaGetLastError(); prio_low = prio_high = 0; }
+  for (size_t i = 0; i < srv->slots.size(); ++i) {
+    Slot& s = srv->slots[i];
+    s.high = cfg.slots > 1 && i < srv->slots.size() / 2;
+    if (cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, s.high ? prio_high : prio_low) != cudaSuccess ||
         cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&s.mom, static_cast<size_t>(mg_mom_count(MG_GG_TTGGG, nmax)) * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&s.me, nmax * sizeof(double)) != cudaSuccess ||
@@ -264,6 +279,9 @@ mg_status mg_serve_submit(mg_server* srv, mg_process proc, uint64_t seed, int64_
   r->seed = seed;
   r->nevt = nevt;
   r->footprint = mg::footprint_bytes(proc, min64(nevt, srv->cfg.max_nevt), srv->cfg.precision);
+  // estimated work: events x FP64 flops per event of the process (mg_flops_per_event, all helicities)
+  static const double kFlopsPerEvent[4] = {8.6e3, 7.56e4, 9.58e5, 1.67e7};
+  r->small = srv->cfg.slots == 1 || static_cast<double>(nevt) * kFlopsPerEvent[proc] <= 65536.0 * kFlopsPerEvent[1];
   r->t_submit = Clock::now();
   {
     std::lock_guard<std::mutex> g(srv->mu);
