@@ -176,6 +176,55 @@ mg_status mg_flops_per_event(mg_process proc, const uint32_t* mask, double* amp_
 mg_status mg_sigmakin_noalloc(mg_ctx* ctx, const double* mom_dev, int64_t nevt, double* me_dev, void* stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Launch-shape autotuner and CUDA-graph batches (no counterpart in the paper; its Sec. 4 and
+ * Fig. 2 show the throughput depending on how many events one launch holds).
+ * --------------------------------------------------------------------------------------------- */
+
+/* Time mg_sigmakin(precision) of nevt probe events (this context's process, fixed seed) for each
+ * launch shape of the matrix-element kernel -- 32, 64 or 128 events per 128-thread block (the other
+ * threads of a block take further helicity combinations of the same events), grid dispatched
+ * event-tile-major or helicity-tile-major -- and keep the fastest for this context and precision.
+ * cache_path (may be NULL): text file of "gpu|process|precision tile_ev slot_major ms" lines; an
+ * existing entry is used without timing, a new result is appended.  *best_ms may be NULL.
+ * Synchronous; allocates probe buffers; nevt >= 32. */
+mg_status mg_autotune(mg_ctx* ctx, mg_precision precision, int64_t nevt, const char* cache_path, double* best_ms);
+
+/* The launch shape mg_sigmakin(precision) uses on this context (default 128 events per block,
+ * event-tile-major). */
+mg_status mg_get_launch_shape(mg_ctx* ctx, mg_precision precision, int* tile_ev, int* slot_major);
+
+/* One job of a graph batch: the step mg_rambo_range(seed, e0, nevt, sqrts, mom_dev) ->
+ * mg_hel_filter(mom_dev, nevt) -> mg_sigmakin(precision, me_dev) on ctx.  Every job of a batch needs
+ * its own context. */
+typedef struct {
+  mg_ctx* ctx;
+  uint64_t seed;
+  int64_t e0, nevt;
+  double sqrts;
+  double* mom_dev;
+  double* me_dev;
+  mg_precision precision;
+} mg_job;
+
+typedef struct mg_graph mg_graph;
+
+/* Capture the steps of njobs jobs (any mix of processes) into ONE CUDA graph, each job on its own
+ * parallel branch; all scratch is reserved first, so launching the graph allocates nothing. */
+mg_status mg_graph_create(const mg_job* jobs, int njobs, mg_graph** out);
+
+/* Replace the jobs' parameters (seeds, event ranges, sizes of an identical topology) in place
+ * (cudaGraphExecUpdate); MG_EINVAL if the new jobs do not fit the captured topology. */
+mg_status mg_graph_update(mg_graph* g, const mg_job* jobs, int njobs);
+
+/* One cudaGraphLaunch of the whole batch on stream; asynchronous. */
+mg_status mg_graph_launch(mg_graph* g, void* stream);
+
+/* Number of nodes (kernels, memsets, event waits) in the captured graph. */
+mg_status mg_graph_nodes(mg_graph* g, int* nodes);
+
+void mg_graph_destroy(mg_graph* g);
+
+/* ---------------------------------------------------------------------------------------------
  * Serving: continuous batching of matrix-element requests (no counterpart in the paper, which runs
  * one batch at a time; the paper's Sec. 4 notes that 8k-event batches underfill a GPU).
  * A request (process, seed, nevt) returns the MEs of events 0..nevt-1 of the seed's Philox stream

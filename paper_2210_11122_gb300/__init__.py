@@ -34,6 +34,12 @@ class Params(ctypes.Structure):
                 ("hel_warmup", ctypes.c_int), ("hel_tau", ctypes.c_double)]
 
 
+class Job(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("e0", ctypes.c_int64), ("nevt", ctypes.c_int64),
+                ("sqrts", ctypes.c_double), ("mom_dev", ctypes.c_void_p), ("me_dev", ctypes.c_void_p),
+                ("precision", ctypes.c_int)]
+
+
 class ServeCfg(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_int), ("max_nevt", ctypes.c_int64), ("hbm_cap_bytes", ctypes.c_int64),
                 ("precision", ctypes.c_int), ("sqrts", ctypes.c_double), ("params", Params)]
@@ -78,6 +84,17 @@ def lib():
     L.mg_hel_mask.argtypes = [vp, P(ctypes.c_uint32), P(i32)]
     L.mg_check.argtypes = [vp, vp, P(ctypes.c_int64)]
     L.mg_flops_per_event.argtypes = [i32, P(ctypes.c_uint32), P(dbl), P(dbl)]
+    L.mg_autotune.argtypes = [vp, i32, i64, ctypes.c_char_p, P(dbl)]
+    L.mg_get_launch_shape.argtypes = [vp, i32, P(i32), P(i32)]
+    L.mg_graph_create.argtypes = [P(Job), i32, P(vp)]
+    L.mg_graph_update.argtypes = [vp, P(Job), i32]
+    L.mg_graph_launch.argtypes = [vp, vp]
+    L.mg_graph_nodes.argtypes = [vp, P(i32)]
+    L.mg_graph_destroy.argtypes = [vp]
+    L.mg_graph_destroy.restype = None
+    for name in ("mg_autotune", "mg_get_launch_shape", "mg_graph_create", "mg_graph_update", "mg_graph_launch",
+                 "mg_graph_nodes"):
+        getattr(L, name).restype = i32
     L.mg_serve_default_cfg.argtypes = [P(ServeCfg)]
     L.mg_serve_default_cfg.restype = None
     L.mg_serve_footprint.argtypes = [i32, i64, i32]
@@ -264,6 +281,15 @@ class Context:
         """FP64 MEs without any device allocation (fixed 16 MiB library scratch; see mg.h)."""
         _check(lib().mg_sigmakin_noalloc(self._h, _ptr(mom), nevt, _ptr(me), _stream(stream)), "mg_sigmakin_noalloc")
 
+    def autotune(self, precision=MG_FP64, nevt=65536, cache_path=None):
+        """Pick the fastest launch shape of the ME kernel for this context; returns (tile_ev, slot_major, ms)."""
+        ms = ctypes.c_double()
+        _check(lib().mg_autotune(self._h, precision, nevt, cache_path.encode() if cache_path else None,
+                                 ctypes.byref(ms)), "mg_autotune")
+        t, s = ctypes.c_int(), ctypes.c_int()
+        _check(lib().mg_get_launch_shape(self._h, precision, ctypes.byref(t), ctypes.byref(s)), "mg_get_launch_shape")
+        return t.value, s.value, ms.value
+
     def hel_mask(self):
         nw = (self.nhel + 31) // 32
         m = (ctypes.c_uint32 * nw)()
@@ -350,3 +376,46 @@ class Server:
 
     def __exit__(self, *a):
         self.close()
+
+
+# ------------------------------------------------------------------------------------------
+# graph batches
+# ------------------------------------------------------------------------------------------
+class GraphBatch:
+    """One CUDA graph running the full step of several jobs on parallel branches (mg_graph_*).
+    jobs: list of (Context, seed, e0, nevt, sqrts, mom_tensor, me_tensor, precision)."""
+
+    def __init__(self, jobs):
+        arr = self._jobs(jobs)
+        h = ctypes.c_void_p()
+        _check(lib().mg_graph_create(arr, len(jobs), ctypes.byref(h)), "mg_graph_create")
+        self._h = h
+
+    @staticmethod
+    def _jobs(jobs):
+        arr = (Job * len(jobs))()
+        for i, (ctx, seed, e0, nevt, sqrts, mom, me, prec) in enumerate(jobs):
+            arr[i] = Job(ctx._h, seed, e0, nevt, sqrts, _ptr(mom), _ptr(me), prec)
+        return arr
+
+    def update(self, jobs):
+        _check(lib().mg_graph_update(self._h, self._jobs(jobs), len(jobs)), "mg_graph_update")
+
+    def launch(self, stream=None):
+        _check(lib().mg_graph_launch(self._h, _stream(stream)), "mg_graph_launch")
+
+    def nodes(self):
+        n = ctypes.c_int()
+        _check(lib().mg_graph_nodes(self._h, ctypes.byref(n)), "mg_graph_nodes")
+        return n.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().mg_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -207,6 +207,7 @@ void mg_destroy(mg_ctx* ctx) {
   cudaFree(ctx->d_ctri);
   cudaFree(ctx->d_ctri_f);
   cudaFree(ctx->d_mask);
+  cudaFree(ctx->d_maxr);
   cudaFree(ctx->d_good);
   cudaFree(ctx->d_ngood);
   cudaFree(ctx->d_allhel);
@@ -271,6 +272,7 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
     std::vector<int> all(c->nhel);
     for (int h = 0; h < c->nhel; ++h) all[h] = h;
     if (cudaMalloc(&c->d_mask, 4 * sizeof(uint32_t)) != cudaSuccess || cudaMalloc(&c->d_good, 128 * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->d_maxr, 128 * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->d_ngood, sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_allhel, c->nhel * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&c->d_nhel, sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_nbad, sizeof(unsigned long long)) != cudaSuccess) {
       st = MG_ENOMEM;
@@ -371,8 +373,8 @@ mg_status mg_hel_filter(mg_ctx* ctx, const double* mom_dev, int64_t nevt, void* 
                                    ctx->d_ctri, cst, ctx->d_part, stride, st));
   }
   MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_nhel, w, stride, 1.0, ctx->d_tot, st));
-  MG_CUDA(mg::launch_hel_mask(ctx->d_part, ctx->d_tot, ctx->nhel, w, stride, ctx->prm.hel_tau, ctx->d_mask,
-                              ctx->d_good, ctx->d_ngood, st));
+  MG_CUDA(mg::launch_hel_mask(ctx->d_part, ctx->d_tot, ctx->nhel, w, stride, ctx->prm.hel_tau, ctx->d_maxr,
+                              ctx->d_mask, ctx->d_good, ctx->d_ngood, st));
   MG_CUDA(mg::launch_gluon_slots(ctx->d_mask, ctx->K, ctx->d_gslots, ctx->d_ngslots, ctx->d_nrows, st));
   ctx->mask_ready = true;
   return MG_OK;
@@ -424,7 +426,7 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
       const double* mom_c = mom_dev + (e0 / mg::kPage) * ctx->npar * 4 * mg::kPage;
       MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_c, ctx->d_prep, n, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
                                      ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, cst_stride, st,
-                                     ctx->d_jamps));
+                                     ctx->d_jamps, ctx->shape[precision]));
       MG_CUDA(mg::launch_colour_tc(ctx->ncol, ctx->d_jamps, n, ctx->nhel, ctx->d_nrows, ctx->d_cmat, cst.colour_scale,
                                    ctx->d_part, cst_stride, st));
       MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_nrows, n, cst_stride, norm, me_dev + e0, st));
@@ -434,7 +436,8 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
     s = grow(&ctx->d_prep, &ctx->prep_cap, stride * mg::event_record_bytes(ctx->K, fp32) / 8 + 1);
     if (s != MG_OK) return s;
     MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_dev, ctx->d_prep, nevt, ctx->d_tab, ctx->d_gslots,
-                                   1 << ctx->K, ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, stride, st));
+                                   1 << ctx->K, ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, stride, st,
+                                   nullptr, ctx->shape[precision]));
     MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_ngslots, nevt, stride, norm, me_dev, st));
   } else {
     MG_CUDA(mg::launch_me_helicity(ctx->K, precision == MG_FP32_AMP, mom_dev, nevt, ctx->d_tab, ctx->d_good, ctx->nhel,

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include "mg_internal.h"
+#include "mg_kernels.h"
 
 struct mg_ctx {
   mg_process proc;
@@ -15,6 +16,7 @@ struct mg_ctx {
   float* d_ctri_f = nullptr;  // the same in FP32 (exact: integers < 2^24)
   int64_t colour_den = 1;
   uint32_t* d_mask = nullptr;
+  double* d_maxr = nullptr;   // per-helicity maximum ratio of the last helicity filter
   int* d_good = nullptr;      // good helicity list
   int* d_ngood = nullptr;
   int* d_allhel = nullptr;    // 0..nhel-1
@@ -38,6 +40,7 @@ struct mg_ctx {
   double* d_me_stage = nullptr;
   int64_t stage_cap = 0;
   bool mask_ready = false;
+  mg::MeShape shape[4];       // launch shape of the matrix-element kernel per precision (autotuned)
   cudaStream_t last = nullptr;
 };
 

@@ -15,6 +15,15 @@ struct MeConst {
   double colour_scale;  // g_s^2 / colour-matrix denominator
 };
 
+// Launch shape of the matrix-element kernel: a block of kMeThreads threads covers tile_ev events x
+// (kMeThreads / tile_ev) gluon-helicity slots (tile_ev in {32, 64, 128}); slot_major orders the grid so
+// that all slot tiles of an event tile are dispatched together (the event's per-event record is then
+// re-read from L2), else all event tiles of a slot tile come first.
+struct MeShape {
+  int tile_ev = 128;
+  bool slot_major = false;
+};
+
 cudaError_t launch_philox(uint64_t seed, int64_t nevt, int nfinal, uint32_t* words, cudaStream_t st);
 cudaError_t launch_rambo(int K, uint64_t seed, int64_t e0, int64_t nevt, double sqrts, double mt, double w0,
                          double* mom, double* wgt, unsigned long long* nbad, cudaStream_t st);
@@ -30,7 +39,8 @@ cudaError_t launch_me_helicity(int K, bool fp32, const double* mom, int64_t nevt
 cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom, void* prep, int64_t nevt,
                                const Tables* tab, const int* gslots, int maxslot, const int* nslot,
                                const uint32_t* mask, const double* ctri64, const float* ctri32, const MeConst& cst,
-                               double* out, int64_t stride, cudaStream_t st, float2* jout = nullptr);
+                               double* out, int64_t stride, cudaStream_t st, float2* jout = nullptr,
+                               MeShape shape = MeShape());
 int64_t event_record_bytes(int K, bool fp32);
 
 // Tensor-core colour sum (mg_colour_tc.cu): out[r * stride + e] = scale * (Re A^T C Re A + Im A^T C Im A)
@@ -43,6 +53,6 @@ cudaError_t launch_gluon_slots(const uint32_t* mask, int K, int* gslots, int* n,
 cudaError_t launch_hel_sum(const double* part, const int* nslot, int64_t nevt, int64_t stride, double norm,
                            double* me, cudaStream_t st);
 cudaError_t launch_hel_mask(const double* part, const double* tot, int nhel, int64_t nevt, int64_t stride, double tau,
-                            uint32_t* mask, int* good, int* ngood, cudaStream_t st);
+                            double* maxr, uint32_t* mask, int* good, int* ngood, cudaStream_t st);
 
 }  // namespace mg

@@ -387,30 +387,39 @@ __global__ void k_hel_sum(const double* __restrict__ part, const int* __restrict
   me[e] = s * norm;
 }
 
-// helicity filter: ratio_e(h) = part[h][e] / tot[e]; good(h) <=> max_e ratio > tau.
-// One block of 128 threads; thread h loops over the warm-up events.
-__global__ void k_hel_mask(const double* __restrict__ part, const double* __restrict__ tot, int nhel, int64_t nevt,
-                           int64_t stride, double tau, uint32_t* __restrict__ mask, int* __restrict__ good,
-                           int* __restrict__ ngood) {
-  __shared__ uint32_t words[4];
-  const int h = threadIdx.x;
-  if (h < 4) words[h] = 0;
-  __syncthreads();
-  if (h < nhel) {
-    double mx = 0.0;
-    for (int64_t e = 0; e < nevt; ++e) {
-      const double r = part[h * stride + e] / tot[e];
-      mx = r > mx ? r : mx;
-    }
-    if (mx > tau) atomicOr(&words[h >> 5], 1u << (h & 31));
+// helicity filter, step 1: maxr[h] = max over the warm-up events of part[h][e] / tot[e]
+// (one block per helicity, fixed-shape tree reduction: order-independent maximum).
+__global__ void k_hel_ratio_max(const double* __restrict__ part, const double* __restrict__ tot, int64_t nevt,
+                                int64_t stride, double* __restrict__ maxr) {
+  __shared__ double red[256];
+  const int h = blockIdx.x;
+  double mx = 0.0;
+  for (int64_t e = threadIdx.x; e < nevt; e += blockDim.x) {
+    const double r = part[h * stride + e] / tot[e];
+    mx = r > mx ? r : mx;
   }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] = red[threadIdx.x + w] > red[threadIdx.x] ? red[threadIdx.x + w] : red[threadIdx.x];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) maxr[h] = red[0];
+}
+
+// step 2: good(h) <=> maxr[h] > tau; mask words, ascending good list and its length.
+__global__ void k_hel_mask(const double* __restrict__ maxr, int nhel, double tau, uint32_t* __restrict__ mask,
+                           int* __restrict__ good, int* __restrict__ ngood) {
+  const int h = threadIdx.x;
+  const bool g = h < nhel && maxr[h] > tau;
+  const unsigned bits = __ballot_sync(0xffffffffu, g);
+  if ((h & 31) == 0 && h < ((nhel + 31) & ~31)) mask[h >> 5] = bits;
   __syncthreads();
   if (h == 0) {
     int n = 0;
     for (int k = 0; k < nhel; ++k)
-      if ((words[k >> 5] >> (k & 31)) & 1u) good[n++] = k;
+      if ((mask[k >> 5] >> (k & 31)) & 1u) good[n++] = k;
     *ngood = n;
-    for (int w = 0; w < (nhel + 31) / 32; ++w) mask[w] = words[w];
   }
 }
 
@@ -450,8 +459,9 @@ cudaError_t launch_hel_sum(const double* part, const int* nslot, int64_t nevt, i
 }
 
 cudaError_t launch_hel_mask(const double* part, const double* tot, int nhel, int64_t nevt, int64_t stride, double tau,
-                            uint32_t* mask, int* good, int* ngood, cudaStream_t st) {
-  k_hel_mask<<<1, 128, 0, st>>>(part, tot, nhel, nevt, stride, tau, mask, good, ngood);
+                            double* maxr, uint32_t* mask, int* good, int* ngood, cudaStream_t st) {
+  k_hel_ratio_max<<<nhel, 256, 0, st>>>(part, tot, nevt, stride, maxr);
+  k_hel_mask<<<1, 128, 0, st>>>(maxr, nhel, tau, mask, good, ngood);
   return cudaGetLastError();
 }
 

@@ -336,14 +336,16 @@ __global__ void __launch_bounds__(kMeThreads)
 k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab,
               const int* __restrict__ gslots, const int* __restrict__ nslot_dev, const uint32_t* __restrict__ mask,
               const T* __restrict__ ctri, MeConst cst, double* __restrict__ out, int64_t stride,
-              float2* __restrict__ jout) {
+              float2* __restrict__ jout, int tile_ev, int slot_major) {
   constexpr int npar = K + 2;
   constexpr int NSEQ = Sizes<K>::nseq;
   constexpr int NCOL = Sizes<K>::ncol;
   constexpr int NFULL = Sizes<K>::nfull;
   constexpr int NSUB = 1 << K;
-  const int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
-  const int slot = blockIdx.y;
+  const int tile_sl = kMeThreads / tile_ev;
+  const unsigned bev = slot_major ? blockIdx.y : blockIdx.x, bsl = slot_major ? blockIdx.x : blockIdx.y;
+  const int64_t e = static_cast<int64_t>(bev) * tile_ev + threadIdx.x % tile_ev;
+  const int slot = static_cast<int>(bsl) * tile_sl + static_cast<int>(threadIdx.x) / tile_ev;
   if (e >= nevt || slot >= *nslot_dev) return;
   const int gc = gslots[slot];   // bit g = helicity (+1) of gluon g
 
@@ -542,22 +544,30 @@ cudaError_t launch_gluon_slots(const uint32_t* mask, int K, int* gslots, int* n,
 template <int K, class T, bool PER_HEL>
 static cudaError_t launch_v2(const double* mom, void* prep, int64_t nevt, const Tables* tab, const int* gslots,
                              int maxslot, const int* nslot, const uint32_t* mask, const void* ctri_any,
-                             const MeConst& cst, double* out, int64_t stride, float2* jout, cudaStream_t st) {
+                             const MeConst& cst, double* out, int64_t stride, float2* jout, MeShape shape,
+                             cudaStream_t st) {
   const T* ctri = static_cast<const T*>(ctri_any);
-  dim3 grid(static_cast<unsigned>((nevt + kMeThreads - 1) / kMeThreads), static_cast<unsigned>(maxslot));
-  if (grid.x == 0 || grid.y == 0) return cudaSuccess;
+  int tev = shape.tile_ev;
+  if (tev != 32 && tev != 64 && tev != 128) tev = 128;
+  const int tsl = kMeThreads / tev;
+  const unsigned nev_t = static_cast<unsigned>((nevt + tev - 1) / tev), nsl_t = static_cast<unsigned>((maxslot + tsl - 1) / tsl);
+  const int sm = shape.slot_major ? 1 : 0;
+  dim3 grid = sm ? dim3(nsl_t, nev_t) : dim3(nev_t, nsl_t);
+  if (nev_t == 0 || nsl_t == 0) return cudaSuccess;
   if (prep && !PER_HEL) {
     T* rec = static_cast<T*>(prep);
     v2::k_event_prep<K, T><<<static_cast<unsigned>((nevt + 127) / 128), 128, 0, st>>>(mom, nevt, cst, rec);
     if (jout)
       v2::k_me_gluonhel<K, T, false, true, true><<<grid, kMeThreads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot, mask,
-                                                                             ctri, cst, out, stride, jout);
+                                                                             ctri, cst, out, stride, jout, tev, sm);
     else
       v2::k_me_gluonhel<K, T, false, true, false><<<grid, kMeThreads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot,
-                                                                              mask, ctri, cst, out, stride, nullptr);
+                                                                              mask, ctri, cst, out, stride, nullptr, tev,
+                                                                              sm);
   } else {
     v2::k_me_gluonhel<K, T, PER_HEL, false, false><<<grid, kMeThreads, 0, st>>>(mom, nullptr, nevt, tab, gslots, nslot,
-                                                                                 mask, ctri, cst, out, stride, nullptr);
+                                                                                 mask, ctri, cst, out, stride, nullptr,
+                                                                                 tev, sm);
   }
   return cudaGetLastError();
 }
@@ -577,17 +587,17 @@ int64_t event_record_bytes(int K, bool fp32) {
 cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom, void* prep, int64_t nevt,
                                const Tables* tab, const int* gslots, int maxslot, const int* nslot,
                                const uint32_t* mask, const double* ctri64, const float* ctri32, const MeConst& cst,
-                               double* out, int64_t stride, cudaStream_t st, float2* jout) {
+                               double* out, int64_t stride, cudaStream_t st, float2* jout, MeShape shape) {
 #define MG_V2_CASE(KK)                                                                                              \
   case KK:                                                                                                          \
     if (per_hel) return fp32 ? launch_v2<KK, float, true>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri32, cst,  \
-                                                          out, stride, jout, st)                                          \
+                                                          out, stride, jout, shape, st)                                          \
                              : launch_v2<KK, double, true>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri64, cst, \
-                                                           out, stride, jout, st);                                        \
+                                                           out, stride, jout, shape, st);                                        \
     return fp32 ? launch_v2<KK, float, false>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri32, cst, out, stride, \
-                                              jout, st)                                                                   \
+                                              jout, shape, st)                                                                   \
                 : launch_v2<KK, double, false>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri64, cst, out, stride,\
-                                               jout, st);
+                                               jout, shape, st);
   switch (K) {
     MG_V2_CASE(2)
     MG_V2_CASE(3)

@@ -1,0 +1,275 @@
+// mg_tune.cu -- autotuner for the matrix-element launch shape, and CUDA-graph batches.
+//
+// Autotuner: for one context and precision, time mg_sigmakin on probe events for every launch
+// shape of the matrix-element kernel (events per block 32 / 64 / 128, the remaining threads of the
+// 128-thread block taking further gluon-helicity slots of the same events; grid dispatched event-
+// tile-major or slot-tile-major) and keep the fastest.  Results can be cached in a text file, one
+// line per (GPU, process, precision).
+//
+// Graph batches: the whole random numbers -> momenta -> matrix elements step (mg_rambo_range ->
+// mg_hel_filter -> mg_sigmakin) of several jobs -- any mix of processes, one context each -- is
+// captured once into a single CUDA graph, the jobs on parallel branches, and then replayed with
+// one cudaGraphLaunch per batch.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mg_ctx.h"
+#include "mg_internal.h"
+#include "mg_kernels.h"
+
+namespace {
+
+std::string cache_key(mg_ctx* ctx, mg_precision precision) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  std::memset(&prop, 0, sizeof(prop));
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaGetDeviceProperties(&prop, dev);
+  std::string name(prop.name);
+  for (char& c : name)
+    if (c == ' ') c = '_';
+  return name + "|" + std::to_string(static_cast<int>(ctx->proc)) + "|" + std::to_string(static_cast<int>(precision));
+}
+
+bool cache_lookup(const char* path, const std::string& key, mg::MeShape* shape, double* ms) {
+  if (!path) return false;
+  FILE* f = std::fopen(path, "r");
+  if (!f) return false;
+  char k[256];
+  int tev = 0, sm = 0;
+  double t = 0;
+  bool found = false;
+  while (std::fscanf(f, "%255s %d %d %lf", k, &tev, &sm, &t) == 4)
+    if (key == k) { shape->tile_ev = tev; shape->slot_major = sm != 0; *ms = t; found = true; }
+  std::fclose(f);
+  return found;
+}
+
+void cache_store(const char* path, const std::string& key, const mg::MeShape& s, double ms) {
+  if (!path) return;
+  FILE* f = std::fopen(path, "a");
+  if (!f) return;
+  std::fprintf(f, "%s %d %d %.6f\n", key.c_str(), s.tile_ev, s.slot_major ? 1 : 0, ms);
+  std::fclose(f);
+}
+
+}  // namespace
+
+extern "C" mg_status mg_autotune(mg_ctx* ctx, mg_precision precision, int64_t nevt, const char* cache_path,
+                                 double* best_ms) {
+  if (!ctx || nevt < 32 || precision < MG_FP64 || precision > MG_MIXED) return MG_EINVAL;
+  const std::string key = cache_key(ctx, precision);
+  mg::MeShape cached;
+  double cms = 0;
+  if (cache_lookup(cache_path, key, &cached, &cms)) {
+    ctx->shape[precision] = cached;
+    if (best_ms) *best_ms = cms;
+    return MG_OK;
+  }
+  double* mom = nullptr;
+  double* me = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  mg_status rc = MG_OK;
+  const mg::MeShape saved = ctx->shape[precision];
+  if (cudaMalloc(&mom, mg_mom_count(ctx->proc, nevt) * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&me, nevt * sizeof(double)) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+      cudaEventCreate(&e1) != cudaSuccess) {
+    cudaGetLastError();
+    rc = MG_ENOMEM;
+  }
+  mg::MeShape best = saved;
+  float best_t = 1e30f;
+  if (rc == MG_OK) rc = mg_rambo(ctx, 0x7E57, nevt, 1500.0, mom, nullptr, st);
+  if (rc == MG_OK) rc = mg_hel_filter(ctx, mom, nevt, st);
+  const int tiles[3] = {32, 64, 128};
+  for (int ti = 0; ti < 3 && rc == MG_OK; ++ti)
+    for (int sm = 0; sm < 2 && rc == MG_OK; ++sm) {
+      mg::MeShape s;
+      s.tile_ev = tiles[ti];
+      s.slot_major = sm != 0;
+      ctx->shape[precision] = s;
+      rc = mg_sigmakin(ctx, mom, nevt, precision, me, st);   // warm-up (and scratch growth)
+      float t = 1e30f;
+      for (int rep = 0; rep < 3 && rc == MG_OK; ++rep) {
+        cudaEventRecord(e0, st);
+        rc = mg_sigmakin(ctx, mom, nevt, precision, me, st);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) { cudaGetLastError(); rc = MG_ECUDA; break; }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < t) t = ms;
+      }
+      if (rc == MG_OK && t < best_t) { best_t = t; best = s; }
+    }
+  ctx->shape[precision] = rc == MG_OK ? best : saved;
+  if (rc == MG_OK) {
+    cache_store(cache_path, key, best, best_t);
+    if (best_ms) *best_ms = best_t;
+  }
+  if (st) cudaStreamSynchronize(st);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  if (mom) cudaFree(mom);
+  if (me) cudaFree(me);
+  ctx->last = nullptr;
+  return rc;
+}
+
+extern "C" mg_status mg_get_launch_shape(mg_ctx* ctx, mg_precision precision, int* tile_ev, int* slot_major) {
+  if (!ctx || precision < MG_FP64 || precision > MG_MIXED) return MG_EINVAL;
+  if (tile_ev) *tile_ev = ctx->shape[precision].tile_ev;
+  if (slot_major) *slot_major = ctx->shape[precision].slot_major ? 1 : 0;
+  return MG_OK;
+}
+
+// ---------------------------------------------------------------------------------------------
+// graph batches
+// ---------------------------------------------------------------------------------------------
+struct mg_graph {
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int launches = 0;
+};
+
+extern "C" void mg_graph_destroy(mg_graph* g) {
+  if (!g) return;
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  delete g;
+}
+
+namespace {
+
+mg_status check_jobs(const mg_job* jobs, int njobs) {
+  if (!jobs || njobs < 1 || njobs > 256) return MG_EINVAL;
+  for (int i = 0; i < njobs; ++i) {
+    const mg_job& j = jobs[i];
+    if (!j.ctx || j.nevt < 1 || j.e0 < 0 || !j.mom_dev || !j.me_dev || j.precision < MG_FP64 || j.precision > MG_MIXED)
+      return MG_EINVAL;
+    for (int k = 0; k < i; ++k)
+      if (jobs[k].ctx == j.ctx) return MG_EINVAL;   // one context per job: scratch is per context
+    if ((j.precision == MG_FP64_TCCOLOR || j.precision == MG_MIXED) && j.ctx->prm.wt != 0.0) return MG_ENOTSUP;
+  }
+  // everything a captured call would allocate or configure happens now, outside the capture
+  for (int i = 0; i < njobs; ++i) {
+    mg_status s = mg::ctx_reserve(jobs[i].ctx, jobs[i].nevt, jobs[i].precision);
+    if (s != MG_OK) return s;
+    if (jobs[i].precision == MG_FP64_TCCOLOR || jobs[i].precision == MG_MIXED)
+      if (mg::launch_colour_tc(jobs[i].ctx->ncol, nullptr, 0, jobs[i].ctx->nhel, nullptr, nullptr, 0.0, nullptr, 0,
+                               nullptr) != cudaSuccess) {
+        cudaGetLastError();
+        return MG_ECUDA;
+      }
+  }
+  return MG_OK;
+}
+
+// Capture the jobs into a new graph: a fork from one origin stream, each job's step on its own
+// branch, a join back.
+mg_status capture(const mg_job* jobs, int njobs, cudaGraph_t* out) {
+  std::vector<cudaStream_t> streams(njobs, nullptr);
+  std::vector<cudaEvent_t> done(njobs, nullptr);
+  cudaStream_t origin = nullptr;
+  cudaEvent_t fork = nullptr;
+  mg_status rc = MG_OK;
+  if (cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess)
+    rc = MG_ECUDA;
+  for (int i = 0; i < njobs && rc == MG_OK; ++i)
+    if (cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&done[i], cudaEventDisableTiming) != cudaSuccess)
+      rc = MG_ECUDA;
+  bool capturing = false;
+  if (rc == MG_OK && cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal) == cudaSuccess) capturing = true;
+  else if (rc == MG_OK) rc = MG_ECUDA;
+  if (rc == MG_OK && cudaEventRecord(fork, origin) != cudaSuccess) rc = MG_ECUDA;
+  for (int i = 0; i < njobs && rc == MG_OK; ++i) {
+    const mg_job& j = jobs[i];
+    if (cudaStreamWaitEvent(streams[i], fork, 0) != cudaSuccess) { rc = MG_ECUDA; break; }
+    rc = mg_rambo_range(j.ctx, j.seed, j.e0, j.nevt, j.sqrts, j.mom_dev, nullptr, streams[i]);
+    if (rc == MG_OK) rc = mg_hel_filter(j.ctx, j.mom_dev, j.nevt, streams[i]);
+    if (rc == MG_OK) rc = mg_sigmakin(j.ctx, j.mom_dev, j.nevt, j.precision, j.me_dev, streams[i]);
+    if (rc == MG_OK && (cudaEventRecord(done[i], streams[i]) != cudaSuccess ||
+                        cudaStreamWaitEvent(origin, done[i], 0) != cudaSuccess))
+      rc = MG_ECUDA;
+  }
+  cudaGraph_t graph = nullptr;
+  if (capturing && cudaStreamEndCapture(origin, &graph) != cudaSuccess && rc == MG_OK) rc = MG_ECUDA;
+  cudaGetLastError();
+  for (int i = 0; i < njobs; ++i) {
+    jobs[i].ctx->last = nullptr;
+    if (done[i]) cudaEventDestroy(done[i]);
+    if (streams[i]) cudaStreamDestroy(streams[i]);
+  }
+  if (fork) cudaEventDestroy(fork);
+  if (origin) cudaStreamDestroy(origin);
+  if (rc != MG_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  *out = graph;
+  return MG_OK;
+}
+
+}  // namespace
+
+extern "C" mg_status mg_graph_create(const mg_job* jobs, int njobs, mg_graph** out) {
+  if (!out) return MG_EINVAL;
+  *out = nullptr;
+  mg_status rc = check_jobs(jobs, njobs);
+  if (rc != MG_OK) return rc;
+  mg_graph* g = new (std::nothrow) mg_graph;
+  if (!g) return MG_ENOMEM;
+  rc = capture(jobs, njobs, &g->graph);
+  if (rc == MG_OK && cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) { cudaGetLastError(); rc = MG_ECUDA; }
+  if (rc == MG_OK) {
+    size_t n = 0;
+    if (cudaGraphGetNodes(g->graph, nullptr, &n) == cudaSuccess) g->launches = static_cast<int>(n);
+  }
+  if (rc != MG_OK) {
+    mg_graph_destroy(g);
+    return rc;
+  }
+  *out = g;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_graph_update(mg_graph* g, const mg_job* jobs, int njobs) {
+  if (!g || !g->exec) return MG_EINVAL;
+  mg_status rc = check_jobs(jobs, njobs);
+  if (rc != MG_OK) return rc;
+  cudaGraph_t ng = nullptr;
+  rc = capture(jobs, njobs, &ng);
+  if (rc != MG_OK) return rc;
+  cudaGraphExecUpdateResultInfo info;
+  if (cudaGraphExecUpdate(g->exec, ng, &info) != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(ng);
+    return MG_EINVAL;   // topology changed (different jobs): create a new graph
+  }
+  cudaGraphDestroy(g->graph);
+  g->graph = ng;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_graph_launch(mg_graph* g, void* stream) {
+  if (!g || !g->exec) return MG_EINVAL;
+  if (cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    cudaGetLastError();
+    return MG_ECUDA;
+  }
+  return MG_OK;
+}
+
+extern "C" mg_status mg_graph_nodes(mg_graph* g, int* nodes) {
+  if (!g || !nodes) return MG_EINVAL;
+  *nodes = g->launches;
+  return MG_OK;
+}
