@@ -250,6 +250,11 @@ def run_ours(args):
 
     if ctx.check(stream) != 0:
         raise RuntimeError("RAMBO did not converge")
+    # launch shape of the matrix-element kernel per precision, picked by the autotuner (setup, untimed)
+    shapes = {}
+    for name, prec in (("fp64", mg.MG_FP64), ("fp32_amp", mg.MG_FP32_AMP), ("fp64_tccolor", mg.MG_FP64_TCCOLOR),
+                       ("mixed", mg.MG_MIXED)):
+        shapes[name] = ctx.autotune(prec, nevt=min(nevt, 65536))[:2]
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -273,6 +278,28 @@ def run_ours(args):
         variants[name] = {"value": world * nevt / (msv * 1e-3), "ms_per_step": msv, "me_kernel_ms": msv_me,
                           "rel_err_vs_fp64": {"max": float(rel.max()), "p99": float(rel.quantile(0.99)),
                                               "median": float(rel.median())}}
+
+    # the same FP64 step captured once as a CUDA graph and replayed (one launch per step)
+    gmom = torch.zeros_like(mom)
+    gme = torch.zeros_like(me)
+    gctx = mg.Context(ng, mt=MT, alphas=ALPHAS)
+    gctx.autotune(mg.MG_FP64, nevt=min(nevt, 65536))
+    graph = mg.GraphBatch([(gctx, seed, e0, nevt, SQRTS, gmom, gme, mg.MG_FP64)])
+    gev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            graph.launch(stream)
+            flush.zero_()
+        for k in range(args.steps):
+            gev[2 * k].record(stream)
+            graph.launch(stream)
+            gev[2 * k + 1].record(stream)
+            flush.zero_()
+    torch.cuda.synchronize()
+    graph_ms = statistics.mean(gev[2 * k].elapsed_time(gev[2 * k + 1]) for k in range(args.steps))
+    graph_same = bool(torch.equal(gme, me))
+    graph.close()
+    gctx.close()
 
     # end to end through the host-buffer entry point (pinned momenta in, MEs out, copies timed)
     host_mom = mom.cpu().pin_memory()
@@ -321,7 +348,10 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_of(args, nevt, {"parallelism": "dp%d (disjoint event ranges)" % world}),
             "me_kernel_ms": ms_me, "wall_s": wall, "nonconverged_events": nbad, "good_helicities": ngood,
-            "modes": variants, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "modes": variants, "launch_shapes": shapes,
+            "graph": {"ms_per_step": graph_ms, "value": world * nevt / (graph_ms * 1e-3), "same_result": graph_same,
+                      "what": "the FP64 step captured as one CUDA graph (mg_graph_create) and replayed"},
+            "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": launches_per_step * args.steps}
     print(json.dumps(line))
     ctx.close()
