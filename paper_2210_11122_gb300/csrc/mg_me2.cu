@@ -127,15 +127,22 @@ __device__ __forceinline__ void gluon_eps(const double* k, int lam, bool outgoin
 }
 
 // ---- current algebra ----
-// acc += s * V3(JL, JR) with momenta PL, PR (incoming):
-// V3 = (JL.JR)(PL - PR) + (JL.(PL + 2 PR)) JR - (JR.(2 PL + PR)) JL
+// acc += s * V3(JL, JR) with incoming momenta PL, PR.  The Feynman-gauge vertex contracted with the
+// two currents is (JL.JR)(PL - PR) + (JL.(PL + 2 PR)) JR - (JR.(2 PL + PR)) JL; Berends-Giele
+// currents of on-shell transverse gluons are conserved (P.J(P) = 0 exactly), so the JL.PL and JR.PR
+// parts vanish and the vertex is evaluated as (JL.JR)(PL - PR) + 2 (JL.PR) JR - 2 (JR.PL) JL: the
+// same value, without adding the rounding noise of two vanishing products (which 1/P^2 factors of
+// nearly collinear pairs amplify in FP32).
 template <class T>
 __device__ __forceinline__ void v3_acc(cx<T>* acc, const cx<T>* JL, const cx<T>* JR, const T* PL, const T* PR, bool neg) {
-  T d[4], u1[4], u2[4];
+  T d[4];
 #pragma unroll
-  for (int m = 0; m < 4; ++m) { d[m] = PL[m] - PR[m]; u1[m] = fma(T(2), PR[m], PL[m]); u2[m] = fma(T(2), PL[m], PR[m]); }
-  cx<T> jj = mdot(JL, JR), cl = mdotr(JL, u1), cr = mdotr(JR, u2);
-  if (neg) { jj = cneg(jj); cl = cneg(cl); cr = cneg(cr); }
+  for (int m = 0; m < 4; ++m) d[m] = PL[m] - PR[m];
+  cx<T> jj = mdot(JL, JR), cl = mdotr(JL, PR), cr = mdotr(JR, PL);
+  const T two = neg ? T(-2) : T(2);
+  if (neg) jj = cneg(jj);
+  cl = cscale(two, cl);
+  cr = cscale(two, cr);
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     cmacr(acc[m], d[m], jj);
