@@ -442,10 +442,16 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
   }
 
   // ---- antitop spinors and (gamma.J) v for both antitop helicities ----
-  cx<T> X[2][NSEQ][4];
+  // (gamma.J) v for every current and both antitop helicities: precomputed in FP64 (saves FP64
+  // instructions); in FP32 each jamp term forms ubar-side (row spinor x gamma.J) on the fly instead,
+  // keeping 2 NSEQ spinors out of the thread's local memory (FP32 arithmetic is cheap, memory is not).
+  constexpr bool kTableX = sizeof(T) == 8;
+  cx<T> X[kTableX ? 2 : 1][kTableX ? NSEQ : 1][4];
+  if (kTableX) {
 #pragma unroll
-  for (int b = 0; b < 2; ++b)
-    for (int s = 0; s < NSEQ; ++s) gamma_col(J[s], vv[b], X[b][s]);
+    for (int b = 0; b < 2; ++b)
+      for (int s = 0; s < NSEQ; ++s) gamma_col(J[s], vv[b], X[b][s]);
+  }
 
   // helicity index of (gc, top helicity a, antitop helicity b)
   int hbase = 0;
@@ -486,15 +492,29 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
       const int fi = tab->full_idx[c];
       const int fidx = fi >= 0 ? fi : -fi - 1;
       const bool fneg = fi < 0 && !(K & 1);   // reflection sign (-1)^(K+1)
+      if (kTableX) {
 #pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        cx<T> amp = mdot(Jq[b], JF[fidx]);   // all gluons on one current: ubar gamma.J v = Jq.J
-        if (fneg) amp = cneg(amp);
+        for (int b = 0; b < 2; ++b) {
+          cx<T> amp = mdot(Jq[b], JF[fidx]);   // all gluons on one current: ubar gamma.J v = Jq.J
+          if (fneg) amp = cneg(amp);
+          for (int j = 1; j < K; ++j) {
+            const int16_t r = tab->sub[c][j][K];
+            sdot_acc(amp, stk[j], X[b][rslot(r)], rneg(r));
+          }
+          A[b][c] = amp;
+        }
+      } else {
+        cx<T> amp0 = mdot(Jq[0], JF[fidx]), amp1 = mdot(Jq[1], JF[fidx]);
+        if (fneg) { amp0 = cneg(amp0); amp1 = cneg(amp1); }
         for (int j = 1; j < K; ++j) {
           const int16_t r = tab->sub[c][j][K];
-          sdot_acc(amp, stk[j], X[b][rslot(r)], rneg(r));
+          cx<T> t[4] = {};
+          row_gamma_acc(t, stk[j], J[rslot(r)], rneg(r));
+          sdot_acc(amp0, t, vv[0], false);
+          sdot_acc(amp1, t, vv[1], false);
         }
-        A[b][c] = amp;
+        A[0][c] = amp0;
+        A[1][c] = amp1;
       }
     }
     if (JOUT) {
