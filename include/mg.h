@@ -61,11 +61,15 @@ typedef enum { MG_GG_TT = 0, MG_GG_TTG = 1, MG_GG_TTGG = 2, MG_GG_TTGGG = 3 } mg
 /* Arithmetic of mg_sigmakin.
  *   MG_FP64         plain FP64 throughout (per-event relative error vs an FP64 reference <= 1e-12);
  *   MG_FP32_AMP     amplitudes and colour sum in FP32; FP64 kept for momenta, propagator
- *                   denominators, the top wavefunctions and the helicity sum;
+ *                   denominators, the top wavefunctions and the helicity sum.  Events whose
+ *                   smallest internal invariant (|P^2| of a gluon propagator or |Q^2 - m^2| of a
+ *                   quark propagator) is below 3e-4 s -- near-collinear or soft gluons, where FP32
+ *                   rounding grows like 1/sqrt(invariant) -- are recomputed in FP64 (0.1-2 % of
+ *                   the events), which keeps every event within 1e-5 of FP64;
  *   MG_FP64_TCCOLOR FP64 amplitudes; colour sum A^dagger C A on the tensor cores: the integer colour
  *                   matrix exact in FP16, every jamp row scaled by a power of two and split hi + lo
  *                   in FP16, FP32 accumulation (~1e-7 relative per helicity);
- *   MG_MIXED        FP32 amplitudes + the tensor-core colour sum.
+ *   MG_MIXED        FP32 amplitudes (with the same FP64 recomputation) + the tensor-core colour sum.
  * The tensor-core modes need zero top width (MG_ENOTSUP otherwise). */
 typedef enum { MG_FP64 = 0, MG_FP32_AMP = 1, MG_FP64_TCCOLOR = 2, MG_MIXED = 3 } mg_precision;
 

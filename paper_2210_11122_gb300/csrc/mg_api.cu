@@ -82,6 +82,22 @@ void flop_model(const mg::Tables& t, const uint32_t* mask, double* amp, double* 
   *col = c;
 }
 
+mg_status grow_repair(mg_ctx* ctx, int64_t n) {
+  if (!ctx->d_nrepair) {
+    if (cudaMalloc(&ctx->d_nrepair, sizeof(int)) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
+  }
+  if (n <= ctx->repair_cap) return MG_OK;
+  if (ctx->d_repair) cudaFree(ctx->d_repair);
+  ctx->d_repair = nullptr;
+  ctx->repair_cap = 0;
+  if (cudaMalloc(&ctx->d_repair, static_cast<size_t>(n) * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    return MG_ENOMEM;
+  }
+  ctx->repair_cap = n;
+  return MG_OK;
+}
+
 }  // namespace
 
 namespace mg {
@@ -114,6 +130,7 @@ mg_status ctx_reserve(mg_ctx* ctx, int64_t nevt, mg_precision precision) {
     }
   }
   if (s == MG_OK) s = grow(&ctx->d_prep, &ctx->prep_cap, chunk * event_record_bytes(ctx->K, fp32) / 8 + 1);
+  if (s == MG_OK) s = grow_repair(ctx, chunk);
   return s;
 }
 
@@ -223,6 +240,8 @@ void mg_destroy(mg_ctx* ctx) {
   cudaFree(ctx->d_part);
   cudaFree(ctx->d_tot);
   cudaFree(ctx->d_prep);
+  cudaFree(ctx->d_repair);
+  cudaFree(ctx->d_nrepair);
   cudaFree(ctx->d_mom_stage);
   cudaFree(ctx->d_me_stage);
   delete ctx;
@@ -419,25 +438,40 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
       ctx->jamp_cap = chunk * per_event;
     }
     s = grow(&ctx->d_prep, &ctx->prep_cap, chunk * mg::event_record_bytes(ctx->K, fp32) / 8 + 1);
+    if (s == MG_OK && fp32) s = grow_repair(ctx, chunk);
     if (s != MG_OK) return s;
     for (int64_t e0 = 0; e0 < nevt; e0 += chunk) {
       const int64_t n = nevt - e0 < chunk ? nevt - e0 : chunk;
       const int64_t cst_stride = pad32(n);
       const double* mom_c = mom_dev + (e0 / mg::kPage) * ctx->npar * 4 * mg::kPage;
+      if (fp32) MG_CUDA(cudaMemsetAsync(ctx->d_nrepair, 0, sizeof(int), st));
       MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_c, ctx->d_prep, n, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
                                      ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, cst_stride, st,
-                                     ctx->d_jamps, ctx->shape[precision]));
+                                     ctx->d_jamps, ctx->shape[precision], fp32 ? ctx->d_repair : nullptr,
+                                     fp32 ? ctx->d_nrepair : nullptr));
       MG_CUDA(mg::launch_colour_tc(ctx->ncol, ctx->d_jamps, n, ctx->nhel, ctx->d_nrows, ctx->d_cmat, cst.colour_scale,
                                    ctx->d_part, cst_stride, st));
+      if (fp32)   // events with a small internal invariant: FP64 amplitudes and colour sum, row layout
+        MG_CUDA(mg::launch_me_gluonhel(ctx->K, false, false, mom_c, nullptr, n, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
+                                       ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part,
+                                       cst_stride, st, nullptr, mg::MeShape(), nullptr, nullptr, ctx->d_repair,
+                                       ctx->d_nrepair, 1));
       MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_nrows, n, cst_stride, norm, me_dev + e0, st));
     }
   } else if (ctx->prm.wt == 0.0) {
     const bool fp32 = precision == MG_FP32_AMP;
     s = grow(&ctx->d_prep, &ctx->prep_cap, stride * mg::event_record_bytes(ctx->K, fp32) / 8 + 1);
+    if (s == MG_OK && fp32) s = grow_repair(ctx, stride);
     if (s != MG_OK) return s;
+    if (fp32) MG_CUDA(cudaMemsetAsync(ctx->d_nrepair, 0, sizeof(int), st));
     MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_dev, ctx->d_prep, nevt, ctx->d_tab, ctx->d_gslots,
                                    1 << ctx->K, ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, stride, st,
-                                   nullptr, ctx->shape[precision]));
+                                   nullptr, ctx->shape[precision], fp32 ? ctx->d_repair : nullptr,
+                                   fp32 ? ctx->d_nrepair : nullptr));
+    if (fp32)   // events with a small internal invariant: recomputed in FP64 (per-slot layout)
+      MG_CUDA(mg::launch_me_gluonhel(ctx->K, false, false, mom_dev, nullptr, nevt, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
+                                     ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, stride,
+                                     st, nullptr, mg::MeShape(), nullptr, nullptr, ctx->d_repair, ctx->d_nrepair, 0));
     MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_ngslots, nevt, stride, norm, me_dev, st));
   } else {
     MG_CUDA(mg::launch_me_helicity(ctx->K, precision == MG_FP32_AMP, mom_dev, nevt, ctx->d_tab, ctx->d_good, ctx->nhel,

@@ -34,6 +34,9 @@ struct mg_ctx {
   int64_t part_cap = 0;
   double* d_tot = nullptr;    // per-event helicity sums of the filter
   double* d_prep = nullptr;   // per-event records (momenta sums, propagators, wavefunctions)
+  int* d_repair = nullptr;    // FP32 modes: events recomputed in FP64, and their count
+  int* d_nrepair = nullptr;
+  int64_t repair_cap = 0;
   int64_t prep_cap = 0;       // in doubles
   int64_t tot_cap = 0;
   double* d_mom_stage = nullptr;

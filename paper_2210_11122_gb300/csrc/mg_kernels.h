@@ -13,6 +13,7 @@ struct MeConst {
   double gs;            // strong coupling g_s = sqrt(4 pi alpha_s)
   double mt, wt;        // top mass and width
   double colour_scale;  // g_s^2 / colour-matrix denominator
+  double fp32_tau = 3e-4;  // FP32 modes: events with an internal invariant below fp32_tau * s are redone in FP64
 };
 
 // Launch shape of the matrix-element kernel: a block of kMeThreads threads covers tile_ev events x
@@ -35,12 +36,16 @@ cudaError_t launch_me_helicity(int K, bool fp32, const double* mom, int64_t nevt
 // One thread per (event, gluon-helicity combination gslots[slot]); per_hel: out[h * stride + e] for every
 // helicity h of the combination, else out[slot * stride + e] = sum over its good helicities.  Zero top width.
 // prep: NULL (every thread computes its event's momenta sums, propagators and wavefunctions) or a
-// buffer of ceil(nevt/32)*32 * event_record_bytes(K, fp32) bytes that a per-event kernel fills first.
+// buffer of ceil(nevt/32)*32 * event_record_bytes(K, fp32) bytes that a per-event kernel fills first;
+// with prep, repair/nrepair (optional) collect the events with a small internal invariant (*nrepair
+// must be zero before the launch).  evlist/nlist (prep == NULL only): work on events evlist[0..*nlist)
+// of the batch; rows_out: write slot totals in the tensor-core row layout (4 rows per slot).
 cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom, void* prep, int64_t nevt,
                                const Tables* tab, const int* gslots, int maxslot, const int* nslot,
                                const uint32_t* mask, const double* ctri64, const float* ctri32, const MeConst& cst,
                                double* out, int64_t stride, cudaStream_t st, float2* jout = nullptr,
-                               MeShape shape = MeShape());
+                               MeShape shape = MeShape(), int* repair = nullptr, int* nrepair = nullptr,
+                               const int* evlist = nullptr, const int* nlist = nullptr, int rows_out = 0);
 int64_t event_record_bytes(int K, bool fp32);
 
 // Tensor-core colour sum (mg_colour_tc.cu): out[r * stride + e] = scale * (Re A^T C Re A + Im A^T C Im A)

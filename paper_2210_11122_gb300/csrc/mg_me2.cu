@@ -249,8 +249,10 @@ template <int K> struct EvLayout {
 
 template <int K, class T>
 __device__ __forceinline__ void event_data(const double (*p)[4], const MeConst& cst, T (*PT)[4], T* gprop, T (*qc)[5],
-                                           cx<T> (*eps)[2][4], cx<T> (*ub)[4], cx<T> (*vv)[4]) {
+                                           cx<T> (*eps)[2][4], cx<T> (*ub)[4], cx<T> (*vv)[4],
+                                           double* min_invariant = nullptr) {
   constexpr int NSUB = 1 << K;
+  double xmin = 1e300;
   double Pst[NSUB][4];
 #pragma unroll
   for (int m = 0; m < 4; ++m) Pst[0][m] = 0.0;
@@ -270,7 +272,12 @@ __device__ __forceinline__ void event_data(const double (*p)[4], const MeConst& 
     const double p2 = P[0] * P[0] - P[1] * P[1] - P[2] * P[2] - P[3] * P[3];
     gprop[S] = static_cast<T>((S & (S - 1)) ? -cst.gs / p2 : 0.0);   // includes one power of g
     const double Q0 = p[2][0] - P[0], Q1 = p[2][1] - P[1], Q2 = p[2][2] - P[2], Q3 = p[2][3] - P[3];
-    const double f = -cst.gs / (Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3 - cst.mt * cst.mt);
+    const double dq = Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3 - cst.mt * cst.mt;
+    const double f = -cst.gs / dq;
+    if (S != 0 && S != NSUB - 1) {   // internal lines only (S = 0 and S = all are the external tops)
+      xmin = fmin(xmin, fabs(dq));
+      if (S & (S - 1)) xmin = fmin(xmin, fabs(p2));
+    }
     qc[S][0] = static_cast<T>((Q0 + Q3) * f);
     qc[S][1] = static_cast<T>((Q0 - Q3) * f);
     qc[S][2] = static_cast<T>(Q1 * f);
@@ -287,12 +294,21 @@ __device__ __forceinline__ void event_data(const double (*p)[4], const MeConst& 
   top_ubar<T>(p[2], cst.mt, 1, ub[1]);
   top_v<T>(p[3], cst.mt, -1, vv[0]);
   top_v<T>(p[3], cst.mt, 1, vv[1]);
+  if (min_invariant) {
+    const double s0 = p[0][0] + p[1][0], s1 = p[0][1] + p[1][1], s2 = p[0][2] + p[1][2], s3 = p[0][3] + p[1][3];
+    const double shat = s0 * s0 - s1 * s1 - s2 * s2 - s3 * s3;   // (p1 + p2)^2
+    *min_invariant = xmin / fabs(shat);
+  }
 }
 
 // One thread per event: the event's record, AoSoA (page of 32 events, value-major within a page).
+// repair != NULL: events whose smallest internal invariant |P^2| or |Q^2 - m^2| (over the gluon and
+// quark propagators of the recursion) is below cst.fp32_tau * s are appended to repair[] (count in
+// *nrepair): FP32 rounding is amplified ~ 1/sqrt(invariant/s) there (collinear and soft gluons).
 template <int K, class T>
 __global__ void __launch_bounds__(128) k_event_prep(const double* __restrict__ mom, int64_t nevt, MeConst cst,
-                                                    T* __restrict__ rec) {
+                                                    T* __restrict__ rec, int* __restrict__ repair,
+                                                    int* __restrict__ nrepair) {
   constexpr int npar = K + 2, NSUB = 1 << K;
   using L = EvLayout<K>;
   const int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -305,7 +321,9 @@ __global__ void __launch_bounds__(128) k_event_prep(const double* __restrict__ m
     for (int m = 0; m < 4; ++m) p[i][m] = __ldg(base + (i * 4 + m) * kPage);
   T PT[NSUB][4], gprop[NSUB], qc[NSUB][5];
   cx<T> eps[K][2][4], ub[2][4], vv[2][4];
-  event_data<K, T>(p, cst, PT, gprop, qc, eps, ub, vv);
+  double xmin = 1.0;
+  event_data<K, T>(p, cst, PT, gprop, qc, eps, ub, vv, &xmin);
+  if (repair && xmin < cst.fp32_tau) repair[atomicAdd(nrepair, 1)] = static_cast<int>(e);
   T* out = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
 #pragma unroll
   for (int S = 0; S < NSUB; ++S) {
@@ -343,7 +361,8 @@ __global__ void __launch_bounds__(kMeThreads)
 k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab,
               const int* __restrict__ gslots, const int* __restrict__ nslot_dev, const uint32_t* __restrict__ mask,
               const T* __restrict__ ctri, MeConst cst, double* __restrict__ out, int64_t stride,
-              float2* __restrict__ jout, int tile_ev, int slot_major) {
+              float2* __restrict__ jout, int tile_ev, int slot_major, const int* __restrict__ evlist,
+              const int* __restrict__ nlist, int rows_out) {
   constexpr int npar = K + 2;
   constexpr int NSEQ = Sizes<K>::nseq;
   constexpr int NCOL = Sizes<K>::ncol;
@@ -351,9 +370,12 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
   constexpr int NSUB = 1 << K;
   const int tile_sl = kMeThreads / tile_ev;
   const unsigned bev = slot_major ? blockIdx.y : blockIdx.x, bsl = slot_major ? blockIdx.x : blockIdx.y;
-  const int64_t e = static_cast<int64_t>(bev) * tile_ev + threadIdx.x % tile_ev;
+  const int64_t et = static_cast<int64_t>(bev) * tile_ev + threadIdx.x % tile_ev;
   const int slot = static_cast<int>(bsl) * tile_sl + static_cast<int>(threadIdx.x) / tile_ev;
-  if (e >= nevt || slot >= *nslot_dev) return;
+  if (et >= nevt || slot >= *nslot_dev) return;
+  // evlist: the thread works on event evlist[et] of the batch (et < *nlist), else on event et
+  if (evlist && et >= *nlist) return;
+  const int64_t e = evlist ? static_cast<int64_t>(evlist[et]) : et;
   const int gc = gslots[slot];   // bit g = helicity (+1) of gluon g
 
   const T gs = static_cast<T>(cst.gs);
@@ -537,7 +559,16 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
       else total += v;
     }
   }
-  if (!PER_HEL && !JOUT) out[slot * stride + e] = total;
+  if (!PER_HEL && !JOUT) {
+    if (rows_out) {   // tensor-core row layout: slot*4 + (2 top + antitop); the slot total in the first row
+      out[(slot * 4) * stride + e] = total;
+      out[(slot * 4 + 1) * stride + e] = 0.0;
+      out[(slot * 4 + 2) * stride + e] = 0.0;
+      out[(slot * 4 + 3) * stride + e] = 0.0;
+    } else {
+      out[slot * stride + e] = total;
+    }
+  }
 }
 
 // Gluon-helicity combinations with at least one good helicity (fixed ascending order).
@@ -572,6 +603,7 @@ template <int K, class T, bool PER_HEL>
 static cudaError_t launch_v2(const double* mom, void* prep, int64_t nevt, const Tables* tab, const int* gslots,
                              int maxslot, const int* nslot, const uint32_t* mask, const void* ctri_any,
                              const MeConst& cst, double* out, int64_t stride, float2* jout, MeShape shape,
+                             int* repair, int* nrepair, const int* evlist, const int* nlist, int rows_out,
                              cudaStream_t st) {
   const T* ctri = static_cast<const T*>(ctri_any);
   int tev = shape.tile_ev;
@@ -583,18 +615,19 @@ static cudaError_t launch_v2(const double* mom, void* prep, int64_t nevt, const 
   if (nev_t == 0 || nsl_t == 0) return cudaSuccess;
   if (prep && !PER_HEL) {
     T* rec = static_cast<T*>(prep);
-    v2::k_event_prep<K, T><<<static_cast<unsigned>((nevt + 127) / 128), 128, 0, st>>>(mom, nevt, cst, rec);
+    v2::k_event_prep<K, T><<<static_cast<unsigned>((nevt + 127) / 128), 128, 0, st>>>(mom, nevt, cst, rec, repair,
+                                                                                     nrepair);
     if (jout)
       v2::k_me_gluonhel<K, T, false, true, true><<<grid, kMeThreads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot, mask,
-                                                                             ctri, cst, out, stride, jout, tev, sm);
+                                                                             ctri, cst, out, stride, jout, tev, sm, nullptr, nullptr, 0);
     else
       v2::k_me_gluonhel<K, T, false, true, false><<<grid, kMeThreads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot,
                                                                               mask, ctri, cst, out, stride, nullptr, tev,
-                                                                              sm);
+                                                                              sm, nullptr, nullptr, 0);
   } else {
     v2::k_me_gluonhel<K, T, PER_HEL, false, false><<<grid, kMeThreads, 0, st>>>(mom, nullptr, nevt, tab, gslots, nslot,
                                                                                  mask, ctri, cst, out, stride, nullptr,
-                                                                                 tev, sm);
+                                                                                 tev, sm, evlist, nlist, rows_out);
   }
   return cudaGetLastError();
 }
@@ -614,17 +647,18 @@ int64_t event_record_bytes(int K, bool fp32) {
 cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom, void* prep, int64_t nevt,
                                const Tables* tab, const int* gslots, int maxslot, const int* nslot,
                                const uint32_t* mask, const double* ctri64, const float* ctri32, const MeConst& cst,
-                               double* out, int64_t stride, cudaStream_t st, float2* jout, MeShape shape) {
+                               double* out, int64_t stride, cudaStream_t st, float2* jout, MeShape shape,
+                               int* repair, int* nrepair, const int* evlist, const int* nlist, int rows_out) {
 #define MG_V2_CASE(KK)                                                                                              \
   case KK:                                                                                                          \
     if (per_hel) return fp32 ? launch_v2<KK, float, true>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri32, cst,  \
-                                                          out, stride, jout, shape, st)                                          \
+                                                          out, stride, jout, shape, repair, nrepair, evlist, nlist, rows_out, st)                                          \
                              : launch_v2<KK, double, true>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri64, cst, \
-                                                           out, stride, jout, shape, st);                                        \
+                                                           out, stride, jout, shape, repair, nrepair, evlist, nlist, rows_out, st);                                        \
     return fp32 ? launch_v2<KK, float, false>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri32, cst, out, stride, \
-                                              jout, shape, st)                                                                   \
+                                              jout, shape, repair, nrepair, evlist, nlist, rows_out, st)                                                                   \
                 : launch_v2<KK, double, false>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri64, cst, out, stride,\
-                                               jout, shape, st);
+                                               jout, shape, repair, nrepair, evlist, nlist, rows_out, st);
   switch (K) {
     MG_V2_CASE(2)
     MG_V2_CASE(3)
