@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--nevt", type=int, default=0, help="events per GPU (default: the workload's)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape (fixed launch order)")
     ap.add_argument("--serve", action="store_true", help="serving workload: request trace, p50/p99 latency")
     ap.add_argument("--requests", type=int, default=2000)
     ap.add_argument("--serve-precision", default="fp64", choices=["fp64", "fp32_amp", "fp64_tccolor", "mixed"])
@@ -252,9 +253,10 @@ def run_ours(args):
         raise RuntimeError("RAMBO did not converge")
     # launch shape of the matrix-element kernel per precision, picked by the autotuner (setup, untimed)
     shapes = {}
-    for name, prec in (("fp64", mg.MG_FP64), ("fp32_amp", mg.MG_FP32_AMP), ("fp64_tccolor", mg.MG_FP64_TCCOLOR),
-                       ("mixed", mg.MG_MIXED)):
-        shapes[name] = ctx.autotune(prec, nevt=min(nevt, 65536))[:2]
+    if not args.no_autotune:
+        for name, prec in (("fp64", mg.MG_FP64), ("fp32_amp", mg.MG_FP32_AMP), ("fp64_tccolor", mg.MG_FP64_TCCOLOR),
+                           ("mixed", mg.MG_MIXED)):
+            shapes[name] = ctx.autotune(prec, nevt=min(nevt, 65536))[:2]
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -283,7 +285,8 @@ def run_ours(args):
     gmom = torch.zeros_like(mom)
     gme = torch.zeros_like(me)
     gctx = mg.Context(ng, mt=MT, alphas=ALPHAS)
-    gctx.autotune(mg.MG_FP64, nevt=min(nevt, 65536))
+    if not args.no_autotune:
+        gctx.autotune(mg.MG_FP64, nevt=min(nevt, 65536))
     graph = mg.GraphBatch([(gctx, seed, e0, nevt, SQRTS, gmom, gme, mg.MG_FP64)])
     gev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
     with torch.cuda.stream(stream):

@@ -49,7 +49,9 @@ mg_status grow(double** buf, int64_t* cap, int64_t need) {
 // the colour sum per good helicity.  mask == NULL means every helicity is good.
 void flop_model(const mg::Tables& t, const uint32_t* mask, double* amp, double* col) {
   const int K = t.K, nsub = 1 << K, npar = K + 2;
-  const double v3 = 158.0, v4 = 192.0, row_gamma = 72.0, row_prop = 56.0, gamma_col = 64.0, sdot = 32.0,
+  // three-gluon vertex in the current-conserving form: d (4) + JL.JR (30) + JL.PR, JR.PL (2 x 14) +
+  // two scalings (4) + 4 x (real-complex and two complex multiply-adds) (80)
+  const double v3 = 146.0, v4 = 192.0, row_gamma = 72.0, row_prop = 56.0, gamma_col = 64.0, sdot = 32.0,
                mdot = 30.0;
   double per_thread = 25.0 * nsub + 30.0 * K + 100.0;              // subsets, gluon and antitop wavefunctions
   for (int s = K; s < t.nseq; ++s) per_thread += v3 * t.seq_nv3[s] + v4 * t.seq_nv4[s] + 8.0;
