@@ -256,7 +256,8 @@ def run_ours(args):
     if not args.no_autotune:
         for name, prec in (("fp64", mg.MG_FP64), ("fp32_amp", mg.MG_FP32_AMP), ("fp64_tccolor", mg.MG_FP64_TCCOLOR),
                            ("mixed", mg.MG_MIXED)):
-            shapes[name] = ctx.autotune(prec, nevt=min(nevt, 65536))[:2]
+            ctx.autotune(prec, nevt=min(nevt, 65536))
+            shapes[name] = dict(zip(("tile_ev", "slot_major", "unrolled"), ctx.launch_shape(prec)))
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -329,12 +330,27 @@ def run_ours(args):
     amp_f, col_f = mg.flops_per_event(ng, mask)
     flops = (amp_f + col_f) * nevt
     peak = mg.measure_fma_peak(fp32=False, iters=2048)
+    # the other modes against the peak of the pipe their amplitudes run on (FP32 FMA for the FP32-
+    # amplitude modes, whose colour sums run on the FP32 pipe or the tensor cores; FP64 otherwise)
+    peak32 = mg.measure_fma_peak(fp32=True, iters=2048)
+    # (the tensor-core colour modes count their amplitude flops only: the colour sums run on the tensor
+    # cores, not on that pipe)
+    for name, prec in (("fp32_amp", mg.MG_FP32_AMP), ("fp64_tccolor", mg.MG_FP64_TCCOLOR), ("mixed", mg.MG_MIXED)):
+        a, c = mg.flops_per_event(ng, mask, prec)
+        if prec in (mg.MG_FP64_TCCOLOR, mg.MG_MIXED):
+            c = 0.0
+        pk = peak32 if prec in (mg.MG_FP32_AMP, mg.MG_MIXED) else peak
+        ach = (a + c) * nevt / (variants[name]["me_kernel_ms"] * 1e-3)
+        variants[name]["roofline"] = {"bound": "alu", "achieved": ach / 1e12, "peak": pk / 1e12, "unit": "TFLOP/s",
+                                      "frac": ach / pk, "flops_per_event": a + c,
+                                      "peak_source": "measured %s FMA-chain microbenchmark (mg_measure_fma_peak)"
+                                                     % ("FP32" if pk is peak32 else "FP64")}
     achieved = flops / (ms_me * 1e-3)
     traffic = profiled_traffic(os.path.join(ROOT, "paper_2210_11122_gb300", "csrc", "mg_me2.cu"),
                                os.path.join(ROOT, "profiles", "k_me_gluonhel_fp64_%s_65536.md" % args.process), nevt)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_me_gluonhel<%d,double> + k_hel_sum (mg_sigmakin)" % (ng + 2),
+                "kernel": "k_event_prep + k_me_gluonhel<%d,double> + k_hel_sum (one mg_sigmakin call)" % (ng + 2),
                 "flops_per_event": amp_f + col_f,
                 "peak_source": "measured FP64 DFMA-chain microbenchmark (mg_measure_fma_peak) on this GPU"}
 

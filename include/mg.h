@@ -155,11 +155,15 @@ mg_status mg_hel_mask(mg_ctx* ctx, uint32_t* mask_host, int* ngood);
  * NULL), MG_ECUDA on an asynchronous CUDA error, else MG_OK.  Clears the condition. */
 mg_status mg_check(mg_ctx* ctx, void* stream, int64_t* nbad);
 
-/* Floating-point operations of one event's FP64 matrix element in this engine's algorithm (the
- * roofline numerator): *amp_flops for wavefunctions, currents and jamps, *colour_flops for the colour
- * sums (4 ncol(ncol+1)/2 + 4 ncol per good helicity), counting an FMA as 2.  mask (ceil(nhel/32)
- * words, as returned by mg_hel_mask) selects the good helicities; NULL = all.  Host only. */
-mg_status mg_flops_per_event(mg_process proc, const uint32_t* mask, double* amp_flops, double* colour_flops);
+/* Floating-point operations of one event's matrix element in this engine's algorithm for the given
+ * precision (the roofline numerator): *amp_flops for the per-event wavefunctions and propagators
+ * (once per event) and the currents and jamps of every gluon-helicity combination with a good
+ * helicity, *colour_flops for the colour sums (4 ncol(ncol+1)/2 + 4 ncol per good helicity), counting
+ * an FMA as 2.  The FP64-amplitude modes tabulate (gamma.J) v per current, the FP32-amplitude modes
+ * form it per jamp term.  mask (ceil(nhel/32) words, as returned by mg_hel_mask) selects the good
+ * helicities; NULL = all.  Host only. */
+mg_status mg_flops_per_event(mg_process proc, mg_precision precision, const uint32_t* mask, double* amp_flops,
+                             double* colour_flops);
 
 /* FP64 matrix elements exactly as mg_sigmakin(..., MG_FP64, ...), for callers that must not have
  * the library allocate device memory during the call (an application that hands the engine a
@@ -187,15 +191,25 @@ mg_status mg_sigmakin_noalloc(mg_ctx* ctx, const double* mom_dev, int64_t nevt, 
 /* Time mg_sigmakin(precision) of nevt probe events (this context's process, fixed seed) for each
  * launch shape of the matrix-element kernel -- 32, 64 or 128 events per 128-thread block (the other
  * threads of a block take further helicity combinations of the same events), grid dispatched
- * event-tile-major or helicity-tile-major -- and keep the fastest for this context and precision.
- * cache_path (may be NULL): text file of "gpu|process|precision tile_ev slot_major ms" lines; an
- * existing entry is used without timing, a new result is appended.  *best_ms may be NULL.
- * Synchronous; allocates probe buffers; nevt >= 32. */
+ * event-tile-major or helicity-tile-major, and, where both exist, the kernel with the recursion
+ * unrolled at compile time or the one reading the recursion tables at run time -- and keep the fastest
+ * for this context and precision.  cache_path (may be NULL): text file of
+ * "gpu|process|precision tile_ev slot_major unrolled ms" lines; an existing entry is used without
+ * timing, a new result is appended.  *best_ms may be NULL.  Synchronous; allocates probe buffers;
+ * nevt >= 32. */
 mg_status mg_autotune(mg_ctx* ctx, mg_precision precision, int64_t nevt, const char* cache_path, double* best_ms);
 
-/* The launch shape mg_sigmakin(precision) uses on this context (default 128 events per block,
- * event-tile-major). */
-mg_status mg_get_launch_shape(mg_ctx* ctx, mg_precision precision, int* tile_ev, int* slot_major);
+/* The launch shape mg_sigmakin(precision) uses on this context (default: 128 events per block,
+ * event-tile-major, unrolled kernel where it exists).  unrolled = 1: the matrix-element kernel with
+ * the recursion expanded at compile time (built for FP32 amplitudes of gg -> t tbar, t tbar g and
+ * t tbar g g); 0: the kernel that reads the
+ * recursion tables at run time.  Any out-pointer may be NULL. */
+mg_status mg_get_launch_shape(mg_ctx* ctx, mg_precision precision, int* tile_ev, int* slot_major, int* unrolled);
+
+/* Set the launch shape of mg_sigmakin(precision) by hand: tile_ev in {32, 64, 128}, slot_major and
+ * unrolled 0 or 1 (unrolled = 1 falls back to the run-time-table kernel where no unrolled one is
+ * built).  MG_EINVAL otherwise. */
+mg_status mg_set_launch_shape(mg_ctx* ctx, mg_precision precision, int tile_ev, int slot_major, int unrolled);
 
 /* One job of a graph batch: the step mg_rambo_range(seed, e0, nevt, sqrts, mom_dev) ->
  * mg_hel_filter(mom_dev, nevt) -> mg_sigmakin(precision, me_dev) on ctx.  Every job of a batch needs

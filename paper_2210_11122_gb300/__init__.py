@@ -83,16 +83,17 @@ def lib():
     L.mg_sigmakin_noalloc.argtypes = [vp, vp, i64, vp, vp]
     L.mg_hel_mask.argtypes = [vp, P(ctypes.c_uint32), P(i32)]
     L.mg_check.argtypes = [vp, vp, P(ctypes.c_int64)]
-    L.mg_flops_per_event.argtypes = [i32, P(ctypes.c_uint32), P(dbl), P(dbl)]
+    L.mg_flops_per_event.argtypes = [i32, i32, P(ctypes.c_uint32), P(dbl), P(dbl)]
     L.mg_autotune.argtypes = [vp, i32, i64, ctypes.c_char_p, P(dbl)]
-    L.mg_get_launch_shape.argtypes = [vp, i32, P(i32), P(i32)]
+    L.mg_get_launch_shape.argtypes = [vp, i32, P(i32), P(i32), P(i32)]
+    L.mg_set_launch_shape.argtypes = [vp, i32, i32, i32, i32]
     L.mg_graph_create.argtypes = [P(Job), i32, P(vp)]
     L.mg_graph_update.argtypes = [vp, P(Job), i32]
     L.mg_graph_launch.argtypes = [vp, vp]
     L.mg_graph_nodes.argtypes = [vp, P(i32)]
     L.mg_graph_destroy.argtypes = [vp]
     L.mg_graph_destroy.restype = None
-    for name in ("mg_autotune", "mg_get_launch_shape", "mg_graph_create", "mg_graph_update", "mg_graph_launch",
+    for name in ("mg_autotune", "mg_get_launch_shape", "mg_set_launch_shape", "mg_graph_create", "mg_graph_update", "mg_graph_launch",
                  "mg_graph_nodes"):
         getattr(L, name).restype = i32
     L.mg_serve_default_cfg.argtypes = [P(ServeCfg)]
@@ -183,13 +184,15 @@ def colour_matrix(process):
     return num, den.value
 
 
-def flops_per_event(process, mask=None):
-    """(amplitude flops, colour-sum flops) of one event's FP64 ME for the given helicity mask."""
+def flops_per_event(process, mask=None, precision=MG_FP64):
+    """(amplitude flops, colour-sum flops) of one event's ME in the given precision mode for the given
+    helicity mask."""
     a, c = ctypes.c_double(), ctypes.c_double()
     m = None
     if mask is not None:
         m = (ctypes.c_uint32 * len(mask))(*[int(x) for x in mask])
-    _check(lib().mg_flops_per_event(_proc(process), m, ctypes.byref(a), ctypes.byref(c)), "mg_flops_per_event")
+    _check(lib().mg_flops_per_event(_proc(process), precision, m, ctypes.byref(a), ctypes.byref(c)),
+           "mg_flops_per_event")
     return a.value, c.value
 
 
@@ -286,9 +289,18 @@ class Context:
         ms = ctypes.c_double()
         _check(lib().mg_autotune(self._h, precision, nevt, cache_path.encode() if cache_path else None,
                                  ctypes.byref(ms)), "mg_autotune")
-        t, s = ctypes.c_int(), ctypes.c_int()
-        _check(lib().mg_get_launch_shape(self._h, precision, ctypes.byref(t), ctypes.byref(s)), "mg_get_launch_shape")
-        return t.value, s.value, ms.value
+        t, s, _ = self.launch_shape(precision)
+        return t, s, ms.value
+
+    def launch_shape(self, precision=MG_FP64):
+        """(tile_ev, slot_major, unrolled) of the ME kernel launch for this precision."""
+        t, s, u = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().mg_get_launch_shape(self._h, precision, ctypes.byref(t), ctypes.byref(s), ctypes.byref(u)),
+               "mg_get_launch_shape")
+        return t.value, s.value, u.value
+
+    def set_launch_shape(self, precision, tile_ev=128, slot_major=0, unrolled=1):
+        _check(lib().mg_set_launch_shape(self._h, precision, tile_ev, slot_major, unrolled), "mg_set_launch_shape")
 
     def hel_mask(self):
         nw = (self.nhel + 31) // 32

@@ -47,23 +47,26 @@ mg_status grow(double** buf, int64_t* cap, int64_t need) {
 // helicity combination with a good helicity; per thread the gluon currents once, (gamma.J) v per
 // antitop helicity, a depth-first walk of the quark-line prefixes per top helicity, the jamps and
 // the colour sum per good helicity.  mask == NULL means every helicity is good.
-void flop_model(const mg::Tables& t, const uint32_t* mask, double* amp, double* col) {
+void flop_model(const mg::Tables& t, const uint32_t* mask, bool fp32, double* amp, double* col) {
   const int K = t.K, nsub = 1 << K, npar = K + 2;
   // three-gluon vertex in the current-conserving form: d (4) + JL.JR (30) + JL.PR, JR.PL (2 x 14) +
   // two scalings (4) + 4 x (real-complex and two complex multiply-adds) (80)
   const double v3 = 146.0, v4 = 192.0, row_gamma = 72.0, row_prop = 56.0, gamma_col = 64.0, sdot = 32.0,
                mdot = 30.0;
-  double per_thread = 25.0 * nsub + 30.0 * K + 100.0;              // subsets, gluon and antitop wavefunctions
-  for (int s = K; s < t.nseq; ++s) per_thread += v3 * t.seq_nv3[s] + v4 * t.seq_nv4[s] + 8.0;
-  for (int f = 0; f < t.nfull; ++f) per_thread += v3 * t.full_nv3[f] + v4 * t.full_nv4[f] + 8.0;
-  per_thread += 2.0 * gamma_col * t.nseq;
+  const double per_event = 25.0 * nsub + 30.0 * K + 100.0;        // subsets, propagators, wavefunctions (once)
+  double per_slot = 0.0;                                           // gluon currents of one helicity combination
+  for (int s = K; s < t.nseq; ++s) per_slot += v3 * t.seq_nv3[s] + v4 * t.seq_nv4[s] + 8.0;
+  for (int f = 0; f < t.nfull; ++f) per_slot += v3 * t.full_nv3[f] + v4 * t.full_nv4[f] + 8.0;
+  // FP64: (gamma.J) v tabulated for every current and both antitop helicities; FP32: formed per jamp term
+  if (!fp32) per_slot += 2.0 * gamma_col * t.nseq;
   double walk = 50.0 + 2.0 * 72.0;                                 // ubar, two quark currents
   for (int c = 0; c < t.ncol; ++c) {
     for (int m = t.lcp[c] + 1; m < K; ++m) walk += row_gamma * m + row_prop;
-    walk += 2.0 * (mdot + sdot * (K - 1));                         // jamps of both antitop helicities
+    walk += fp32 ? 2.0 * mdot + (K - 1) * (row_gamma + 2.0 * sdot)  // jamps of both antitop helicities
+                 : 2.0 * (mdot + sdot * (K - 1));
   }
   const double colour = 4.0 * t.ncol * (t.ncol + 1) / 2.0 + 4.0 * t.ncol;
-  double a = 0, c = 0;
+  double a = per_event, c = 0;
   for (int gc = 0; gc < nsub; ++gc) {
     int hb = 0;
     for (int g = 0; g < K; ++g)
@@ -75,7 +78,7 @@ void flop_model(const mg::Tables& t, const uint32_t* mask, double* amp, double* 
       any |= good[k];
     }
     if (!any) continue;
-    a += per_thread;
+    a += per_slot;
     for (int top = 0; top < 2; ++top)
       if (good[2 * top] || good[2 * top + 1]) a += walk;
     for (int k = 0; k < 4; ++k) c += good[k] ? colour : 0.0;
@@ -90,9 +93,12 @@ mg_status grow_repair(mg_ctx* ctx, int64_t n) {
   }
   if (n <= ctx->repair_cap) return MG_OK;
   if (ctx->d_repair) cudaFree(ctx->d_repair);
+  if (ctx->d_flag) cudaFree(ctx->d_flag);
   ctx->d_repair = nullptr;
+  ctx->d_flag = nullptr;
   ctx->repair_cap = 0;
-  if (cudaMalloc(&ctx->d_repair, static_cast<size_t>(n) * sizeof(int)) != cudaSuccess) {
+  if (cudaMalloc(&ctx->d_repair, static_cast<size_t>(n) * sizeof(int)) != cudaSuccess ||
+      cudaMalloc(&ctx->d_flag, static_cast<size_t>(n)) != cudaSuccess) {
     cudaGetLastError();
     return MG_ENOMEM;
   }
@@ -144,6 +150,7 @@ int64_t footprint_bytes(mg_process proc, int64_t nevt, mg_precision precision) {
   const bool fp32 = precision == MG_FP32_AMP || precision == MG_MIXED;
   const bool tc = precision == MG_FP64_TCCOLOR || precision == MG_MIXED;
   int64_t b = stride * npar * 4 * 8 + stride * 8 + stride * nhel * 8 + stride * event_record_bytes(K, fp32);
+  if (fp32) b += stride * (sizeof(int) + 1);   // recomputation list and flags
   if (tc) b += stride * nhel * ncol * 8;
   return b;
 }
@@ -206,13 +213,14 @@ mg_status mg_colour_matrix(mg_process proc, int64_t* num, int64_t* den) {
   return MG_OK;
 }
 
-mg_status mg_flops_per_event(mg_process proc, const uint32_t* mask, double* amp_flops, double* colour_flops) {
-  if (!valid_proc(proc)) return MG_EINVAL;
+mg_status mg_flops_per_event(mg_process proc, mg_precision precision, const uint32_t* mask, double* amp_flops,
+                             double* colour_flops) {
+  if (!valid_proc(proc) || precision < MG_FP64 || precision > MG_MIXED) return MG_EINVAL;
   mg::Tables* t = new (std::nothrow) mg::Tables;
   if (!t) return MG_ENOMEM;
   mg::build_tables(mg::gluons_of(proc), *t);
   double a, c;
-  flop_model(*t, mask, &a, &c);
+  flop_model(*t, mask, precision == MG_FP32_AMP || precision == MG_MIXED, &a, &c);
   delete t;
   if (amp_flops) *amp_flops = a;
   if (colour_flops) *colour_flops = c;
@@ -244,6 +252,10 @@ void mg_destroy(mg_ctx* ctx) {
   cudaFree(ctx->d_prep);
   cudaFree(ctx->d_repair);
   cudaFree(ctx->d_nrepair);
+  cudaFree(ctx->d_flag);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
   cudaFree(ctx->d_mom_stage);
   cudaFree(ctx->d_me_stage);
   delete ctx;
@@ -286,6 +298,7 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
         tri.push_back(static_cast<double>(num[static_cast<size_t>(a) * c->ncol + b]) * (a == b ? 1.0 : 2.0));
     e = cudaMalloc(&c->d_ctri, tri.size() * sizeof(double));
     if (e == cudaSuccess) e = cudaMemcpy(c->d_ctri, tri.data(), tri.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = mg::me_static_upload_colour(c->K, tri.data(), static_cast<int>(tri.size()));
     std::vector<float> trif(tri.begin(), tri.end());
     if (e == cudaSuccess) e = cudaMalloc(&c->d_ctri_f, trif.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(c->d_ctri_f, trif.data(), trif.size() * sizeof(float), cudaMemcpyHostToDevice);
@@ -326,6 +339,16 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
         cudaMemset(c->d_nbad, 0, sizeof(unsigned long long)) != cudaSuccess ||
         cudaMemset(c->d_mask, 0, 4 * sizeof(uint32_t)) != cudaSuccess ||
         cudaMemset(c->d_ngood, 0, sizeof(int)) != cudaSuccess) {
+      st = MG_ECUDA;
+      break;
+    }
+    // side stream of the FP32 modes' FP64 recomputation: highest priority, so that its few blocks are
+    // dispatched ahead of the FP32 launch's
+    int lo = 0, hi = 0;
+    if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
+        cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
       st = MG_ECUDA;
       break;
     }
@@ -401,6 +424,22 @@ mg_status mg_hel_filter(mg_ctx* ctx, const double* mom_dev, int64_t nevt, void* 
   return MG_OK;
 }
 
+// The FP32 modes' FP64 recomputation of the events listed in ctx->d_repair, forked onto ctx->side
+// after the work already queued on st (the per-event records and the list), and joined back.
+static cudaError_t fork_repair(mg_ctx* ctx, const double* mom, int64_t nevt, const mg::MeConst& cst, int64_t stride,
+                               int rows_out, cudaStream_t st) {
+  cudaError_t e = cudaEventRecord(ctx->ev_fork, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
+  if (e == cudaSuccess)
+    e = mg::launch_me_gluonhel(ctx->K, false, false, mom, nullptr, nevt, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
+                               ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, stride,
+                               ctx->side, nullptr, mg::MeShape(), nullptr, ctx->d_repair, ctx->d_nrepair, rows_out);
+  if (e == cudaSuccess) e = cudaEventRecord(ctx->ev_join, ctx->side);
+  return e;
+}
+
+static cudaError_t join_repair(mg_ctx* ctx, cudaStream_t st) { return cudaStreamWaitEvent(st, ctx->ev_join, 0); }
+
 mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_precision precision, double* me_dev,
                       void* stream) {
   if (!ctx || nevt < 0 || (nevt > 0 && (!mom_dev || !me_dev))) return MG_EINVAL;
@@ -447,17 +486,17 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
       const int64_t cst_stride = pad32(n);
       const double* mom_c = mom_dev + (e0 / mg::kPage) * ctx->npar * 4 * mg::kPage;
       if (fp32) MG_CUDA(cudaMemsetAsync(ctx->d_nrepair, 0, sizeof(int), st));
+      MG_CUDA(mg::launch_event_prep(ctx->K, fp32, mom_c, n, cst, ctx->d_prep, fp32 ? ctx->d_repair : nullptr,
+                                    fp32 ? ctx->d_nrepair : nullptr, fp32 ? ctx->d_flag : nullptr, st));
+      // events with a small internal invariant: FP64 amplitudes and colour sum (row layout), on the
+      // side stream while the FP32 launches, which skip them, run
+      if (fp32) MG_CUDA(fork_repair(ctx, mom_c, n, cst, cst_stride, 1, st));
       MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_c, ctx->d_prep, n, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
                                      ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, cst_stride, st,
-                                     ctx->d_jamps, ctx->shape[precision], fp32 ? ctx->d_repair : nullptr,
-                                     fp32 ? ctx->d_nrepair : nullptr));
+                                     ctx->d_jamps, ctx->shape[precision], fp32 ? ctx->d_flag : nullptr));
       MG_CUDA(mg::launch_colour_tc(ctx->ncol, ctx->d_jamps, n, ctx->nhel, ctx->d_nrows, ctx->d_cmat, cst.colour_scale,
-                                   ctx->d_part, cst_stride, st));
-      if (fp32)   // events with a small internal invariant: FP64 amplitudes and colour sum, row layout
-        MG_CUDA(mg::launch_me_gluonhel(ctx->K, false, false, mom_c, nullptr, n, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
-                                       ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part,
-                                       cst_stride, st, nullptr, mg::MeShape(), nullptr, nullptr, ctx->d_repair,
-                                       ctx->d_nrepair, 1));
+                                   ctx->d_part, cst_stride, st, fp32 ? ctx->d_flag : nullptr));
+      if (fp32) MG_CUDA(join_repair(ctx, st));
       MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_nrows, n, cst_stride, norm, me_dev + e0, st));
     }
   } else if (ctx->prm.wt == 0.0) {
@@ -466,14 +505,14 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
     if (s == MG_OK && fp32) s = grow_repair(ctx, stride);
     if (s != MG_OK) return s;
     if (fp32) MG_CUDA(cudaMemsetAsync(ctx->d_nrepair, 0, sizeof(int), st));
+    MG_CUDA(mg::launch_event_prep(ctx->K, fp32, mom_dev, nevt, cst, ctx->d_prep, fp32 ? ctx->d_repair : nullptr,
+                                  fp32 ? ctx->d_nrepair : nullptr, fp32 ? ctx->d_flag : nullptr, st));
+    // events with a small internal invariant: recomputed in FP64 (per-slot layout) on the side stream
+    if (fp32) MG_CUDA(fork_repair(ctx, mom_dev, nevt, cst, stride, 0, st));
     MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_dev, ctx->d_prep, nevt, ctx->d_tab, ctx->d_gslots,
                                    1 << ctx->K, ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, stride, st,
-                                   nullptr, ctx->shape[precision], fp32 ? ctx->d_repair : nullptr,
-                                   fp32 ? ctx->d_nrepair : nullptr));
-    if (fp32)   // events with a small internal invariant: recomputed in FP64 (per-slot layout)
-      MG_CUDA(mg::launch_me_gluonhel(ctx->K, false, false, mom_dev, nullptr, nevt, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
-                                     ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, stride,
-                                     st, nullptr, mg::MeShape(), nullptr, nullptr, ctx->d_repair, ctx->d_nrepair, 0));
+                                   nullptr, ctx->shape[precision], fp32 ? ctx->d_flag : nullptr));
+    if (fp32) MG_CUDA(join_repair(ctx, st));
     MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_ngslots, nevt, stride, norm, me_dev, st));
   } else {
     MG_CUDA(mg::launch_me_helicity(ctx->K, precision == MG_FP32_AMP, mom_dev, nevt, ctx->d_tab, ctx->d_good, ctx->nhel,

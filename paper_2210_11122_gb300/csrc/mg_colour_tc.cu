@@ -45,7 +45,8 @@ struct TcShape {
 template <int NCOL>
 __global__ void __launch_bounds__(128) k_colour_tc(const float2* __restrict__ jamps, int64_t nevt, int rows_alloc,
                                                    const int* __restrict__ nrows_dev, const __half* __restrict__ cmat,
-                                                   double scale, double* __restrict__ out, int64_t stride) {
+                                                   double scale, double* __restrict__ out, int64_t stride,
+                                                   const uint8_t* __restrict__ skip) {
   using S = TcShape<NCOL>;
   constexpr int KP = S::KP, NT = S::NT, NP = S::NP, LDH = S::LDH, LDF = S::LDF;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -71,7 +72,7 @@ __global__ void __launch_bounds__(128) k_colour_tc(const float2* __restrict__ ja
       if (qq < npairs && b < NCOL) {
         const int64_t e = qq / nrows;
         const int r = static_cast<int>(qq - e * nrows);
-        v = jamps[(e * rows_alloc + r) * NCOL + b];
+        if (!skip || !skip[e]) v = jamps[(e * rows_alloc + r) * NCOL + b];   // skipped events: no jamps
       }
       sF[(2 * p) * LDF + b] = v.x;
       sF[(2 * p + 1) * LDF + b] = v.y;
@@ -140,11 +141,11 @@ __global__ void __launch_bounds__(128) k_colour_tc(const float2* __restrict__ ja
       const int64_t qa = tile * 8 + g / 2, qb = tile * 8 + 4 + g / 2;
       if (qa < npairs) {
         const int64_t e = qa / nrows;
-        out[(qa - e * nrows) * stride + e] = w0 * scale;
+        if (!skip || !skip[e]) out[(qa - e * nrows) * stride + e] = w0 * scale;
       }
       if (qb < npairs) {
         const int64_t e = qb / nrows;
-        out[(qb - e * nrows) * stride + e] = w1 * scale;
+        if (!skip || !skip[e]) out[(qb - e * nrows) * stride + e] = w1 * scale;
       }
     }
     __syncwarp();
@@ -153,7 +154,7 @@ __global__ void __launch_bounds__(128) k_colour_tc(const float2* __restrict__ ja
 
 template <int NCOL>
 cudaError_t launch_tc(const float2* jamps, int64_t nevt, int rows_alloc, const int* nrows, const __half* cmat,
-                      double scale, double* out, int64_t stride, cudaStream_t st) {
+                      double scale, double* out, int64_t stride, const uint8_t* skip, cudaStream_t st) {
   using S = TcShape<NCOL>;
   const size_t smem = S::smem_bytes();
   static bool configured = false;
@@ -171,7 +172,7 @@ cudaError_t launch_tc(const float2* jamps, int64_t nevt, int rows_alloc, const i
   if (blocks > cap) blocks = cap;
   if (blocks < 1) return cudaSuccess;
   k_colour_tc<NCOL><<<static_cast<unsigned>(blocks), 128, smem, st>>>(jamps, nevt, rows_alloc, nrows, cmat, scale, out,
-                                                                       stride);
+                                                                       stride, skip);
   return cudaGetLastError();
 }
 
@@ -207,13 +208,14 @@ void colour_tc_pack(int ncol, const int64_t* num, uint16_t* out_halves) {
 }
 
 cudaError_t launch_colour_tc(int ncol, const float2* jamps, int64_t nevt, int rows_alloc, const int* nrows,
-                             const void* cmat, double scale, double* out, int64_t stride, cudaStream_t st) {
+                             const void* cmat, double scale, double* out, int64_t stride, cudaStream_t st,
+                             const uint8_t* skip) {
   const __half* c = static_cast<const __half*>(cmat);
   switch (ncol) {
-    case 2: return launch_tc<2>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, st);
-    case 6: return launch_tc<6>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, st);
-    case 24: return launch_tc<24>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, st);
-    case 120: return launch_tc<120>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, st);
+    case 2: return launch_tc<2>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, st);
+    case 6: return launch_tc<6>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, st);
+    case 24: return launch_tc<24>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, st);
+    case 120: return launch_tc<120>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, st);
     default: return cudaErrorInvalidValue;
   }
 }

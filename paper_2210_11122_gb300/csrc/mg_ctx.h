@@ -36,7 +36,10 @@ struct mg_ctx {
   double* d_prep = nullptr;   // per-event records (momenta sums, propagators, wavefunctions)
   int* d_repair = nullptr;    // FP32 modes: events recomputed in FP64, and their count
   int* d_nrepair = nullptr;
+  uint8_t* d_flag = nullptr;  // FP32 modes: 1 for the events in d_repair (the FP32 launches skip them)
   int64_t repair_cap = 0;
+  cudaStream_t side = nullptr;         // FP32 modes: the FP64 recomputation runs here, beside the FP32 launches
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int64_t prep_cap = 0;       // in doubles
   int64_t tot_cap = 0;
   double* d_mom_stage = nullptr;

@@ -20,9 +20,12 @@ struct MeConst {
 // (kMeThreads / tile_ev) gluon-helicity slots (tile_ev in {32, 64, 128}); slot_major orders the grid so
 // that all slot tiles of an event tile are dispatched together (the event's per-event record is then
 // re-read from L2), else all event tiles of a slot tile come first.
+// unrolled: use the kernel with the recursion expanded at compile time (mg_me3.cu) where it exists
+// (me_static_available), else the one that reads the recursion tables at run time (mg_me2.cu).
 struct MeShape {
   int tile_ev = 128;
   bool slot_major = false;
+  bool unrolled = true;
 };
 
 cudaError_t launch_philox(uint64_t seed, int64_t nevt, int nfinal, uint32_t* words, cudaStream_t st);
@@ -33,27 +36,42 @@ cudaError_t launch_rambo(int K, uint64_t seed, int64_t e0, int64_t nevt, double 
 cudaError_t launch_me_helicity(int K, bool fp32, const double* mom, int64_t nevt, const Tables* tab, const int* hels,
                                int maxslot, const int* nslot, const double* ctri, const MeConst& cst, double* out,
                                int64_t stride, cudaStream_t st);
+// Per-event record (momenta sums, propagator factors, wavefunctions; FP64 arithmetic, stored as FP32 or
+// FP64) of every event into rec (ceil(nevt/32)*32 * event_record_bytes(K, fp32) bytes).  repair/nrepair
+// (optional, *nrepair zero before the launch): the events with a small internal invariant are appended;
+// flag (optional): flag[e] = 1 for those events, else 0.
+cudaError_t launch_event_prep(int K, bool fp32, const double* mom, int64_t nevt, const MeConst& cst, void* rec,
+                              int* repair, int* nrepair, uint8_t* flag, cudaStream_t st);
 // One thread per (event, gluon-helicity combination gslots[slot]); per_hel: out[h * stride + e] for every
 // helicity h of the combination, else out[slot * stride + e] = sum over its good helicities.  Zero top width.
-// prep: NULL (every thread computes its event's momenta sums, propagators and wavefunctions) or a
-// buffer of ceil(nevt/32)*32 * event_record_bytes(K, fp32) bytes that a per-event kernel fills first;
-// with prep, repair/nrepair (optional) collect the events with a small internal invariant (*nrepair
-// must be zero before the launch).  evlist/nlist (prep == NULL only): work on events evlist[0..*nlist)
-// of the batch; rows_out: write slot totals in the tensor-core row layout (4 rows per slot).
+// prep: NULL (every thread computes its event's momenta sums, propagators and wavefunctions) or the
+// records launch_event_prep wrote; with prep, events with skip[e] != 0 (skip optional) are left out
+// (nothing written).  evlist/nlist (prep == NULL only): work on events evlist[0..*nlist) of the batch;
+// rows_out: write slot totals in the tensor-core row layout (4 rows per slot).
 cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom, void* prep, int64_t nevt,
                                const Tables* tab, const int* gslots, int maxslot, const int* nslot,
                                const uint32_t* mask, const double* ctri64, const float* ctri32, const MeConst& cst,
                                double* out, int64_t stride, cudaStream_t st, float2* jout = nullptr,
-                               MeShape shape = MeShape(), int* repair = nullptr, int* nrepair = nullptr,
+                               MeShape shape = MeShape(), const uint8_t* skip = nullptr,
                                const int* evlist = nullptr, const int* nlist = nullptr, int rows_out = 0);
 int64_t event_record_bytes(int K, bool fp32);
+// The compile-time-unrolled matrix-element kernel (mg_me3.cu): same contract as launch_me_gluonhel with
+// a per-event record rec (filled by k_event_prep), for the (K, precision) pairs me_static_available
+// lists.  me_static_upload_colour: its colour triangle (constant memory), once per device and K.
+bool me_static_available(int K, bool fp32);
+cudaError_t me_static_upload_colour(int K, const double* tri, int n);
+cudaError_t launch_me_static(int K, bool fp32, const void* rec, int64_t nevt, const int* gslots, int maxslot,
+                             const int* nslot, const uint32_t* mask, const MeConst& cst, double* out, int64_t stride,
+                             float2* jout, MeShape shape, const uint8_t* skip, cudaStream_t st);
 
 // Tensor-core colour sum (mg_colour_tc.cu): out[r * stride + e] = scale * (Re A^T C Re A + Im A^T C Im A)
-// for the jamp rows jamps[(e * rows_alloc + r) * ncol ...], r < *nrows.
+// for the jamp rows jamps[(e * rows_alloc + r) * ncol ...], r < *nrows; events with skip[e] != 0 (skip
+// optional) are not written.
 int colour_tc_cmat_halves(int ncol);
 void colour_tc_pack(int ncol, const int64_t* num, uint16_t* out_halves);
 cudaError_t launch_colour_tc(int ncol, const float2* jamps, int64_t nevt, int rows_alloc, const int* nrows,
-                             const void* cmat, double scale, double* out, int64_t stride, cudaStream_t st);
+                             const void* cmat, double scale, double* out, int64_t stride, cudaStream_t st,
+                             const uint8_t* skip = nullptr);
 cudaError_t launch_gluon_slots(const uint32_t* mask, int K, int* gslots, int* n, int* nrows, cudaStream_t st);
 cudaError_t launch_hel_sum(const double* part, const int* nslot, int64_t nevt, int64_t stride, double norm,
                            double* me, cudaStream_t st);

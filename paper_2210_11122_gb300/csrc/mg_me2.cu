@@ -17,289 +17,10 @@
 
 #include "mg_internal.h"
 #include "mg_kernels.h"
+#include "mg_me_algebra.cuh"
 
 namespace mg {
 namespace v2 {
-
-template <class T>
-struct cx {
-  T r, i;
-};
-
-template <class T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
-  return {fma(a.r, b.r, -(a.i * b.i)), fma(a.r, b.i, a.i * b.r)};
-}
-template <class T> __device__ __forceinline__ void cmac(cx<T>& c, cx<T> a, cx<T> b) {   // c += a b
-  c.r = fma(a.r, b.r, c.r); c.r = fma(-a.i, b.i, c.r);
-  c.i = fma(a.r, b.i, c.i); c.i = fma(a.i, b.r, c.i);
-}
-template <class T> __device__ __forceinline__ void cmsub(cx<T>& c, cx<T> a, cx<T> b) {  // c -= a b
-  c.r = fma(-a.r, b.r, c.r); c.r = fma(a.i, b.i, c.r);
-  c.i = fma(-a.r, b.i, c.i); c.i = fma(-a.i, b.r, c.i);
-}
-template <class T> __device__ __forceinline__ void cmacr(cx<T>& c, T s, cx<T> a) {      // c += s a, s real
-  c.r = fma(s, a.r, c.r); c.i = fma(s, a.i, c.i);
-}
-template <class T> __device__ __forceinline__ cx<T> cscale(T s, cx<T> a) { return {s * a.r, s * a.i}; }
-template <class T> __device__ __forceinline__ cx<T> cneg(cx<T> a) { return {-a.r, -a.i}; }
-
-// Minkowski dot products
-template <class T> __device__ __forceinline__ cx<T> mdot(const cx<T>* a, const cx<T>* b) {
-  cx<T> r = cmul(a[0], b[0]);
-  cmsub(r, a[1], b[1]); cmsub(r, a[2], b[2]); cmsub(r, a[3], b[3]);
-  return r;
-}
-template <class T> __device__ __forceinline__ cx<T> mdotr(const cx<T>* a, const T* p) {
-  cx<T> r = cscale(p[0], a[0]);
-  cmacr(r, -p[1], a[1]); cmacr(r, -p[2], a[2]); cmacr(r, -p[3], a[3]);
-  return r;
-}
-
-template <int K> struct Sizes;
-template <> struct Sizes<2> { static constexpr int ncol = 2, nseq = 2, nfull = 1; };
-template <> struct Sizes<3> { static constexpr int ncol = 6, nseq = 6, nfull = 3; };
-template <> struct Sizes<4> { static constexpr int ncol = 24, nseq = 22, nfull = 12; };
-template <> struct Sizes<5> { static constexpr int ncol = 120, nseq = 105, nfull = 60; };
-
-__device__ __forceinline__ int rslot(int16_t r) { return r >> 1; }
-__device__ __forceinline__ bool rneg(int16_t r) { return r & 1; }
-
-// ---- external wavefunctions (FP64) ----
-__device__ __forceinline__ void chi2(const double* p, int lam, cx<double>* c) {
-  const double px = p[1], py = p[2], pz = p[3];
-  const double pt2 = px * px + py * py;
-  const double pa = sqrt(pt2 + pz * pz);
-  const double apz = pz >= 0.0 ? pa + pz : pt2 / (pa - pz);
-  if (apz > 0.0) {
-    const double n = rsqrt(2.0 * pa * apz);
-    if (lam > 0) { c[0] = {apz * n, 0.0}; c[1] = {px * n, py * n}; }
-    else { c[0] = {-px * n, py * n}; c[1] = {apz * n, 0.0}; }
-  } else {
-    if (lam > 0) { c[0] = {0.0, 0.0}; c[1] = {1.0, 0.0}; }
-    else { c[0] = {-1.0, 0.0}; c[1] = {0.0, 0.0}; }
-  }
-}
-
-template <class T>
-__device__ __forceinline__ void top_ubar(const double* p, double m, int lam, cx<T>* w) {
-  const double pa = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
-  const double sp = sqrt(p[0] + pa);
-  const double sm = m > 0.0 ? m / sp : 0.0;
-  cx<double> c[2];
-  chi2(p, lam, c);
-  const double fl = lam > 0 ? sm : sp, fr = lam > 0 ? sp : sm;
-  w[0] = {T(fr * c[0].r), T(-fr * c[0].i)}; w[1] = {T(fr * c[1].r), T(-fr * c[1].i)};
-  w[2] = {T(fl * c[0].r), T(-fl * c[0].i)}; w[3] = {T(fl * c[1].r), T(-fl * c[1].i)};
-}
-
-template <class T>
-__device__ __forceinline__ void top_v(const double* p, double m, int lam, cx<T>* w) {
-  const double pa = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
-  const double sp = sqrt(p[0] + pa);
-  const double sm = m > 0.0 ? m / sp : 0.0;
-  cx<double> c[2];
-  chi2(p, -lam, c);
-  const double fl = lam > 0 ? -sp : sm, fr = lam > 0 ? sm : -sp;
-  w[0] = {T(fl * c[0].r), T(fl * c[0].i)}; w[1] = {T(fl * c[1].r), T(fl * c[1].i)};
-  w[2] = {T(fr * c[0].r), T(fr * c[0].i)}; w[3] = {T(fr * c[1].r), T(fr * c[1].i)};
-}
-
-template <class T>
-__device__ __forceinline__ void gluon_eps(const double* k, int lam, bool outgoing, cx<T>* w) {
-  const double kx = k[1], ky = k[2], kz = k[3];
-  const double kt = sqrt(kx * kx + ky * ky);
-  const double ka = sqrt(kx * kx + ky * ky + kz * kz);
-  double et[3], ep[3];
-  if (kt > 0.0) {
-    const double inv = 1.0 / (ka * kt);
-    et[0] = kx * kz * inv; et[1] = ky * kz * inv; et[2] = -kt / ka;
-    ep[0] = -ky / kt; ep[1] = kx / kt; ep[2] = 0.0;
-  } else {
-    et[0] = kz < 0.0 ? -1.0 : 1.0; et[1] = 0.0; et[2] = 0.0;
-    ep[0] = 0.0; ep[1] = 1.0; ep[2] = 0.0;
-  }
-  const double r = 0.70710678118654752440;
-  const double sl = lam > 0 ? -r : r;
-  const double si = outgoing ? r : -r;
-  w[0] = {T(0), T(0)};
-#pragma unroll
-  for (int i = 0; i < 3; ++i) w[1 + i] = {T(sl * et[i]), T(si * ep[i])};
-}
-
-// ---- current algebra ----
-// acc += s * V3(JL, JR) with incoming momenta PL, PR.  The Feynman-gauge vertex contracted with the
-// two currents is (JL.JR)(PL - PR) + (JL.(PL + 2 PR)) JR - (JR.(2 PL + PR)) JL; Berends-Giele
-// currents of on-shell transverse gluons are conserved (P.J(P) = 0 exactly), so the JL.PL and JR.PR
-// parts vanish and the vertex is evaluated as (JL.JR)(PL - PR) + 2 (JL.PR) JR - 2 (JR.PL) JL: the
-// same value, without adding the rounding noise of two vanishing products (which 1/P^2 factors of
-// nearly collinear pairs amplify in FP32).
-template <class T>
-__device__ __forceinline__ void v3_acc(cx<T>* acc, const cx<T>* JL, const cx<T>* JR, const T* PL, const T* PR, bool neg) {
-  T d[4];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) d[m] = PL[m] - PR[m];
-  cx<T> jj = mdot(JL, JR), cl = mdotr(JL, PR), cr = mdotr(JR, PL);
-  const T two = neg ? T(-2) : T(2);
-  if (neg) jj = cneg(jj);
-  cl = cscale(two, cl);
-  cr = cscale(two, cr);
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    cmacr(acc[m], d[m], jj);
-    cmac(acc[m], cl, JR[m]);
-    cmsub(acc[m], cr, JL[m]);
-  }
-}
-
-// acc += s * g * V4(JA, JB, JC), V4 = (JA.JB) JC + (JB.JC) JA - 2 (JA.JC) JB
-template <class T>
-__device__ __forceinline__ void v4_acc(cx<T>* acc, const cx<T>* JA, const cx<T>* JB, const cx<T>* JC, T g, bool neg) {
-  const T s = neg ? -g : g;
-  const cx<T> ab = cscale(s, mdot(JA, JB)), bc = cscale(s, mdot(JB, JC)), ac = cscale(T(2) * s, mdot(JA, JC));
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    cmac(acc[m], ab, JC[m]);
-    cmac(acc[m], bc, JA[m]);
-    cmsub(acc[m], ac, JB[m]);
-  }
-}
-
-// acc (+/-)= s gamma.J  (row spinor s, gluon current J)
-template <class T>
-__device__ __forceinline__ void row_gamma_acc(cx<T>* acc, const cx<T>* s, const cx<T>* J, bool neg) {
-  cx<T> jm = {J[1].r + J[2].i, J[1].i - J[2].r};   // J1 - i J2
-  cx<T> jp = {J[1].r - J[2].i, J[1].i + J[2].r};   // J1 + i J2
-  cx<T> a = {J[0].r + J[3].r, J[0].i + J[3].i}, b = {J[0].r - J[3].r, J[0].i - J[3].i};
-  if (neg) { jm = cneg(jm); jp = cneg(jp); a = cneg(a); b = cneg(b); }
-  cmac(acc[0], s[2], a); cmac(acc[0], s[3], jp);
-  cmac(acc[1], s[2], jm); cmac(acc[1], s[3], b);
-  cmac(acc[2], s[0], b); cmsub(acc[2], s[1], jp);
-  cmac(acc[3], s[1], a); cmsub(acc[3], s[0], jm);
-}
-
-// (gamma.J) v
-template <class T>
-__device__ __forceinline__ void gamma_col(const cx<T>* J, const cx<T>* v, cx<T>* o) {
-  const cx<T> jm = {J[1].r + J[2].i, J[1].i - J[2].r};
-  const cx<T> jp = {J[1].r - J[2].i, J[1].i + J[2].r};
-  const cx<T> a = {J[0].r + J[3].r, J[0].i + J[3].i}, b = {J[0].r - J[3].r, J[0].i - J[3].i};
-  o[0] = cmul(b, v[2]); cmsub(o[0], jm, v[3]);
-  o[1] = cmul(a, v[3]); cmsub(o[1], jp, v[2]);
-  o[2] = cmul(a, v[0]); cmac(o[2], jm, v[1]);
-  o[3] = cmul(jp, v[0]); cmac(o[3], b, v[1]);
-}
-
-// quark propagator with factor: o = s (Qslash + m) f, coefficients q = {(Q0+Q3) f, (Q0-Q3) f, Q1 f, Q2 f, m f}
-template <class T>
-__device__ __forceinline__ void row_prop(const cx<T>* s, const T* q, cx<T>* o) {
-  const T qa = q[0], qb = q[1], q1 = q[2], q2 = q[3], qm = q[4];
-  // o0 = qa s2 + (q1 + i q2) s3 + qm s0 ; o1 = (q1 - i q2) s2 + qb s3 + qm s1
-  // o2 = qb s0 - (q1 + i q2) s1 + qm s2 ; o3 = qa s1 - (q1 - i q2) s0 + qm s3
-  const cx<T> qp = {q1, q2}, qn = {q1, -q2};
-  o[0] = cscale(qa, s[2]); cmac(o[0], qp, s[3]); cmacr(o[0], qm, s[0]);
-  o[1] = cscale(qb, s[3]); cmac(o[1], qn, s[2]); cmacr(o[1], qm, s[1]);
-  o[2] = cscale(qb, s[0]); cmsub(o[2], qp, s[1]); cmacr(o[2], qm, s[2]);
-  o[3] = cscale(qa, s[1]); cmsub(o[3], qn, s[0]); cmacr(o[3], qm, s[3]);
-}
-
-template <class T> __device__ __forceinline__ void sdot_acc(cx<T>& c, const cx<T>* a, const cx<T>* b, bool neg) {
-  if (neg) { cmsub(c, a[0], b[0]); cmsub(c, a[1], b[1]); cmsub(c, a[2], b[2]); cmsub(c, a[3], b[3]); }
-  else { cmac(c, a[0], b[0]); cmac(c, a[1], b[1]); cmac(c, a[2], b[2]); cmac(c, a[3], b[3]); }
-}
-
-// quark current Jq^mu = ubar gamma^mu v
-template <class T> __device__ __forceinline__ void quark_current(const cx<T>* u, const cx<T>* v, cx<T>* Jq) {
-  // a = u[0..1], b = u[2..3], vL = v[0..1], vR = v[2..3]
-  const cx<T> a0r0 = cmul(u[0], v[2]), a0r1 = cmul(u[0], v[3]), a1r0 = cmul(u[1], v[2]), a1r1 = cmul(u[1], v[3]);
-  const cx<T> b0l0 = cmul(u[2], v[0]), b0l1 = cmul(u[2], v[1]), b1l0 = cmul(u[3], v[0]), b1l1 = cmul(u[3], v[1]);
-  Jq[0] = {a0r0.r + a1r1.r + b0l0.r + b1l1.r, a0r0.i + a1r1.i + b0l0.i + b1l1.i};
-  Jq[1] = {(a0r1.r + a1r0.r) - (b0l1.r + b1l0.r), (a0r1.i + a1r0.i) - (b0l1.i + b1l0.i)};
-  const cx<T> t = {(a1r0.r - a0r1.r) - (b1l0.r - b0l1.r), (a1r0.i - a0r1.i) - (b1l0.i - b0l1.i)};
-  Jq[2] = {-t.i, t.r};
-  Jq[3] = {(a0r0.r - a1r1.r) - (b0l0.r - b1l1.r), (a0r0.i - a1r1.i) - (b0l0.i - b1l1.i)};
-}
-
-// colour sum of one helicity: sum_a A_a^* (sum_b Ctri_ab A_b), packed upper triangle
-template <int NCOL, class T>
-__device__ __forceinline__ T colour_sum(const cx<T>* A, const T* __restrict__ ctri) {
-  T sum = 0;
-  int idx = 0;
-  for (int a = 0; a < NCOL; ++a) {
-    T wr = 0, wi = 0;
-    for (int b = a; b < NCOL; ++b, ++idx) {
-      const T c = __ldg(ctri + idx);
-      wr = fma(c, A[b].r, wr);
-      wi = fma(c, A[b].i, wi);
-    }
-    sum = fma(A[a].r, wr, sum);
-    sum = fma(A[a].i, wi, sum);
-  }
-  return sum;
-}
-
-// ---- per-event data shared by every helicity of an event (FP64 arithmetic, stored as T) ----
-// Layout of one event's record (NITEM values of T): PT[S][4] (incoming gluon momentum of subset S),
-// gprop[S] (-g/P_S^2), qc[S][5] (quark propagator coefficients), eps[g][hel][4] complex,
-// ubar[hel][4] complex, v[hel][4] complex.
-template <int K> struct EvLayout {
-  static constexpr int NSUB = 1 << K;
-  static constexpr int PT = 0, GP = 4 * NSUB, QC = 5 * NSUB, EPS = 10 * NSUB, UB = EPS + 16 * K, VV = UB + 16;
-  static constexpr int NITEM = VV + 16;
-};
-
-template <int K, class T>
-__device__ __forceinline__ void event_data(const double (*p)[4], const MeConst& cst, T (*PT)[4], T* gprop, T (*qc)[5],
-                                           cx<T> (*eps)[2][4], cx<T> (*ub)[4], cx<T> (*vv)[4],
-                                           double* min_invariant = nullptr) {
-  constexpr int NSUB = 1 << K;
-  double xmin = 1e300;
-  double Pst[NSUB][4];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) Pst[0][m] = 0.0;
-#pragma unroll
-  for (int S = 1; S < NSUB; ++S) {
-    const int g = __ffs(S) - 1;
-    const int part = g < 2 ? g : g + 2;
-    const double sg = g < 2 ? 1.0 : -1.0;
-#pragma unroll
-    for (int m = 0; m < 4; ++m) Pst[S][m] = Pst[S & (S - 1)][m] + sg * p[part][m];
-  }
-#pragma unroll
-  for (int S = 0; S < NSUB; ++S) {
-    const double* P = Pst[S];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) PT[S][m] = static_cast<T>(P[m]);
-    const double p2 = P[0] * P[0] - P[1] * P[1] - P[2] * P[2] - P[3] * P[3];
-    gprop[S] = static_cast<T>((S & (S - 1)) ? -cst.gs / p2 : 0.0);   // includes one power of g
-    const double Q0 = p[2][0] - P[0], Q1 = p[2][1] - P[1], Q2 = p[2][2] - P[2], Q3 = p[2][3] - P[3];
-    const double dq = Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3 - cst.mt * cst.mt;
-    const double f = -cst.gs / dq;
-    if (S != 0 && S != NSUB - 1) {   // internal lines only (S = 0 and S = all are the external tops)
-      xmin = fmin(xmin, fabs(dq));
-      if (S & (S - 1)) xmin = fmin(xmin, fabs(p2));
-    }
-    qc[S][0] = static_cast<T>((Q0 + Q3) * f);
-    qc[S][1] = static_cast<T>((Q0 - Q3) * f);
-    qc[S][2] = static_cast<T>(Q1 * f);
-    qc[S][3] = static_cast<T>(Q2 * f);
-    qc[S][4] = static_cast<T>(cst.mt * f);
-  }
-#pragma unroll
-  for (int g = 0; g < K; ++g) {
-    const int part = g < 2 ? g : g + 2;
-    gluon_eps<T>(p[part], -1, g >= 2, eps[g][0]);
-    gluon_eps<T>(p[part], 1, g >= 2, eps[g][1]);
-  }
-  top_ubar<T>(p[2], cst.mt, -1, ub[0]);
-  top_ubar<T>(p[2], cst.mt, 1, ub[1]);
-  top_v<T>(p[3], cst.mt, -1, vv[0]);
-  top_v<T>(p[3], cst.mt, 1, vv[1]);
-  if (min_invariant) {
-    const double s0 = p[0][0] + p[1][0], s1 = p[0][1] + p[1][1], s2 = p[0][2] + p[1][2], s3 = p[0][3] + p[1][3];
-    const double shat = s0 * s0 - s1 * s1 - s2 * s2 - s3 * s3;   // (p1 + p2)^2
-    *min_invariant = xmin / fabs(shat);
-  }
-}
 
 // One thread per event: the event's record, AoSoA (page of 32 events, value-major within a page).
 // repair != NULL: events whose smallest internal invariant |P^2| or |Q^2 - m^2| (over the gluon and
@@ -308,7 +29,7 @@ __device__ __forceinline__ void event_data(const double (*p)[4], const MeConst& 
 template <int K, class T>
 __global__ void __launch_bounds__(128) k_event_prep(const double* __restrict__ mom, int64_t nevt, MeConst cst,
                                                     T* __restrict__ rec, int* __restrict__ repair,
-                                                    int* __restrict__ nrepair) {
+                                                    int* __restrict__ nrepair, uint8_t* __restrict__ flag) {
   constexpr int npar = K + 2, NSUB = 1 << K;
   using L = EvLayout<K>;
   const int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
@@ -323,7 +44,9 @@ __global__ void __launch_bounds__(128) k_event_prep(const double* __restrict__ m
   cx<T> eps[K][2][4], ub[2][4], vv[2][4];
   double xmin = 1.0;
   event_data<K, T>(p, cst, PT, gprop, qc, eps, ub, vv, &xmin);
-  if (repair && xmin < cst.fp32_tau) repair[atomicAdd(nrepair, 1)] = static_cast<int>(e);
+  const bool redo = repair && xmin < cst.fp32_tau;
+  if (redo) repair[atomicAdd(nrepair, 1)] = static_cast<int>(e);
+  if (flag) flag[e] = redo ? 1 : 0;
   T* out = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
 #pragma unroll
   for (int S = 0; S < NSUB; ++S) {
@@ -362,7 +85,7 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
               const int* __restrict__ gslots, const int* __restrict__ nslot_dev, const uint32_t* __restrict__ mask,
               const T* __restrict__ ctri, MeConst cst, double* __restrict__ out, int64_t stride,
               float2* __restrict__ jout, int tile_ev, int slot_major, const int* __restrict__ evlist,
-              const int* __restrict__ nlist, int rows_out) {
+              const int* __restrict__ nlist, int rows_out, const uint8_t* __restrict__ skip) {
   constexpr int npar = K + 2;
   constexpr int NSEQ = Sizes<K>::nseq;
   constexpr int NCOL = Sizes<K>::ncol;
@@ -376,6 +99,7 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
   // evlist: the thread works on event evlist[et] of the batch (et < *nlist), else on event et
   if (evlist && et >= *nlist) return;
   const int64_t e = evlist ? static_cast<int64_t>(evlist[et]) : et;
+  if (PREP && skip && skip[e]) return;   // recomputed by another launch
   const int gc = gslots[slot];   // bit g = helicity (+1) of gluon g
 
   const T gs = static_cast<T>(cst.gs);
@@ -603,8 +327,7 @@ template <int K, class T, bool PER_HEL>
 static cudaError_t launch_v2(const double* mom, void* prep, int64_t nevt, const Tables* tab, const int* gslots,
                              int maxslot, const int* nslot, const uint32_t* mask, const void* ctri_any,
                              const MeConst& cst, double* out, int64_t stride, float2* jout, MeShape shape,
-                             int* repair, int* nrepair, const int* evlist, const int* nlist, int rows_out,
-                             cudaStream_t st) {
+                             const uint8_t* skip, const int* evlist, const int* nlist, int rows_out, cudaStream_t st) {
   const T* ctri = static_cast<const T*>(ctri_any);
   int tev = shape.tile_ev;
   if (tev != 32 && tev != 64 && tev != 128) tev = 128;
@@ -614,22 +337,49 @@ static cudaError_t launch_v2(const double* mom, void* prep, int64_t nevt, const 
   dim3 grid = sm ? dim3(nsl_t, nev_t) : dim3(nev_t, nsl_t);
   if (nev_t == 0 || nsl_t == 0) return cudaSuccess;
   if (prep && !PER_HEL) {
-    T* rec = static_cast<T*>(prep);
-    v2::k_event_prep<K, T><<<static_cast<unsigned>((nevt + 127) / 128), 128, 0, st>>>(mom, nevt, cst, rec, repair,
-                                                                                     nrepair);
+    const T* rec = static_cast<const T*>(prep);
+    if (shape.unrolled && me_static_available(K, sizeof(T) == 4))
+      return launch_me_static(K, sizeof(T) == 4, rec, nevt, gslots, maxslot, nslot, mask, cst, out, stride, jout, shape,
+                              skip, st);
     if (jout)
       v2::k_me_gluonhel<K, T, false, true, true><<<grid, kMeThreads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot, mask,
-                                                                             ctri, cst, out, stride, jout, tev, sm, nullptr, nullptr, 0);
+                                                                             ctri, cst, out, stride, jout, tev, sm, nullptr,
+                                                                             nullptr, 0, skip);
     else
       v2::k_me_gluonhel<K, T, false, true, false><<<grid, kMeThreads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot,
                                                                               mask, ctri, cst, out, stride, nullptr, tev,
-                                                                              sm, nullptr, nullptr, 0);
+                                                                              sm, nullptr, nullptr, 0, skip);
   } else {
     v2::k_me_gluonhel<K, T, PER_HEL, false, false><<<grid, kMeThreads, 0, st>>>(mom, nullptr, nevt, tab, gslots, nslot,
                                                                                  mask, ctri, cst, out, stride, nullptr,
-                                                                                 tev, sm, evlist, nlist, rows_out);
+                                                                                 tev, sm, evlist, nlist, rows_out,
+                                                                                 nullptr);
   }
   return cudaGetLastError();
+}
+
+template <int K, class T>
+static cudaError_t launch_prep(const double* mom, int64_t nevt, const MeConst& cst, void* rec, int* repair,
+                               int* nrepair, uint8_t* flag, cudaStream_t st) {
+  if (nevt <= 0) return cudaSuccess;
+  v2::k_event_prep<K, T><<<static_cast<unsigned>((nevt + 127) / 128), 128, 0, st>>>(mom, nevt, cst, static_cast<T*>(rec),
+                                                                                   repair, nrepair, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_event_prep(int K, bool fp32, const double* mom, int64_t nevt, const MeConst& cst, void* rec,
+                              int* repair, int* nrepair, uint8_t* flag, cudaStream_t st) {
+  switch (K) {
+    case 2: return fp32 ? launch_prep<2, float>(mom, nevt, cst, rec, repair, nrepair, flag, st)
+                        : launch_prep<2, double>(mom, nevt, cst, rec, repair, nrepair, flag, st);
+    case 3: return fp32 ? launch_prep<3, float>(mom, nevt, cst, rec, repair, nrepair, flag, st)
+                        : launch_prep<3, double>(mom, nevt, cst, rec, repair, nrepair, flag, st);
+    case 4: return fp32 ? launch_prep<4, float>(mom, nevt, cst, rec, repair, nrepair, flag, st)
+                        : launch_prep<4, double>(mom, nevt, cst, rec, repair, nrepair, flag, st);
+    case 5: return fp32 ? launch_prep<5, float>(mom, nevt, cst, rec, repair, nrepair, flag, st)
+                        : launch_prep<5, double>(mom, nevt, cst, rec, repair, nrepair, flag, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 int64_t event_record_bytes(int K, bool fp32) {
@@ -648,17 +398,17 @@ cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom
                                const Tables* tab, const int* gslots, int maxslot, const int* nslot,
                                const uint32_t* mask, const double* ctri64, const float* ctri32, const MeConst& cst,
                                double* out, int64_t stride, cudaStream_t st, float2* jout, MeShape shape,
-                               int* repair, int* nrepair, const int* evlist, const int* nlist, int rows_out) {
+                               const uint8_t* skip, const int* evlist, const int* nlist, int rows_out) {
 #define MG_V2_CASE(KK)                                                                                              \
   case KK:                                                                                                          \
     if (per_hel) return fp32 ? launch_v2<KK, float, true>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri32, cst,  \
-                                                          out, stride, jout, shape, repair, nrepair, evlist, nlist, rows_out, st)                                          \
+                                                          out, stride, jout, shape, skip, evlist, nlist, rows_out, st)                                          \
                              : launch_v2<KK, double, true>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri64, cst, \
-                                                           out, stride, jout, shape, repair, nrepair, evlist, nlist, rows_out, st);                                        \
+                                                           out, stride, jout, shape, skip, evlist, nlist, rows_out, st);                                        \
     return fp32 ? launch_v2<KK, float, false>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri32, cst, out, stride, \
-                                              jout, shape, repair, nrepair, evlist, nlist, rows_out, st)                                                                   \
+                                              jout, shape, skip, evlist, nlist, rows_out, st)                                                                   \
                 : launch_v2<KK, double, false>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri64, cst, out, stride,\
-                                               jout, shape, repair, nrepair, evlist, nlist, rows_out, st);
+                                               jout, shape, skip, evlist, nlist, rows_out, st);
   switch (K) {
     MG_V2_CASE(2)
     MG_V2_CASE(3)

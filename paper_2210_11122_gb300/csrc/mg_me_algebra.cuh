@@ -1,0 +1,336 @@
+// mg_me_algebra.cuh -- device algebra shared by the matrix-element kernels (mg_me2.cu, mg_me3.cu):
+// complex FMA chains, HELAS-convention external wavefunctions (helicity spinors of the tops in the
+// chiral basis, transverse gluon polarisations), the Feynman-gauge three- and four-gluon vertices
+// and the quark-line vertex/propagator contracted with currents, the colour quadratic form, and the
+// per-event record (subset momenta, propagator factors, wavefunctions) that a per-event kernel
+// computes once in FP64 for every helicity of the event.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "mg_internal.h"
+#include "mg_kernels.h"
+
+namespace mg {
+namespace v2 {
+
+template <class T>
+struct cx {
+  T r, i;
+};
+
+template <class T> __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  return {fma(a.r, b.r, -(a.i * b.i)), fma(a.r, b.i, a.i * b.r)};
+}
+template <class T> __device__ __forceinline__ void cmac(cx<T>& c, cx<T> a, cx<T> b) {   // c += a b
+  c.r = fma(a.r, b.r, c.r); c.r = fma(-a.i, b.i, c.r);
+  c.i = fma(a.r, b.i, c.i); c.i = fma(a.i, b.r, c.i);
+}
+template <class T> __device__ __forceinline__ void cmsub(cx<T>& c, cx<T> a, cx<T> b) {  // c -= a b
+  c.r = fma(-a.r, b.r, c.r); c.r = fma(a.i, b.i, c.r);
+  c.i = fma(-a.r, b.i, c.i); c.i = fma(-a.i, b.r, c.i);
+}
+template <class T> __device__ __forceinline__ void cmacr(cx<T>& c, T s, cx<T> a) {      // c += s a, s real
+  c.r = fma(s, a.r, c.r); c.i = fma(s, a.i, c.i);
+}
+template <class T> __device__ __forceinline__ cx<T> cscale(T s, cx<T> a) { return {s * a.r, s * a.i}; }
+template <class T> __device__ __forceinline__ cx<T> cneg(cx<T> a) { return {-a.r, -a.i}; }
+
+// Minkowski dot products
+template <class T> __device__ __forceinline__ cx<T> mdot(const cx<T>* a, const cx<T>* b) {
+  cx<T> r = cmul(a[0], b[0]);
+  cmsub(r, a[1], b[1]); cmsub(r, a[2], b[2]); cmsub(r, a[3], b[3]);
+  return r;
+}
+template <class T> __device__ __forceinline__ cx<T> mdotr(const cx<T>* a, const T* p) {
+  cx<T> r = cscale(p[0], a[0]);
+  cmacr(r, -p[1], a[1]); cmacr(r, -p[2], a[2]); cmacr(r, -p[3], a[3]);
+  return r;
+}
+
+template <int K> struct Sizes;
+template <> struct Sizes<2> { static constexpr int ncol = 2, nseq = 2, nfull = 1; };
+template <> struct Sizes<3> { static constexpr int ncol = 6, nseq = 6, nfull = 3; };
+template <> struct Sizes<4> { static constexpr int ncol = 24, nseq = 22, nfull = 12; };
+template <> struct Sizes<5> { static constexpr int ncol = 120, nseq = 105, nfull = 60; };
+
+__device__ __forceinline__ int rslot(int16_t r) { return r >> 1; }
+__device__ __forceinline__ bool rneg(int16_t r) { return r & 1; }
+
+// ---- external wavefunctions (FP64) ----
+__device__ __forceinline__ void chi2(const double* p, int lam, cx<double>* c) {
+  const double px = p[1], py = p[2], pz = p[3];
+  const double pt2 = px * px + py * py;
+  const double pa = sqrt(pt2 + pz * pz);
+  const double apz = pz >= 0.0 ? pa + pz : pt2 / (pa - pz);
+  if (apz > 0.0) {
+    const double n = rsqrt(2.0 * pa * apz);
+    if (lam > 0) { c[0] = {apz * n, 0.0}; c[1] = {px * n, py * n}; }
+    else { c[0] = {-px * n, py * n}; c[1] = {apz * n, 0.0}; }
+  } else {
+    if (lam > 0) { c[0] = {0.0, 0.0}; c[1] = {1.0, 0.0}; }
+    else { c[0] = {-1.0, 0.0}; c[1] = {0.0, 0.0}; }
+  }
+}
+
+template <class T>
+__device__ __forceinline__ void top_ubar(const double* p, double m, int lam, cx<T>* w) {
+  const double pa = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+  const double sp = sqrt(p[0] + pa);
+  const double sm = m > 0.0 ? m / sp : 0.0;
+  cx<double> c[2];
+  chi2(p, lam, c);
+  const double fl = lam > 0 ? sm : sp, fr = lam > 0 ? sp : sm;
+  w[0] = {T(fr * c[0].r), T(-fr * c[0].i)}; w[1] = {T(fr * c[1].r), T(-fr * c[1].i)};
+  w[2] = {T(fl * c[0].r), T(-fl * c[0].i)}; w[3] = {T(fl * c[1].r), T(-fl * c[1].i)};
+}
+
+template <class T>
+__device__ __forceinline__ void top_v(const double* p, double m, int lam, cx<T>* w) {
+  const double pa = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+  const double sp = sqrt(p[0] + pa);
+  const double sm = m > 0.0 ? m / sp : 0.0;
+  cx<double> c[2];
+  chi2(p, -lam, c);
+  const double fl = lam > 0 ? -sp : sm, fr = lam > 0 ? sm : -sp;
+  w[0] = {T(fl * c[0].r), T(fl * c[0].i)}; w[1] = {T(fl * c[1].r), T(fl * c[1].i)};
+  w[2] = {T(fr * c[0].r), T(fr * c[0].i)}; w[3] = {T(fr * c[1].r), T(fr * c[1].i)};
+}
+
+// Reciprocal and reciprocal square root for the FP32-amplitude path's record: an FP32 seed refined by
+// one Newton-Raphson step in FP64 (r <- r (2 - x r) for 1/x, y <- y (3 - x y^2) / 2 for 1/sqrt(x); each
+// step squares the seed's relative error, ~2^-23 -> ~2^-45), so that the values stored in FP32 carry
+// only their final rounding, at a fraction of the FP64 cost of a correctly rounded division.  Outside
+// the FP32 exponent range the FP64 operation is used.
+__device__ __forceinline__ double rcp_nr(double x) {
+  const double ax = fabs(x);
+  if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
+  const double r0 = static_cast<double>(__frcp_rn(static_cast<float>(x)));
+  return r0 * fma(-x, r0, 2.0);
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return rsqrt(x);
+  const double y0 = static_cast<double>(rsqrtf(static_cast<float>(x)));
+  return y0 * fma(-0.5 * x * y0, y0, 1.5);
+}
+
+// Transverse polarisation of a gluon of momentum k (unit vectors e_theta, e_phi of its direction):
+// correctly rounded FP64 on the FP64 path; Newton-refined reciprocals on the FP32-amplitude path.
+template <class T>
+__device__ __forceinline__ void gluon_eps(const double* k, int lam, bool outgoing, cx<T>* w) {
+  const double kx = k[1], ky = k[2], kz = k[3];
+  const double kt2 = kx * kx + ky * ky;
+  double et[3], ep[3];
+  if (kt2 > 0.0) {
+    if constexpr (sizeof(T) == 8) {
+      const double kt = sqrt(kt2), ka = sqrt(kt2 + kz * kz);
+      const double inv = 1.0 / (ka * kt);
+      et[0] = kx * kz * inv; et[1] = ky * kz * inv; et[2] = -kt / ka;
+      ep[0] = -ky / kt; ep[1] = kx / kt; ep[2] = 0.0;
+    } else {
+      const double rt = rsqrt_nr(kt2), ra = rsqrt_nr(kt2 + kz * kz);
+      const double inv = ra * rt;
+      et[0] = kx * kz * inv; et[1] = ky * kz * inv; et[2] = -(kt2 * rt) * ra;
+      ep[0] = -ky * rt; ep[1] = kx * rt; ep[2] = 0.0;
+    }
+  } else {
+    et[0] = kz < 0.0 ? -1.0 : 1.0; et[1] = 0.0; et[2] = 0.0;
+    ep[0] = 0.0; ep[1] = 1.0; ep[2] = 0.0;
+  }
+  const double r = 0.70710678118654752440;
+  const double sl = lam > 0 ? -r : r;
+  const double si = outgoing ? r : -r;
+  w[0] = {T(0), T(0)};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) w[1 + i] = {T(sl * et[i]), T(si * ep[i])};
+}
+
+// ---- current algebra ----
+// acc += s * V3(JL, JR) with incoming momenta PL, PR.  The Feynman-gauge vertex contracted with the
+// two currents is (JL.JR)(PL - PR) + (JL.(PL + 2 PR)) JR - (JR.(2 PL + PR)) JL; Berends-Giele
+// currents of on-shell transverse gluons are conserved (P.J(P) = 0 exactly), so the JL.PL and JR.PR
+// parts vanish and the vertex is evaluated as (JL.JR)(PL - PR) + 2 (JL.PR) JR - 2 (JR.PL) JL: the
+// same value, without adding the rounding noise of two vanishing products (which 1/P^2 factors of
+// nearly collinear pairs amplify in FP32).
+template <class T>
+__device__ __forceinline__ void v3_acc(cx<T>* acc, const cx<T>* JL, const cx<T>* JR, const T* PL, const T* PR, bool neg) {
+  T d[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) d[m] = PL[m] - PR[m];
+  cx<T> jj = mdot(JL, JR), cl = mdotr(JL, PR), cr = mdotr(JR, PL);
+  const T two = neg ? T(-2) : T(2);
+  if (neg) jj = cneg(jj);
+  cl = cscale(two, cl);
+  cr = cscale(two, cr);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    cmacr(acc[m], d[m], jj);
+    cmac(acc[m], cl, JR[m]);
+    cmsub(acc[m], cr, JL[m]);
+  }
+}
+
+// acc += s * g * V4(JA, JB, JC), V4 = (JA.JB) JC + (JB.JC) JA - 2 (JA.JC) JB
+template <class T>
+__device__ __forceinline__ void v4_acc(cx<T>* acc, const cx<T>* JA, const cx<T>* JB, const cx<T>* JC, T g, bool neg) {
+  const T s = neg ? -g : g;
+  const cx<T> ab = cscale(s, mdot(JA, JB)), bc = cscale(s, mdot(JB, JC)), ac = cscale(T(2) * s, mdot(JA, JC));
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    cmac(acc[m], ab, JC[m]);
+    cmac(acc[m], bc, JA[m]);
+    cmsub(acc[m], ac, JB[m]);
+  }
+}
+
+// acc (+/-)= s gamma.J  (row spinor s, gluon current J)
+template <class T>
+__device__ __forceinline__ void row_gamma_acc(cx<T>* acc, const cx<T>* s, const cx<T>* J, bool neg) {
+  cx<T> jm = {J[1].r + J[2].i, J[1].i - J[2].r};   // J1 - i J2
+  cx<T> jp = {J[1].r - J[2].i, J[1].i + J[2].r};   // J1 + i J2
+  cx<T> a = {J[0].r + J[3].r, J[0].i + J[3].i}, b = {J[0].r - J[3].r, J[0].i - J[3].i};
+  if (neg) { jm = cneg(jm); jp = cneg(jp); a = cneg(a); b = cneg(b); }
+  cmac(acc[0], s[2], a); cmac(acc[0], s[3], jp);
+  cmac(acc[1], s[2], jm); cmac(acc[1], s[3], b);
+  cmac(acc[2], s[0], b); cmsub(acc[2], s[1], jp);
+  cmac(acc[3], s[1], a); cmsub(acc[3], s[0], jm);
+}
+
+// (gamma.J) v
+template <class T>
+__device__ __forceinline__ void gamma_col(const cx<T>* J, const cx<T>* v, cx<T>* o) {
+  const cx<T> jm = {J[1].r + J[2].i, J[1].i - J[2].r};
+  const cx<T> jp = {J[1].r - J[2].i, J[1].i + J[2].r};
+  const cx<T> a = {J[0].r + J[3].r, J[0].i + J[3].i}, b = {J[0].r - J[3].r, J[0].i - J[3].i};
+  o[0] = cmul(b, v[2]); cmsub(o[0], jm, v[3]);
+  o[1] = cmul(a, v[3]); cmsub(o[1], jp, v[2]);
+  o[2] = cmul(a, v[0]); cmac(o[2], jm, v[1]);
+  o[3] = cmul(jp, v[0]); cmac(o[3], b, v[1]);
+}
+
+// quark propagator with factor: o = s (Qslash + m) f, coefficients q = {(Q0+Q3) f, (Q0-Q3) f, Q1 f, Q2 f, m f}
+template <class T>
+__device__ __forceinline__ void row_prop(const cx<T>* s, const T* q, cx<T>* o) {
+  const T qa = q[0], qb = q[1], q1 = q[2], q2 = q[3], qm = q[4];
+  // o0 = qa s2 + (q1 + i q2) s3 + qm s0 ; o1 = (q1 - i q2) s2 + qb s3 + qm s1
+  // o2 = qb s0 - (q1 + i q2) s1 + qm s2 ; o3 = qa s1 - (q1 - i q2) s0 + qm s3
+  const cx<T> qp = {q1, q2}, qn = {q1, -q2};
+  o[0] = cscale(qa, s[2]); cmac(o[0], qp, s[3]); cmacr(o[0], qm, s[0]);
+  o[1] = cscale(qb, s[3]); cmac(o[1], qn, s[2]); cmacr(o[1], qm, s[1]);
+  o[2] = cscale(qb, s[0]); cmsub(o[2], qp, s[1]); cmacr(o[2], qm, s[2]);
+  o[3] = cscale(qa, s[1]); cmsub(o[3], qn, s[0]); cmacr(o[3], qm, s[3]);
+}
+
+template <class T> __device__ __forceinline__ void sdot_acc(cx<T>& c, const cx<T>* a, const cx<T>* b, bool neg) {
+  if (neg) { cmsub(c, a[0], b[0]); cmsub(c, a[1], b[1]); cmsub(c, a[2], b[2]); cmsub(c, a[3], b[3]); }
+  else { cmac(c, a[0], b[0]); cmac(c, a[1], b[1]); cmac(c, a[2], b[2]); cmac(c, a[3], b[3]); }
+}
+
+// quark current Jq^mu = ubar gamma^mu v
+template <class T> __device__ __forceinline__ void quark_current(const cx<T>* u, const cx<T>* v, cx<T>* Jq) {
+  // a = u[0..1], b = u[2..3], vL = v[0..1], vR = v[2..3]
+  const cx<T> a0r0 = cmul(u[0], v[2]), a0r1 = cmul(u[0], v[3]), a1r0 = cmul(u[1], v[2]), a1r1 = cmul(u[1], v[3]);
+  const cx<T> b0l0 = cmul(u[2], v[0]), b0l1 = cmul(u[2], v[1]), b1l0 = cmul(u[3], v[0]), b1l1 = cmul(u[3], v[1]);
+  Jq[0] = {a0r0.r + a1r1.r + b0l0.r + b1l1.r, a0r0.i + a1r1.i + b0l0.i + b1l1.i};
+  Jq[1] = {(a0r1.r + a1r0.r) - (b0l1.r + b1l0.r), (a0r1.i + a1r0.i) - (b0l1.i + b1l0.i)};
+  const cx<T> t = {(a1r0.r - a0r1.r) - (b1l0.r - b0l1.r), (a1r0.i - a0r1.i) - (b1l0.i - b0l1.i)};
+  Jq[2] = {-t.i, t.r};
+  Jq[3] = {(a0r0.r - a1r1.r) - (b0l0.r - b1l1.r), (a0r0.i - a1r1.i) - (b0l0.i - b1l1.i)};
+}
+
+// colour sum of one helicity: sum_a A_a^* (sum_b Ctri_ab A_b), packed upper triangle
+template <int NCOL, class T>
+__device__ __forceinline__ T colour_sum(const cx<T>* A, const T* __restrict__ ctri) {
+  T sum = 0;
+  int idx = 0;
+  for (int a = 0; a < NCOL; ++a) {
+    T wr = 0, wi = 0;
+    for (int b = a; b < NCOL; ++b, ++idx) {
+      const T c = __ldg(ctri + idx);
+      wr = fma(c, A[b].r, wr);
+      wi = fma(c, A[b].i, wi);
+    }
+    sum = fma(A[a].r, wr, sum);
+    sum = fma(A[a].i, wi, sum);
+  }
+  return sum;
+}
+
+// ---- per-event data shared by every helicity of an event (FP64 arithmetic, stored as T) ----
+// Layout of one event's record (NITEM values of T): PT[S][4] (incoming gluon momentum of subset S),
+// gprop[S] (-g/P_S^2), qc[S][5] (quark propagator coefficients), eps[g][hel][4] complex,
+// ubar[hel][4] complex, v[hel][4] complex.
+template <int K> struct EvLayout {
+  static constexpr int NSUB = 1 << K;
+  static constexpr int PT = 0, GP = 4 * NSUB, QC = 5 * NSUB, EPS = 10 * NSUB, UB = EPS + 16 * K, VV = UB + 16;
+  static constexpr int NITEM = VV + 16;
+};
+
+template <int K, class T>
+__device__ __forceinline__ void event_data(const double (*p)[4], const MeConst& cst, T (*PT)[4], T* gprop, T (*qc)[5],
+                                           cx<T> (*eps)[2][4], cx<T> (*ub)[4], cx<T> (*vv)[4],
+                                           double* min_invariant = nullptr) {
+  constexpr int NSUB = 1 << K;
+  double xmin = 1e300;
+  double Pst[NSUB][4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) Pst[0][m] = 0.0;
+#pragma unroll
+  for (int S = 1; S < NSUB; ++S) {
+    const int g = __ffs(S) - 1;
+    const int part = g < 2 ? g : g + 2;
+    const double sg = g < 2 ? 1.0 : -1.0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) Pst[S][m] = Pst[S & (S - 1)][m] + sg * p[part][m];
+  }
+#pragma unroll
+  for (int S = 0; S < NSUB; ++S) {
+    const double* P = Pst[S];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) PT[S][m] = static_cast<T>(P[m]);
+    const double p2 = P[0] * P[0] - P[1] * P[1] - P[2] * P[2] - P[3] * P[3];
+    const double Q0 = p[2][0] - P[0], Q1 = p[2][1] - P[1], Q2 = p[2][2] - P[2], Q3 = p[2][3] - P[3];
+    const double dq = Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3 - cst.mt * cst.mt;
+    if (S != 0 && S != NSUB - 1) {   // internal lines only (S = 0 and S = all are the external tops)
+      xmin = fmin(xmin, fabs(dq));
+      if (S & (S - 1)) xmin = fmin(xmin, fabs(p2));
+    }
+    if constexpr (sizeof(T) == 8) {
+      gprop[S] = static_cast<T>((S & (S - 1)) ? -cst.gs / p2 : 0.0);   // includes one power of g
+      const double f = -cst.gs / dq;
+      qc[S][0] = static_cast<T>((Q0 + Q3) * f);
+      qc[S][1] = static_cast<T>((Q0 - Q3) * f);
+      qc[S][2] = static_cast<T>(Q1 * f);
+      qc[S][3] = static_cast<T>(Q2 * f);
+      qc[S][4] = static_cast<T>(cst.mt * f);
+    } else {
+      // FP32 amplitudes: the denominators P^2 and Q^2 - m^2 (where the cancellations are) and the
+      // products in FP64, the reciprocals Newton-refined from FP32 seeds; one rounding to FP32 at the end
+      gprop[S] = static_cast<T>((S & (S - 1)) ? -cst.gs * rcp_nr(p2) : 0.0);
+      const double f = -cst.gs * rcp_nr(dq);
+      qc[S][0] = static_cast<T>((Q0 + Q3) * f);
+      qc[S][1] = static_cast<T>((Q0 - Q3) * f);
+      qc[S][2] = static_cast<T>(Q1 * f);
+      qc[S][3] = static_cast<T>(Q2 * f);
+      qc[S][4] = static_cast<T>(cst.mt * f);
+    }
+  }
+#pragma unroll
+  for (int g = 0; g < K; ++g) {
+    const int part = g < 2 ? g : g + 2;
+    gluon_eps<T>(p[part], -1, g >= 2, eps[g][0]);
+    gluon_eps<T>(p[part], 1, g >= 2, eps[g][1]);
+  }
+  top_ubar<T>(p[2], cst.mt, -1, ub[0]);
+  top_ubar<T>(p[2], cst.mt, 1, ub[1]);
+  top_v<T>(p[3], cst.mt, -1, vv[0]);
+  top_v<T>(p[3], cst.mt, 1, vv[1]);
+  if (min_invariant) {
+    const double s0 = p[0][0] + p[1][0], s1 = p[0][1] + p[1][1], s2 = p[0][2] + p[1][2], s3 = p[0][3] + p[1][3];
+    const double shat = s0 * s0 - s1 * s1 - s2 * s2 - s3 * s3;   // (p1 + p2)^2
+    *min_invariant = xmin / fabs(shat);
+  }
+}
+
+}  // namespace v2
+}  // namespace mg

@@ -39,12 +39,21 @@ bool cache_lookup(const char* path, const std::string& key, mg::MeShape* shape, 
   if (!path) return false;
   FILE* f = std::fopen(path, "r");
   if (!f) return false;
-  char k[256];
-  int tev = 0, sm = 0;
-  double t = 0;
+  char line[512];
   bool found = false;
-  while (std::fscanf(f, "%255s %d %d %lf", k, &tev, &sm, &t) == 4)
-    if (key == k) { shape->tile_ev = tev; shape->slot_major = sm != 0; *ms = t; found = true; }
+  while (std::fgets(line, sizeof(line), f)) {
+    char k[256];
+    int tev = 0, sm = 0, un = 1;
+    double t = 0;
+    if (std::sscanf(line, "%255s %d %d %d %lf", k, &tev, &sm, &un, &t) != 5) continue;
+    if (key == k && (tev == 32 || tev == 64 || tev == 128)) {
+      shape->tile_ev = tev;
+      shape->slot_major = sm != 0;
+      shape->unrolled = un != 0;
+      *ms = t;
+      found = true;
+    }
+  }
   std::fclose(f);
   return found;
 }
@@ -53,7 +62,7 @@ void cache_store(const char* path, const std::string& key, const mg::MeShape& s,
   if (!path) return;
   FILE* f = std::fopen(path, "a");
   if (!f) return;
-  std::fprintf(f, "%s %d %d %.6f\n", key.c_str(), s.tile_ev, s.slot_major ? 1 : 0, ms);
+  std::fprintf(f, "%s %d %d %d %.6f\n", key.c_str(), s.tile_ev, s.slot_major ? 1 : 0, s.unrolled ? 1 : 0, ms);
   std::fclose(f);
 }
 
@@ -88,11 +97,15 @@ extern "C" mg_status mg_autotune(mg_ctx* ctx, mg_precision precision, int64_t ne
   if (rc == MG_OK) rc = mg_rambo(ctx, 0x7E57, nevt, 1500.0, mom, nullptr, st);
   if (rc == MG_OK) rc = mg_hel_filter(ctx, mom, nevt, st);
   const int tiles[3] = {32, 64, 128};
+  const bool fp32 = precision == MG_FP32_AMP || precision == MG_MIXED;
+  const int nun = mg::me_static_available(ctx->K, fp32) && ctx->prm.wt == 0.0 ? 2 : 1;
+  for (int un = 0; un < nun && rc == MG_OK; ++un)
   for (int ti = 0; ti < 3 && rc == MG_OK; ++ti)
     for (int sm = 0; sm < 2 && rc == MG_OK; ++sm) {
       mg::MeShape s;
       s.tile_ev = tiles[ti];
       s.slot_major = sm != 0;
+      s.unrolled = nun == 2 ? un == 0 : true;
       ctx->shape[precision] = s;
       rc = mg_sigmakin(ctx, mom, nevt, precision, me, st);   // warm-up (and scratch growth)
       float t = 1e30f;
@@ -122,10 +135,24 @@ extern "C" mg_status mg_autotune(mg_ctx* ctx, mg_precision precision, int64_t ne
   return rc;
 }
 
-extern "C" mg_status mg_get_launch_shape(mg_ctx* ctx, mg_precision precision, int* tile_ev, int* slot_major) {
+extern "C" mg_status mg_get_launch_shape(mg_ctx* ctx, mg_precision precision, int* tile_ev, int* slot_major,
+                                         int* unrolled) {
   if (!ctx || precision < MG_FP64 || precision > MG_MIXED) return MG_EINVAL;
   if (tile_ev) *tile_ev = ctx->shape[precision].tile_ev;
   if (slot_major) *slot_major = ctx->shape[precision].slot_major ? 1 : 0;
+  if (unrolled) *unrolled = ctx->shape[precision].unrolled ? 1 : 0;
+  return MG_OK;
+}
+
+extern "C" mg_status mg_set_launch_shape(mg_ctx* ctx, mg_precision precision, int tile_ev, int slot_major,
+                                         int unrolled) {
+  if (!ctx || precision < MG_FP64 || precision > MG_MIXED) return MG_EINVAL;
+  if ((tile_ev != 32 && tile_ev != 64 && tile_ev != 128) || (slot_major != 0 && slot_major != 1) ||
+      (unrolled != 0 && unrolled != 1))
+    return MG_EINVAL;
+  ctx->shape[precision].tile_ev = tile_ev;
+  ctx->shape[precision].slot_major = slot_major != 0;
+  ctx->shape[precision].unrolled = unrolled != 0;
   return MG_OK;
 }
 

@@ -97,6 +97,14 @@ def test_flop_model(mg):
         mask[0] = 1
         amp1, col1 = mg.flops_per_event(proc, mask)
         assert col1 == 4.0 * n * (n + 1) / 2 + 4 * n and 0 < amp1 < amp
+        # the tensor-core colour mode keeps the FP64 amplitude algorithm; the FP32 modes form (gamma.J) v
+        # per jamp term instead of tabulating it, the same colour sums
+        assert mg.flops_per_event(proc, None, mg.MG_FP64_TCCOLOR) == (amp, col)
+        a32, c32 = mg.flops_per_event(proc, None, mg.MG_FP32_AMP)
+        assert c32 == col and a32 != amp
+        assert mg.flops_per_event(proc, None, mg.MG_MIXED) == (a32, c32)
+    with pytest.raises(mg.MGError):
+        mg.flops_per_event("ggttg", None, 7)
 
 
 def test_invalid_arguments_rejected_without_gpu(mg):
