@@ -8,7 +8,9 @@
 //   * every row (the real or the imaginary part of one jamp vector) is scaled by a power of two to
 //     max |a| in [1/2, 1) and split a = hi + lo 2^-11 with hi, lo FP16, so a is carried to ~22 bits;
 //   * Y = C a is accumulated in FP32 (two accumulators, hi and lo), and the row's quadratic form
-//     a . Y is formed in FP32 with the unsplit (FP32) a, then unscaled exactly.
+//     a . Y is formed in FP32 with a = hi + lo 2^-11, then unscaled exactly;
+//   * each warp stages its next tile of jamp vectors into shared memory with cp.async while it computes
+//     the current one, whose A fragments are built once in registers for all column tiles.
 // Relative error per (event, helicity) ~1e-7 (the colour matrices are well conditioned: kappa <= 16).
 // Rows: jamps[(e * rows_alloc + r) * ncol + sigma] (FP32 complex), r < *nrows_dev; output:
 // out[r * stride + e] = colour sum * scale, in FP64.
@@ -32,111 +34,168 @@ __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, const uint
 template <int NCOL>
 struct TcShape {
   static constexpr int KP = (NCOL + 15) / 16 * 16;   // contraction length, padded to the MMA k
+  static constexpr int KS = KP / 16;                 // MMA k steps
   static constexpr int NT = (NCOL + 7) / 8;          // output column tiles of 8
   static constexpr int NP = NT * 8;
-  static constexpr int LDH = KP + 8;                 // half pitch (breaks bank conflicts)
-  static constexpr int LDF = KP + 4;                 // float pitch
+  static constexpr int LDH = KP + 8;                 // half pitch of C (breaks bank conflicts)
   static constexpr int WARPS = 4;
-  static constexpr size_t smem_bytes() {
-    return sizeof(__half) * (size_t(NP) * LDH + size_t(WARPS) * 2 * 16 * LDH) + sizeof(float) * size_t(WARPS) * 16 * LDF;
-  }
+  static constexpr int CHUNKS = 8 * NCOL / 2;        // 16-byte pieces of one tile (8 jamp vectors)
+  static constexpr size_t c_bytes() { return sizeof(__half) * size_t(NP) * LDH; }
+  static constexpr size_t smem_bytes() { return c_bytes() + sizeof(float2) * size_t(WARPS) * 2 * 8 * NCOL; }
 };
 
+__device__ __forceinline__ void cp_async16(void* dst_smem, const void* src, bool valid) {
+  const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(dst_smem));
+  const int n = valid ? 16 : 0;   // 0: nothing is read, the 16 bytes are zero-filled
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_h2(__half lo_half, __half hi_half) {
+  return static_cast<uint32_t>(__half_as_ushort(lo_half)) | (static_cast<uint32_t>(__half_as_ushort(hi_half)) << 16);
+}
+
+// hi/lo FP16 split of a scaled value t: t ~ hi + lo 2^-11
+__device__ __forceinline__ void split_h(float t, __half& hi, __half& lo) {
+  hi = __float2half_rn(t);
+  lo = __float2half_rn((t - __half2float(hi)) * 2048.f);
+}
+
+// value of the FP16 pair element k (0 low, 1 high) of a hi/lo split, as FP32
+__device__ __forceinline__ float unsplit(uint32_t h, uint32_t l, int k) {
+  const __half hh = __ushort_as_half(static_cast<unsigned short>(k ? h >> 16 : h & 0xffffu));
+  const __half lh = __ushort_as_half(static_cast<unsigned short>(k ? l >> 16 : l & 0xffffu));
+  return fmaf(__half2float(lh), 1.f / 2048.f, __half2float(hh));
+}
+
+// One warp per tile of 8 (event, helicity) jamp vectors = 16 MMA rows (row 2p: Re, 2p+1: Im of vector p),
+// tiles strided over the grid.  The next tile is staged into shared memory with cp.async while the
+// current one is computed; the current tile's A fragments (hi and lo) are built once, in registers, and
+// serve every column tile of Y = C a and the row's quadratic form a . Y.
 template <int NCOL>
 __global__ void __launch_bounds__(128) k_colour_tc(const float2* __restrict__ jamps, int64_t nevt, int rows_alloc,
                                                    const int* __restrict__ nrows_dev, const __half* __restrict__ cmat,
                                                    double scale, double* __restrict__ out, int64_t stride,
                                                    const uint8_t* __restrict__ skip) {
   using S = TcShape<NCOL>;
-  constexpr int KP = S::KP, NT = S::NT, NP = S::NP, LDH = S::LDH, LDF = S::LDF;
+  constexpr int KS = S::KS, NT = S::NT, NP = S::NP, LDH = S::LDH;
   extern __shared__ __align__(16) unsigned char smem[];
   __half* sC = reinterpret_cast<__half*>(smem);                       // [NP][LDH]: C[n][k]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  __half* sHi = sC + NP * LDH + warp * 2 * 16 * LDH;                  // [16][LDH]
-  __half* sLo = sHi + 16 * LDH;
-  float* sF = reinterpret_cast<float*>(sC + NP * LDH + S::WARPS * 2 * 16 * LDH) + warp * 16 * LDF;   // [16][LDF]
+  float2* sRaw = reinterpret_cast<float2*>(smem + S::c_bytes()) + warp * 2 * 8 * NCOL;   // [2][8][NCOL]
 
   for (int i = threadIdx.x; i < NP * LDH; i += blockDim.x) sC[i] = cmat[i];
   __syncthreads();
 
   const int nrows = *nrows_dev;
   const int64_t npairs = nevt * nrows;
+  const int64_t ntiles = (npairs + 7) / 8;
+  const int64_t tstep = static_cast<int64_t>(gridDim.x) * S::WARPS;
   const int g = lane >> 2, q = lane & 3;
-  for (int64_t tile = static_cast<int64_t>(blockIdx.x) * S::WARPS + warp; tile * 8 < npairs;
-       tile += static_cast<int64_t>(gridDim.x) * S::WARPS) {
-    // stage 8 (event, helicity) jamp vectors as 16 rows: row 2p = Re, 2p+1 = Im of pair p
-    for (int idx = lane; idx < 8 * KP; idx += 32) {
-      const int p = idx / KP, b = idx - p * KP;
+
+  auto stage = [&](int64_t tile, int buf) {
+    float2* dst = sRaw + buf * 8 * NCOL;
+    for (int i = lane; i < S::CHUNKS; i += 32) {
+      const int p = i / (NCOL / 2), w = i - p * (NCOL / 2);
       const int64_t qq = tile * 8 + p;
-      float2 v = make_float2(0.f, 0.f);
-      if (qq < npairs && b < NCOL) {
+      const float2* src = jamps;
+      bool valid = false;
+      if (tile < ntiles && qq < npairs) {
         const int64_t e = qq / nrows;
         const int r = static_cast<int>(qq - e * nrows);
-        if (!skip || !skip[e]) v = jamps[(e * rows_alloc + r) * NCOL + b];   // skipped events: no jamps
+        valid = !skip || !skip[e];   // skipped events: no jamps (zeros)
+        src = jamps + (e * rows_alloc + r) * NCOL + 2 * w;
       }
-      sF[(2 * p) * LDF + b] = v.x;
-      sF[(2 * p + 1) * LDF + b] = v.y;
+      cp_async16(dst + p * NCOL + 2 * w, src, valid);
     }
+    cp_async_commit();
+  };
+
+  int64_t tile = static_cast<int64_t>(blockIdx.x) * S::WARPS + warp;
+  int buf = 0;
+  if (tile < ntiles) stage(tile, 0);
+  for (; tile < ntiles; tile += tstep, buf ^= 1) {
+    stage(tile + tstep, buf ^ 1);   // next tile (an empty group past the end)
+    cp_async_wait1();
     __syncwarp();
-    // per-row power-of-two scale and hi/lo split: two lanes per row
-    const int row = lane >> 1, half = lane & 1;
-    float mx = 0.f;
-    for (int b = half; b < KP; b += 2) mx = fmaxf(mx, fabsf(sF[row * LDF + b]));
-    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
-    int ex = 0;
-    if (mx > 0.f) frexpf(mx, &ex);
-    const float sc = ldexpf(1.f, -ex);
-    for (int b = half; b < KP; b += 2) {
-      const float t = sF[row * LDF + b] * sc;
-      const __half hi = __float2half_rn(t);
-      const __half lo = __float2half_rn((t - __half2float(hi)) * 2048.f);
-      sF[row * LDF + b] = t;
-      sHi[row * LDH + b] = hi;
-      sLo[row * LDH + b] = lo;
-    }
-    __syncwarp();
-    // Y = C a (rows g and g+8 of this thread's fragments), then the quadratic form a . Y
+    const float2* raw = sRaw + buf * 8 * NCOL;
+    // rows g and g + 8 of the MMA tile: vectors g/2 and g/2 + 4, real (g even) or imaginary part
+    const float2* v0 = raw + (g >> 1) * NCOL;
+    const float2* v1 = raw + ((g >> 1) + 4) * NCOL;
+    const bool im = g & 1;
+    auto elem = [&](const float2* v, int c) -> float {
+      if (c >= NCOL) return 0.f;
+      const float2 x = v[c];
+      return im ? x.y : x.x;
+    };
+    // per-row power-of-two scale: max |a| over the row (4 lanes of a quad hold it)
+    float m0 = 0.f, m1 = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = ks * 16 + 2 * q + (j & 1) + (j >> 1) * 8;
+        m0 = fmaxf(m0, fabsf(elem(v0, c)));
+        m1 = fmaxf(m1, fabsf(elem(v1, c)));
+      }
+    m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, 1));
+    m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, 2));
+    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 1));
+    m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 2));
+    int ex0 = 0, ex1 = 0;
+    if (m0 > 0.f) frexpf(m0, &ex0);
+    if (m1 > 0.f) frexpf(m1, &ex1);
+    const float sc0 = ldexpf(1.f, -ex0), sc1 = ldexpf(1.f, -ex1);
+    // A fragments (m16n8k16, row-major A): regs 0/1 rows g / g+8 at k = 2q, 2q+1; regs 2/3 at k + 8
+    uint32_t ah[KS][4], al[KS][4];
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+      for (int rg = 0; rg < 4; ++rg) {
+        const int c = ks * 16 + 2 * q + (rg >> 1) * 8;
+        const float2* v = (rg & 1) ? v1 : v0;
+        const float sc = (rg & 1) ? sc1 : sc0;
+        __half h0, l0, h1, l1;
+        split_h(elem(v, c) * sc, h0, l0);
+        split_h(elem(v, c + 1) * sc, h1, l1);
+        ah[ks][rg] = pack_h2(h0, h1);
+        al[ks][rg] = pack_h2(l0, l1);
+      }
+    __syncwarp();   // this buffer is staged again two tiles later
+    // Y = C a, column tile by column tile; the quadratic form a . Y of rows g and g + 8
     float s0 = 0.f, s1 = 0.f;
-#pragma unroll 1
+#pragma unroll
     for (int nt = 0; nt < NT; ++nt) {
       float dh[4] = {0.f, 0.f, 0.f, 0.f}, dl[4] = {0.f, 0.f, 0.f, 0.f};
+      const __half* cb = sC + (nt * 8 + g) * LDH + 2 * q;
 #pragma unroll
-      for (int ks = 0; ks < KP / 16; ++ks) {
-        const int k0 = ks * 16 + q * 2;
-        uint32_t ah[4], al[4], bf[2];
-        ah[0] = *reinterpret_cast<const uint32_t*>(sHi + g * LDH + k0);
-        ah[1] = *reinterpret_cast<const uint32_t*>(sHi + (g + 8) * LDH + k0);
-        ah[2] = *reinterpret_cast<const uint32_t*>(sHi + g * LDH + k0 + 8);
-        ah[3] = *reinterpret_cast<const uint32_t*>(sHi + (g + 8) * LDH + k0 + 8);
-        al[0] = *reinterpret_cast<const uint32_t*>(sLo + g * LDH + k0);
-        al[1] = *reinterpret_cast<const uint32_t*>(sLo + (g + 8) * LDH + k0);
-        al[2] = *reinterpret_cast<const uint32_t*>(sLo + g * LDH + k0 + 8);
-        al[3] = *reinterpret_cast<const uint32_t*>(sLo + (g + 8) * LDH + k0 + 8);
-        const int n = nt * 8 + g;
-        bf[0] = *reinterpret_cast<const uint32_t*>(sC + n * LDH + k0);
-        bf[1] = *reinterpret_cast<const uint32_t*>(sC + n * LDH + k0 + 8);
-        mma16816(dh, ah, bf);
-        mma16816(dl, al, bf);
+      for (int ks = 0; ks < KS; ++ks) {
+        uint32_t bf[2];
+        bf[0] = *reinterpret_cast<const uint32_t*>(cb + ks * 16);
+        bf[1] = *reinterpret_cast<const uint32_t*>(cb + ks * 16 + 8);
+        mma16816(dh, ah[ks], bf);
+        mma16816(dl, al[ks], bf);
       }
-      const int c = nt * 8 + q * 2;
+      // this thread's Y columns nt*8 + 2q, +1 are the a columns it holds in k step nt/2, half nt%2
+      const int ksa = nt >> 1, hb = (nt & 1) * 2;
       const float r = 1.f / 2048.f;
-      s0 = fmaf(sF[g * LDF + c], fmaf(dl[0], r, dh[0]), s0);
-      s0 = fmaf(sF[g * LDF + c + 1], fmaf(dl[1], r, dh[1]), s0);
-      s1 = fmaf(sF[(g + 8) * LDF + c], fmaf(dl[2], r, dh[2]), s1);
-      s1 = fmaf(sF[(g + 8) * LDF + c + 1], fmaf(dl[3], r, dh[3]), s1);
+      s0 = fmaf(unsplit(ah[ksa][hb], al[ksa][hb], 0), fmaf(dl[0], r, dh[0]), s0);
+      s0 = fmaf(unsplit(ah[ksa][hb], al[ksa][hb], 1), fmaf(dl[1], r, dh[1]), s0);
+      s1 = fmaf(unsplit(ah[ksa][hb + 1], al[ksa][hb + 1], 0), fmaf(dl[2], r, dh[2]), s1);
+      s1 = fmaf(unsplit(ah[ksa][hb + 1], al[ksa][hb + 1], 1), fmaf(dl[3], r, dh[3]), s1);
     }
     s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
     s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
     s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
     s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
-    // undo the row scales (exact powers of two): rows g and g+8 belong to lanes 2g and 2(g+8)
-    const float sc0 = __shfl_sync(0xffffffffu, sc, 2 * g);
-    const float sc1 = __shfl_sync(0xffffffffu, sc, 2 * (g + 8));
-    const double v0 = static_cast<double>(s0) / (static_cast<double>(sc0) * sc0);
-    const double v1 = static_cast<double>(s1) / (static_cast<double>(sc1) * sc1);
-    // rows 2p (Re) and 2p+1 (Im) of a pair sit in quads g and g^1
-    const double w0 = v0 + __shfl_xor_sync(0xffffffffu, v0, 4);
-    const double w1 = v1 + __shfl_xor_sync(0xffffffffu, v1, 4);
+    // undo the row scales (exact powers of two)
+    const double v0d = static_cast<double>(s0) / (static_cast<double>(sc0) * sc0);
+    const double v1d = static_cast<double>(s1) / (static_cast<double>(sc1) * sc1);
+    // the real and imaginary rows of a vector sit in quads g and g^1 (lanes 4 apart)
+    const double w0 = v0d + __shfl_xor_sync(0xffffffffu, v0d, 4);
+    const double w1 = v1d + __shfl_xor_sync(0xffffffffu, v1d, 4);
     if (q == 0 && (g & 1) == 0) {
       const int64_t qa = tile * 8 + g / 2, qb = tile * 8 + 4 + g / 2;
       if (qa < npairs) {
@@ -148,8 +207,8 @@ __global__ void __launch_bounds__(128) k_colour_tc(const float2* __restrict__ ja
         if (!skip || !skip[e]) out[(qb - e * nrows) * stride + e] = w1 * scale;
       }
     }
-    __syncwarp();
   }
+  cp_async_wait0();
 }
 
 template <int NCOL>
@@ -163,12 +222,14 @@ cudaError_t launch_tc(const float2* jamps, int64_t nevt, int rows_alloc, const i
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  int dev = 0, nsm = 0;
+  int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_colour_tc<NCOL>, 128, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
   const int64_t tiles = (nevt * rows_alloc + 7) / 8;
   int64_t blocks = (tiles + S::WARPS - 1) / S::WARPS;
-  const int64_t cap = static_cast<int64_t>(nsm) * 8;
+  const int64_t cap = static_cast<int64_t>(nsm) * per_sm;   // resident blocks; tiles are strided over them
   if (blocks > cap) blocks = cap;
   if (blocks < 1) return cudaSuccess;
   k_colour_tc<NCOL><<<static_cast<unsigned>(blocks), 128, smem, st>>>(jamps, nevt, rows_alloc, nrows, cmat, scale, out,

@@ -40,10 +40,10 @@ __global__ void __launch_bounds__(128) k_event_prep(const double* __restrict__ m
   for (int i = 0; i < npar; ++i)
 #pragma unroll
     for (int m = 0; m < 4; ++m) p[i][m] = __ldg(base + (i * 4 + m) * kPage);
-  T PT[NSUB][4], gprop[NSUB], qc[NSUB][5];
-  cx<T> eps[K][2][4], ub[2][4], vv[2][4];
+  T PT[NSUB][4], gprop[NSUB], qc[NSUB][5], pol[K][5];
+  cx<T> ub[2][4], vv[2][4];
   double xmin = 1.0;
-  event_data<K, T>(p, cst, PT, gprop, qc, eps, ub, vv, &xmin);
+  event_data<K, T>(p, cst, PT, gprop, qc, pol, ub, vv, &xmin);
   const bool redo = repair && xmin < cst.fp32_tau;
   if (redo) repair[atomicAdd(nrepair, 1)] = static_cast<int>(e);
   if (flag) flag[e] = redo ? 1 : 0;
@@ -59,12 +59,7 @@ __global__ void __launch_bounds__(128) k_event_prep(const double* __restrict__ m
 #pragma unroll
   for (int g = 0; g < K; ++g)
 #pragma unroll
-    for (int l = 0; l < 2; ++l)
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        out[(L::EPS + ((g * 2 + l) * 4 + m) * 2) * kPage] = eps[g][l][m].r;
-        out[(L::EPS + ((g * 2 + l) * 4 + m) * 2 + 1) * kPage] = eps[g][l][m].i;
-      }
+    for (int i = 0; i < 5; ++i) out[(L::EPS + 5 * g + i) * kPage] = pol[g][i];
 #pragma unroll
   for (int l = 0; l < 2; ++l)
 #pragma unroll
@@ -121,11 +116,10 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
     }
 #pragma unroll
     for (int g = 0; g < K; ++g) {
-      const int l = (gc >> g) & 1;
+      T pol[5];
 #pragma unroll
-      for (int m = 0; m < 4; ++m)
-        J[g][m] = {__ldg(in + (L::EPS + ((g * 2 + l) * 4 + m) * 2) * kPage),
-                   __ldg(in + (L::EPS + ((g * 2 + l) * 4 + m) * 2 + 1) * kPage)};
+      for (int i = 0; i < 5; ++i) pol[i] = __ldg(in + (L::EPS + 5 * g + i) * kPage);
+      ext_gluon(pol, (gc >> g) & 1 ? 1 : -1, g >= 2, J[g]);
     }
 #pragma unroll
     for (int l = 0; l < 2; ++l)
@@ -141,12 +135,10 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
     for (int i = 0; i < npar; ++i)
 #pragma unroll
       for (int m = 0; m < 4; ++m) p[i][m] = __ldg(base + (i * 4 + m) * kPage);
-    cx<T> eps[K][2][4];
-    event_data<K, T>(p, cst, PT, gprop, qc, eps, ub, vv);
+    T pol[K][5];
+    event_data<K, T>(p, cst, PT, gprop, qc, pol, ub, vv);
 #pragma unroll
-    for (int g = 0; g < K; ++g)
-#pragma unroll
-      for (int m = 0; m < 4; ++m) J[g][m] = eps[g][(gc >> g) & 1][m];
+    for (int g = 0; g < K; ++g) ext_gluon(pol[g], (gc >> g) & 1 ? 1 : -1, g >= 2, J[g]);
   }
 
   // ---- gluon currents (helicities of gc) ----
@@ -263,7 +255,7 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
         A[1][c] = amp1;
       }
     }
-    if (JOUT) {
+    if constexpr (JOUT) {
 #pragma unroll
       for (int b = 0; b < 2; ++b) {
         const bool good = b ? good1 : good0;
@@ -272,15 +264,16 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
           row[c] = good ? make_float2(static_cast<float>(A[b][c].r), static_cast<float>(A[b][c].i)) : make_float2(0.f, 0.f);
       }
       continue;
-    }
+    } else {
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const int h = b ? h1 : h0;
-      const bool good = b ? good1 : good0;
-      if (!good) continue;
-      const double v = static_cast<double>(colour_sum<NCOL, T>(A[b], ctri)) * cst.colour_scale;
-      if (PER_HEL) out[h * stride + e] = v;
-      else total += v;
+      for (int b = 0; b < 2; ++b) {
+        const int h = b ? h1 : h0;
+        const bool good = b ? good1 : good0;
+        if (!good) continue;
+        const double v = static_cast<double>(colour_sum<NCOL, T>(A[b], ctri)) * cst.colour_scale;
+        if (PER_HEL) out[h * stride + e] = v;
+        else total += v;
+      }
     }
   }
   if (!PER_HEL && !JOUT) {

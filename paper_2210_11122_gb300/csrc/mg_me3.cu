@@ -71,9 +71,10 @@ k_me_static(const T* __restrict__ rec, int64_t nevt, const int* __restrict__ gsl
   cx<T> J[NSEQ][4];
   sfor<0, K>([&](auto gI) {
     constexpr int g = decltype(gI)::value;
-    const int item = L::EPS + (g * 2 + ((gc >> g) & 1)) * 8;
+    T pol[5];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) J[g][m] = {ld(item + 2 * m), ld(item + 2 * m + 1)};
+    for (int i = 0; i < 5; ++i) pol[i] = ld(L::EPS + 5 * g + i);
+    v2::ext_gluon(pol, (gc >> g) & 1 ? 1 : -1, g >= 2, J[g]);
   });
   sfor<K, NSEQ>([&](auto sI) {
     constexpr int s = decltype(sI)::value;

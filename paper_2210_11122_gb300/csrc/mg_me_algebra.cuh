@@ -57,14 +57,49 @@ template <> struct Sizes<5> { static constexpr int ncol = 120, nseq = 105, nfull
 __device__ __forceinline__ int rslot(int16_t r) { return r >> 1; }
 __device__ __forceinline__ bool rneg(int16_t r) { return r & 1; }
 
-// ---- external wavefunctions (FP64) ----
-__device__ __forceinline__ void chi2(const double* p, int lam, cx<double>* c) {
+// ---- FP64 helpers of the per-event record ----
+// Reciprocal and reciprocal square root for the FP32-amplitude path's record: an FP32 seed refined by
+// one Newton-Raphson step in FP64 (r <- r (2 - x r) for 1/x, y <- y (3 - x y^2) / 2 for 1/sqrt(x); each
+// step squares the seed's relative error, ~2^-23 -> ~2^-45), so that the values stored in FP32 carry
+// only their final rounding, at a fraction of the FP64 cost of a correctly rounded division.  Outside
+// 2^-99 < |x| < 2^99 (tested on the exponent bits, on the integer pipe) the FP64 operation is used.
+__device__ __forceinline__ bool in_f32_range(double x) {
+  const int e = (__double2hiint(x) >> 20) & 0x7ff;
+  return e > 1023 - 99 && e < 1023 + 99;
+}
+__device__ __forceinline__ double rcp_nr(double x) {
+  if (!in_f32_range(x)) return 1.0 / x;
+  const double r0 = static_cast<double>(__frcp_rn(static_cast<float>(x)));
+  return r0 * fma(-x, r0, 2.0);
+}
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  if (!(__double2hiint(x) > 0 && in_f32_range(x))) return rsqrt(x);
+  const double y0 = static_cast<double>(rsqrtf(static_cast<float>(x)));
+  return y0 * fma(-0.5 * x * y0, y0, 1.5);
+}
+// NR = false: correctly rounded FP64 operations (FP64 path); true: the Newton-refined forms above
+template <bool NR> __device__ __forceinline__ double r_sqrt(double x) {
+  if constexpr (NR) return x > 0.0 ? x * rsqrt_nr(x) : 0.0;
+  else return sqrt(x);
+}
+template <bool NR> __device__ __forceinline__ double r_rsqrt(double x) {
+  if constexpr (NR) return rsqrt_nr(x);
+  else return rsqrt(x);
+}
+template <bool NR> __device__ __forceinline__ double r_div(double a, double b) {
+  if constexpr (NR) return a * rcp_nr(b);
+  else return a / b;
+}
+
+// ---- external wavefunctions (FP64 arithmetic) ----
+// two-component helicity eigenstates chi_lam of the direction of p
+template <bool NR>
+__device__ __forceinline__ void chi2(const double* p, double pa, int lam, cx<double>* c) {
   const double px = p[1], py = p[2], pz = p[3];
   const double pt2 = px * px + py * py;
-  const double pa = sqrt(pt2 + pz * pz);
-  const double apz = pz >= 0.0 ? pa + pz : pt2 / (pa - pz);
+  const double apz = pz >= 0.0 ? pa + pz : r_div<NR>(pt2, pa - pz);
   if (apz > 0.0) {
-    const double n = rsqrt(2.0 * pa * apz);
+    const double n = r_rsqrt<NR>(2.0 * pa * apz);
     if (lam > 0) { c[0] = {apz * n, 0.0}; c[1] = {px * n, py * n}; }
     else { c[0] = {-px * n, py * n}; c[1] = {apz * n, 0.0}; }
   } else {
@@ -73,13 +108,27 @@ __device__ __forceinline__ void chi2(const double* p, int lam, cx<double>* c) {
   }
 }
 
+// |p|, sqrt(E + |p|) and m / sqrt(E + |p|) of a massive fermion
+template <bool NR>
+__device__ __forceinline__ void spinor_norms(const double* p, double m, double& pa, double& sp, double& sm) {
+  pa = r_sqrt<NR>(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+  if constexpr (NR) {
+    const double rs = rsqrt_nr(p[0] + pa);
+    sp = (p[0] + pa) * rs;
+    sm = m > 0.0 ? m * rs : 0.0;
+  } else {
+    sp = sqrt(p[0] + pa);
+    sm = m > 0.0 ? m / sp : 0.0;
+  }
+}
+
 template <class T>
 __device__ __forceinline__ void top_ubar(const double* p, double m, int lam, cx<T>* w) {
-  const double pa = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
-  const double sp = sqrt(p[0] + pa);
-  const double sm = m > 0.0 ? m / sp : 0.0;
+  constexpr bool NR = sizeof(T) == 4;
+  double pa, sp, sm;
+  spinor_norms<NR>(p, m, pa, sp, sm);
   cx<double> c[2];
-  chi2(p, lam, c);
+  chi2<NR>(p, pa, lam, c);
   const double fl = lam > 0 ? sm : sp, fr = lam > 0 ? sp : sm;
   w[0] = {T(fr * c[0].r), T(-fr * c[0].i)}; w[1] = {T(fr * c[1].r), T(-fr * c[1].i)};
   w[2] = {T(fl * c[0].r), T(-fl * c[0].i)}; w[3] = {T(fl * c[1].r), T(-fl * c[1].i)};
@@ -87,62 +136,55 @@ __device__ __forceinline__ void top_ubar(const double* p, double m, int lam, cx<
 
 template <class T>
 __device__ __forceinline__ void top_v(const double* p, double m, int lam, cx<T>* w) {
-  const double pa = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
-  const double sp = sqrt(p[0] + pa);
-  const double sm = m > 0.0 ? m / sp : 0.0;
+  constexpr bool NR = sizeof(T) == 4;
+  double pa, sp, sm;
+  spinor_norms<NR>(p, m, pa, sp, sm);
   cx<double> c[2];
-  chi2(p, -lam, c);
+  chi2<NR>(p, pa, -lam, c);
   const double fl = lam > 0 ? -sp : sm, fr = lam > 0 ? sm : -sp;
   w[0] = {T(fl * c[0].r), T(fl * c[0].i)}; w[1] = {T(fl * c[1].r), T(fl * c[1].i)};
   w[2] = {T(fr * c[0].r), T(fr * c[0].i)}; w[3] = {T(fr * c[1].r), T(fr * c[1].i)};
 }
 
-// Reciprocal and reciprocal square root for the FP32-amplitude path's record: an FP32 seed refined by
-// one Newton-Raphson step in FP64 (r <- r (2 - x r) for 1/x, y <- y (3 - x y^2) / 2 for 1/sqrt(x); each
-// step squares the seed's relative error, ~2^-23 -> ~2^-45), so that the values stored in FP32 carry
-// only their final rounding, at a fraction of the FP64 cost of a correctly rounded division.  Outside
-// the FP32 exponent range the FP64 operation is used.
-__device__ __forceinline__ double rcp_nr(double x) {
-  const double ax = fabs(x);
-  if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
-  const double r0 = static_cast<double>(__frcp_rn(static_cast<float>(x)));
-  return r0 * fma(-x, r0, 2.0);
-}
-__device__ __forceinline__ double rsqrt_nr(double x) {
-  if (!(x > 1e-30 && x < 1e30)) return rsqrt(x);
-  const double y0 = static_cast<double>(rsqrtf(static_cast<float>(x)));
-  return y0 * fma(-0.5 * x * y0, y0, 1.5);
-}
-
-// Transverse polarisation of a gluon of momentum k (unit vectors e_theta, e_phi of its direction):
-// correctly rounded FP64 on the FP64 path; Newton-refined reciprocals on the FP32-amplitude path.
+// Transverse polarisation basis of a gluon of momentum k, pre-scaled by 1/sqrt(2):
+// pol = (e_theta / sqrt2 [3 components], e_phi / sqrt2 [x, y]; e_phi has no z component).  Correctly
+// rounded FP64 on the FP64 path; Newton-refined reciprocals on the FP32-amplitude path.
 template <class T>
-__device__ __forceinline__ void gluon_eps(const double* k, int lam, bool outgoing, cx<T>* w) {
+__device__ __forceinline__ void gluon_pol(const double* k, T* pol) {
   const double kx = k[1], ky = k[2], kz = k[3];
   const double kt2 = kx * kx + ky * ky;
-  double et[3], ep[3];
+  const double r = 0.70710678118654752440;
+  double et[3], ep[2];
   if (kt2 > 0.0) {
     if constexpr (sizeof(T) == 8) {
       const double kt = sqrt(kt2), ka = sqrt(kt2 + kz * kz);
       const double inv = 1.0 / (ka * kt);
       et[0] = kx * kz * inv; et[1] = ky * kz * inv; et[2] = -kt / ka;
-      ep[0] = -ky / kt; ep[1] = kx / kt; ep[2] = 0.0;
+      ep[0] = -ky / kt; ep[1] = kx / kt;
     } else {
       const double rt = rsqrt_nr(kt2), ra = rsqrt_nr(kt2 + kz * kz);
       const double inv = ra * rt;
       et[0] = kx * kz * inv; et[1] = ky * kz * inv; et[2] = -(kt2 * rt) * ra;
-      ep[0] = -ky * rt; ep[1] = kx * rt; ep[2] = 0.0;
+      ep[0] = -ky * rt; ep[1] = kx * rt;
     }
   } else {
     et[0] = kz < 0.0 ? -1.0 : 1.0; et[1] = 0.0; et[2] = 0.0;
-    ep[0] = 0.0; ep[1] = 1.0; ep[2] = 0.0;
+    ep[0] = 0.0; ep[1] = 1.0;
   }
-  const double r = 0.70710678118654752440;
-  const double sl = lam > 0 ? -r : r;
-  const double si = outgoing ? r : -r;
-  w[0] = {T(0), T(0)};
 #pragma unroll
-  for (int i = 0; i < 3; ++i) w[1 + i] = {T(sl * et[i]), T(si * ep[i])};
+  for (int i = 0; i < 3; ++i) pol[i] = T(r * et[i]);
+  pol[3] = T(r * ep[0]);
+  pol[4] = T(r * ep[1]);
+}
+
+// External gluon current of helicity lam: eps = (-lam e_theta + i s e_phi) / sqrt2, s = +1 for an
+// outgoing gluon (eps*), -1 for an incoming one; from the pre-scaled basis by exact sign flips.
+template <class T>
+__device__ __forceinline__ void ext_gluon(const T* pol, int lam, bool outgoing, cx<T>* w) {
+  w[0] = {T(0), T(0)};
+  w[1] = {lam > 0 ? -pol[0] : pol[0], outgoing ? pol[3] : -pol[3]};
+  w[2] = {lam > 0 ? -pol[1] : pol[1], outgoing ? pol[4] : -pol[4]};
+  w[3] = {lam > 0 ? -pol[2] : pol[2], T(0)};
 }
 
 // ---- current algebra ----
@@ -258,17 +300,17 @@ __device__ __forceinline__ T colour_sum(const cx<T>* A, const T* __restrict__ ct
 
 // ---- per-event data shared by every helicity of an event (FP64 arithmetic, stored as T) ----
 // Layout of one event's record (NITEM values of T): PT[S][4] (incoming gluon momentum of subset S),
-// gprop[S] (-g/P_S^2), qc[S][5] (quark propagator coefficients), eps[g][hel][4] complex,
-// ubar[hel][4] complex, v[hel][4] complex.
+// gprop[S] (-g/P_S^2), qc[S][5] (quark propagator coefficients), pol[g][5] (gluon polarisation basis,
+// see gluon_pol), ubar[hel][4] complex, v[hel][4] complex.
 template <int K> struct EvLayout {
   static constexpr int NSUB = 1 << K;
-  static constexpr int PT = 0, GP = 4 * NSUB, QC = 5 * NSUB, EPS = 10 * NSUB, UB = EPS + 16 * K, VV = UB + 16;
+  static constexpr int PT = 0, GP = 4 * NSUB, QC = 5 * NSUB, EPS = 10 * NSUB, UB = EPS + 5 * K, VV = UB + 16;
   static constexpr int NITEM = VV + 16;
 };
 
 template <int K, class T>
 __device__ __forceinline__ void event_data(const double (*p)[4], const MeConst& cst, T (*PT)[4], T* gprop, T (*qc)[5],
-                                           cx<T> (*eps)[2][4], cx<T> (*ub)[4], cx<T> (*vv)[4],
+                                           T (*pol)[5], cx<T> (*ub)[4], cx<T> (*vv)[4],
                                            double* min_invariant = nullptr) {
   constexpr int NSUB = 1 << K;
   double xmin = 1e300;
@@ -316,11 +358,7 @@ __device__ __forceinline__ void event_data(const double (*p)[4], const MeConst& 
     }
   }
 #pragma unroll
-  for (int g = 0; g < K; ++g) {
-    const int part = g < 2 ? g : g + 2;
-    gluon_eps<T>(p[part], -1, g >= 2, eps[g][0]);
-    gluon_eps<T>(p[part], 1, g >= 2, eps[g][1]);
-  }
+  for (int g = 0; g < K; ++g) gluon_pol<T>(p[g < 2 ? g : g + 2], pol[g]);
   top_ubar<T>(p[2], cst.mt, -1, ub[0]);
   top_ubar<T>(p[2], cst.mt, 1, ub[1]);
   top_v<T>(p[3], cst.mt, -1, vv[0]);
