@@ -257,7 +257,9 @@ def run_ours(args):
         for name, prec in (("fp64", mg.MG_FP64), ("fp32_amp", mg.MG_FP32_AMP), ("fp64_tccolor", mg.MG_FP64_TCCOLOR),
                            ("mixed", mg.MG_MIXED)):
             ctx.autotune(prec, nevt=min(nevt, 65536))
-            shapes[name] = dict(zip(("tile_ev", "slot_major", "unrolled"), ctx.launch_shape(prec)))
+            tev, slm, fl = ctx.launch_shape(prec)
+            shapes[name] = {"tile_ev": tev, "slot_major": slm, "unrolled": bool(fl & mg.LAUNCH_UNROLLED),
+                            "df_redo": bool(fl & mg.LAUNCH_DF_REDO)}
 
     clocks = ClockSampler(local)
     clocks.start()

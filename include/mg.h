@@ -64,12 +64,13 @@ typedef enum { MG_GG_TT = 0, MG_GG_TTG = 1, MG_GG_TTGG = 2, MG_GG_TTGGG = 3 } mg
  *                   denominators, the top wavefunctions and the helicity sum.  Events whose
  *                   smallest internal invariant (|P^2| of a gluon propagator or |Q^2 - m^2| of a
  *                   quark propagator) is below 3e-4 s -- near-collinear or soft gluons, where FP32
- *                   rounding grows like 1/sqrt(invariant) -- are recomputed in FP64 (0.1-2 % of
- *                   the events), which keeps every event within 1e-5 of FP64;
+ *                   rounding grows like 1/sqrt(invariant) -- are recomputed (0.1-2 % of the events)
+ *                   with double-float (pairs of FP32 values, ~48 bits; MG_LAUNCH_DF_REDO) or FP64
+ *                   amplitudes from FP64 per-event data, which keeps every event within 1e-5 of FP64;
  *   MG_FP64_TCCOLOR FP64 amplitudes; colour sum A^dagger C A on the tensor cores: the integer colour
  *                   matrix exact in FP16, every jamp row scaled by a power of two and split hi + lo
  *                   in FP16, FP32 accumulation (~1e-7 relative per helicity);
- *   MG_MIXED        FP32 amplitudes (with the same FP64 recomputation) + the tensor-core colour sum.
+ *   MG_MIXED        FP32 amplitudes (with the same recomputation) + the tensor-core colour sum.
  * The tensor-core modes need zero top width (MG_ENOTSUP otherwise). */
 typedef enum { MG_FP64 = 0, MG_FP32_AMP = 1, MG_FP64_TCCOLOR = 2, MG_MIXED = 3 } mg_precision;
 
@@ -188,28 +189,33 @@ mg_status mg_sigmakin_noalloc(mg_ctx* ctx, const double* mom_dev, int64_t nevt, 
  * Fig. 2 show the throughput depending on how many events one launch holds).
  * --------------------------------------------------------------------------------------------- */
 
+/* Launch options of the matrix-element kernel (the flags of mg_get/set_launch_shape):
+ *   MG_LAUNCH_UNROLLED  the kernel with the recursion unrolled at compile time, where built (FP32
+ *                       amplitudes of gg -> t tbar, t tbar g and t tbar g g; elsewhere the flag falls
+ *                       back to the kernel that reads the recursion tables at run time);
+ *   MG_LAUNCH_DF_REDO   FP32 modes: the events recomputed for a small internal invariant get
+ *                       double-float amplitudes (FP32 pipe) instead of FP64 ones (FP64 pipe, which
+ *                       otherwise idles beside the FP32 launch). */
+#define MG_LAUNCH_UNROLLED 1
+#define MG_LAUNCH_DF_REDO 2
+
 /* Time mg_sigmakin(precision) of nevt probe events (this context's process, fixed seed) for each
  * launch shape of the matrix-element kernel -- 32, 64 or 128 events per 128-thread block (the other
  * threads of a block take further helicity combinations of the same events), grid dispatched
- * event-tile-major or helicity-tile-major, and, where both exist, the kernel with the recursion
- * unrolled at compile time or the one reading the recursion tables at run time -- and keep the fastest
+ * event-tile-major or helicity-tile-major, with and without MG_LAUNCH_UNROLLED where that kernel
+ * exists -- then, for the FP32 modes, the fastest with MG_LAUNCH_DF_REDO toggled, and keep the fastest
  * for this context and precision.  cache_path (may be NULL): text file of
- * "gpu|process|precision tile_ev slot_major unrolled ms" lines; an existing entry is used without
- * timing, a new result is appended.  *best_ms may be NULL.  Synchronous; allocates probe buffers;
- * nevt >= 32. */
+ * "gpu|process|precision tile_ev slot_major flags ms" lines; an existing entry is used without timing,
+ * a new result is appended.  *best_ms may be NULL.  Synchronous; allocates probe buffers; nevt >= 32. */
 mg_status mg_autotune(mg_ctx* ctx, mg_precision precision, int64_t nevt, const char* cache_path, double* best_ms);
 
 /* The launch shape mg_sigmakin(precision) uses on this context (default: 128 events per block,
- * event-tile-major, unrolled kernel where it exists).  unrolled = 1: the matrix-element kernel with
- * the recursion expanded at compile time (built for FP32 amplitudes of gg -> t tbar, t tbar g and
- * t tbar g g); 0: the kernel that reads the
- * recursion tables at run time.  Any out-pointer may be NULL. */
-mg_status mg_get_launch_shape(mg_ctx* ctx, mg_precision precision, int* tile_ev, int* slot_major, int* unrolled);
+ * event-tile-major, flags MG_LAUNCH_UNROLLED | MG_LAUNCH_DF_REDO).  Any out-pointer may be NULL. */
+mg_status mg_get_launch_shape(mg_ctx* ctx, mg_precision precision, int* tile_ev, int* slot_major, int* flags);
 
-/* Set the launch shape of mg_sigmakin(precision) by hand: tile_ev in {32, 64, 128}, slot_major and
- * unrolled 0 or 1 (unrolled = 1 falls back to the run-time-table kernel where no unrolled one is
- * built).  MG_EINVAL otherwise. */
-mg_status mg_set_launch_shape(mg_ctx* ctx, mg_precision precision, int tile_ev, int slot_major, int unrolled);
+/* Set the launch shape of mg_sigmakin(precision) by hand: tile_ev in {32, 64, 128}, slot_major 0 or 1,
+ * flags a combination of the MG_LAUNCH_ bits.  MG_EINVAL otherwise. */
+mg_status mg_set_launch_shape(mg_ctx* ctx, mg_precision precision, int tile_ev, int slot_major, int flags);
 
 /* One job of a graph batch: the step mg_rambo_range(seed, e0, nevt, sqrts, mom_dev) ->
  * mg_hel_filter(mom_dev, nevt) -> mg_sigmakin(precision, me_dev) on ctx.  Every job of a batch needs

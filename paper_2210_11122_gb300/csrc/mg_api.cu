@@ -342,7 +342,7 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
       st = MG_ECUDA;
       break;
     }
-    // side stream of the FP32 modes' FP64 recomputation: highest priority, so that its few blocks are
+    // side stream of the FP32 modes' recomputation: highest priority, so that its few blocks are
     // dispatched ahead of the FP32 launch's
     int lo = 0, hi = 0;
     if (cudaDeviceGetStreamPriorityRange(&lo, &hi) != cudaSuccess ||
@@ -424,13 +424,17 @@ mg_status mg_hel_filter(mg_ctx* ctx, const double* mom_dev, int64_t nevt, void* 
   return MG_OK;
 }
 
-// The FP32 modes' FP64 recomputation of the events listed in ctx->d_repair, forked onto ctx->side
-// after the work already queued on st (the per-event records and the list), and joined back.
+// The FP32 modes' recomputation (double-float or FP64 amplitudes) of the events listed in
+// ctx->d_repair, forked onto ctx->side after the work already queued on st (the per-event records and
+// the list), and joined back.
 static cudaError_t fork_repair(mg_ctx* ctx, const double* mom, int64_t nevt, const mg::MeConst& cst, int64_t stride,
-                               int rows_out, cudaStream_t st) {
+                               int rows_out, bool df, cudaStream_t st) {
   cudaError_t e = cudaEventRecord(ctx->ev_fork, st);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && df)
+    e = mg::launch_me_repair(ctx->K, mom, nevt, ctx->d_tab, ctx->d_gslots, 1 << ctx->K, ctx->d_ngslots, ctx->d_mask,
+                             ctx->d_ctri_f, cst, ctx->d_part, stride, ctx->d_repair, ctx->d_nrepair, rows_out, ctx->side);
+  else if (e == cudaSuccess)
     e = mg::launch_me_gluonhel(ctx->K, false, false, mom, nullptr, nevt, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
                                ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, stride,
                                ctx->side, nullptr, mg::MeShape(), nullptr, ctx->d_repair, ctx->d_nrepair, rows_out);
@@ -488,9 +492,9 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
       if (fp32) MG_CUDA(cudaMemsetAsync(ctx->d_nrepair, 0, sizeof(int), st));
       MG_CUDA(mg::launch_event_prep(ctx->K, fp32, mom_c, n, cst, ctx->d_prep, fp32 ? ctx->d_repair : nullptr,
                                     fp32 ? ctx->d_nrepair : nullptr, fp32 ? ctx->d_flag : nullptr, st));
-      // events with a small internal invariant: FP64 amplitudes and colour sum (row layout), on the
+      // events with a small internal invariant: double-float or FP64 amplitudes (row layout), on the
       // side stream while the FP32 launches, which skip them, run
-      if (fp32) MG_CUDA(fork_repair(ctx, mom_c, n, cst, cst_stride, 1, st));
+      if (fp32) MG_CUDA(fork_repair(ctx, mom_c, n, cst, cst_stride, 1, ctx->shape[precision].df_redo, st));
       MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_c, ctx->d_prep, n, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
                                      ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, cst_stride, st,
                                      ctx->d_jamps, ctx->shape[precision], fp32 ? ctx->d_flag : nullptr));
@@ -507,8 +511,9 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
     if (fp32) MG_CUDA(cudaMemsetAsync(ctx->d_nrepair, 0, sizeof(int), st));
     MG_CUDA(mg::launch_event_prep(ctx->K, fp32, mom_dev, nevt, cst, ctx->d_prep, fp32 ? ctx->d_repair : nullptr,
                                   fp32 ? ctx->d_nrepair : nullptr, fp32 ? ctx->d_flag : nullptr, st));
-    // events with a small internal invariant: recomputed in FP64 (per-slot layout) on the side stream
-    if (fp32) MG_CUDA(fork_repair(ctx, mom_dev, nevt, cst, stride, 0, st));
+    // events with a small internal invariant: recomputed with double-float or FP64 amplitudes (per-slot
+    // layout) on the side stream
+    if (fp32) MG_CUDA(fork_repair(ctx, mom_dev, nevt, cst, stride, 0, ctx->shape[precision].df_redo, st));
     MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_dev, ctx->d_prep, nevt, ctx->d_tab, ctx->d_gslots,
                                    1 << ctx->K, ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, stride, st,
                                    nullptr, ctx->shape[precision], fp32 ? ctx->d_flag : nullptr));

@@ -22,10 +22,12 @@ struct MeConst {
 // re-read from L2), else all event tiles of a slot tile come first.
 // unrolled: use the kernel with the recursion expanded at compile time (mg_me3.cu) where it exists
 // (me_static_available), else the one that reads the recursion tables at run time (mg_me2.cu).
+// df_redo: the FP32 modes recompute their flagged events with double-float (else FP64) amplitudes.
 struct MeShape {
   int tile_ev = 128;
   bool slot_major = false;
   bool unrolled = true;
+  bool df_redo = true;
 };
 
 cudaError_t launch_philox(uint64_t seed, int64_t nevt, int nfinal, uint32_t* words, cudaStream_t st);
@@ -55,6 +57,12 @@ cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom
                                MeShape shape = MeShape(), const uint8_t* skip = nullptr,
                                const int* evlist = nullptr, const int* nlist = nullptr, int rows_out = 0);
 int64_t event_record_bytes(int K, bool fp32);
+// The FP32 modes' recomputation of events evlist[0..*nlist) with double-float amplitudes (mg_me_dd.cu):
+// launch_me_gluonhel's contract for prep == NULL, per_hel false, FP32 colour table ctri32.
+cudaError_t launch_me_repair(int K, const double* mom, int64_t nevt, const Tables* tab, const int* gslots, int maxslot,
+                             const int* nslot, const uint32_t* mask, const float* ctri32, const MeConst& cst,
+                             double* out, int64_t stride, const int* evlist, const int* nlist, int rows_out,
+                             cudaStream_t st);
 // The compile-time-unrolled matrix-element kernel (mg_me3.cu): same contract as launch_me_gluonhel with
 // a per-event record rec (filled by k_event_prep), for the (K, precision) pairs me_static_available
 // lists.  me_static_upload_colour: its colour triangle (constant memory), once per device and K.

@@ -18,6 +18,7 @@
 #include "mg_internal.h"
 #include "mg_kernels.h"
 #include "mg_me_algebra.cuh"
+#include "mg_me_kernel.cuh"
 
 namespace mg {
 namespace v2 {
@@ -69,223 +70,6 @@ __global__ void __launch_bounds__(128) k_event_prep(const double* __restrict__ m
       out[(L::VV + (l * 4 + a) * 2) * kPage] = vv[l][a].r;
       out[(L::VV + (l * 4 + a) * 2 + 1) * kPage] = vv[l][a].i;
     }
-}
-
-// JOUT: instead of colour sums, write the jamps of every helicity of the slot as FP32 complex
-// numbers to jout[((e * 4 * 2^K) + slot * 4 + 2 * top + antitop) * ncol + sigma] (zeros for helicities
-// outside the mask), for the tensor-core colour sum.
-template <int K, class T, bool PER_HEL, bool PREP, bool JOUT>
-__global__ void __launch_bounds__(kMeThreads)
-k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab,
-              const int* __restrict__ gslots, const int* __restrict__ nslot_dev, const uint32_t* __restrict__ mask,
-              const T* __restrict__ ctri, MeConst cst, double* __restrict__ out, int64_t stride,
-              float2* __restrict__ jout, int tile_ev, int slot_major, const int* __restrict__ evlist,
-              const int* __restrict__ nlist, int rows_out, const uint8_t* __restrict__ skip) {
-  constexpr int npar = K + 2;
-  constexpr int NSEQ = Sizes<K>::nseq;
-  constexpr int NCOL = Sizes<K>::ncol;
-  constexpr int NFULL = Sizes<K>::nfull;
-  constexpr int NSUB = 1 << K;
-  const int tile_sl = kMeThreads / tile_ev;
-  const unsigned bev = slot_major ? blockIdx.y : blockIdx.x, bsl = slot_major ? blockIdx.x : blockIdx.y;
-  const int64_t et = static_cast<int64_t>(bev) * tile_ev + threadIdx.x % tile_ev;
-  const int slot = static_cast<int>(bsl) * tile_sl + static_cast<int>(threadIdx.x) / tile_ev;
-  if (et >= nevt || slot >= *nslot_dev) return;
-  // evlist: the thread works on event evlist[et] of the batch (et < *nlist), else on event et
-  if (evlist && et >= *nlist) return;
-  const int64_t e = evlist ? static_cast<int64_t>(evlist[et]) : et;
-  if (PREP && skip && skip[e]) return;   // recomputed by another launch
-  const int gc = gslots[slot];   // bit g = helicity (+1) of gluon g
-
-  const T gs = static_cast<T>(cst.gs);
-  T PT[NSUB][4];
-  T gprop[NSUB];
-  T qc[NSUB][5];
-  cx<T> J[NSEQ][4];
-  cx<T> ub[2][4], vv[2][4];
-  if (PREP) {
-    using L = EvLayout<K>;
-    const T* in = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
-#pragma unroll
-    for (int S = 0; S < NSUB; ++S) {
-#pragma unroll
-      for (int m = 0; m < 4; ++m) PT[S][m] = __ldg(in + (L::PT + 4 * S + m) * kPage);
-      gprop[S] = __ldg(in + (L::GP + S) * kPage);
-#pragma unroll
-      for (int c = 0; c < 5; ++c) qc[S][c] = __ldg(in + (L::QC + 5 * S + c) * kPage);
-    }
-#pragma unroll
-    for (int g = 0; g < K; ++g) {
-      T pol[5];
-#pragma unroll
-      for (int i = 0; i < 5; ++i) pol[i] = __ldg(in + (L::EPS + 5 * g + i) * kPage);
-      ext_gluon(pol, (gc >> g) & 1 ? 1 : -1, g >= 2, J[g]);
-    }
-#pragma unroll
-    for (int l = 0; l < 2; ++l)
-#pragma unroll
-      for (int a = 0; a < 4; ++a) {
-        ub[l][a] = {__ldg(in + (L::UB + (l * 4 + a) * 2) * kPage), __ldg(in + (L::UB + (l * 4 + a) * 2 + 1) * kPage)};
-        vv[l][a] = {__ldg(in + (L::VV + (l * 4 + a) * 2) * kPage), __ldg(in + (L::VV + (l * 4 + a) * 2 + 1) * kPage)};
-      }
-  } else {
-    double p[npar][4];
-    const double* base = mom + (e / kPage) * npar * 4 * kPage + (e % kPage);
-#pragma unroll
-    for (int i = 0; i < npar; ++i)
-#pragma unroll
-      for (int m = 0; m < 4; ++m) p[i][m] = __ldg(base + (i * 4 + m) * kPage);
-    T pol[K][5];
-    event_data<K, T>(p, cst, PT, gprop, qc, pol, ub, vv);
-#pragma unroll
-    for (int g = 0; g < K; ++g) ext_gluon(pol[g], (gc >> g) & 1 ? 1 : -1, g >= 2, J[g]);
-  }
-
-  // ---- gluon currents (helicities of gc) ----
-  for (int s = K; s < NSEQ; ++s) {
-    cx<T> acc[4] = {};
-    const int n3 = tab->seq_nv3[s];
-    for (int k = 0; k < n3; ++k) {
-      const int16_t rl = tab->seq_v3[s][k][0], rr = tab->seq_v3[s][k][1];
-      const int il = rslot(rl), ir = rslot(rr);
-      v3_acc(acc, J[il], J[ir], PT[tab->seq_mask[il]], PT[tab->seq_mask[ir]], rneg(rl) != rneg(rr));
-    }
-    const int n4 = tab->seq_nv4[s];
-    for (int k = 0; k < n4; ++k) {
-      const int16_t ra = tab->seq_v4[s][k][0], rb = tab->seq_v4[s][k][1], rc = tab->seq_v4[s][k][2];
-      v4_acc(acc, J[rslot(ra)], J[rslot(rb)], J[rslot(rc)], gs, rneg(ra) ^ rneg(rb) ^ rneg(rc));
-    }
-    const T f = gprop[tab->seq_mask[s]];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) J[s][m] = cscale(f, acc[m]);
-  }
-  // all gluons on one current (canonical orderings)
-  cx<T> JF[NFULL][4];
-  for (int f = 0; f < NFULL; ++f) {
-    cx<T> acc[4] = {};
-    const int n3 = tab->full_nv3[f];
-    for (int k = 0; k < n3; ++k) {
-      const int16_t rl = tab->full_v3[f][k][0], rr = tab->full_v3[f][k][1];
-      const int il = rslot(rl), ir = rslot(rr);
-      v3_acc(acc, J[il], J[ir], PT[tab->seq_mask[il]], PT[tab->seq_mask[ir]], rneg(rl) != rneg(rr));
-    }
-    const int n4 = tab->full_nv4[f];
-    for (int k = 0; k < n4; ++k) {
-      const int16_t ra = tab->full_v4[f][k][0], rb = tab->full_v4[f][k][1], rc = tab->full_v4[f][k][2];
-      v4_acc(acc, J[rslot(ra)], J[rslot(rb)], J[rslot(rc)], gs, rneg(ra) ^ rneg(rb) ^ rneg(rc));
-    }
-    const T fz = gprop[NSUB - 1];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) JF[f][m] = cscale(fz, acc[m]);
-  }
-
-  // ---- antitop spinors and (gamma.J) v for both antitop helicities ----
-  // (gamma.J) v for every current and both antitop helicities: precomputed in FP64 (saves FP64
-  // instructions); in FP32 each jamp term forms ubar-side (row spinor x gamma.J) on the fly instead,
-  // keeping 2 NSEQ spinors out of the thread's local memory (FP32 arithmetic is cheap, memory is not).
-  constexpr bool kTableX = sizeof(T) == 8;
-  cx<T> X[kTableX ? 2 : 1][kTableX ? NSEQ : 1][4];
-  if (kTableX) {
-#pragma unroll
-    for (int b = 0; b < 2; ++b)
-      for (int s = 0; s < NSEQ; ++s) gamma_col(J[s], vv[b], X[b][s]);
-  }
-
-  // helicity index of (gc, top helicity a, antitop helicity b)
-  int hbase = 0;
-#pragma unroll
-  for (int g = 0; g < K; ++g)
-    if ((gc >> g) & 1) hbase |= 1 << (npar - 1 - (g < 2 ? g : g + 2));
-  const int bit_t = 1 << (npar - 3), bit_tb = 1 << (npar - 4);
-
-  double total = 0.0;
-  for (int a = 0; a < 2; ++a) {
-    const int h0 = hbase | (a ? bit_t : 0), h1 = h0 | bit_tb;
-    const bool good0 = PER_HEL || ((mask[h0 >> 5] >> (h0 & 31)) & 1u);
-    const bool good1 = PER_HEL || ((mask[h1 >> 5] >> (h1 & 31)) & 1u);
-    if (!good0 && !good1) {
-      if (JOUT) {
-        float2* row = jout + (e * (4 << K) + slot * 4 + 2 * a) * NCOL;
-        for (int c = 0; c < 2 * NCOL; ++c) row[c] = make_float2(0.f, 0.f);
-      }
-      continue;
-    }
-    cx<T> stk[K][4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) stk[0][q] = ub[a][q];
-    cx<T> Jq[2][4];
-    quark_current(stk[0], vv[0], Jq[0]);
-    quark_current(stk[0], vv[1], Jq[1]);
-    cx<T> A[2][NCOL];
-    for (int c = 0; c < NCOL; ++c) {
-      const int l = tab->lcp[c];
-      for (int m = l + 1; m < K; ++m) {
-        cx<T> acc[4] = {};
-        for (int j = 0; j < m; ++j) {
-          const int16_t r = tab->sub[c][j][m];
-          row_gamma_acc(acc, stk[j], J[rslot(r)], rneg(r));
-        }
-        row_prop(acc, qc[tab->prefix_mask[c][m]], stk[m]);
-      }
-      const int fi = tab->full_idx[c];
-      const int fidx = fi >= 0 ? fi : -fi - 1;
-      const bool fneg = fi < 0 && !(K & 1);   // reflection sign (-1)^(K+1)
-      if (kTableX) {
-#pragma unroll
-        for (int b = 0; b < 2; ++b) {
-          cx<T> amp = mdot(Jq[b], JF[fidx]);   // all gluons on one current: ubar gamma.J v = Jq.J
-          if (fneg) amp = cneg(amp);
-          for (int j = 1; j < K; ++j) {
-            const int16_t r = tab->sub[c][j][K];
-            sdot_acc(amp, stk[j], X[b][rslot(r)], rneg(r));
-          }
-          A[b][c] = amp;
-        }
-      } else {
-        cx<T> amp0 = mdot(Jq[0], JF[fidx]), amp1 = mdot(Jq[1], JF[fidx]);
-        if (fneg) { amp0 = cneg(amp0); amp1 = cneg(amp1); }
-        for (int j = 1; j < K; ++j) {
-          const int16_t r = tab->sub[c][j][K];
-          cx<T> t[4] = {};
-          row_gamma_acc(t, stk[j], J[rslot(r)], rneg(r));
-          sdot_acc(amp0, t, vv[0], false);
-          sdot_acc(amp1, t, vv[1], false);
-        }
-        A[0][c] = amp0;
-        A[1][c] = amp1;
-      }
-    }
-    if constexpr (JOUT) {
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        const bool good = b ? good1 : good0;
-        float2* row = jout + (e * (4 << K) + slot * 4 + 2 * a + b) * NCOL;
-        for (int c = 0; c < NCOL; ++c)
-          row[c] = good ? make_float2(static_cast<float>(A[b][c].r), static_cast<float>(A[b][c].i)) : make_float2(0.f, 0.f);
-      }
-      continue;
-    } else {
-#pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        const int h = b ? h1 : h0;
-        const bool good = b ? good1 : good0;
-        if (!good) continue;
-        const double v = static_cast<double>(colour_sum<NCOL, T>(A[b], ctri)) * cst.colour_scale;
-        if (PER_HEL) out[h * stride + e] = v;
-        else total += v;
-      }
-    }
-  }
-  if (!PER_HEL && !JOUT) {
-    if (rows_out) {   // tensor-core row layout: slot*4 + (2 top + antitop); the slot total in the first row
-      out[(slot * 4) * stride + e] = total;
-      out[(slot * 4 + 1) * stride + e] = 0.0;
-      out[(slot * 4 + 2) * stride + e] = 0.0;
-      out[(slot * 4 + 3) * stride + e] = 0.0;
-    } else {
-      out[slot * stride + e] = total;
-    }
-  }
 }
 
 // Gluon-helicity combinations with at least one good helicity (fixed ascending order).

@@ -12,6 +12,58 @@
 #include "mg_kernels.h"
 
 namespace mg {
+namespace dd {
+
+// Double-float number: an unevaluated sum hi + lo of two FP32 values, |lo| <= ulp(hi) / 2, carrying
+// ~48 significant bits with FP32 instructions only (Dekker, Numer. Math. 18 (1971) 224; Knuth, TAOCP
+// vol. 2, 4.2.2: error-free sum of two floats; the product error from one FMA).  Every step uses the
+// non-contractible __fadd_rn / __fmul_rn intrinsics so that the compiler cannot fuse an error-free
+// transformation into an FMA.  Sums use the short form (no renormalisation of the low parts first),
+// whose relative error is ~2^-46 times the cancellation ratio |a| / |a + b|.
+struct df {
+  float hi, lo;
+  df() = default;
+  __host__ __device__ constexpr df(float h, float l) : hi(h), lo(l) {}
+  __device__ df(double x) : hi(static_cast<float>(x)), lo(static_cast<float>(x - static_cast<double>(static_cast<float>(x)))) {}
+  __device__ explicit operator double() const { return static_cast<double>(hi) + static_cast<double>(lo); }
+};
+
+__device__ __forceinline__ df two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ df quick_two_sum(float a, float b) {   // |a| >= |b|
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df operator+(df a, df b) {
+  const df s = two_sum(a.hi, b.hi);
+  return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df operator-(df a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df operator-(df a, df b) { return a + (-b); }
+__device__ __forceinline__ df operator*(df a, df b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ df fma(df a, df b, df c) {   // a b + c
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  const df s = two_sum(p, c.hi);
+  return quick_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
+}
+
+}  // namespace dd
+}  // namespace mg
+
+namespace mg {
 namespace v2 {
 
 template <class T>
@@ -297,6 +349,29 @@ __device__ __forceinline__ T colour_sum(const cx<T>* A, const T* __restrict__ ct
   }
   return sum;
 }
+
+// colour sum of one helicity from double-float jamps, evaluated in FP32 on their high parts (the
+// quadratic form is well conditioned; the precision is needed in the jamps, not here)
+template <int NCOL>
+__device__ __forceinline__ float colour_sum_hi(const cx<dd::df>* A, const float* __restrict__ ctri) {
+  float sum = 0.f;
+  int idx = 0;
+  for (int a = 0; a < NCOL; ++a) {
+    float wr = 0.f, wi = 0.f;
+    for (int b = a; b < NCOL; ++b, ++idx) {
+      const float c = __ldg(ctri + idx);
+      wr = fmaf(c, A[b].r.hi, wr);
+      wi = fmaf(c, A[b].i.hi, wi);
+    }
+    sum = fmaf(A[a].r.hi, wr, sum);
+    sum = fmaf(A[a].i.hi, wi, sum);
+  }
+  return sum;
+}
+
+// the colour table type of an amplitude type (FP32 integers for the double-float kernel)
+template <class T> struct ColourT { using type = T; };
+template <> struct ColourT<dd::df> { using type = float; };
 
 // ---- per-event data shared by every helicity of an event (FP64 arithmetic, stored as T) ----
 // Layout of one event's record (NITEM values of T): PT[S][4] (incoming gluon momentum of subset S),
