@@ -57,12 +57,15 @@ def parse():
     return ap.parse_args()
 
 
-def profiled_traffic(kernel_file, profile_md, nevt):
-    """DRAM bytes of one launch scaled from a committed ncu summary, or None when the kernel source
-    has changed since the counters were taken."""
+def profiled_traffic(kernel_files, profile_md, nevt):
+    """DRAM bytes of one launch scaled from a committed ncu summary, or None when the kernel sources
+    (hashed in the order given) have changed since the counters were taken."""
     import hashlib
     try:
-        sha = hashlib.sha256(open(kernel_file, "rb").read()).hexdigest()[:16]
+        h = hashlib.sha256()
+        for f in kernel_files:
+            h.update(open(f, "rb").read())
+        sha = h.hexdigest()[:16]
         fields = {}
         for line in open(profile_md):
             if ":" in line and line.split(":")[0].strip() in ("source_sha256_16", "traffic_bytes_per_event"):
@@ -259,7 +262,7 @@ def run_ours(args):
             ctx.autotune(prec, nevt=min(nevt, 65536))
             tev, slm, fl = ctx.launch_shape(prec)
             shapes[name] = {"tile_ev": tev, "slot_major": slm, "unrolled": bool(fl & mg.LAUNCH_UNROLLED),
-                            "df_redo": bool(fl & mg.LAUNCH_DF_REDO)}
+                            "df_redo": bool(fl & mg.LAUNCH_DF_REDO), "fused": bool(fl & mg.LAUNCH_FUSED)}
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -348,7 +351,8 @@ def run_ours(args):
                                       "peak_source": "measured %s FMA-chain microbenchmark (mg_measure_fma_peak)"
                                                      % ("FP32" if pk is peak32 else "FP64")}
     achieved = flops / (ms_me * 1e-3)
-    traffic = profiled_traffic(os.path.join(ROOT, "paper_2210_11122_gb300", "csrc", "mg_me2.cu"),
+    csrc = os.path.join(ROOT, "paper_2210_11122_gb300", "csrc")
+    traffic = profiled_traffic([os.path.join(csrc, f) for f in ("mg_me_kernel.cuh", "mg_me_algebra.cuh")],
                                os.path.join(ROOT, "profiles", "k_me_gluonhel_fp64_%s_65536.md" % args.process), nevt)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,

@@ -195,22 +195,28 @@ mg_status mg_sigmakin_noalloc(mg_ctx* ctx, const double* mom_dev, int64_t nevt, 
  *                       back to the kernel that reads the recursion tables at run time);
  *   MG_LAUNCH_DF_REDO   FP32 modes: the events recomputed for a small internal invariant get
  *                       double-float amplitudes (FP32 pipe) instead of FP64 ones (FP64 pipe, which
- *                       otherwise idles beside the FP32 launch). */
+ *                       otherwise idles beside the FP32 launch);
+ *   MG_LAUNCH_FUSED     with MG_LAUNCH_UNROLLED: the per-event FP64 record is computed inside the
+ *                       matrix-element kernel (32 events per block; tile_ev and slot_major unused), so
+ *                       that its FP64 work overlaps the FP32 work of other blocks. */
 #define MG_LAUNCH_UNROLLED 1
 #define MG_LAUNCH_DF_REDO 2
+#define MG_LAUNCH_FUSED 4
 
 /* Time mg_sigmakin(precision) of nevt probe events (this context's process, fixed seed) for each
  * launch shape of the matrix-element kernel -- 32, 64 or 128 events per 128-thread block (the other
  * threads of a block take further helicity combinations of the same events), grid dispatched
  * event-tile-major or helicity-tile-major, with and without MG_LAUNCH_UNROLLED where that kernel
- * exists -- then, for the FP32 modes, the fastest with MG_LAUNCH_DF_REDO toggled, and keep the fastest
+ * exists, and MG_LAUNCH_UNROLLED | MG_LAUNCH_FUSED -- then, for the FP32 modes, the fastest with
+ * MG_LAUNCH_DF_REDO toggled, and keep the fastest
  * for this context and precision.  cache_path (may be NULL): text file of
  * "gpu|process|precision tile_ev slot_major flags ms" lines; an existing entry is used without timing,
  * a new result is appended.  *best_ms may be NULL.  Synchronous; allocates probe buffers; nevt >= 32. */
 mg_status mg_autotune(mg_ctx* ctx, mg_precision precision, int64_t nevt, const char* cache_path, double* best_ms);
 
 /* The launch shape mg_sigmakin(precision) uses on this context (default: 128 events per block,
- * event-tile-major, flags MG_LAUNCH_UNROLLED | MG_LAUNCH_DF_REDO).  Any out-pointer may be NULL. */
+ * event-tile-major, flags MG_LAUNCH_UNROLLED | MG_LAUNCH_DF_REDO | MG_LAUNCH_FUSED).  Any out-pointer may
+ * be NULL. */
 mg_status mg_get_launch_shape(mg_ctx* ctx, mg_precision precision, int* tile_ev, int* slot_major, int* flags);
 
 /* Set the launch shape of mg_sigmakin(precision) by hand: tile_ev in {32, 64, 128}, slot_major 0 or 1,

@@ -467,6 +467,8 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
     // amplitudes -> FP32 jamps -> tensor-core colour sums, in chunks of whole pages that keep the jamp
     // buffer within 4 GiB
     const bool fp32 = precision == MG_MIXED;
+    const bool fused = fp32 && ctx->shape[precision].fused && ctx->shape[precision].unrolled &&
+                       mg::me_static_available(ctx->K, true);
     const int64_t per_event = static_cast<int64_t>(ctx->nhel) * ctx->ncol;   // float2 per event
     int64_t chunk = (int64_t(1) << 29) / per_event;                          // 2^29 float2 = 4 GiB
     chunk = chunk / mg::kPage * mg::kPage;
@@ -489,15 +491,21 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
       const int64_t n = nevt - e0 < chunk ? nevt - e0 : chunk;
       const int64_t cst_stride = pad32(n);
       const double* mom_c = mom_dev + (e0 / mg::kPage) * ctx->npar * 4 * mg::kPage;
-      if (fp32) MG_CUDA(cudaMemsetAsync(ctx->d_nrepair, 0, sizeof(int), st));
-      MG_CUDA(mg::launch_event_prep(ctx->K, fp32, mom_c, n, cst, ctx->d_prep, fp32 ? ctx->d_repair : nullptr,
-                                    fp32 ? ctx->d_nrepair : nullptr, fp32 ? ctx->d_flag : nullptr, st));
+      if (fp32) {
+        MG_CUDA(cudaMemsetAsync(ctx->d_nrepair, 0, sizeof(int), st));
+        MG_CUDA(mg::launch_event_flags(ctx->K, mom_c, n, cst, ctx->d_repair, ctx->d_nrepair, ctx->d_flag, st));
+      }
+      if (!fused) MG_CUDA(mg::launch_event_prep(ctx->K, fp32, mom_c, n, cst, ctx->d_prep, st));
       // events with a small internal invariant: double-float or FP64 amplitudes (row layout), on the
       // side stream while the FP32 launches, which skip them, run
       if (fp32) MG_CUDA(fork_repair(ctx, mom_c, n, cst, cst_stride, 1, ctx->shape[precision].df_redo, st));
-      MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_c, ctx->d_prep, n, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
-                                     ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, cst_stride, st,
-                                     ctx->d_jamps, ctx->shape[precision], fp32 ? ctx->d_flag : nullptr));
+      if (fused)
+        MG_CUDA(mg::launch_me_fused(ctx->K, true, mom_c, n, ctx->d_gslots, ctx->d_ngslots, ctx->d_mask, cst, ctx->d_part,
+                                    cst_stride, ctx->d_jamps, ctx->d_flag, st));
+      else
+        MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_c, ctx->d_prep, n, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
+                                       ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, cst_stride,
+                                       st, ctx->d_jamps, ctx->shape[precision], fp32 ? ctx->d_flag : nullptr));
       MG_CUDA(mg::launch_colour_tc(ctx->ncol, ctx->d_jamps, n, ctx->nhel, ctx->d_nrows, ctx->d_cmat, cst.colour_scale,
                                    ctx->d_part, cst_stride, st, fp32 ? ctx->d_flag : nullptr));
       if (fp32) MG_CUDA(join_repair(ctx, st));
@@ -505,18 +513,26 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
     }
   } else if (ctx->prm.wt == 0.0) {
     const bool fp32 = precision == MG_FP32_AMP;
+    const bool fused = fp32 && ctx->shape[precision].fused && ctx->shape[precision].unrolled &&
+                       mg::me_static_available(ctx->K, true);
     s = grow(&ctx->d_prep, &ctx->prep_cap, stride * mg::event_record_bytes(ctx->K, fp32) / 8 + 1);
     if (s == MG_OK && fp32) s = grow_repair(ctx, stride);
     if (s != MG_OK) return s;
-    if (fp32) MG_CUDA(cudaMemsetAsync(ctx->d_nrepair, 0, sizeof(int), st));
-    MG_CUDA(mg::launch_event_prep(ctx->K, fp32, mom_dev, nevt, cst, ctx->d_prep, fp32 ? ctx->d_repair : nullptr,
-                                  fp32 ? ctx->d_nrepair : nullptr, fp32 ? ctx->d_flag : nullptr, st));
+    if (fp32) {
+      MG_CUDA(cudaMemsetAsync(ctx->d_nrepair, 0, sizeof(int), st));
+      MG_CUDA(mg::launch_event_flags(ctx->K, mom_dev, nevt, cst, ctx->d_repair, ctx->d_nrepair, ctx->d_flag, st));
+    }
+    if (!fused) MG_CUDA(mg::launch_event_prep(ctx->K, fp32, mom_dev, nevt, cst, ctx->d_prep, st));
     // events with a small internal invariant: recomputed with double-float or FP64 amplitudes (per-slot
     // layout) on the side stream
     if (fp32) MG_CUDA(fork_repair(ctx, mom_dev, nevt, cst, stride, 0, ctx->shape[precision].df_redo, st));
-    MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_dev, ctx->d_prep, nevt, ctx->d_tab, ctx->d_gslots,
-                                   1 << ctx->K, ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, stride, st,
-                                   nullptr, ctx->shape[precision], fp32 ? ctx->d_flag : nullptr));
+    if (fused)
+      MG_CUDA(mg::launch_me_fused(ctx->K, true, mom_dev, nevt, ctx->d_gslots, ctx->d_ngslots, ctx->d_mask, cst,
+                                  ctx->d_part, stride, nullptr, ctx->d_flag, st));
+    else
+      MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_dev, ctx->d_prep, nevt, ctx->d_tab, ctx->d_gslots,
+                                     1 << ctx->K, ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part,
+                                     stride, st, nullptr, ctx->shape[precision], fp32 ? ctx->d_flag : nullptr));
     if (fp32) MG_CUDA(join_repair(ctx, st));
     MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_ngslots, nevt, stride, norm, me_dev, st));
   } else {

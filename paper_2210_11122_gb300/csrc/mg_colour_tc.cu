@@ -164,27 +164,37 @@ __global__ void __launch_bounds__(128) k_colour_tc(const float2* __restrict__ ja
         al[ks][rg] = pack_h2(l0, l1);
       }
     __syncwarp();   // this buffer is staged again two tiles later
-    // Y = C a, column tile by column tile; the quadratic form a . Y of rows g and g + 8
+    // Y = C a, two column tiles at a time (four independent accumulator chains); the quadratic form
+    // a . Y of rows g and g + 8
     float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-      float dh[4] = {0.f, 0.f, 0.f, 0.f}, dl[4] = {0.f, 0.f, 0.f, 0.f};
-      const __half* cb = sC + (nt * 8 + g) * LDH + 2 * q;
+    for (int n0 = 0; n0 < NT; n0 += 2) {
+      constexpr int W = 2;
+      float dh[W][4] = {}, dl[W][4] = {};
 #pragma unroll
-      for (int ks = 0; ks < KS; ++ks) {
-        uint32_t bf[2];
-        bf[0] = *reinterpret_cast<const uint32_t*>(cb + ks * 16);
-        bf[1] = *reinterpret_cast<const uint32_t*>(cb + ks * 16 + 8);
-        mma16816(dh, ah[ks], bf);
-        mma16816(dl, al[ks], bf);
+      for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+          if (n0 + j >= NT) continue;
+          const __half* cb = sC + ((n0 + j) * 8 + g) * LDH + 2 * q + ks * 16;
+          uint32_t bf[2];
+          bf[0] = *reinterpret_cast<const uint32_t*>(cb);
+          bf[1] = *reinterpret_cast<const uint32_t*>(cb + 8);
+          mma16816(dh[j], ah[ks], bf);
+          mma16816(dl[j], al[ks], bf);
+        }
+#pragma unroll
+      for (int j = 0; j < W; ++j) {
+        const int nt = n0 + j;
+        if (nt >= NT) continue;
+        // this thread's Y columns nt*8 + 2q, +1 are the a columns it holds in k step nt/2, half nt%2
+        const int ksa = nt >> 1, hb = (nt & 1) * 2;
+        const float r = 1.f / 2048.f;
+        s0 = fmaf(unsplit(ah[ksa][hb], al[ksa][hb], 0), fmaf(dl[j][0], r, dh[j][0]), s0);
+        s0 = fmaf(unsplit(ah[ksa][hb], al[ksa][hb], 1), fmaf(dl[j][1], r, dh[j][1]), s0);
+        s1 = fmaf(unsplit(ah[ksa][hb + 1], al[ksa][hb + 1], 0), fmaf(dl[j][2], r, dh[j][2]), s1);
+        s1 = fmaf(unsplit(ah[ksa][hb + 1], al[ksa][hb + 1], 1), fmaf(dl[j][3], r, dh[j][3]), s1);
       }
-      // this thread's Y columns nt*8 + 2q, +1 are the a columns it holds in k step nt/2, half nt%2
-      const int ksa = nt >> 1, hb = (nt & 1) * 2;
-      const float r = 1.f / 2048.f;
-      s0 = fmaf(unsplit(ah[ksa][hb], al[ksa][hb], 0), fmaf(dl[0], r, dh[0]), s0);
-      s0 = fmaf(unsplit(ah[ksa][hb], al[ksa][hb], 1), fmaf(dl[1], r, dh[1]), s0);
-      s1 = fmaf(unsplit(ah[ksa][hb + 1], al[ksa][hb + 1], 0), fmaf(dl[2], r, dh[2]), s1);
-      s1 = fmaf(unsplit(ah[ksa][hb + 1], al[ksa][hb + 1], 1), fmaf(dl[3], r, dh[3]), s1);
     }
     s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
     s0 += __shfl_xor_sync(0xffffffffu, s0, 2);

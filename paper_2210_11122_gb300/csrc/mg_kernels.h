@@ -23,11 +23,14 @@ struct MeConst {
 // unrolled: use the kernel with the recursion expanded at compile time (mg_me3.cu) where it exists
 // (me_static_available), else the one that reads the recursion tables at run time (mg_me2.cu).
 // df_redo: the FP32 modes recompute their flagged events with double-float (else FP64) amplitudes.
+// fused: (unrolled FP32 kernel only) the per-event record is computed inside the matrix-element kernel
+// (k_me_fused: 32 events per block, the slots looped by its warps; tile_ev and slot_major unused).
 struct MeShape {
   int tile_ev = 128;
   bool slot_major = false;
   bool unrolled = true;
   bool df_redo = true;
+  bool fused = true;
 };
 
 cudaError_t launch_philox(uint64_t seed, int64_t nevt, int nfinal, uint32_t* words, cudaStream_t st);
@@ -39,11 +42,13 @@ cudaError_t launch_me_helicity(int K, bool fp32, const double* mom, int64_t nevt
                                int maxslot, const int* nslot, const double* ctri, const MeConst& cst, double* out,
                                int64_t stride, cudaStream_t st);
 // Per-event record (momenta sums, propagator factors, wavefunctions; FP64 arithmetic, stored as FP32 or
-// FP64) of every event into rec (ceil(nevt/32)*32 * event_record_bytes(K, fp32) bytes).  repair/nrepair
-// (optional, *nrepair zero before the launch): the events with a small internal invariant are appended;
-// flag (optional): flag[e] = 1 for those events, else 0.
+// FP64) of every event into rec (ceil(nevt/32)*32 * event_record_bytes(K, fp32) bytes).
 cudaError_t launch_event_prep(int K, bool fp32, const double* mom, int64_t nevt, const MeConst& cst, void* rec,
-                              int* repair, int* nrepair, uint8_t* flag, cudaStream_t st);
+                              cudaStream_t st);
+// FP32 modes: flag[e] = 1 and e appended to repair[] (count *nrepair, zero before the launch) for the events
+// whose smallest internal invariant is below cst.fp32_tau * s; flag[e] = 0 for the others.
+cudaError_t launch_event_flags(int K, const double* mom, int64_t nevt, const MeConst& cst, int* repair, int* nrepair,
+                               uint8_t* flag, cudaStream_t st);
 // One thread per (event, gluon-helicity combination gslots[slot]); per_hel: out[h * stride + e] for every
 // helicity h of the combination, else out[slot * stride + e] = sum over its good helicities.  Zero top width.
 // prep: NULL (every thread computes its event's momenta sums, propagators and wavefunctions) or the
@@ -71,6 +76,10 @@ cudaError_t me_static_upload_colour(int K, const double* tri, int n);
 cudaError_t launch_me_static(int K, bool fp32, const void* rec, int64_t nevt, const int* gslots, int maxslot,
                              const int* nslot, const uint32_t* mask, const MeConst& cst, double* out, int64_t stride,
                              float2* jout, MeShape shape, const uint8_t* skip, cudaStream_t st);
+// The same with the record computed inside the kernel from the momenta (no per-event kernel first).
+cudaError_t launch_me_fused(int K, bool fp32, const double* mom, int64_t nevt, const int* gslots, const int* nslot,
+                            const uint32_t* mask, const MeConst& cst, double* out, int64_t stride, float2* jout,
+                            const uint8_t* skip, cudaStream_t st);
 
 // Tensor-core colour sum (mg_colour_tc.cu): out[r * stride + e] = scale * (Re A^T C Re A + Im A^T C Im A)
 // for the jamp rows jamps[(e * rows_alloc + r) * ncol ...], r < *nrows; events with skip[e] != 0 (skip

@@ -24,14 +24,10 @@ namespace mg {
 namespace v2 {
 
 // One thread per event: the event's record, AoSoA (page of 32 events, value-major within a page).
-// repair != NULL: events whose smallest internal invariant |P^2| or |Q^2 - m^2| (over the gluon and
-// quark propagators of the recursion) is below cst.fp32_tau * s are appended to repair[] (count in
-// *nrepair): FP32 rounding is amplified ~ 1/sqrt(invariant/s) there (collinear and soft gluons).
 template <int K, class T>
 __global__ void __launch_bounds__(128) k_event_prep(const double* __restrict__ mom, int64_t nevt, MeConst cst,
-                                                    T* __restrict__ rec, int* __restrict__ repair,
-                                                    int* __restrict__ nrepair, uint8_t* __restrict__ flag) {
-  constexpr int npar = K + 2, NSUB = 1 << K;
+                                                    T* __restrict__ rec) {
+  constexpr int npar = K + 2;
   using L = EvLayout<K>;
   const int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
   if (e >= nevt) return;
@@ -41,35 +37,30 @@ __global__ void __launch_bounds__(128) k_event_prep(const double* __restrict__ m
   for (int i = 0; i < npar; ++i)
 #pragma unroll
     for (int m = 0; m < 4; ++m) p[i][m] = __ldg(base + (i * 4 + m) * kPage);
-  T PT[NSUB][4], gprop[NSUB], qc[NSUB][5], pol[K][5];
-  cx<T> ub[2][4], vv[2][4];
-  double xmin = 1.0;
-  event_data<K, T>(p, cst, PT, gprop, qc, pol, ub, vv, &xmin);
-  const bool redo = repair && xmin < cst.fp32_tau;
-  if (redo) repair[atomicAdd(nrepair, 1)] = static_cast<int>(e);
-  if (flag) flag[e] = redo ? 1 : 0;
   T* out = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
+  record_all<K, T>(p, cst, [&](int i, T v) { out[i * kPage] = v; });
+}
+
+// FP32 modes: events whose smallest internal invariant |P^2| or |Q^2 - m^2| (over the gluon and quark
+// propagators of the recursion) is below tau * s get flag[e] = 1 and are appended to repair[] (count in
+// *nrepair, zero before the launch); the others get flag[e] = 0.  FP32 rounding of the amplitudes is
+// amplified ~ 1/sqrt(invariant / s) there (collinear and soft gluons).
+template <int K>
+__global__ void __launch_bounds__(128) k_event_flags(const double* __restrict__ mom, int64_t nevt, float mt, float tau,
+                                                     int* __restrict__ repair, int* __restrict__ nrepair,
+                                                     uint8_t* __restrict__ flag) {
+  constexpr int npar = K + 2;
+  const int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+  if (e >= nevt) return;
+  double p[npar][4];
+  const double* base = mom + (e / kPage) * npar * 4 * kPage + (e % kPage);
 #pragma unroll
-  for (int S = 0; S < NSUB; ++S) {
+  for (int i = 0; i < npar; ++i)
 #pragma unroll
-    for (int m = 0; m < 4; ++m) out[(L::PT + 4 * S + m) * kPage] = PT[S][m];
-    out[(L::GP + S) * kPage] = gprop[S];
-#pragma unroll
-    for (int c = 0; c < 5; ++c) out[(L::QC + 5 * S + c) * kPage] = qc[S][c];
-  }
-#pragma unroll
-  for (int g = 0; g < K; ++g)
-#pragma unroll
-    for (int i = 0; i < 5; ++i) out[(L::EPS + 5 * g + i) * kPage] = pol[g][i];
-#pragma unroll
-  for (int l = 0; l < 2; ++l)
-#pragma unroll
-    for (int a = 0; a < 4; ++a) {
-      out[(L::UB + (l * 4 + a) * 2) * kPage] = ub[l][a].r;
-      out[(L::UB + (l * 4 + a) * 2 + 1) * kPage] = ub[l][a].i;
-      out[(L::VV + (l * 4 + a) * 2) * kPage] = vv[l][a].r;
-      out[(L::VV + (l * 4 + a) * 2 + 1) * kPage] = vv[l][a].i;
-    }
+    for (int m = 0; m < 4; ++m) p[i][m] = __ldg(base + (i * 4 + m) * kPage);
+  const bool redo = min_invariant_ratio<K>(p, mt) < tau;
+  if (redo) repair[atomicAdd(nrepair, 1)] = static_cast<int>(e);
+  flag[e] = redo ? 1 : 0;
 }
 
 // Gluon-helicity combinations with at least one good helicity (fixed ascending order).
@@ -136,25 +127,39 @@ static cudaError_t launch_v2(const double* mom, void* prep, int64_t nevt, const 
 }
 
 template <int K, class T>
-static cudaError_t launch_prep(const double* mom, int64_t nevt, const MeConst& cst, void* rec, int* repair,
-                               int* nrepair, uint8_t* flag, cudaStream_t st) {
+static cudaError_t launch_prep(const double* mom, int64_t nevt, const MeConst& cst, void* rec, cudaStream_t st) {
   if (nevt <= 0) return cudaSuccess;
-  v2::k_event_prep<K, T><<<static_cast<unsigned>((nevt + 127) / 128), 128, 0, st>>>(mom, nevt, cst, static_cast<T*>(rec),
-                                                                                   repair, nrepair, flag);
+  v2::k_event_prep<K, T><<<static_cast<unsigned>((nevt + 127) / 128), 128, 0, st>>>(mom, nevt, cst, static_cast<T*>(rec));
   return cudaGetLastError();
 }
 
 cudaError_t launch_event_prep(int K, bool fp32, const double* mom, int64_t nevt, const MeConst& cst, void* rec,
-                              int* repair, int* nrepair, uint8_t* flag, cudaStream_t st) {
+                              cudaStream_t st) {
   switch (K) {
-    case 2: return fp32 ? launch_prep<2, float>(mom, nevt, cst, rec, repair, nrepair, flag, st)
-                        : launch_prep<2, double>(mom, nevt, cst, rec, repair, nrepair, flag, st);
-    case 3: return fp32 ? launch_prep<3, float>(mom, nevt, cst, rec, repair, nrepair, flag, st)
-                        : launch_prep<3, double>(mom, nevt, cst, rec, repair, nrepair, flag, st);
-    case 4: return fp32 ? launch_prep<4, float>(mom, nevt, cst, rec, repair, nrepair, flag, st)
-                        : launch_prep<4, double>(mom, nevt, cst, rec, repair, nrepair, flag, st);
-    case 5: return fp32 ? launch_prep<5, float>(mom, nevt, cst, rec, repair, nrepair, flag, st)
-                        : launch_prep<5, double>(mom, nevt, cst, rec, repair, nrepair, flag, st);
+    case 2: return fp32 ? launch_prep<2, float>(mom, nevt, cst, rec, st) : launch_prep<2, double>(mom, nevt, cst, rec, st);
+    case 3: return fp32 ? launch_prep<3, float>(mom, nevt, cst, rec, st) : launch_prep<3, double>(mom, nevt, cst, rec, st);
+    case 4: return fp32 ? launch_prep<4, float>(mom, nevt, cst, rec, st) : launch_prep<4, double>(mom, nevt, cst, rec, st);
+    case 5: return fp32 ? launch_prep<5, float>(mom, nevt, cst, rec, st) : launch_prep<5, double>(mom, nevt, cst, rec, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int K>
+static cudaError_t launch_flags(const double* mom, int64_t nevt, const MeConst& cst, int* repair, int* nrepair,
+                                uint8_t* flag, cudaStream_t st) {
+  if (nevt <= 0) return cudaSuccess;
+  v2::k_event_flags<K><<<static_cast<unsigned>((nevt + 127) / 128), 128, 0, st>>>(
+      mom, nevt, static_cast<float>(cst.mt), static_cast<float>(cst.fp32_tau), repair, nrepair, flag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_event_flags(int K, const double* mom, int64_t nevt, const MeConst& cst, int* repair, int* nrepair,
+                               uint8_t* flag, cudaStream_t st) {
+  switch (K) {
+    case 2: return launch_flags<2>(mom, nevt, cst, repair, nrepair, flag, st);
+    case 3: return launch_flags<3>(mom, nevt, cst, repair, nrepair, flag, st);
+    case 4: return launch_flags<4>(mom, nevt, cst, repair, nrepair, flag, st);
+    case 5: return launch_flags<5>(mom, nevt, cst, repair, nrepair, flag, st);
     default: return cudaErrorInvalidValue;
   }
 }

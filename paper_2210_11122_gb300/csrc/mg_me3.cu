@@ -44,27 +44,20 @@ template <> __device__ __forceinline__ double tri<double>(int i) { return c_tri_
 
 using v2::cx;
 
-template <int K, class T, bool JOUT>
-__global__ void __launch_bounds__(kMeThreads)
-k_me_static(const T* __restrict__ rec, int64_t nevt, const int* __restrict__ gslots, const int* __restrict__ nslot_dev,
-            const uint32_t* __restrict__ mask, MeConst cst, double* __restrict__ out, int64_t stride,
-            float2* __restrict__ jout, int tile_ev, int slot_major, const uint8_t* __restrict__ skip) {
-  using L = v2::EvLayout<K>;
+// The matrix element of event e for gluon-helicity slot `slot` (gluon helicities gc), its record read
+// through ld(item): out[slot * stride + e] = sum over the slot's good helicities of the colour sums, or
+// (JOUT) the jamps of its four helicities into jout.
+template <int K, class T, bool JOUT, class Ld>
+__device__ __forceinline__ void me_static_body(Ld&& ld, int64_t e, int slot, int gc, const uint32_t* __restrict__ mask,
+                                               const MeConst& cst, double* __restrict__ out, int64_t stride,
+                                               float2* __restrict__ jout) {
   constexpr int npar = K + 2;
+  using L = v2::EvLayout<K>;
   constexpr int NSEQ = nseq<K>();
   constexpr int NCOL = ncol<K>();
   constexpr int NFULL = nfull<K>();
   constexpr int NSUB = 1 << K;
   constexpr int TRI = kTriOff[K];
-  const int tile_sl = kMeThreads / tile_ev;
-  const unsigned bev = slot_major ? blockIdx.y : blockIdx.x, bsl = slot_major ? blockIdx.x : blockIdx.y;
-  const int64_t e = static_cast<int64_t>(bev) * tile_ev + threadIdx.x % tile_ev;
-  const int slot = static_cast<int>(bsl) * tile_sl + static_cast<int>(threadIdx.x) / tile_ev;
-  if (e >= nevt || slot >= *nslot_dev) return;
-  if (skip && skip[e]) return;   // recomputed by another launch
-  const int gc = gslots[slot];   // bit g = helicity (+1) of gluon g
-  const T* in = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
-  auto ld = [&](int item) -> T { return __ldg(in + item * kPage); };
   const T gs = static_cast<T>(cst.gs);
 
   // ---- gluon currents: external polarisations, then every canonical sequence by length ----
@@ -229,6 +222,60 @@ k_me_static(const T* __restrict__ rec, int64_t nevt, const int* __restrict__ gsl
   if (!JOUT) out[slot * stride + e] = total;
 }
 
+// Record from the per-event kernel (global memory); one thread per (event, slot), launch shape as mg_me2.cu.
+template <int K, class T, bool JOUT>
+__global__ void __launch_bounds__(kMeThreads)
+k_me_static(const T* __restrict__ rec, int64_t nevt, const int* __restrict__ gslots, const int* __restrict__ nslot_dev,
+            const uint32_t* __restrict__ mask, MeConst cst, double* __restrict__ out, int64_t stride,
+            float2* __restrict__ jout, int tile_ev, int slot_major, const uint8_t* __restrict__ skip) {
+  using L = v2::EvLayout<K>;
+  const int tile_sl = kMeThreads / tile_ev;
+  const unsigned bev = slot_major ? blockIdx.y : blockIdx.x, bsl = slot_major ? blockIdx.x : blockIdx.y;
+  const int64_t e = static_cast<int64_t>(bev) * tile_ev + threadIdx.x % tile_ev;
+  const int slot = static_cast<int>(bsl) * tile_sl + static_cast<int>(threadIdx.x) / tile_ev;
+  if (e >= nevt || slot >= *nslot_dev) return;
+  if (skip && skip[e]) return;   // recomputed by another launch
+  const T* in = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
+  me_static_body<K, T, JOUT>([&](int item) -> T { return __ldg(in + item * kPage); }, e, slot, gslots[slot], mask, cst,
+                             out, stride, jout);
+}
+
+// Record computed in the kernel: a block takes 32 events (one per lane); its four warps first compute the
+// four parts of their records in FP64 (subsets of the lower and upper half, gluon polarisations, top
+// spinors) into shared memory, then each warp runs the matrix elements of slots warp, warp + 4, ... of
+// the 32 events.  The FP64 record work of one block overlaps the FP32 work of the others on the SM.
+template <int K, class T, bool JOUT>
+__global__ void __launch_bounds__(kMeThreads)
+k_me_fused(const double* __restrict__ mom, int64_t nevt, const int* __restrict__ gslots, const int* __restrict__ nslot_dev,
+           const uint32_t* __restrict__ mask, MeConst cst, double* __restrict__ out, int64_t stride,
+           float2* __restrict__ jout, const uint8_t* __restrict__ skip) {
+  static_assert(kMeThreads == 128, "four warps: four record parts");
+  using L = v2::EvLayout<K>;
+  constexpr int npar = K + 2, NSUB = 1 << K;
+  __shared__ T rec[L::NITEM * 32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t e = static_cast<int64_t>(blockIdx.x) * 32 + lane;
+  if (e < nevt) {
+    double p[npar][4];
+    const double* base = mom + (e / kPage) * npar * 4 * kPage + (e % kPage);
+#pragma unroll
+    for (int i = 0; i < npar; ++i)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) p[i][m] = __ldg(base + (i * 4 + m) * kPage);
+    auto put = [&](int i, T v) { rec[i * 32 + lane] = v; };
+    if (warp == 0) v2::record_subsets<K, T, 0, NSUB / 2>(p, cst, put);
+    else if (warp == 1) v2::record_subsets<K, T, NSUB / 2, NSUB>(p, cst, put);
+    else if (warp == 2) v2::record_pols<K, T>(p, put);
+    else v2::record_tops<K, T>(p, cst, put);
+  }
+  __syncthreads();
+  if (e >= nevt || (skip && skip[e])) return;   // skipped events: recomputed by another launch
+  const int nslot = *nslot_dev;
+  for (int slot = warp; slot < nslot; slot += 4)
+    me_static_body<K, T, JOUT>([&](int item) -> T { return rec[item * 32 + lane]; }, e, slot, gslots[slot], mask, cst,
+                               out, stride, jout);
+}
+
 std::mutex g_tri_mu;
 bool g_tri_done[64][6] = {};
 
@@ -273,6 +320,33 @@ static cudaError_t launch_static(const void* rec, int64_t nevt, const int* gslot
     st::k_me_static<K, T, false><<<grid, kMeThreads, 0, stream>>>(r, nevt, gslots, nslot, mask, cst, out, stride,
                                                                   nullptr, tev, sm, skip);
   return cudaGetLastError();
+}
+
+template <int K, class T>
+static cudaError_t launch_fused(const double* mom, int64_t nevt, const int* gslots, const int* nslot,
+                                const uint32_t* mask, const MeConst& cst, double* out, int64_t stride, float2* jout,
+                                const uint8_t* skip, cudaStream_t stream) {
+  const unsigned blocks = static_cast<unsigned>((nevt + 31) / 32);
+  if (blocks == 0) return cudaSuccess;
+  if (jout)
+    st::k_me_fused<K, T, true><<<blocks, kMeThreads, 0, stream>>>(mom, nevt, gslots, nslot, mask, cst, out, stride, jout,
+                                                                  skip);
+  else
+    st::k_me_fused<K, T, false><<<blocks, kMeThreads, 0, stream>>>(mom, nevt, gslots, nslot, mask, cst, out, stride,
+                                                                   nullptr, skip);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_me_fused(int K, bool fp32, const double* mom, int64_t nevt, const int* gslots, const int* nslot,
+                            const uint32_t* mask, const MeConst& cst, double* out, int64_t stride, float2* jout,
+                            const uint8_t* skip, cudaStream_t st) {
+  if (!me_static_available(K, fp32)) return cudaErrorInvalidValue;
+  switch (K) {
+    case 2: return launch_fused<2, float>(mom, nevt, gslots, nslot, mask, cst, out, stride, jout, skip, st);
+    case 3: return launch_fused<3, float>(mom, nevt, gslots, nslot, mask, cst, out, stride, jout, skip, st);
+    case 4: return launch_fused<4, float>(mom, nevt, gslots, nslot, mask, cst, out, stride, jout, skip, st);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_me_static(int K, bool fp32, const void* rec, int64_t nevt, const int* gslots, int maxslot,

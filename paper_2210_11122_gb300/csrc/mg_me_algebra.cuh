@@ -383,66 +383,153 @@ template <int K> struct EvLayout {
   static constexpr int NITEM = VV + 16;
 };
 
+// The record in parts, each written through put(item, value): subsets S in [S0, S1) (S0 = 0 or 2^(K-1),
+// so that every subset's momentum sum builds on one of the same range), the gluon polarisation bases,
+// the top spinors.  A per-event kernel computes all parts; the fused FP32 kernel spreads them over warps.
+template <int K, class T, int S0, int S1, class Put>
+__device__ __forceinline__ void record_subsets(const double (*p)[4], const MeConst& cst, Put&& put) {
+  using L = EvLayout<K>;
+  static_assert(S0 == 0 || S0 == (1 << (K - 1)), "subset range");
+  double Pst[S1 - S0][4];
+#pragma unroll
+  for (int S = S0; S < S1; ++S) {
+    const int g = __ffs(S) - 1;
+    const int part = g < 2 ? g : g + 2;
+    const double sg = g < 2 ? 1.0 : -1.0;   // incoming gluons enter with +p, outgoing with -p
+    if (S == 0) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) Pst[0][m] = 0.0;
+    } else if ((S & (S - 1)) == 0 && S0 != 0) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) Pst[S - S0][m] = sg * p[part][m];
+    } else {
+#pragma unroll
+      for (int m = 0; m < 4; ++m) Pst[S - S0][m] = Pst[(S & (S - 1)) - S0][m] + sg * p[part][m];
+    }
+  }
+#pragma unroll
+  for (int S = S0; S < S1; ++S) {
+    const double* P = Pst[S - S0];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) put(L::PT + 4 * S + m, static_cast<T>(P[m]));
+    const double p2 = P[0] * P[0] - P[1] * P[1] - P[2] * P[2] - P[3] * P[3];
+    const double Q0 = p[2][0] - P[0], Q1 = p[2][1] - P[1], Q2 = p[2][2] - P[2], Q3 = p[2][3] - P[3];
+    const double dq = Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3 - cst.mt * cst.mt;
+    double gp, f;
+    if constexpr (sizeof(T) == 8) {
+      gp = (S & (S - 1)) ? -cst.gs / p2 : 0.0;   // includes one power of g
+      f = -cst.gs / dq;
+    } else {
+      // FP32 amplitudes: the denominators P^2 and Q^2 - m^2 (where the cancellations are) and the
+      // products in FP64, the reciprocals Newton-refined from FP32 seeds; one rounding to FP32 at the end
+      gp = (S & (S - 1)) ? -cst.gs * rcp_nr(p2) : 0.0;
+      f = -cst.gs * rcp_nr(dq);
+    }
+    put(L::GP + S, static_cast<T>(gp));
+    put(L::QC + 5 * S + 0, static_cast<T>((Q0 + Q3) * f));
+    put(L::QC + 5 * S + 1, static_cast<T>((Q0 - Q3) * f));
+    put(L::QC + 5 * S + 2, static_cast<T>(Q1 * f));
+    put(L::QC + 5 * S + 3, static_cast<T>(Q2 * f));
+    put(L::QC + 5 * S + 4, static_cast<T>(cst.mt * f));
+  }
+}
+
+template <int K, class T, class Put>
+__device__ __forceinline__ void record_pols(const double (*p)[4], Put&& put) {
+  using L = EvLayout<K>;
+#pragma unroll
+  for (int g = 0; g < K; ++g) {
+    T pol[5];
+    gluon_pol<T>(p[g < 2 ? g : g + 2], pol);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) put(L::EPS + 5 * g + i, pol[i]);
+  }
+}
+
+template <int K, class T, class Put>
+__device__ __forceinline__ void record_tops(const double (*p)[4], const MeConst& cst, Put&& put) {
+  using L = EvLayout<K>;
+#pragma unroll
+  for (int l = 0; l < 2; ++l) {
+    cx<T> ub[4], vv[4];
+    top_ubar<T>(p[2], cst.mt, l ? 1 : -1, ub);
+    top_v<T>(p[3], cst.mt, l ? 1 : -1, vv);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      put(L::UB + (l * 4 + a) * 2, ub[a].r);
+      put(L::UB + (l * 4 + a) * 2 + 1, ub[a].i);
+      put(L::VV + (l * 4 + a) * 2, vv[a].r);
+      put(L::VV + (l * 4 + a) * 2 + 1, vv[a].i);
+    }
+  }
+}
+
+template <int K, class T, class Put>
+__device__ __forceinline__ void record_all(const double (*p)[4], const MeConst& cst, Put&& put) {
+  record_subsets<K, T, 0, (1 << K)>(p, cst, put);
+  record_pols<K, T>(p, put);
+  record_tops<K, T>(p, cst, put);
+}
+
+// The whole record of one event as arrays (the kernels that compute it per thread)
 template <int K, class T>
 __device__ __forceinline__ void event_data(const double (*p)[4], const MeConst& cst, T (*PT)[4], T* gprop, T (*qc)[5],
-                                           T (*pol)[5], cx<T> (*ub)[4], cx<T> (*vv)[4],
-                                           double* min_invariant = nullptr) {
+                                           T (*pol)[5], cx<T> (*ub)[4], cx<T> (*vv)[4]) {
+  using L = EvLayout<K>;
+  T r[L::NITEM];
+  record_all<K, T>(p, cst, [&](int i, T v) { r[i] = v; });
   constexpr int NSUB = 1 << K;
-  double xmin = 1e300;
-  double Pst[NSUB][4];
 #pragma unroll
-  for (int m = 0; m < 4; ++m) Pst[0][m] = 0.0;
+  for (int S = 0; S < NSUB; ++S) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) PT[S][m] = r[L::PT + 4 * S + m];
+    gprop[S] = r[L::GP + S];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) qc[S][c] = r[L::QC + 5 * S + c];
+  }
+#pragma unroll
+  for (int g = 0; g < K; ++g)
+#pragma unroll
+    for (int i = 0; i < 5; ++i) pol[g][i] = r[L::EPS + 5 * g + i];
+#pragma unroll
+  for (int l = 0; l < 2; ++l)
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+      ub[l][a] = {r[L::UB + (l * 4 + a) * 2], r[L::UB + (l * 4 + a) * 2 + 1]};
+      vv[l][a] = {r[L::VV + (l * 4 + a) * 2], r[L::VV + (l * 4 + a) * 2 + 1]};
+    }
+}
+
+// Smallest internal invariant of an event relative to s = (p1 + p2)^2: over the gluon propagators |P_S^2|
+// (|S| >= 2) and the quark propagators |(p_t - P_S)^2 - m^2| (S neither empty nor all gluons), in FP32
+// (absolute error ~1e-7 s, far below the thresholds it is compared with).
+template <int K>
+__device__ __forceinline__ float min_invariant_ratio(const double (*p)[4], float mt) {
+  constexpr int NSUB = 1 << K;
+  float q[K + 2][4];
+#pragma unroll
+  for (int i = 0; i < K + 2; ++i)
+#pragma unroll
+    for (int m = 0; m < 4; ++m) q[i][m] = static_cast<float>(p[i][m]);
+  float Pst[NSUB][4];
+  float xmin = 3.0e38f;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) Pst[0][m] = 0.f;
 #pragma unroll
   for (int S = 1; S < NSUB; ++S) {
     const int g = __ffs(S) - 1;
     const int part = g < 2 ? g : g + 2;
-    const double sg = g < 2 ? 1.0 : -1.0;
+    const float sg = g < 2 ? 1.f : -1.f;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) Pst[S][m] = Pst[S & (S - 1)][m] + sg * p[part][m];
+    for (int m = 0; m < 4; ++m) Pst[S][m] = Pst[S & (S - 1)][m] + sg * q[part][m];
+    if (S == NSUB - 1) continue;
+    const float* P = Pst[S];
+    const float Q0 = q[2][0] - P[0], Q1 = q[2][1] - P[1], Q2 = q[2][2] - P[2], Q3 = q[2][3] - P[3];
+    xmin = fminf(xmin, fabsf(Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3 - mt * mt));
+    if (S & (S - 1)) xmin = fminf(xmin, fabsf(P[0] * P[0] - P[1] * P[1] - P[2] * P[2] - P[3] * P[3]));
   }
-#pragma unroll
-  for (int S = 0; S < NSUB; ++S) {
-    const double* P = Pst[S];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) PT[S][m] = static_cast<T>(P[m]);
-    const double p2 = P[0] * P[0] - P[1] * P[1] - P[2] * P[2] - P[3] * P[3];
-    const double Q0 = p[2][0] - P[0], Q1 = p[2][1] - P[1], Q2 = p[2][2] - P[2], Q3 = p[2][3] - P[3];
-    const double dq = Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3 - cst.mt * cst.mt;
-    if (S != 0 && S != NSUB - 1) {   // internal lines only (S = 0 and S = all are the external tops)
-      xmin = fmin(xmin, fabs(dq));
-      if (S & (S - 1)) xmin = fmin(xmin, fabs(p2));
-    }
-    if constexpr (sizeof(T) == 8) {
-      gprop[S] = static_cast<T>((S & (S - 1)) ? -cst.gs / p2 : 0.0);   // includes one power of g
-      const double f = -cst.gs / dq;
-      qc[S][0] = static_cast<T>((Q0 + Q3) * f);
-      qc[S][1] = static_cast<T>((Q0 - Q3) * f);
-      qc[S][2] = static_cast<T>(Q1 * f);
-      qc[S][3] = static_cast<T>(Q2 * f);
-      qc[S][4] = static_cast<T>(cst.mt * f);
-    } else {
-      // FP32 amplitudes: the denominators P^2 and Q^2 - m^2 (where the cancellations are) and the
-      // products in FP64, the reciprocals Newton-refined from FP32 seeds; one rounding to FP32 at the end
-      gprop[S] = static_cast<T>((S & (S - 1)) ? -cst.gs * rcp_nr(p2) : 0.0);
-      const double f = -cst.gs * rcp_nr(dq);
-      qc[S][0] = static_cast<T>((Q0 + Q3) * f);
-      qc[S][1] = static_cast<T>((Q0 - Q3) * f);
-      qc[S][2] = static_cast<T>(Q1 * f);
-      qc[S][3] = static_cast<T>(Q2 * f);
-      qc[S][4] = static_cast<T>(cst.mt * f);
-    }
-  }
-#pragma unroll
-  for (int g = 0; g < K; ++g) gluon_pol<T>(p[g < 2 ? g : g + 2], pol[g]);
-  top_ubar<T>(p[2], cst.mt, -1, ub[0]);
-  top_ubar<T>(p[2], cst.mt, 1, ub[1]);
-  top_v<T>(p[3], cst.mt, -1, vv[0]);
-  top_v<T>(p[3], cst.mt, 1, vv[1]);
-  if (min_invariant) {
-    const double s0 = p[0][0] + p[1][0], s1 = p[0][1] + p[1][1], s2 = p[0][2] + p[1][2], s3 = p[0][3] + p[1][3];
-    const double shat = s0 * s0 - s1 * s1 - s2 * s2 - s3 * s3;   // (p1 + p2)^2
-    *min_invariant = xmin / fabs(shat);
-  }
+  const float s0 = q[0][0] + q[1][0], s1 = q[0][1] + q[1][1], s2 = q[0][2] + q[1][2], s3 = q[0][3] + q[1][3];
+  return xmin / fabsf(s0 * s0 - s1 * s1 - s2 * s2 - s3 * s3);
 }
 
 }  // namespace v2

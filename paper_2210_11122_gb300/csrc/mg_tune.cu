@@ -36,7 +36,7 @@ std::string cache_key(mg_ctx* ctx, mg_precision precision) {
 }
 
 int launch_flags(const mg::MeShape& s) {
-  return (s.unrolled ? MG_LAUNCH_UNROLLED : 0) | (s.df_redo ? MG_LAUNCH_DF_REDO : 0);
+  return (s.unrolled ? MG_LAUNCH_UNROLLED : 0) | (s.df_redo ? MG_LAUNCH_DF_REDO : 0) | (s.fused ? MG_LAUNCH_FUSED : 0);
 }
 
 bool cache_lookup(const char* path, const std::string& key, mg::MeShape* shape, double* ms) {
@@ -55,6 +55,7 @@ bool cache_lookup(const char* path, const std::string& key, mg::MeShape* shape, 
       shape->slot_major = sm != 0;
       shape->unrolled = (un & MG_LAUNCH_UNROLLED) != 0;
       shape->df_redo = (un & MG_LAUNCH_DF_REDO) != 0;
+      shape->fused = (un & MG_LAUNCH_FUSED) != 0;
       *ms = t;
       found = true;
     }
@@ -127,10 +128,18 @@ extern "C" mg_status mg_autotune(mg_ctx* ctx, mg_precision precision, int64_t ne
         s.tile_ev = tiles[ti];
         s.slot_major = sm != 0;
         s.unrolled = nun == 2 ? un == 0 : true;
+        s.fused = false;
         float t = 1e30f;
         rc = time_shape(s, &t);
         if (rc == MG_OK && t < best_t) { best_t = t; best = s; }
       }
+  if (nun == 2 && rc == MG_OK) {   // the unrolled kernel with the record computed inside (fixed shape)
+    mg::MeShape s;
+    s.fused = true;
+    float t = 1e30f;
+    rc = time_shape(s, &t);
+    if (rc == MG_OK && t < best_t) { best_t = t; best = s; }
+  }
   if (fp32 && rc == MG_OK) {   // the recomputation arithmetic, on the best shape
     mg::MeShape s = best;
     s.df_redo = !s.df_redo;
@@ -166,12 +175,13 @@ extern "C" mg_status mg_set_launch_shape(mg_ctx* ctx, mg_precision precision, in
                                          int flags) {
   if (!ctx || precision < MG_FP64 || precision > MG_MIXED) return MG_EINVAL;
   if ((tile_ev != 32 && tile_ev != 64 && tile_ev != 128) || (slot_major != 0 && slot_major != 1) ||
-      (flags & ~(MG_LAUNCH_UNROLLED | MG_LAUNCH_DF_REDO)) != 0)
+      (flags & ~(MG_LAUNCH_UNROLLED | MG_LAUNCH_DF_REDO | MG_LAUNCH_FUSED)) != 0)
     return MG_EINVAL;
   ctx->shape[precision].tile_ev = tile_ev;
   ctx->shape[precision].slot_major = slot_major != 0;
   ctx->shape[precision].unrolled = (flags & MG_LAUNCH_UNROLLED) != 0;
   ctx->shape[precision].df_redo = (flags & MG_LAUNCH_DF_REDO) != 0;
+  ctx->shape[precision].fused = (flags & MG_LAUNCH_FUSED) != 0;
   return MG_OK;
 }
 
