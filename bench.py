@@ -262,7 +262,8 @@ def run_ours(args):
             ctx.autotune(prec, nevt=min(nevt, 65536))
             tev, slm, fl = ctx.launch_shape(prec)
             shapes[name] = {"tile_ev": tev, "slot_major": slm, "unrolled": bool(fl & mg.LAUNCH_UNROLLED),
-                            "df_redo": bool(fl & mg.LAUNCH_DF_REDO), "fused": bool(fl & mg.LAUNCH_FUSED)}
+                            "df_redo": bool(fl & mg.LAUNCH_DF_REDO), "fused": bool(fl & mg.LAUNCH_FUSED),
+                            "warp": bool(fl & mg.LAUNCH_WARP)}
 
     clocks = ClockSampler(local)
     clocks.start()

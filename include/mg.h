@@ -198,16 +198,20 @@ mg_status mg_sigmakin_noalloc(mg_ctx* ctx, const double* mom_dev, int64_t nevt, 
  *                       otherwise idles beside the FP32 launch);
  *   MG_LAUNCH_FUSED     with MG_LAUNCH_UNROLLED: the per-event FP64 record is computed inside the
  *                       matrix-element kernel (32 events per block; tile_ev and slot_major unused), so
- *                       that its FP64 work overlaps the FP32 work of other blocks. */
+ *                       that its FP64 work overlaps the FP32 work of other blocks;
+ *   MG_LAUNCH_WARP      FP32 amplitudes of gg -> t tbar + 1..3 gluons: one warp per (event, gluon-helicity
+ *                       combination), its currents and jamps in shared memory, the work split over the
+ *                       lanes (takes precedence over MG_LAUNCH_UNROLLED). */
 #define MG_LAUNCH_UNROLLED 1
 #define MG_LAUNCH_DF_REDO 2
 #define MG_LAUNCH_FUSED 4
+#define MG_LAUNCH_WARP 8
 
 /* Time mg_sigmakin(precision) of nevt probe events (this context's process, fixed seed) for each
  * launch shape of the matrix-element kernel -- 32, 64 or 128 events per 128-thread block (the other
  * threads of a block take further helicity combinations of the same events), grid dispatched
  * event-tile-major or helicity-tile-major, with and without MG_LAUNCH_UNROLLED where that kernel
- * exists, and MG_LAUNCH_UNROLLED | MG_LAUNCH_FUSED -- then, for the FP32 modes, the fastest with
+ * exists, MG_LAUNCH_UNROLLED | MG_LAUNCH_FUSED and MG_LAUNCH_WARP -- then, for the FP32 modes, the fastest with
  * MG_LAUNCH_DF_REDO toggled, and keep the fastest
  * for this context and precision.  cache_path (may be NULL): text file of
  * "gpu|process|precision tile_ev slot_major flags ms" lines; an existing entry is used without timing,

@@ -233,6 +233,7 @@ void mg_destroy(mg_ctx* ctx) {
   cudaFree(ctx->d_tab);
   cudaFree(ctx->d_ctri);
   cudaFree(ctx->d_ctri_f);
+  cudaFree(ctx->d_cfull);
   cudaFree(ctx->d_mask);
   cudaFree(ctx->d_maxr);
   cudaFree(ctx->d_good);
@@ -299,6 +300,9 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
     e = cudaMalloc(&c->d_ctri, tri.size() * sizeof(double));
     if (e == cudaSuccess) e = cudaMemcpy(c->d_ctri, tri.data(), tri.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = mg::me_static_upload_colour(c->K, tri.data(), static_cast<int>(tri.size()));
+    std::vector<float> full(num.begin(), num.end());
+    if (e == cudaSuccess) e = cudaMalloc(&c->d_cfull, full.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(c->d_cfull, full.data(), full.size() * sizeof(float), cudaMemcpyHostToDevice);
     std::vector<float> trif(tri.begin(), tri.end());
     if (e == cudaSuccess) e = cudaMalloc(&c->d_ctri_f, trif.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(c->d_ctri_f, trif.data(), trif.size() * sizeof(float), cudaMemcpyHostToDevice);
@@ -467,7 +471,8 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
     // amplitudes -> FP32 jamps -> tensor-core colour sums, in chunks of whole pages that keep the jamp
     // buffer within 4 GiB
     const bool fp32 = precision == MG_MIXED;
-    const bool fused = fp32 && ctx->shape[precision].fused && ctx->shape[precision].unrolled &&
+    const bool warp = fp32 && ctx->shape[precision].warp && mg::me_warp_available(ctx->K, true);
+    const bool fused = fp32 && !warp && ctx->shape[precision].fused && ctx->shape[precision].unrolled &&
                        mg::me_static_available(ctx->K, true);
     const int64_t per_event = static_cast<int64_t>(ctx->nhel) * ctx->ncol;   // float2 per event
     int64_t chunk = (int64_t(1) << 29) / per_event;                          // 2^29 float2 = 4 GiB
@@ -502,6 +507,9 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
       if (fused)
         MG_CUDA(mg::launch_me_fused(ctx->K, true, mom_c, n, ctx->d_gslots, ctx->d_ngslots, ctx->d_mask, cst, ctx->d_part,
                                     cst_stride, ctx->d_jamps, ctx->d_flag, st));
+      else if (warp)
+        MG_CUDA(mg::launch_me_warp(ctx->K, ctx->d_prep, n, ctx->d_tab, ctx->d_gslots, 1 << ctx->K, ctx->d_ngslots,
+                                   ctx->d_mask, ctx->d_cfull, cst, ctx->d_part, cst_stride, ctx->d_jamps, ctx->d_flag, st));
       else
         MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_c, ctx->d_prep, n, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
                                        ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, cst_stride,
@@ -513,7 +521,8 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
     }
   } else if (ctx->prm.wt == 0.0) {
     const bool fp32 = precision == MG_FP32_AMP;
-    const bool fused = fp32 && ctx->shape[precision].fused && ctx->shape[precision].unrolled &&
+    const bool warp = fp32 && ctx->shape[precision].warp && mg::me_warp_available(ctx->K, true);
+    const bool fused = fp32 && !warp && ctx->shape[precision].fused && ctx->shape[precision].unrolled &&
                        mg::me_static_available(ctx->K, true);
     s = grow(&ctx->d_prep, &ctx->prep_cap, stride * mg::event_record_bytes(ctx->K, fp32) / 8 + 1);
     if (s == MG_OK && fp32) s = grow_repair(ctx, stride);
@@ -529,6 +538,9 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
     if (fused)
       MG_CUDA(mg::launch_me_fused(ctx->K, true, mom_dev, nevt, ctx->d_gslots, ctx->d_ngslots, ctx->d_mask, cst,
                                   ctx->d_part, stride, nullptr, ctx->d_flag, st));
+    else if (warp)
+      MG_CUDA(mg::launch_me_warp(ctx->K, ctx->d_prep, nevt, ctx->d_tab, ctx->d_gslots, 1 << ctx->K, ctx->d_ngslots,
+                                 ctx->d_mask, ctx->d_cfull, cst, ctx->d_part, stride, nullptr, ctx->d_flag, st));
     else
       MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_dev, ctx->d_prep, nevt, ctx->d_tab, ctx->d_gslots,
                                      1 << ctx->K, ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part,

@@ -14,6 +14,7 @@ struct mg_ctx {
   mg::Tables* d_tab = nullptr;
   double* d_ctri = nullptr;   // packed upper triangle of the integer colour matrix, off-diagonal doubled
   float* d_ctri_f = nullptr;  // the same in FP32 (exact: integers < 2^24)
+  float* d_cfull = nullptr;   // the full ncol x ncol numerator matrix in FP32 (warp-per-slot kernel)
   int64_t colour_den = 1;
   uint32_t* d_mask = nullptr;
   double* d_maxr = nullptr;   // per-helicity maximum ratio of the last helicity filter
