@@ -36,7 +36,12 @@ def test_autotune_keeps_results_and_caches(env, proc, precision, tmp_path):
         tev, sm, ms = ctx.autotune(precision, nevt=2048, cache_path=cache)
         assert tev in (32, 64, 128) and sm in (0, 1) and ms > 0
         got = step(torch, mg, ctx, 5, 0, 1000, precision)
-    assert np.array_equal(got, ref)          # the shape changes scheduling, not arithmetic
+    if precision == mg.MG_FP64:
+        assert np.array_equal(got, ref)      # FP64: the shape changes scheduling, not arithmetic
+    else:
+        # FP32 modes: the autotuner also chooses among kernels (other FP32 summation orders); every one
+        # stays within 1e-5 of FP64, so two of them agree within 2e-5
+        assert np.max(np.abs(got / ref - 1)) <= 2e-5
     line = open(cache).read().split()
     assert int(line[1]) == tev and int(line[2]) == sm
     with mg.Context(proc) as ctx2:           # second context: taken from the cache without timing
