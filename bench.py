@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shape (fixed launch order)")
     ap.add_argument("--serve", action="store_true", help="serving workload: request trace, p50/p99 latency")
     ap.add_argument("--requests", type=int, default=2000)
-    ap.add_argument("--serve-precision", default="fp64", choices=["fp64", "fp32_amp", "fp64_tccolor", "mixed"])
+    ap.add_argument("--serve-precision", default="fp64",
+                    help="precision of the served form: fp64, fp32_amp, fp64_tccolor or mixed; a comma-separated "
+                         "list serves each in turn against one one-at-a-time FP64 baseline")
     ap.add_argument("--slots", type=int, default=8)
     return ap.parse_args()
 
@@ -429,12 +431,16 @@ def run_serve(args):
     from paper_2210_11122_gb300 import build as mgbuild
     mgbuild.build()
     import paper_2210_11122_gb300 as mg
-    prec = {"fp64": mg.MG_FP64, "fp32_amp": mg.MG_FP32_AMP, "fp64_tccolor": mg.MG_FP64_TCCOLOR,
-            "mixed": mg.MG_MIXED}[args.serve_precision]
+    names = [x.strip() for x in args.serve_precision.split(",") if x.strip()]
+    table = {"fp64": mg.MG_FP64, "fp32_amp": mg.MG_FP32_AMP, "fp64_tccolor": mg.MG_FP64_TCCOLOR, "mixed": mg.MG_MIXED}
+    for n in names:
+        if n not in table:
+            raise SystemExit("unknown --serve-precision %r" % n)
     proc, nevt, expo = serve_trace(mg, torch, args.requests)
     total = int(nevt.sum())
+    runs = [("served_" + n, args.slots, table[n]) for n in names] + [("one_at_a_time_fp64", 1, mg.MG_FP64)]
     out = {}
-    for label, slots, precision in (("served", args.slots, prec), ("one_at_a_time_fp64", 1, mg.MG_FP64)):
+    for label, slots, precision in runs:
         with mg.Server(slots=slots, precision=precision) as srv:
             w = [srv.submit(p, 10**9 + p, 2048) for p in range(4)]       # warm-up
             for t in w:
@@ -446,16 +452,19 @@ def run_serve(args):
                           "open_loop_rate_req_per_s": 0.8 * cap, "open_loop_MEs_per_s": total / span2,
                           "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                           "peak": srv.stats()}
-    s, o = out["served"], out["one_at_a_time_fp64"]
+    s, o = out["served_" + names[0]], out["one_at_a_time_fp64"]
     line = {"metric": "served MEs/s (closed loop) and p50/p99 latency at 80% of capacity", "value":
             s["closed_loop_MEs_per_s"], "unit": "MEs/s", "n_gpus": 1, "higher_is_better": True,
-            "dtype": args.serve_precision, "data": "synthetic",
+            "dtype": names[0], "data": "synthetic",
             "config": {"workload": "serving mix: %d requests, gg->tt/ttg/ttgg/ttggg with p=0.4/0.3/0.2/0.1, nevt "
                                    "log-uniform in [32, 65536] (multiple of 32), seed = request id, Poisson "
                                    "arrivals at 80%% of measured capacity, HBM admission cap 64 GiB" % args.requests,
                        "requests": args.requests, "events": total},
             "served": s, "one_at_a_time_fp64": o,
             "speedup_closed_loop": s["closed_loop_MEs_per_s"] / o["closed_loop_MEs_per_s"]}
+    if len(names) > 1:
+        line["served_modes"] = {n: dict(out["served_" + n], speedup_closed_loop=out["served_" + n]["closed_loop_MEs_per_s"]
+                                                                           / o["closed_loop_MEs_per_s"]) for n in names}
     print(json.dumps(line))
     return 0
 
