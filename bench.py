@@ -40,6 +40,31 @@ L2_FLUSH_BYTES = 256 << 20
 METRIC = "MEs/s"
 
 
+# ------------------------------------------------------------------------------------------
+# multi-rank bookkeeping (one process per GPU; weak scaling, no collective on the data path)
+# ------------------------------------------------------------------------------------------
+def rank_first_event(rank, nevt_per_rank):
+    """Ranks take consecutive disjoint ranges of the seed's event stream: rank r processes events
+    [r nevt, (r + 1) nevt), so N ranks reproduce the single-GPU sample of N nevt events."""
+    return rank * nevt_per_rank
+
+
+def max_over_ranks(values, world, device="cpu"):
+    """Element-wise maximum over the ranks (the slowest rank sets a step's time)."""
+    if world <= 1:
+        return list(values)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor(list(values), dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def aggregate_rate(world, nevt_per_rank, ms):
+    """Whole-job MEs/s: the events of all ranks over the slowest rank's time per step."""
+    return world * nevt_per_rank / (ms * 1e-3)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -214,7 +239,7 @@ def run_ours(args):
     w = WORKLOADS[args.process]
     ng, seed = w["ng"], w["seed"]
     nevt = args.nevt or w["nevt"]
-    e0 = rank * nevt
+    e0 = rank_first_event(rank, nevt)
     stream = torch.cuda.Stream()
     ctx = mg.Context(ng, mt=MT, alphas=ALPHAS)
     mom = torch.zeros(ctx.mom_count(nevt), dtype=torch.float64, device="cuda")
@@ -272,11 +297,8 @@ def run_ours(args):
     ms_step, ms_me, wall = timed(mg.MG_FP64, args.steps, max(3, args.warmup))
     clk = clocks.stop()
     nbad = ctx.check(stream)
-    if world > 1:
-        t = torch.tensor([ms_step, ms_me], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step, ms_me = t.tolist()
-    value = world * nevt / (ms_step * 1e-3)
+    ms_step, ms_me = max_over_ranks([ms_step, ms_me], world, "cuda")
+    value = aggregate_rate(world, nevt, ms_step)
 
     # the other arithmetic modes on the same step: FP32 amplitudes; FP64 or FP32 amplitudes with the
     # colour sum on the tensor cores
@@ -285,8 +307,9 @@ def run_ours(args):
     for name, prec in (("fp32_amp", mg.MG_FP32_AMP), ("fp64_tccolor", mg.MG_FP64_TCCOLOR), ("mixed", mg.MG_MIXED)):
         msv, msv_me, _ = timed(prec, max(3, args.steps // 2), 3)
         torch.cuda.synchronize()
+        msv, msv_me = max_over_ranks([msv, msv_me], world, "cuda")
         rel = ((me32.double().cpu() / ref64) - 1).abs()
-        variants[name] = {"value": world * nevt / (msv * 1e-3), "ms_per_step": msv, "me_kernel_ms": msv_me,
+        variants[name] = {"value": aggregate_rate(world, nevt, msv), "ms_per_step": msv, "me_kernel_ms": msv_me,
                           "rel_err_vs_fp64": {"max": float(rel.max()), "p99": float(rel.quantile(0.99)),
                                               "median": float(rel.median())}}
 
@@ -309,6 +332,7 @@ def run_ours(args):
             flush.zero_()
     torch.cuda.synchronize()
     graph_ms = statistics.mean(gev[2 * k].elapsed_time(gev[2 * k + 1]) for k in range(args.steps))
+    graph_ms = max_over_ranks([graph_ms], world, "cuda")[0]
     graph_same = bool(torch.equal(gme, me))
     graph.close()
     gctx.close()
@@ -323,8 +347,8 @@ def run_ours(args):
     t0 = time.perf_counter()
     for _ in range(ne2e):
         ctx.sigmakin_host(host_mom, nevt, host_me, mg.MG_FP64, stream=stream)
-    e2e_s = (time.perf_counter() - t0) / ne2e
-    e2e = {"value": world * nevt / e2e_s, "unit": "MEs/s", "h2d_bytes_per_step": int(host_mom.numel() * 8),
+    e2e_s = max_over_ranks([(time.perf_counter() - t0) / ne2e], world, "cuda")[0]
+    e2e = {"value": aggregate_rate(world, nevt, e2e_s * 1e3), "unit": "MEs/s", "h2d_bytes_per_step": int(host_mom.numel() * 8),
            "d2h_bytes_per_step": int(nevt * 8),
            "api": "mg_sigmakin_host: pinned AoSoA momenta -> device -> FP64 MEs -> host"}
 
@@ -377,7 +401,7 @@ def run_ours(args):
             "config": config_of(args, nevt, {"parallelism": "dp%d (disjoint event ranges)" % world}),
             "me_kernel_ms": ms_me, "wall_s": wall, "nonconverged_events": nbad, "good_helicities": ngood,
             "modes": variants, "launch_shapes": shapes,
-            "graph": {"ms_per_step": graph_ms, "value": world * nevt / (graph_ms * 1e-3), "same_result": graph_same,
+            "graph": {"ms_per_step": graph_ms, "value": aggregate_rate(world, nevt, graph_ms), "same_result": graph_same,
                       "what": "the FP64 step captured as one CUDA graph (mg_graph_create) and replayed"},
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": launches_per_step * args.steps}
