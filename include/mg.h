@@ -199,9 +199,10 @@ mg_status mg_sigmakin_noalloc(mg_ctx* ctx, const double* mom_dev, int64_t nevt, 
  *   MG_LAUNCH_FUSED     with MG_LAUNCH_UNROLLED: the per-event FP64 record is computed inside the
  *                       matrix-element kernel (32 events per block; tile_ev and slot_major unused), so
  *                       that its FP64 work overlaps the FP32 work of other blocks;
- *   MG_LAUNCH_WARP      FP32 amplitudes of gg -> t tbar + 1..3 gluons: one warp per (event, gluon-helicity
- *                       combination), its currents and jamps in shared memory, the work split over the
- *                       lanes (takes precedence over MG_LAUNCH_UNROLLED). */
+ *   MG_LAUNCH_WARP      FP32 amplitudes of gg -> t tbar + 1..3 gluons: one group of lanes (4, 8 or 32 for
+ *                       1, 2 or 3 final-state gluons) per (event, gluon-helicity combination), its
+ *                       currents and jamps in shared memory, the work split over the lanes (takes
+ *                       precedence over MG_LAUNCH_UNROLLED). */
 #define MG_LAUNCH_UNROLLED 1
 #define MG_LAUNCH_DF_REDO 2
 #define MG_LAUNCH_FUSED 4
@@ -220,7 +221,7 @@ mg_status mg_autotune(mg_ctx* ctx, mg_precision precision, int64_t nevt, const c
 
 /* The launch shape mg_sigmakin(precision) uses on this context (default: 128 events per block,
  * event-tile-major, flags MG_LAUNCH_UNROLLED | MG_LAUNCH_DF_REDO | MG_LAUNCH_FUSED, plus MG_LAUNCH_WARP for
- * gg -> t tbar g g g).  Any out-pointer may be NULL. */
+ * gg -> t tbar g g and t tbar g g g).  Any out-pointer may be NULL. */
 mg_status mg_get_launch_shape(mg_ctx* ctx, mg_precision precision, int* tile_ev, int* slot_major, int* flags);
 
 /* Set the launch shape of mg_sigmakin(precision) by hand: tile_ev in {32, 64, 128}, slot_major 0 or 1,

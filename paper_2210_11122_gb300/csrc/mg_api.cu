@@ -346,9 +346,9 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
       st = MG_ECUDA;
       break;
     }
-    // five gluons: the FP32 modes default to the warp-per-slot kernel (the per-thread state does not
-    // fit on chip); the autotuner can change it
-    if (c->K == 5)
+    // four and five gluons: the FP32 modes default to the lane-group-per-slot kernel (the per-thread
+    // state does not fit on chip); the autotuner can change it
+    if (c->K >= 4)
       for (int p = 0; p < 4; ++p) c->shape[p].warp = true;
     // side stream of the FP32 modes' recomputation: highest priority, so that its few blocks are
     // dispatched ahead of the FP32 launch's

@@ -1,16 +1,18 @@
-// mg_me_warp.cu -- FP32 matrix-element kernel with one warp per (event, gluon-helicity slot).
+// mg_me_warp.cu -- FP32 matrix-element kernel with one lane group (a warp or part of one) per (event,
+// gluon-helicity slot).
 //
 // Same physics, record input and outputs as the per-thread kernels (mg_me_kernel.cuh, mg_me3.cu), for
 // processes whose per-slot state does not fit in a thread: with 5 gluons a slot carries 105 gluon
 // currents, 60 all-gluon currents and 4 x 120 jamps (~9 KB), which a thread can only keep in local
-// memory (spilled to L2 and DRAM at the occupancy the FP32 pipe needs).  Here the 32 lanes of a warp
-// share that state in shared memory and split the work:
+// memory (spilled to L2 and DRAM at the occupancy the FP32 pipe needs).  Here the G lanes of a group
+// (G = 32 for 5 gluons, 8 for 4, 4 for 3) share that state in shared memory and split the work:
 //   * currents level by level (all sequences of one length are independent): one sequence per lane;
-//   * the quark-line walk: lanes 0-15 take top helicity -, lanes 16-31 top helicity +, each lane a
-//     contiguous run of colour orderings (prefix spinors shared along the run, in registers);
+//   * the quark-line walk: the first half of the group takes top helicity -, the second half top
+//     helicity +, each lane a contiguous run of colour orderings (prefix spinors shared along the run,
+//     in registers);
 //   * the colour sums of the four helicities together: rows of C A per lane (register-blocked over
-//     rows and helicities), then warp sums; or (jamp output) the jamps are written out for the
-//     tensor-core colour sum.
+//     rows and helicities), then sums over the group; or (jamp output) the jamps are written out for
+//     the tensor-core colour sum.
 #include <cuda_runtime.h>
 
 #include "mg_internal.h"
@@ -22,12 +24,13 @@ namespace wk {
 
 using v2::cx;
 
-constexpr int kWarps = 4;   // warps (slots of one event) per block
+constexpr int kWarps = 4;   // warps per block; a block holds slots of one event
 
+// lanes per slot G: the work of one slot spread over as many lanes as its widest stage keeps busy
 template <int K> struct WSizes;
-template <> struct WSizes<3> { static constexpr int ncol = 6, nseq = 6, nfull = 3; };
-template <> struct WSizes<4> { static constexpr int ncol = 24, nseq = 22, nfull = 12; };
-template <> struct WSizes<5> { static constexpr int ncol = 120, nseq = 105, nfull = 60; };
+template <> struct WSizes<3> { static constexpr int ncol = 6, nseq = 6, nfull = 3, G = 4; };
+template <> struct WSizes<4> { static constexpr int ncol = 24, nseq = 22, nfull = 12, G = 8; };
+template <> struct WSizes<5> { static constexpr int ncol = 120, nseq = 105, nfull = 60, G = 32; };
 
 // shared state of one slot: component-major, so that lanes reading different currents hit different banks
 template <int K>
@@ -60,13 +63,15 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
   using L = v2::EvLayout<K>;
   constexpr int npar = K + 2, NCOL = WSizes<K>::ncol, NFULL = WSizes<K>::nfull;
   constexpr int NSUB = 1 << K;
-  __shared__ SlotState<K> sh[kWarps];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr int G = WSizes<K>::G, GPW = 32 / G;   // lanes per slot, slots per warp
+  __shared__ SlotState<K> sh[kWarps * GPW];
+  const int warp = threadIdx.x >> 5, grp = (threadIdx.x & 31) / G, lane = threadIdx.x % G;
+  const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << (G & 31)) - 1u)) << (grp * G);   // this group's lanes
   const int64_t e = blockIdx.x;
-  const int slot = blockIdx.y * kWarps + warp;
-  if (e >= nevt || slot >= *nslot_dev) return;
+  const int slot = (blockIdx.y * kWarps + warp) * GPW + grp;
+  if (e >= nevt || slot >= *nslot_dev) return;   // whole groups leave: every sync below is per group
   if (skip && skip[e]) return;   // recomputed by another launch
-  SlotState<K>& S = sh[warp];
+  SlotState<K>& S = sh[warp * GPW + grp];
   const int gc = gslots[slot];   // bit g = helicity (+1) of gluon g
   const float* in = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
   auto ld = [&](int item) -> float { return __ldg(in + item * kPage); };
@@ -82,7 +87,7 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
 #pragma unroll
     for (int m = 0; m < 4; ++m) S.J[m][lane] = f2(w[m]);
   }
-  __syncwarp();
+  __syncwarp(gmask);
   auto getJ = [&](int slot_ref, cx<float>* j) {
 #pragma unroll
     for (int m = 0; m < 4; ++m) j[m] = c2(S.J[m][slot_ref >> 1]);
@@ -117,26 +122,26 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
   // ---- gluon currents by length: the sequences of one length are independent ----
 #pragma unroll
   for (int len = 2; len < K; ++len) {
-    for (int s = seq_start(K, len) + lane; s < seq_start(K, len + 1); s += 32) {
+    for (int s = seq_start(K, len) + lane; s < seq_start(K, len + 1); s += G) {
       cx<float> acc[4] = {};
       current(tab->seq_nv3[s], tab->seq_v3[s], tab->seq_nv4[s], tab->seq_v4[s], acc);
       const float f = ld(L::GP + tab->seq_mask[s]);
 #pragma unroll
       for (int m = 0; m < 4; ++m) S.J[m][s] = f2(v2::cscale(f, acc[m]));
     }
-    __syncwarp();
+    __syncwarp(gmask);
   }
   // ---- all gluons on one current (canonical orderings) ----
   {
     const float fz = ld(L::GP + NSUB - 1);
-    for (int f = lane; f < NFULL; f += 32) {
+    for (int f = lane; f < NFULL; f += G) {
       cx<float> acc[4] = {};
       current(tab->full_nv3[f], tab->full_v3[f], tab->full_nv4[f], tab->full_v4[f], acc);
 #pragma unroll
       for (int m = 0; m < 4; ++m) S.JF[m][f] = f2(v2::cscale(fz, acc[m]));
     }
   }
-  __syncwarp();
+  __syncwarp(gmask);
 
   // ---- quark line: half-warp per top helicity, a run of orderings per lane ----
   int hbase = 0;
@@ -151,8 +156,9 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
     good[k] = (mask[h >> 5] >> (h & 31)) & 1u;
   }
   {
-    const int a = lane >> 4, hl = lane & 15;
-    const int c0 = hl * NCOL / 16, c1 = (hl + 1) * NCOL / 16;
+    constexpr int H = G / 2;   // lanes per top helicity
+    const int a = lane / H, hl = lane % H;
+    const int c0 = hl * NCOL / H, c1 = (hl + 1) * NCOL / H;
     if (good[2 * a] || good[2 * a + 1]) {
       cx<float> vv[2][4], stk[K][4], Jq[2][4];
 #pragma unroll
@@ -212,15 +218,15 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
       }
     }
   }
-  __syncwarp();
+  __syncwarp(gmask);
 
   if constexpr (JOUT) {
     float2* row = jout + (e * (4 << K) + slot * 4) * NCOL;
-    for (int i = lane; i < 4 * NCOL; i += 32) row[i] = S.A[i / NCOL][i % NCOL];
+    for (int i = lane; i < 4 * NCOL; i += G) row[i] = S.A[i / NCOL][i % NCOL];
   } else {
-    // colour sums of the four helicities at once: lane l forms rows x = l, l + 32, ... of w_h = C A_h
+    // colour sums of the four helicities at once: lane l forms rows x = l, l + G, ... of w_h = C A_h
     // (C symmetric: row y of C read along x, coalesced; each C value feeds 8 FMAs), then A_h^* . w_h
-    constexpr int XR = (NCOL + 31) / 32;   // rows per lane
+    constexpr int XR = (NCOL + G - 1) / G;   // rows per lane
     float wr[4][XR] = {}, wi[4][XR] = {};
     for (int y = 0; y < NCOL; ++y) {
       float2 ay[4];
@@ -228,7 +234,7 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
       for (int h = 0; h < 4; ++h) ay[h] = S.A[h][y];
 #pragma unroll
       for (int k = 0; k < XR; ++k) {
-        const int x = lane + 32 * k;
+        const int x = lane + G * k;
         const float cxy = x < NCOL ? __ldg(cfull + y * NCOL + x) : 0.f;
 #pragma unroll
         for (int h = 0; h < 4; ++h) {
@@ -239,12 +245,11 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
     }
     double total = 0.0;
 #pragma unroll
-    for (int h = 0; h < 4; ++h) {
-      if (!good[h]) continue;   // uniform across the warp
+    for (int h = 0; h < 4; ++h) {   // jamps of helicities outside the mask are zero: no branch needed
       float s = 0.f;
 #pragma unroll
       for (int k = 0; k < XR; ++k) {
-        const int x = lane + 32 * k;
+        const int x = lane + G * k;
         if (x < NCOL) {
           const float2 ax = S.A[h][x];
           s = fmaf(ax.x, wr[h][k], s);
@@ -252,8 +257,8 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
         }
       }
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      total += static_cast<double>(s) * cst.colour_scale;
+      for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, G);
+      if (good[h]) total += static_cast<double>(s) * cst.colour_scale;
     }
     if (lane == 0) out[slot * stride + e] = total;
   }
@@ -265,7 +270,8 @@ static cudaError_t launch_k(const void* rec, int64_t nevt, const Tables* tab, co
                             int64_t stride, float2* jout, const uint8_t* skip, cudaStream_t st) {
   if (nevt <= 0 || maxslot <= 0) return cudaSuccess;
   if (nevt > 0x7fffffffLL) return cudaErrorInvalidValue;
-  const dim3 grid(static_cast<unsigned>(nevt), static_cast<unsigned>((maxslot + kWarps - 1) / kWarps));
+  constexpr int per_block = kWarps * (32 / WSizes<K>::G);   // slots per block
+  const dim3 grid(static_cast<unsigned>(nevt), static_cast<unsigned>((maxslot + per_block - 1) / per_block));
   const float* r = static_cast<const float*>(rec);
   if (jout)
     k_me_warp<K, true><<<grid, kWarps * 32, 0, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, cst, out, stride, jout,
