@@ -394,7 +394,9 @@ def run_ours(args):
                "sample": "first %d events of the workload (of %d), FP64 ME only, %.1f s on %d threads"
                          % (n, nevt, dt, cores)}
 
-    launches_per_step = 1 + 3 + 2   # rambo; filter (ME, sum, mask); sigmakin (ME, sum)
+    # rambo; helicity filter (per-helicity ME, helicity sum, ratio maximum, mask, slot list); FP64
+    # sigmakin (per-event record, ME, helicity sum)
+    launches_per_step = 1 + 5 + 3
     line = {"metric": METRIC, "value": value, "unit": "MEs/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
