@@ -202,18 +202,22 @@ mg_status mg_sigmakin_noalloc(mg_ctx* ctx, const double* mom_dev, int64_t nevt, 
  *   MG_LAUNCH_WARP      FP32 amplitudes of gg -> t tbar + 1..3 gluons: one group of lanes (4, 8 or 32 for
  *                       1, 2 or 3 final-state gluons) per (event, gluon-helicity combination), its
  *                       currents and jamps in shared memory, the work split over the lanes (takes
- *                       precedence over MG_LAUNCH_UNROLLED). */
+ *                       precedence over MG_LAUNCH_UNROLLED); with MG_MIXED it also sums the colours on
+ *                       the tensor cores itself, unless
+ *   MG_LAUNCH_TC_APART  MG_MIXED with MG_LAUNCH_WARP: write the jamps out for the separate tensor-core
+ *                       colour kernel instead. */
 #define MG_LAUNCH_UNROLLED 1
 #define MG_LAUNCH_DF_REDO 2
 #define MG_LAUNCH_FUSED 4
 #define MG_LAUNCH_WARP 8
+#define MG_LAUNCH_TC_APART 16
 
 /* Time mg_sigmakin(precision) of nevt probe events (this context's process, fixed seed) for each
  * launch shape of the matrix-element kernel -- 32, 64 or 128 events per 128-thread block (the other
  * threads of a block take further helicity combinations of the same events), grid dispatched
  * event-tile-major or helicity-tile-major, with and without MG_LAUNCH_UNROLLED where that kernel
- * exists, MG_LAUNCH_UNROLLED | MG_LAUNCH_FUSED and MG_LAUNCH_WARP -- then, for the FP32 modes, the fastest with
- * MG_LAUNCH_DF_REDO toggled, and keep the fastest
+ * exists, MG_LAUNCH_UNROLLED | MG_LAUNCH_FUSED, MG_LAUNCH_WARP and (MG_MIXED) MG_LAUNCH_WARP | MG_LAUNCH_TC_APART
+ * -- then, for the FP32 modes, the fastest with MG_LAUNCH_DF_REDO toggled, and keep the fastest
  * for this context and precision.  cache_path (may be NULL): text file of
  * "gpu|process|precision tile_ev slot_major flags ms" lines; an existing entry is used without timing,
  * a new result is appended.  *best_ms may be NULL.  Synchronous; allocates probe buffers; nevt >= 32. */

@@ -110,6 +110,11 @@ mg_status grow_repair(mg_ctx* ctx, int64_t n) {
 
 namespace mg {
 
+bool mixed_in_kernel(const mg_ctx* ctx, mg_precision precision) {
+  return precision == MG_MIXED && ctx->prm.wt == 0.0 && ctx->shape[precision].warp &&
+         !ctx->shape[precision].tc_apart && me_warp_available(ctx->K, true);
+}
+
 // Grow every scratch buffer of ctx so that mg_hel_filter and mg_sigmakin(precision) on up to nevt
 // events allocate nothing (used by the serving loop, which must not synchronise the device).
 mg_status ctx_reserve(mg_ctx* ctx, int64_t nevt, mg_precision precision) {
@@ -119,7 +124,7 @@ mg_status ctx_reserve(mg_ctx* ctx, int64_t nevt, mg_precision precision) {
   mg_status s = grow(&ctx->d_part, &ctx->part_cap, (stride > wstride ? stride : wstride) * ctx->nhel);
   if (s == MG_OK) s = grow(&ctx->d_tot, &ctx->tot_cap, wstride);
   const bool fp32 = precision == MG_FP32_AMP || precision == MG_MIXED;
-  const bool tc = precision == MG_FP64_TCCOLOR || precision == MG_MIXED;
+  const bool tc = (precision == MG_FP64_TCCOLOR || precision == MG_MIXED) && !mixed_in_kernel(ctx, precision);
   int64_t chunk = stride;
   if (tc) {
     const int64_t per_event = static_cast<int64_t>(ctx->nhel) * ctx->ncol;
@@ -148,7 +153,10 @@ int64_t footprint_bytes(mg_process proc, int64_t nevt, mg_precision precision) {
   const int K = gluons_of(proc), npar = K + 2, nhel = 1 << npar, ncol = factorial(K);
   const int64_t stride = pad32(nevt);
   const bool fp32 = precision == MG_FP32_AMP || precision == MG_MIXED;
-  const bool tc = precision == MG_FP64_TCCOLOR || precision == MG_MIXED;
+  // jamps in device memory: the tensor-core colour modes, except FP32 amplitudes with four or five
+  // gluons, whose default lane-group kernel sums the colours on the tensor cores itself
+  const bool tc = precision == MG_FP64_TCCOLOR || (precision == MG_MIXED && !me_warp_available(K, true)) ||
+                  (precision == MG_MIXED && K < 4);
   int64_t b = stride * npar * 4 * 8 + stride * 8 + stride * nhel * 8 + stride * event_record_bytes(K, fp32);
   if (fp32) b += stride * (sizeof(int) + 1);   // recomputation list and flags
   if (tc) b += stride * nhel * ncol * 8;
@@ -350,6 +358,8 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
     // state does not fit on chip); the autotuner can change it
     if (c->K >= 4)
       for (int p = 0; p < 4; ++p) c->shape[p].warp = true;
+    // five gluons, FP32 amplitudes + tensor-core colour: the separate colour kernel (measured faster there)
+    if (c->K == 5) c->shape[MG_MIXED].tc_apart = true;
     // side stream of the FP32 modes' recomputation: highest priority, so that its few blocks are
     // dispatched ahead of the FP32 launch's
     int lo = 0, hi = 0;
@@ -460,6 +470,8 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
   const bool tc = precision == MG_FP64_TCCOLOR || precision == MG_MIXED;
   if (tc && ctx->prm.wt != 0.0) return MG_ENOTSUP;   // the tensor-core colour path has zero top width
   if (nevt == 0) return MG_OK;
+  // FP32 amplitudes with the lane-group kernel: the tensor-core colour sum runs inside it (no jamps)
+  const bool mixed_in_kernel = mg::mixed_in_kernel(ctx, precision);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (!ctx->mask_ready) {
     mg_status s = mg_hel_filter(ctx, mom_dev, nevt, stream);
@@ -471,7 +483,7 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
   ctx->last = st;
   const mg::MeConst cst = me_const(ctx);
   const double norm = 1.0 / (256.0 * mg::factorial(ctx->ng));
-  if (tc) {
+  if (tc && !mixed_in_kernel) {
     // amplitudes -> FP32 jamps -> tensor-core colour sums, in chunks of whole pages that keep the jamp
     // buffer within 4 GiB
     const bool fp32 = precision == MG_MIXED;
@@ -513,7 +525,8 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
                                     cst_stride, ctx->d_jamps, ctx->d_flag, st));
       else if (warp)
         MG_CUDA(mg::launch_me_warp(ctx->K, ctx->d_prep, n, ctx->d_tab, ctx->d_gslots, 1 << ctx->K, ctx->d_ngslots,
-                                   ctx->d_mask, ctx->d_cfull, cst, ctx->d_part, cst_stride, ctx->d_jamps, ctx->d_flag, st));
+                                   ctx->d_mask, ctx->d_cfull, ctx->d_cmat, 1, cst, ctx->d_part, cst_stride, ctx->d_jamps,
+                                   ctx->d_flag, st));
       else
         MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_c, ctx->d_prep, n, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
                                        ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, cst_stride,
@@ -524,7 +537,7 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
       MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_nrows, n, cst_stride, norm, me_dev + e0, st));
     }
   } else if (ctx->prm.wt == 0.0) {
-    const bool fp32 = precision == MG_FP32_AMP;
+    const bool fp32 = precision == MG_FP32_AMP || mixed_in_kernel;
     const bool warp = fp32 && ctx->shape[precision].warp && mg::me_warp_available(ctx->K, true);
     const bool fused = fp32 && !warp && ctx->shape[precision].fused && ctx->shape[precision].unrolled &&
                        mg::me_static_available(ctx->K, true);
@@ -544,7 +557,8 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
                                   ctx->d_part, stride, nullptr, ctx->d_flag, st));
     else if (warp)
       MG_CUDA(mg::launch_me_warp(ctx->K, ctx->d_prep, nevt, ctx->d_tab, ctx->d_gslots, 1 << ctx->K, ctx->d_ngslots,
-                                 ctx->d_mask, ctx->d_cfull, cst, ctx->d_part, stride, nullptr, ctx->d_flag, st));
+                                 ctx->d_mask, ctx->d_cfull, ctx->d_cmat, mixed_in_kernel ? 2 : 0, cst, ctx->d_part,
+                                 stride, nullptr, ctx->d_flag, st));
     else
       MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_dev, ctx->d_prep, nevt, ctx->d_tab, ctx->d_gslots,
                                      1 << ctx->K, ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part,

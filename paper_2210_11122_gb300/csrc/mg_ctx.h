@@ -53,6 +53,8 @@ struct mg_ctx {
 
 
 namespace mg {
+// MG_MIXED on the lane-group kernel: colour sums on the tensor cores inside it, per-slot outputs
+bool mixed_in_kernel(const mg_ctx* ctx, mg_precision precision);
 mg_status ctx_reserve(mg_ctx* ctx, int64_t nevt, mg_precision precision);
 int64_t footprint_bytes(mg_process proc, int64_t nevt, mg_precision precision);
 }  // namespace mg

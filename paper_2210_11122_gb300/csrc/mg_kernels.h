@@ -25,8 +25,9 @@ struct MeConst {
 // df_redo: the FP32 modes recompute their flagged events with double-float (else FP64) amplitudes.
 // fused: (unrolled FP32 kernel only) the per-event record is computed inside the matrix-element kernel
 // (k_me_fused: 32 events per block, the slots looped by its warps; tile_ev and slot_major unused).
-// warp: (FP32, where me_warp_available) one warp per (event, slot), state in shared memory (mg_me_warp.cu);
-// takes precedence over unrolled.
+// warp: (FP32, where me_warp_available) one lane group per (event, slot), state in shared memory
+// (mg_me_warp.cu); takes precedence over unrolled.  tc_apart: MG_MIXED with warp writes the jamps out for
+// launch_colour_tc instead of summing the colours on the tensor cores in the kernel.
 struct MeShape {
   int tile_ev = 128;
   bool slot_major = false;
@@ -34,6 +35,7 @@ struct MeShape {
   bool df_redo = true;
   bool fused = true;
   bool warp = false;
+  bool tc_apart = false;
 };
 
 cudaError_t launch_philox(uint64_t seed, int64_t nevt, int nfinal, uint32_t* words, cudaStream_t st);
@@ -79,12 +81,15 @@ cudaError_t me_static_upload_colour(int K, const double* tri, int n);
 cudaError_t launch_me_static(int K, bool fp32, const void* rec, int64_t nevt, const int* gslots, int maxslot,
                              const int* nslot, const uint32_t* mask, const MeConst& cst, double* out, int64_t stride,
                              float2* jout, MeShape shape, const uint8_t* skip, cudaStream_t st);
-// The warp-per-(event, slot) FP32 kernel (mg_me_warp.cu): launch_me_gluonhel's contract with a record rec
-// (FP32) from launch_event_prep; cfull = the full ncol x ncol colour matrix numerators in FP32.
+// The lane-group-per-(event, slot) FP32 kernel (mg_me_warp.cu): launch_me_gluonhel's contract with a record
+// rec (FP32) from launch_event_prep.  epi 0: colour sums in FP32 with cfull (the full ncol x ncol numerator
+// matrix in FP32); 1: jamps to jout for launch_colour_tc; 2: colour sums on the tensor cores in the kernel
+// with cmat16 (the FP16 operand of launch_colour_tc).  Epilogues 0 and 2 write out[slot * stride + e].
 bool me_warp_available(int K, bool fp32);
 cudaError_t launch_me_warp(int K, const void* rec, int64_t nevt, const Tables* tab, const int* gslots, int maxslot,
-                           const int* nslot, const uint32_t* mask, const float* cfull, const MeConst& cst, double* out,
-                           int64_t stride, float2* jout, const uint8_t* skip, cudaStream_t st);
+                           const int* nslot, const uint32_t* mask, const float* cfull, const void* cmat16, int epi,
+                           const MeConst& cst, double* out, int64_t stride, float2* jout, const uint8_t* skip,
+                           cudaStream_t st);
 // The same with the record computed inside the kernel from the momenta (no per-event kernel first).
 cudaError_t launch_me_fused(int K, bool fp32, const double* mom, int64_t nevt, const int* gslots, const int* nslot,
                             const uint32_t* mask, const MeConst& cst, double* out, int64_t stride, float2* jout,

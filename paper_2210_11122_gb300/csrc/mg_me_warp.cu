@@ -13,6 +13,7 @@
 //   * the colour sums of the four helicities together: rows of C A per lane (register-blocked over
 //     rows and helicities), then sums over the group; or (jamp output) the jamps are written out for
 //     the tensor-core colour sum.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "mg_internal.h"
@@ -54,12 +55,38 @@ __host__ __device__ constexpr int seq_start(int K, int L) {
   return L <= 1 ? 0 : s;
 }
 
-template <int K, bool JOUT>
-__global__ void __launch_bounds__(kWarps * 32)
+// Epilogues: the colour sums in FP32 on the FP32 pipe (SIMT), the jamps written out for the separate
+// tensor-core colour kernel (JAMPS), or the colour sums on the tensor cores inside this kernel (MMA)
+enum Epi { kSimt = 0, kJamps = 1, kMma = 2 };
+
+// 2^k as a double, built from its exponent bits (exact; |k| < 1000): undoes a power-of-two row scale
+// with one multiplication instead of an FP64 division
+__device__ __forceinline__ double pow2d(int k) { return __longlong_as_double(static_cast<long long>(1023 + k) << 52); }
+
+__device__ __forceinline__ void mma16816(float* d, const uint32_t* a, const uint32_t* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+__device__ __forceinline__ uint32_t pack_h2(__half lo_half, __half hi_half) {
+  return static_cast<uint32_t>(__half_as_ushort(lo_half)) | (static_cast<uint32_t>(__half_as_ushort(hi_half)) << 16);
+}
+__device__ __forceinline__ float unsplit(uint32_t h, uint32_t l, int k) {
+  const __half hh = __ushort_as_half(static_cast<unsigned short>(k ? h >> 16 : h & 0xffffu));
+  const __half lh = __ushort_as_half(static_cast<unsigned short>(k ? l >> 16 : l & 0xffffu));
+  return fmaf(__half2float(lh), 1.f / 2048.f, __half2float(hh));
+}
+
+// (resident blocks per SM: 5, or 4 with the tensor-core epilogue, whose fragments must not cost the
+// amplitude phase more occupancy than that)
+template <int K, int EPI>
+__global__ void __launch_bounds__(kWarps * 32, EPI == kMma ? 4 : 5)
 k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab, const int* __restrict__ gslots,
           const int* __restrict__ nslot_dev, const uint32_t* __restrict__ mask, const float* __restrict__ cfull,
-          MeConst cst, double* __restrict__ out, int64_t stride, float2* __restrict__ jout,
-          const uint8_t* __restrict__ skip) {
+          const __half* __restrict__ cmat16, MeConst cst, double* __restrict__ out, int64_t stride,
+          float2* __restrict__ jout, const uint8_t* __restrict__ skip) {
   using L = v2::EvLayout<K>;
   constexpr int npar = K + 2, NCOL = WSizes<K>::ncol, NFULL = WSizes<K>::nfull;
   constexpr int NSUB = 1 << K;
@@ -67,83 +94,21 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
   __shared__ SlotState<K> sh[kWarps * GPW];
   const int warp = threadIdx.x >> 5, grp = (threadIdx.x & 31) / G, lane = threadIdx.x % G;
   const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << (G & 31)) - 1u)) << (grp * G);   // this group's lanes
-  const int64_t e = blockIdx.x;
-  const int slot = (blockIdx.y * kWarps + warp) * GPW + grp;
-  if (e >= nevt || slot >= *nslot_dev) return;   // whole groups leave: every sync below is per group
-  if (skip && skip[e]) return;   // recomputed by another launch
+  const int64_t e = blockIdx.x;   // one block per event: e < nevt
+  const int slot0 = (blockIdx.y * kWarps + warp) * GPW;   // the warp's first slot
+  const int slot = slot0 + grp;
+  const int nslot = *nslot_dev;
+  if (skip && skip[e]) return;   // recomputed by another launch (the whole block: one event)
+  const bool active = slot < nslot;
+  // groups past the last slot leave (every sync of the slot work is per group), except with the
+  // tensor-core epilogue, whose MMAs take the whole warp: there they contribute zero jamps
+  if (EPI != kMma && !active) return;
   SlotState<K>& S = sh[warp * GPW + grp];
-  const int gc = gslots[slot];   // bit g = helicity (+1) of gluon g
+  const int gc = active ? gslots[slot] : 0;   // bit g = helicity (+1) of gluon g
   const float* in = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
   auto ld = [&](int item) -> float { return __ldg(in + item * kPage); };
   const float gs = static_cast<float>(cst.gs);
-
-  // ---- external gluon currents ----
-  if (lane < K) {
-    float pol[5];
-#pragma unroll
-    for (int i = 0; i < 5; ++i) pol[i] = ld(L::EPS + 5 * lane + i);
-    cx<float> w[4];
-    v2::ext_gluon(pol, (gc >> lane) & 1 ? 1 : -1, lane >= 2, w);
-#pragma unroll
-    for (int m = 0; m < 4; ++m) S.J[m][lane] = f2(w[m]);
-  }
-  __syncwarp(gmask);
-  auto getJ = [&](int slot_ref, cx<float>* j) {
-#pragma unroll
-    for (int m = 0; m < 4; ++m) j[m] = c2(S.J[m][slot_ref >> 1]);
-  };
-  auto getP = [&](int seq, float* P) {
-    const int msk = tab->seq_mask[seq];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) P[m] = ld(L::PT + 4 * msk + m);
-  };
-  // current of sequence s (splits from the tables) into acc
-  auto current = [&](int nv3, const int16_t (*v3)[2], int nv4, const int16_t (*v4)[3], cx<float>* acc) {
-    for (int k = 0; k < nv3; ++k) {
-      const int rl = v3[k][0], rr = v3[k][1];
-      cx<float> JL[4], JR[4];
-      float PL[4], PR[4];
-      getJ(rl, JL);
-      getJ(rr, JR);
-      getP(rl >> 1, PL);
-      getP(rr >> 1, PR);
-      v2::v3_acc(acc, JL, JR, PL, PR, ((rl ^ rr) & 1) != 0);
-    }
-    for (int k = 0; k < nv4; ++k) {
-      const int ra = v4[k][0], rb = v4[k][1], rc = v4[k][2];
-      cx<float> JA[4], JB[4], JC[4];
-      getJ(ra, JA);
-      getJ(rb, JB);
-      getJ(rc, JC);
-      v2::v4_acc(acc, JA, JB, JC, gs, ((ra ^ rb ^ rc) & 1) != 0);
-    }
-  };
-
-  // ---- gluon currents by length: the sequences of one length are independent ----
-#pragma unroll
-  for (int len = 2; len < K; ++len) {
-    for (int s = seq_start(K, len) + lane; s < seq_start(K, len + 1); s += G) {
-      cx<float> acc[4] = {};
-      current(tab->seq_nv3[s], tab->seq_v3[s], tab->seq_nv4[s], tab->seq_v4[s], acc);
-      const float f = ld(L::GP + tab->seq_mask[s]);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) S.J[m][s] = f2(v2::cscale(f, acc[m]));
-    }
-    __syncwarp(gmask);
-  }
-  // ---- all gluons on one current (canonical orderings) ----
-  {
-    const float fz = ld(L::GP + NSUB - 1);
-    for (int f = lane; f < NFULL; f += G) {
-      cx<float> acc[4] = {};
-      current(tab->full_nv3[f], tab->full_v3[f], tab->full_nv4[f], tab->full_v4[f], acc);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) S.JF[m][f] = f2(v2::cscale(fz, acc[m]));
-    }
-  }
-  __syncwarp(gmask);
-
-  // ---- quark line: half-warp per top helicity, a run of orderings per lane ----
+  // helicity index of (gc, top helicity, antitop helicity), and which of the four are in the mask
   int hbase = 0;
 #pragma unroll
   for (int g = 0; g < K; ++g)
@@ -153,77 +118,149 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
     const int h = hbase | ((k >> 1) ? bit_t : 0) | ((k & 1) ? bit_tb : 0);
-    good[k] = (mask[h >> 5] >> (h & 31)) & 1u;
+    good[k] = active && ((mask[h >> 5] >> (h & 31)) & 1u);
   }
-  {
-    constexpr int H = G / 2;   // lanes per top helicity
-    const int a = lane / H, hl = lane % H;
-    const int c0 = hl * NCOL / H, c1 = (hl + 1) * NCOL / H;
-    if (good[2 * a] || good[2 * a + 1]) {
-      cx<float> vv[2][4], stk[K][4], Jq[2][4];
+  if (active) {
+
+    // ---- external gluon currents ----
+    if (lane < K) {
+      float pol[5];
 #pragma unroll
-      for (int b = 0; b < 2; ++b)
+      for (int i = 0; i < 5; ++i) pol[i] = ld(L::EPS + 5 * lane + i);
+      cx<float> w[4];
+      v2::ext_gluon(pol, (gc >> lane) & 1 ? 1 : -1, lane >= 2, w);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) vv[b][q] = {ld(L::VV + (b * 4 + q) * 2), ld(L::VV + (b * 4 + q) * 2 + 1)};
+      for (int m = 0; m < 4; ++m) S.J[m][lane] = f2(w[m]);
+    }
+    __syncwarp(gmask);
+    auto getJ = [&](int slot_ref, cx<float>* j) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) stk[0][q] = {ld(L::UB + (a * 4 + q) * 2), ld(L::UB + (a * 4 + q) * 2 + 1)};
-      v2::quark_current(stk[0], vv[0], Jq[0]);
-      v2::quark_current(stk[0], vv[1], Jq[1]);
-      for (int c = c0; c < c1; ++c) {
-        const int l = c == c0 ? 0 : tab->lcp[c];
+      for (int m = 0; m < 4; ++m) j[m] = c2(S.J[m][slot_ref >> 1]);
+    };
+    auto getP = [&](int seq, float* P) {
+      const int msk = tab->seq_mask[seq];
 #pragma unroll
-        for (int m = 1; m < K; ++m) {
-          if (m <= l) continue;
-          cx<float> acc[4] = {};
-#pragma unroll
-          for (int j = 0; j < m; ++j) {
-            const int r = tab->sub[c][j][m];
-            cx<float> Jr[4];
-            getJ(r, Jr);
-            v2::row_gamma_acc(acc, stk[j], Jr, (r & 1) != 0);
-          }
-          const int pm = tab->prefix_mask[c][m];
-          float q[5];
-#pragma unroll
-          for (int k = 0; k < 5; ++k) q[k] = ld(L::QC + 5 * pm + k);
-          v2::row_prop(acc, q, stk[m]);
-        }
-        const int fi = tab->full_idx[c];
-        const int fj = fi >= 0 ? fi : -fi - 1;
-        const bool fneg = fi < 0 && !(K & 1);   // reflection sign (-1)^(K+1)
-        cx<float> JFc[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) JFc[m] = c2(S.JF[m][fj]);
-        cx<float> amp0 = v2::mdot(Jq[0], JFc), amp1 = v2::mdot(Jq[1], JFc);
-        if (fneg) {
-          amp0 = v2::cneg(amp0);
-          amp1 = v2::cneg(amp1);
-        }
-#pragma unroll
-        for (int j = 1; j < K; ++j) {
-          const int r = tab->sub[c][j][K];
-          cx<float> Jr[4], t[4] = {};
-          getJ(r, Jr);
-          v2::row_gamma_acc(t, stk[j], Jr, (r & 1) != 0);
-          v2::sdot_acc(amp0, t, vv[0], false);
-          v2::sdot_acc(amp1, t, vv[1], false);
-        }
-        S.A[2 * a][c] = good[2 * a] ? f2(amp0) : make_float2(0.f, 0.f);
-        S.A[2 * a + 1][c] = good[2 * a + 1] ? f2(amp1) : make_float2(0.f, 0.f);
+      for (int m = 0; m < 4; ++m) P[m] = ld(L::PT + 4 * msk + m);
+    };
+    // current of sequence s (splits from the tables) into acc
+    auto current = [&](int nv3, const int16_t (*v3)[2], int nv4, const int16_t (*v4)[3], cx<float>* acc) {
+      for (int k = 0; k < nv3; ++k) {
+        const int rl = v3[k][0], rr = v3[k][1];
+        cx<float> JL[4], JR[4];
+        float PL[4], PR[4];
+        getJ(rl, JL);
+        getJ(rr, JR);
+        getP(rl >> 1, PL);
+        getP(rr >> 1, PR);
+        v2::v3_acc(acc, JL, JR, PL, PR, ((rl ^ rr) & 1) != 0);
       }
-    } else {
-      for (int c = c0; c < c1; ++c) {
-        S.A[2 * a][c] = make_float2(0.f, 0.f);
-        S.A[2 * a + 1][c] = make_float2(0.f, 0.f);
+      for (int k = 0; k < nv4; ++k) {
+        const int ra = v4[k][0], rb = v4[k][1], rc = v4[k][2];
+        cx<float> JA[4], JB[4], JC[4];
+        getJ(ra, JA);
+        getJ(rb, JB);
+        getJ(rc, JC);
+        v2::v4_acc(acc, JA, JB, JC, gs, ((ra ^ rb ^ rc) & 1) != 0);
+      }
+    };
+
+    // ---- gluon currents by length: the sequences of one length are independent ----
+#pragma unroll
+    for (int len = 2; len < K; ++len) {
+      for (int s = seq_start(K, len) + lane; s < seq_start(K, len + 1); s += G) {
+        cx<float> acc[4] = {};
+        current(tab->seq_nv3[s], tab->seq_v3[s], tab->seq_nv4[s], tab->seq_v4[s], acc);
+        const float f = ld(L::GP + tab->seq_mask[s]);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) S.J[m][s] = f2(v2::cscale(f, acc[m]));
+      }
+      __syncwarp(gmask);
+    }
+    // ---- all gluons on one current (canonical orderings) ----
+    {
+      const float fz = ld(L::GP + NSUB - 1);
+      for (int f = lane; f < NFULL; f += G) {
+        cx<float> acc[4] = {};
+        current(tab->full_nv3[f], tab->full_v3[f], tab->full_nv4[f], tab->full_v4[f], acc);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) S.JF[m][f] = f2(v2::cscale(fz, acc[m]));
       }
     }
-  }
-  __syncwarp(gmask);
+    __syncwarp(gmask);
 
-  if constexpr (JOUT) {
+    // ---- quark line: half-group per top helicity, a run of orderings per lane ----
+    {
+      constexpr int H = G / 2;   // lanes per top helicity
+      const int a = lane / H, hl = lane % H;
+      const int c0 = hl * NCOL / H, c1 = (hl + 1) * NCOL / H;
+      if (good[2 * a] || good[2 * a + 1]) {
+        cx<float> vv[2][4], stk[K][4], Jq[2][4];
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) vv[b][q] = {ld(L::VV + (b * 4 + q) * 2), ld(L::VV + (b * 4 + q) * 2 + 1)};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) stk[0][q] = {ld(L::UB + (a * 4 + q) * 2), ld(L::UB + (a * 4 + q) * 2 + 1)};
+        v2::quark_current(stk[0], vv[0], Jq[0]);
+        v2::quark_current(stk[0], vv[1], Jq[1]);
+        for (int c = c0; c < c1; ++c) {
+          const int l = c == c0 ? 0 : tab->lcp[c];
+#pragma unroll
+          for (int m = 1; m < K; ++m) {
+            if (m <= l) continue;
+            cx<float> acc[4] = {};
+#pragma unroll
+            for (int j = 0; j < m; ++j) {
+              const int r = tab->sub[c][j][m];
+              cx<float> Jr[4];
+              getJ(r, Jr);
+              v2::row_gamma_acc(acc, stk[j], Jr, (r & 1) != 0);
+            }
+            const int pm = tab->prefix_mask[c][m];
+            float q[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) q[k] = ld(L::QC + 5 * pm + k);
+            v2::row_prop(acc, q, stk[m]);
+          }
+          const int fi = tab->full_idx[c];
+          const int fj = fi >= 0 ? fi : -fi - 1;
+          const bool fneg = fi < 0 && !(K & 1);   // reflection sign (-1)^(K+1)
+          cx<float> JFc[4];
+#pragma unroll
+          for (int m = 0; m < 4; ++m) JFc[m] = c2(S.JF[m][fj]);
+          cx<float> amp0 = v2::mdot(Jq[0], JFc), amp1 = v2::mdot(Jq[1], JFc);
+          if (fneg) {
+            amp0 = v2::cneg(amp0);
+            amp1 = v2::cneg(amp1);
+          }
+#pragma unroll
+          for (int j = 1; j < K; ++j) {
+            const int r = tab->sub[c][j][K];
+            cx<float> Jr[4], t[4] = {};
+            getJ(r, Jr);
+            v2::row_gamma_acc(t, stk[j], Jr, (r & 1) != 0);
+            v2::sdot_acc(amp0, t, vv[0], false);
+            v2::sdot_acc(amp1, t, vv[1], false);
+          }
+          S.A[2 * a][c] = good[2 * a] ? f2(amp0) : make_float2(0.f, 0.f);
+          S.A[2 * a + 1][c] = good[2 * a + 1] ? f2(amp1) : make_float2(0.f, 0.f);
+        }
+      } else {
+        for (int c = c0; c < c1; ++c) {
+          S.A[2 * a][c] = make_float2(0.f, 0.f);
+          S.A[2 * a + 1][c] = make_float2(0.f, 0.f);
+        }
+      }
+    }
+    __syncwarp(gmask);
+  } else {   // a slot past the last one (tensor-core epilogue only): zero jamps
+    for (int i = lane; i < 4 * NCOL; i += G) S.A[i / NCOL][i % NCOL] = make_float2(0.f, 0.f);
+  }
+
+  if constexpr (EPI == kJamps) {
     float2* row = jout + (e * (4 << K) + slot * 4) * NCOL;
     for (int i = lane; i < 4 * NCOL; i += G) row[i] = S.A[i / NCOL][i % NCOL];
-  } else {
+  } else if constexpr (EPI == kSimt) {
     // colour sums of the four helicities at once: lane l forms rows x = l, l + G, ... of w_h = C A_h
     // (C symmetric: row y of C read along x, coalesced; each C value feeds 8 FMAs), then A_h^* . w_h
     constexpr int XR = (NCOL + G - 1) / G;   // rows per lane
@@ -261,24 +298,117 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
       if (good[h]) total += static_cast<double>(s) * cst.colour_scale;
     }
     if (lane == 0) out[slot * stride + e] = total;
+  } else {
+    // colour sums on the tensor cores, the warp's slots together: MMA rows = (slot, helicity, Re/Im),
+    // 8 per slot; each row scaled by a power of two and split hi + lo 2^-11 in FP16 against the exact
+    // FP16 integer colour matrix, FP32 accumulation (as the separate tensor-core colour kernel)
+    __syncwarp();
+    constexpr int KP = (NCOL + 15) / 16 * 16, KS = KP / 16, NT = (NCOL + 7) / 8, LDH = KP + 8;
+    constexpr int ROWS = 8 * GPW, MT = (ROWS + 15) / 16;
+    const int lw = threadIdx.x & 31, gq = lw >> 2, q = lw & 3;
+    const SlotState<K>* SW = &sh[warp * GPW];
+    auto elem = [&](int r, int c) -> float {
+      if (r >= ROWS || c >= NCOL) return 0.f;
+      const float2 v = SW[r >> 3].A[(r & 7) >> 1][c];
+      return (r & 1) ? v.y : v.x;
+    };
+#pragma unroll
+    for (int t = 0; t < MT; ++t) {
+      const int r0 = 16 * t + gq, r1 = r0 + 8;
+      float m0 = 0.f, m1 = 0.f;
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = ks * 16 + 2 * q + (j & 1) + (j >> 1) * 8;
+          m0 = fmaxf(m0, fabsf(elem(r0, c)));
+          m1 = fmaxf(m1, fabsf(elem(r1, c)));
+        }
+      m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, 1));
+      m0 = fmaxf(m0, __shfl_xor_sync(0xffffffffu, m0, 2));
+      m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 1));
+      m1 = fmaxf(m1, __shfl_xor_sync(0xffffffffu, m1, 2));
+      int ex0 = 0, ex1 = 0;
+      if (m0 > 0.f) frexpf(m0, &ex0);
+      if (m1 > 0.f) frexpf(m1, &ex1);
+      const float sc0 = ldexpf(1.f, -ex0), sc1 = ldexpf(1.f, -ex1);
+      uint32_t ah[KS][4], al[KS][4];
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+        for (int rg = 0; rg < 4; ++rg) {
+          const int c = ks * 16 + 2 * q + (rg >> 1) * 8;
+          const int r = (rg & 1) ? r1 : r0;
+          const float sc = (rg & 1) ? sc1 : sc0;
+          const float x0 = elem(r, c) * sc, x1 = elem(r, c + 1) * sc;
+          const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
+          const __half l0 = __float2half_rn((x0 - __half2float(h0)) * 2048.f);
+          const __half l1 = __float2half_rn((x1 - __half2float(h1)) * 2048.f);
+          ah[ks][rg] = pack_h2(h0, h1);
+          al[ks][rg] = pack_h2(l0, l1);
+        }
+      float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+      for (int nt = 0; nt < NT; ++nt) {
+        float dh[4] = {0.f, 0.f, 0.f, 0.f}, dl[4] = {0.f, 0.f, 0.f, 0.f};
+        const __half* cb = cmat16 + (nt * 8 + gq) * LDH + 2 * q;
+#pragma unroll
+        for (int ks = 0; ks < KS; ++ks) {
+          uint32_t bf[2];
+          bf[0] = __ldg(reinterpret_cast<const unsigned int*>(cb + ks * 16));
+          bf[1] = __ldg(reinterpret_cast<const unsigned int*>(cb + ks * 16 + 8));
+          mma16816(dh, ah[ks], bf);
+          mma16816(dl, al[ks], bf);
+        }
+        // this thread's Y columns nt*8 + 2q, +1 are the a columns it holds in k step nt/2, half nt%2
+        const int ksa = nt >> 1, hb = (nt & 1) * 2;
+        const float r = 1.f / 2048.f;
+        s0 = fmaf(unsplit(ah[ksa][hb], al[ksa][hb], 0), fmaf(dl[0], r, dh[0]), s0);
+        s0 = fmaf(unsplit(ah[ksa][hb], al[ksa][hb], 1), fmaf(dl[1], r, dh[1]), s0);
+        s1 = fmaf(unsplit(ah[ksa][hb + 1], al[ksa][hb + 1], 0), fmaf(dl[2], r, dh[2]), s1);
+        s1 = fmaf(unsplit(ah[ksa][hb + 1], al[ksa][hb + 1], 1), fmaf(dl[3], r, dh[3]), s1);
+      }
+      s0 += __shfl_xor_sync(0xffffffffu, s0, 1);
+      s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
+      // unscale (exact powers of two), then sum the 8 rows of a slot: rows gq = 0..7 sit in lanes 4 gq
+      double v0 = static_cast<double>(s0) * pow2d(2 * ex0);
+      double v1 = static_cast<double>(s1) * pow2d(2 * ex1);
+#pragma unroll
+      for (int o = 4; o < 32; o <<= 1) {
+        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+      }
+      if (lw == 0) {
+        const int sa = 2 * t, sb = 2 * t + 1;   // the slots of rows 0-7 and 8-15 of this tile
+        if (sa < GPW && slot0 + sa < nslot) out[(slot0 + sa) * stride + e] = v0 * cst.colour_scale;
+        if (sb < GPW && slot0 + sb < nslot) out[(slot0 + sb) * stride + e] = v1 * cst.colour_scale;
+      }
+    }
   }
 }
 
 template <int K>
 static cudaError_t launch_k(const void* rec, int64_t nevt, const Tables* tab, const int* gslots, int maxslot,
-                            const int* nslot, const uint32_t* mask, const float* cfull, const MeConst& cst, double* out,
-                            int64_t stride, float2* jout, const uint8_t* skip, cudaStream_t st) {
+                            const int* nslot, const uint32_t* mask, const float* cfull, const void* cmat16, int epi,
+                            const MeConst& cst, double* out, int64_t stride, float2* jout, const uint8_t* skip,
+                            cudaStream_t st) {
   if (nevt <= 0 || maxslot <= 0) return cudaSuccess;
   if (nevt > 0x7fffffffLL) return cudaErrorInvalidValue;
   constexpr int per_block = kWarps * (32 / WSizes<K>::G);   // slots per block
   const dim3 grid(static_cast<unsigned>(nevt), static_cast<unsigned>((maxslot + per_block - 1) / per_block));
   const float* r = static_cast<const float*>(rec);
-  if (jout)
-    k_me_warp<K, true><<<grid, kWarps * 32, 0, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, cst, out, stride, jout,
-                                                      skip);
+  const __half* c16 = static_cast<const __half*>(cmat16);
+  if (epi == kJamps)
+    k_me_warp<K, kJamps><<<grid, kWarps * 32, 0, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, c16, cst, out, stride,
+                                                       jout, skip);
+  else if (epi == kMma)
+    k_me_warp<K, kMma><<<grid, kWarps * 32, 0, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, c16, cst, out, stride,
+                                                     nullptr, skip);
   else
-    k_me_warp<K, false><<<grid, kWarps * 32, 0, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, cst, out, stride,
-                                                       nullptr, skip);
+    k_me_warp<K, kSimt><<<grid, kWarps * 32, 0, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, c16, cst, out, stride,
+                                                      nullptr, skip);
   return cudaGetLastError();
 }
 
@@ -287,12 +417,13 @@ static cudaError_t launch_k(const void* rec, int64_t nevt, const Tables* tab, co
 bool me_warp_available(int K, bool fp32) { return fp32 && K >= 3 && K <= 5; }
 
 cudaError_t launch_me_warp(int K, const void* rec, int64_t nevt, const Tables* tab, const int* gslots, int maxslot,
-                           const int* nslot, const uint32_t* mask, const float* cfull, const MeConst& cst, double* out,
-                           int64_t stride, float2* jout, const uint8_t* skip, cudaStream_t st) {
+                           const int* nslot, const uint32_t* mask, const float* cfull, const void* cmat16, int epi,
+                           const MeConst& cst, double* out, int64_t stride, float2* jout, const uint8_t* skip,
+                           cudaStream_t st) {
   switch (K) {
-    case 3: return wk::launch_k<3>(rec, nevt, tab, gslots, maxslot, nslot, mask, cfull, cst, out, stride, jout, skip, st);
-    case 4: return wk::launch_k<4>(rec, nevt, tab, gslots, maxslot, nslot, mask, cfull, cst, out, stride, jout, skip, st);
-    case 5: return wk::launch_k<5>(rec, nevt, tab, gslots, maxslot, nslot, mask, cfull, cst, out, stride, jout, skip, st);
+    case 3: return wk::launch_k<3>(rec, nevt, tab, gslots, maxslot, nslot, mask, cfull, cmat16, epi, cst, out, stride, jout, skip, st);
+    case 4: return wk::launch_k<4>(rec, nevt, tab, gslots, maxslot, nslot, mask, cfull, cmat16, epi, cst, out, stride, jout, skip, st);
+    case 5: return wk::launch_k<5>(rec, nevt, tab, gslots, maxslot, nslot, mask, cfull, cmat16, epi, cst, out, stride, jout, skip, st);
     default: return cudaErrorInvalidValue;
   }
 }
