@@ -410,6 +410,15 @@ __device__ __forceinline__ void record_subsets(const double (*p)[4], const MeCon
 #pragma unroll
   for (int S = S0; S < S1; ++S) {
     const double* P = Pst[S - S0];
+    if (S == 0 || S == (1 << K) - 1) {
+      // the empty set and the set of all gluons: no current or quark-line prefix reads their momentum
+      // sum or quark propagator; of the two, only the all-gluon propagator factor is read
+      if (S != 0) {
+        const double p2 = P[0] * P[0] - P[1] * P[1] - P[2] * P[2] - P[3] * P[3];
+        put(L::GP + S, static_cast<T>(sizeof(T) == 8 ? -cst.gs / p2 : -cst.gs * rcp_nr(p2)));
+      }
+      continue;
+    }
 #pragma unroll
     for (int m = 0; m < 4; ++m) put(L::PT + 4 * S + m, static_cast<T>(P[m]));
     const double p2 = P[0] * P[0] - P[1] * P[1] - P[2] * P[2] - P[3] * P[3];
@@ -476,7 +485,7 @@ template <int K, class T>
 __device__ __forceinline__ void event_data(const double (*p)[4], const MeConst& cst, T (*PT)[4], T* gprop, T (*qc)[5],
                                            T (*pol)[5], cx<T> (*ub)[4], cx<T> (*vv)[4]) {
   using L = EvLayout<K>;
-  T r[L::NITEM];
+  T r[L::NITEM] = {};   // (the items no kernel reads stay zero)
   record_all<K, T>(p, cst, [&](int i, T v) { r[i] = v; });
   constexpr int NSUB = 1 << K;
 #pragma unroll
