@@ -97,3 +97,27 @@ def test_launch_shape_set_and_get(env):
         for bad in ((48, 0, 1), (64, 2, 1), (64, 0, 32)):
             with pytest.raises(mg.MGError):
                 ctx.set_launch_shape(mg.MG_FP32_AMP, *bad)
+
+
+@pytest.mark.parametrize("precision", [1, 3])
+def test_graph_batch_fp32_modes(env, precision):
+    """The FP32-amplitude modes captured into a graph batch -- their FP32 pre-pass, the recomputation
+    forked onto each context's side stream and joined back, the tensor-core colour sums -- give the
+    same bits as the same steps called one by one."""
+    torch, mg = env
+    sizes = {"ggtt": 3000, "ggttg": 2000, "ggttgg": 700, "ggttggg": 96}
+    ctxs = {p: mg.Context(p) for p in sizes}
+    bufs = {p: (torch.zeros(ctxs[p].mom_count(n), dtype=torch.float64, device="cuda"),
+                torch.zeros(n, dtype=torch.float64, device="cuda")) for p, n in sizes.items()}
+    jobs = [(ctxs[p], 300 + i, 0, n, SQRTS, bufs[p][0], bufs[p][1], precision) for i, (p, n) in enumerate(sizes.items())]
+    g = mg.GraphBatch(jobs)
+    for _ in range(2):
+        g.launch()
+    torch.cuda.synchronize()
+    got = {p: bufs[p][1].cpu().numpy().copy() for p in sizes}
+    for i, (p, n) in enumerate(sizes.items()):
+        ref = step(torch, mg, ctxs[p], 300 + i, 0, n, precision)
+        assert np.array_equal(got[p], ref), p
+    g.close()
+    for c in ctxs.values():
+        c.close()
