@@ -92,6 +92,7 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
   constexpr int NSUB = 1 << K;
   constexpr int G = WSizes<K>::G, GPW = 32 / G;   // lanes per slot, slots per warp
   __shared__ SlotState<K> sh[kWarps * GPW];
+  __shared__ float rs[L::NITEM];   // the event's record, read by every slot of the block
   const int warp = threadIdx.x >> 5, grp = (threadIdx.x & 31) / G, lane = threadIdx.x % G;
   const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << (G & 31)) - 1u)) << (grp * G);   // this group's lanes
   const int64_t e = blockIdx.x;   // one block per event: e < nevt
@@ -99,14 +100,18 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
   const int slot = slot0 + grp;
   const int nslot = *nslot_dev;
   if (skip && skip[e]) return;   // recomputed by another launch (the whole block: one event)
+  {
+    const float* in = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
+    for (int i = threadIdx.x; i < L::NITEM; i += blockDim.x) rs[i] = __ldg(in + i * kPage);
+  }
+  __syncthreads();
   const bool active = slot < nslot;
   // groups past the last slot leave (every sync of the slot work is per group), except with the
   // tensor-core epilogue, whose MMAs take the whole warp: there they contribute zero jamps
   if (EPI != kMma && !active) return;
   SlotState<K>& S = sh[warp * GPW + grp];
   const int gc = active ? gslots[slot] : 0;   // bit g = helicity (+1) of gluon g
-  const float* in = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
-  auto ld = [&](int item) -> float { return __ldg(in + item * kPage); };
+  auto ld = [&](int item) -> float { return rs[item]; };
   const float gs = static_cast<float>(cst.gs);
   // helicity index of (gc, top helicity, antitop helicity), and which of the four are in the mask
   int hbase = 0;
