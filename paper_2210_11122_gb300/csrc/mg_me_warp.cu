@@ -79,11 +79,18 @@ __device__ __forceinline__ float unsplit(uint32_t h, uint32_t l, int k) {
   return fmaf(__half2float(lh), 1.f / 2048.f, __half2float(hh));
 }
 
-// (resident blocks per SM: 5, or 4 with the tensor-core epilogue, whose fragments must not cost the
-// amplitude phase more occupancy than that)
+template <int K>
+struct SmemLayout {
+  static constexpr int GPW = 32 / WSizes<K>::G;
+  static constexpr size_t rec_off = sizeof(SlotState<K>) * kWarps * GPW;
+  static constexpr size_t tab_off = (rec_off + sizeof(float) * v2::EvLayout<K>::NITEM + 15) / 16 * 16;
+  static constexpr size_t bytes = tab_off + sizeof(Tables);
+};
+
+// (resident blocks per SM: 4 (the shared memory allows that many) and the registers to match)
 template <int K, int EPI>
-__global__ void __launch_bounds__(kWarps * 32, EPI == kMma ? 4 : 5)
-k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab, const int* __restrict__ gslots,
+__global__ void __launch_bounds__(kWarps * 32, 4)
+k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab_g, const int* __restrict__ gslots,
           const int* __restrict__ nslot_dev, const uint32_t* __restrict__ mask, const float* __restrict__ cfull,
           const __half* __restrict__ cmat16, MeConst cst, double* __restrict__ out, int64_t stride,
           float2* __restrict__ jout, const uint8_t* __restrict__ skip) {
@@ -91,8 +98,12 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
   constexpr int npar = K + 2, NCOL = WSizes<K>::ncol, NFULL = WSizes<K>::nfull;
   constexpr int NSUB = 1 << K;
   constexpr int G = WSizes<K>::G, GPW = 32 / G;   // lanes per slot, slots per warp
-  __shared__ SlotState<K> sh[kWarps * GPW];
-  __shared__ float rs[L::NITEM];   // the event's record, read by every slot of the block
+  // shared memory (dynamic, see warp_smem_bytes): the slots' state, the event's record (read by every slot
+  // of the block), the recursion tables (read with per-lane indices)
+  extern __shared__ __align__(16) unsigned char wsm[];
+  SlotState<K>* sh = reinterpret_cast<SlotState<K>*>(wsm);
+  float* rs = reinterpret_cast<float*>(wsm + SmemLayout<K>::rec_off);
+  Tables& tabs = *reinterpret_cast<Tables*>(wsm + SmemLayout<K>::tab_off);
   const int warp = threadIdx.x >> 5, grp = (threadIdx.x & 31) / G, lane = threadIdx.x % G;
   const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << (G & 31)) - 1u)) << (grp * G);   // this group's lanes
   const int64_t e = blockIdx.x;   // one block per event: e < nevt
@@ -103,8 +114,13 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
   {
     const float* in = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
     for (int i = threadIdx.x; i < L::NITEM; i += blockDim.x) rs[i] = __ldg(in + i * kPage);
+    static_assert(sizeof(Tables) % 4 == 0, "table copy in words");
+    const unsigned* src = reinterpret_cast<const unsigned*>(tab_g);
+    unsigned* dst = reinterpret_cast<unsigned*>(&tabs);
+    for (int i = threadIdx.x; i < static_cast<int>(sizeof(Tables) / 4); i += blockDim.x) dst[i] = __ldg(src + i);
   }
   __syncthreads();
+  const Tables* __restrict__ tab = &tabs;
   const bool active = slot < nslot;
   // groups past the last slot leave (every sync of the slot work is per group), except with the
   // tensor-core epilogue, whose MMAs take the whole warp: there they contribute zero jamps
@@ -405,15 +421,24 @@ static cudaError_t launch_k(const void* rec, int64_t nevt, const Tables* tab, co
   const dim3 grid(static_cast<unsigned>(nevt), static_cast<unsigned>((maxslot + per_block - 1) / per_block));
   const float* r = static_cast<const float*>(rec);
   const __half* c16 = static_cast<const __half*>(cmat16);
+  constexpr size_t smem = SmemLayout<K>::bytes;
+  static bool configured = false;   // opt in to more than 48 KB of dynamic shared memory, once
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(k_me_warp<K, kJamps>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_me_warp<K, kMma>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_me_warp<K, kSimt>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
   if (epi == kJamps)
-    k_me_warp<K, kJamps><<<grid, kWarps * 32, 0, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, c16, cst, out, stride,
-                                                       jout, skip);
+    k_me_warp<K, kJamps><<<grid, kWarps * 32, smem, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, c16, cst, out,
+                                                          stride, jout, skip);
   else if (epi == kMma)
-    k_me_warp<K, kMma><<<grid, kWarps * 32, 0, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, c16, cst, out, stride,
-                                                     nullptr, skip);
+    k_me_warp<K, kMma><<<grid, kWarps * 32, smem, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, c16, cst, out, stride,
+                                                        nullptr, skip);
   else
-    k_me_warp<K, kSimt><<<grid, kWarps * 32, 0, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, c16, cst, out, stride,
-                                                      nullptr, skip);
+    k_me_warp<K, kSimt><<<grid, kWarps * 32, smem, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, c16, cst, out,
+                                                         stride, nullptr, skip);
   return cudaGetLastError();
 }
 
