@@ -290,7 +290,8 @@ def run_ours(args):
             tev, slm, fl = ctx.launch_shape(prec)
             shapes[name] = {"tile_ev": tev, "slot_major": slm, "unrolled": bool(fl & mg.LAUNCH_UNROLLED),
                             "df_redo": bool(fl & mg.LAUNCH_DF_REDO), "fused": bool(fl & mg.LAUNCH_FUSED),
-                            "warp": bool(fl & mg.LAUNCH_WARP), "tc_apart": bool(fl & mg.LAUNCH_TC_APART)}
+                            "warp": bool(fl & mg.LAUNCH_WARP), "tc_apart": bool(fl & mg.LAUNCH_TC_APART),
+                            "shared": bool(fl & mg.LAUNCH_SHARED)}
 
     clocks = ClockSampler(local)
     clocks.start()

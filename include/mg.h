@@ -161,8 +161,10 @@ mg_status mg_check(mg_ctx* ctx, void* stream, int64_t* nbad);
  * (once per event) and the currents and jamps of every gluon-helicity combination with a good
  * helicity, *colour_flops for the colour sums (4 ncol(ncol+1)/2 + 4 ncol per good helicity), counting
  * an FMA as 2.  The FP64-amplitude modes tabulate (gamma.J) v per current, the FP32-amplitude modes
- * form it per jamp term.  mask (ceil(nhel/32) words, as returned by mg_hel_mask) selects the good
- * helicities; NULL = all.  Host only. */
+ * form it per jamp term; for gg -> t tbar g and t tbar g g g the FP64-amplitude count is that of the
+ * default MG_LAUNCH_SHARED algorithm (the currents of fewer than all gluons, with their (gamma.J) v, once
+ * per helicity assignment of their own gluons per event).  mask (ceil(nhel/32) words, as returned by
+ * mg_hel_mask) selects the good helicities; NULL = all.  Host only. */
 mg_status mg_flops_per_event(mg_process proc, mg_precision precision, const uint32_t* mask, double* amp_flops,
                              double* colour_flops);
 
@@ -205,27 +207,34 @@ mg_status mg_sigmakin_noalloc(mg_ctx* ctx, const double* mom_dev, int64_t nevt, 
  *                       precedence over MG_LAUNCH_UNROLLED); with MG_MIXED it also sums the colours on
  *                       the tensor cores itself, unless
  *   MG_LAUNCH_TC_APART  MG_MIXED with MG_LAUNCH_WARP: write the jamps out for the separate tensor-core
- *                       colour kernel instead. */
+ *                       colour kernel instead;
+ *   MG_LAUNCH_SHARED    MG_FP64: the gluon currents of fewer than all gluons (and their products with the
+ *                       antitop spinors) are computed once per helicity assignment of their own gluons, by
+ *                       a pass before the matrix-element kernel, instead of once per gluon-helicity
+ *                       combination. */
 #define MG_LAUNCH_UNROLLED 1
 #define MG_LAUNCH_DF_REDO 2
 #define MG_LAUNCH_FUSED 4
 #define MG_LAUNCH_WARP 8
 #define MG_LAUNCH_TC_APART 16
+#define MG_LAUNCH_SHARED 32
 
 /* Time mg_sigmakin(precision) of nevt probe events (this context's process, fixed seed) for each
  * launch shape of the matrix-element kernel -- 32, 64 or 128 events per 128-thread block (the other
  * threads of a block take further helicity combinations of the same events), grid dispatched
  * event-tile-major or helicity-tile-major, with and without MG_LAUNCH_UNROLLED where that kernel
  * exists, MG_LAUNCH_UNROLLED | MG_LAUNCH_FUSED, MG_LAUNCH_WARP and (MG_MIXED) MG_LAUNCH_WARP | MG_LAUNCH_TC_APART
- * -- then, for the FP32 modes, the fastest with MG_LAUNCH_DF_REDO toggled, and keep the fastest
+ * -- then the fastest with MG_LAUNCH_DF_REDO (FP32 modes) or MG_LAUNCH_SHARED (MG_FP64) toggled, and keep
+ * the fastest
  * for this context and precision.  cache_path (may be NULL): text file of
  * "gpu|process|precision tile_ev slot_major flags ms" lines; an existing entry is used without timing,
  * a new result is appended.  *best_ms may be NULL.  Synchronous; allocates probe buffers; nevt >= 32. */
 mg_status mg_autotune(mg_ctx* ctx, mg_precision precision, int64_t nevt, const char* cache_path, double* best_ms);
 
 /* The launch shape mg_sigmakin(precision) uses on this context (default: 128 events per block,
- * event-tile-major, flags MG_LAUNCH_UNROLLED | MG_LAUNCH_DF_REDO | MG_LAUNCH_FUSED, plus MG_LAUNCH_WARP for
- * gg -> t tbar g g and t tbar g g g).  Any out-pointer may be NULL. */
+ * event-tile-major, flags MG_LAUNCH_UNROLLED | MG_LAUNCH_DF_REDO | MG_LAUNCH_FUSED, plus MG_LAUNCH_SHARED
+ * for gg -> t tbar g and t tbar g g g, MG_LAUNCH_WARP for t tbar g g and t tbar g g g, and
+ * MG_LAUNCH_TC_APART for t tbar g g g).  Any out-pointer may be NULL. */
 mg_status mg_get_launch_shape(mg_ctx* ctx, mg_precision precision, int* tile_ev, int* slot_major, int* flags);
 
 /* Set the launch shape of mg_sigmakin(precision) by hand: tile_ev in {32, 64, 128}, slot_major 0 or 1,

@@ -17,7 +17,7 @@ from . import build as _build
 MG_GG_TT, MG_GG_TTG, MG_GG_TTGG, MG_GG_TTGGG = 0, 1, 2, 3
 PROCESSES = {"ggtt": 0, "ggttg": 1, "ggttgg": 2, "ggttggg": 3}
 MG_FP64, MG_FP32_AMP, MG_FP64_TCCOLOR, MG_MIXED = 0, 1, 2, 3
-LAUNCH_UNROLLED, LAUNCH_DF_REDO, LAUNCH_FUSED, LAUNCH_WARP, LAUNCH_TC_APART = 1, 2, 4, 8, 16   # mg.h MG_LAUNCH_*
+LAUNCH_UNROLLED, LAUNCH_DF_REDO, LAUNCH_FUSED, LAUNCH_WARP, LAUNCH_TC_APART, LAUNCH_SHARED = 1, 2, 4, 8, 16, 32
 PAGE = 32
 
 STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "MG_ENOCONV", 5: "MG_EAGAIN",
@@ -295,13 +295,13 @@ class Context:
 
     def launch_shape(self, precision=MG_FP64):
         """(tile_ev, slot_major, flags) of the ME kernel launch for this precision (flags: LAUNCH_UNROLLED,
-        LAUNCH_DF_REDO, LAUNCH_FUSED, LAUNCH_WARP, LAUNCH_TC_APART bits)."""
+        LAUNCH_DF_REDO, LAUNCH_FUSED, LAUNCH_WARP, LAUNCH_TC_APART, LAUNCH_SHARED bits: mg.h MG_LAUNCH_*)."""
         t, s, u = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().mg_get_launch_shape(self._h, precision, ctypes.byref(t), ctypes.byref(s), ctypes.byref(u)),
                "mg_get_launch_shape")
         return t.value, s.value, u.value
 
-    def set_launch_shape(self, precision, tile_ev=128, slot_major=0, flags=7):
+    def set_launch_shape(self, precision, tile_ev=128, slot_major=0, flags=39):
         _check(lib().mg_set_launch_shape(self._h, precision, tile_ev, slot_major, flags), "mg_set_launch_shape")
 
     def hel_mask(self):

@@ -47,7 +47,7 @@ mg_status grow(double** buf, int64_t* cap, int64_t need) {
 // helicity combination with a good helicity; per thread the gluon currents once, (gamma.J) v per
 // antitop helicity, a depth-first walk of the quark-line prefixes per top helicity, the jamps and
 // the colour sum per good helicity.  mask == NULL means every helicity is good.
-void flop_model(const mg::Tables& t, const uint32_t* mask, bool fp32, double* amp, double* col) {
+void flop_model(const mg::Tables& t, const uint32_t* mask, bool fp32, bool shared, double* amp, double* col) {
   const int K = t.K, nsub = 1 << K, npar = K + 2;
   // three-gluon vertex in the current-conserving form: d (4) + JL.JR (30) + JL.PR, JR.PL (2 x 14) +
   // two scalings (4) + 4 x (real-complex and two complex multiply-adds) (80)
@@ -55,10 +55,20 @@ void flop_model(const mg::Tables& t, const uint32_t* mask, bool fp32, double* am
                mdot = 30.0;
   const double per_event = 25.0 * nsub + 30.0 * K + 100.0;        // subsets, propagators, wavefunctions (once)
   double per_slot = 0.0;                                           // gluon currents of one helicity combination
-  for (int s = K; s < t.nseq; ++s) per_slot += v3 * t.seq_nv3[s] + v4 * t.seq_nv4[s] + 8.0;
+  double shared_work = 0.0;                                        // (shared: once per event)
+  for (int s = K; s < t.nseq; ++s) {
+    const double c = v3 * t.seq_nv3[s] + v4 * t.seq_nv4[s] + 8.0;
+    if (shared) shared_work += c * (1 << t.seq_len[s]);   // once per helicity assignment of its own gluons
+    else per_slot += c;
+  }
   for (int f = 0; f < t.nfull; ++f) per_slot += v3 * t.full_nv3[f] + v4 * t.full_nv4[f] + 8.0;
   // FP64: (gamma.J) v tabulated for every current and both antitop helicities; FP32: formed per jamp term
-  if (!fp32) per_slot += 2.0 * gamma_col * t.nseq;
+  if (!fp32) {
+    if (shared)
+      for (int s = 0; s < t.nseq; ++s) shared_work += 2.0 * gamma_col * (1 << t.seq_len[s]);
+    else
+      per_slot += 2.0 * gamma_col * t.nseq;
+  }
   double walk = 50.0 + 2.0 * 72.0;                                 // ubar, two quark currents
   for (int c = 0; c < t.ncol; ++c) {
     for (int m = t.lcp[c] + 1; m < K; ++m) walk += row_gamma * m + row_prop;
@@ -66,7 +76,7 @@ void flop_model(const mg::Tables& t, const uint32_t* mask, bool fp32, double* am
                  : 2.0 * (mdot + sdot * (K - 1));
   }
   const double colour = 4.0 * t.ncol * (t.ncol + 1) / 2.0 + 4.0 * t.ncol;
-  double a = per_event, c = 0;
+  double a = per_event + shared_work, c = 0;
   for (int gc = 0; gc < nsub; ++gc) {
     int hb = 0;
     for (int g = 0; g < K; ++g)
@@ -110,6 +120,13 @@ mg_status grow_repair(mg_ctx* ctx, int64_t n) {
 
 namespace mg {
 
+int64_t share_chunk(int K, int64_t stride) {
+  const int64_t per_event = static_cast<int64_t>(share_items(K)) * 24;   // doubles
+  int64_t chunk = (int64_t(1) << 28) / per_event / kPage * kPage;       // 2^28 doubles = 2 GiB
+  if (chunk < kPage) chunk = kPage;
+  return chunk < stride ? chunk : stride;
+}
+
 bool mixed_in_kernel(const mg_ctx* ctx, mg_precision precision) {
   return precision == MG_MIXED && ctx->prm.wt == 0.0 && ctx->shape[precision].warp &&
          !ctx->shape[precision].tc_apart && me_warp_available(ctx->K, true);
@@ -144,6 +161,11 @@ mg_status ctx_reserve(mg_ctx* ctx, int64_t nevt, mg_precision precision) {
   }
   if (s == MG_OK) s = grow(&ctx->d_prep, &ctx->prep_cap, chunk * event_record_bytes(ctx->K, fp32) / 8 + 1);
   if (s == MG_OK) s = grow_repair(ctx, chunk);
+  if (s == MG_OK && (precision == MG_FP64 || precision == MG_FP64_TCCOLOR) && ctx->shape[precision].shared &&
+      ctx->prm.wt == 0.0) {
+    const int64_t sc = share_chunk(ctx->K, stride);
+    s = grow(&ctx->d_share, &ctx->share_cap, (sc < chunk ? sc : chunk) * share_items(ctx->K) * 24);
+  }
   return s;
 }
 
@@ -228,7 +250,11 @@ mg_status mg_flops_per_event(mg_process proc, mg_precision precision, const uint
   if (!t) return MG_ENOMEM;
   mg::build_tables(mg::gluons_of(proc), *t);
   double a, c;
-  flop_model(*t, mask, precision == MG_FP32_AMP || precision == MG_MIXED, &a, &c);
+  // the default algorithm of each mode: FP64 amplitudes share the currents of fewer than all gluons
+  // between gluon-helicity combinations for 1 and 3 final-state gluons (as mg_create's launch shapes)
+  const int K = mg::gluons_of(proc);
+  const bool fp32 = precision == MG_FP32_AMP || precision == MG_MIXED;
+  flop_model(*t, mask, fp32, !fp32 && (K == 3 || K == 5), &a, &c);
   delete t;
   if (amp_flops) *amp_flops = a;
   if (colour_flops) *colour_flops = c;
@@ -262,6 +288,7 @@ void mg_destroy(mg_ctx* ctx) {
   cudaFree(ctx->d_repair);
   cudaFree(ctx->d_nrepair);
   cudaFree(ctx->d_flag);
+  cudaFree(ctx->d_share);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->side) cudaStreamDestroy(ctx->side);
@@ -360,6 +387,9 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
       for (int p = 0; p < 4; ++p) c->shape[p].warp = true;
     // five gluons, FP32 amplitudes + tensor-core colour: the separate colour kernel (measured faster there)
     if (c->K == 5) c->shape[MG_MIXED].tc_apart = true;
+    // FP64 amplitudes: share the currents of fewer than all gluons between gluon-helicity combinations
+    // where that was measured faster (1 and 3 final-state gluons); the autotuner can change it
+    for (int p = 0; p < 4; ++p) c->shape[p].shared = c->K == 3 || c->K == 5;
     // side stream of the FP32 modes' recomputation: highest priority, so that its few blocks are
     // dispatched ahead of the FP32 launch's
     int lo = 0, hi = 0;
@@ -495,6 +525,14 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
     chunk = chunk / mg::kPage * mg::kPage;
     if (chunk < mg::kPage) chunk = mg::kPage;
     if (chunk > stride) chunk = stride;
+    // FP64 amplitudes: optionally the currents shared between gluon-helicity combinations (as MG_FP64)
+    const bool shared = !fp32 && ctx->shape[precision].shared;
+    if (shared) {
+      const int64_t sc = mg::share_chunk(ctx->K, stride);
+      if (sc < chunk) chunk = sc;
+      s = grow(&ctx->d_share, &ctx->share_cap, chunk * mg::share_items(ctx->K) * 24);
+      if (s != MG_OK) return s;
+    }
     if (ctx->jamp_cap < chunk * per_event) {
       if (ctx->d_jamps) cudaFree(ctx->d_jamps);
       ctx->d_jamps = nullptr;
@@ -527,6 +565,13 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
         MG_CUDA(mg::launch_me_warp(ctx->K, ctx->d_prep, n, ctx->d_tab, ctx->d_gslots, 1 << ctx->K, ctx->d_ngslots,
                                    ctx->d_mask, ctx->d_cfull, ctx->d_cmat, 1, cst, ctx->d_part, cst_stride, ctx->d_jamps,
                                    ctx->d_flag, st));
+      else if (shared) {
+        MG_CUDA(mg::launch_share(ctx->K, ctx->d_prep, n, ctx->d_tab, cst, ctx->d_share, st));
+        MG_CUDA(mg::launch_me_gluonhel(ctx->K, false, false, mom_c, ctx->d_prep, n, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
+                                       ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part,
+                                       cst_stride, st, ctx->d_jamps, ctx->shape[precision], nullptr, nullptr, nullptr, 0,
+                                       ctx->d_share));
+      }
       else
         MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_c, ctx->d_prep, n, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
                                        ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, cst_stride,
@@ -552,7 +597,25 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
     // events with a small internal invariant: recomputed with double-float or FP64 amplitudes (per-slot
     // layout) on the side stream
     if (fp32) MG_CUDA(fork_repair(ctx, mom_dev, nevt, cst, stride, 0, ctx->shape[precision].df_redo, st));
-    if (fused)
+    const bool shared = !fp32 && ctx->shape[precision].shared;
+    if (shared) {
+      // FP64: the currents of fewer than all gluons once per helicity assignment of their gluons, then
+      // the matrix elements reading them; in chunks of events that bound the scratch
+      const int64_t chunk = mg::share_chunk(ctx->K, stride);
+      s = grow(&ctx->d_share, &ctx->share_cap, chunk * mg::share_items(ctx->K) * 24);
+      if (s != MG_OK) return s;
+      const int64_t nitem = mg::event_record_bytes(ctx->K, false) / 8;
+      for (int64_t e0 = 0; e0 < nevt; e0 += chunk) {
+        const int64_t n = nevt - e0 < chunk ? nevt - e0 : chunk;
+        const double* rec_c = ctx->d_prep + (e0 / mg::kPage) * nitem * mg::kPage;
+        const double* mom_c = mom_dev + (e0 / mg::kPage) * ctx->npar * 4 * mg::kPage;
+        MG_CUDA(mg::launch_share(ctx->K, rec_c, n, ctx->d_tab, cst, ctx->d_share, st));
+        MG_CUDA(mg::launch_me_gluonhel(ctx->K, false, false, mom_c, const_cast<double*>(rec_c), n, ctx->d_tab,
+                                       ctx->d_gslots, 1 << ctx->K, ctx->d_ngslots, ctx->d_mask, ctx->d_ctri,
+                                       ctx->d_ctri_f, cst, ctx->d_part + e0, stride, st, nullptr, ctx->shape[precision],
+                                       nullptr, nullptr, nullptr, 0, ctx->d_share));
+      }
+    } else if (fused)
       MG_CUDA(mg::launch_me_fused(ctx->K, true, mom_dev, nevt, ctx->d_gslots, ctx->d_ngslots, ctx->d_mask, cst,
                                   ctx->d_part, stride, nullptr, ctx->d_flag, st));
     else if (warp)

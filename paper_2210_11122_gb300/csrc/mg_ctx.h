@@ -39,6 +39,8 @@ struct mg_ctx {
   int* d_nrepair = nullptr;
   uint8_t* d_flag = nullptr;  // FP32 modes: 1 for the events in d_repair (the FP32 launches skip them)
   int64_t repair_cap = 0;
+  double* d_share = nullptr;   // FP64: currents shared between gluon-helicity combinations (one chunk of events)
+  int64_t share_cap = 0;      // in doubles
   cudaStream_t side = nullptr;         // FP32 modes: the FP64 recomputation runs here, beside the FP32 launches
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int64_t prep_cap = 0;       // in doubles
@@ -53,6 +55,8 @@ struct mg_ctx {
 
 
 namespace mg {
+// events per chunk of the FP64 shared-current path (its scratch stays within 2 GiB)
+int64_t share_chunk(int K, int64_t stride);
 // MG_MIXED on the lane-group kernel: colour sums on the tensor cores inside it, per-slot outputs
 bool mixed_in_kernel(const mg_ctx* ctx, mg_precision precision);
 mg_status ctx_reserve(mg_ctx* ctx, int64_t nevt, mg_precision precision);

@@ -50,7 +50,25 @@ struct Tables {
   int16_t full_v4[kMaxNcol / 2][6][3];
   uint8_t full_nv3[kMaxNcol / 2], full_nv4[kMaxNcol / 2];
   uint8_t full_split_mask[kMaxNcol / 2][kMaxGluons - 1];   // mask of the left part of each V3 split
+  // currents shared between gluon-helicity combinations: canonical sequence s with the helicities of its
+  // own gluons h (2^len(s) of them) is item share_base[s] + h; share_n items per event
+  int16_t share_base[kMaxSeq];
+  int share_n;
 };
+
+// helicity bits of the gluons in mask, packed (bit g of gc -> the rank of g among mask's bits), and back
+inline constexpr int pext_bits(int gc, int mask) {
+  int r = 0, k = 0;
+  for (int g = 0; g < kMaxGluons; ++g)
+    if ((mask >> g) & 1) r |= ((gc >> g) & 1) << k++;
+  return r;
+}
+inline constexpr int pdep_bits(int h, int mask) {
+  int r = 0, k = 0;
+  for (int g = 0; g < kMaxGluons; ++g)
+    if ((mask >> g) & 1) r |= ((h >> k++) & 1) << g;
+  return r;
+}
 
 void build_tables(int K, Tables& t);
 

@@ -36,6 +36,7 @@ struct MeShape {
   bool fused = true;
   bool warp = false;
   bool tc_apart = false;
+  bool shared = true;   // FP64 amplitudes: currents of fewer than all gluons shared between slots
 };
 
 cudaError_t launch_philox(uint64_t seed, int64_t nevt, int nfinal, uint32_t* words, cudaStream_t st);
@@ -65,7 +66,14 @@ cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom
                                const uint32_t* mask, const double* ctri64, const float* ctri32, const MeConst& cst,
                                double* out, int64_t stride, cudaStream_t st, float2* jout = nullptr,
                                MeShape shape = MeShape(), const uint8_t* skip = nullptr,
-                               const int* evlist = nullptr, const int* nlist = nullptr, int rows_out = 0);
+                               const int* evlist = nullptr, const int* nlist = nullptr, int rows_out = 0,
+                               const double* share = nullptr);
+// FP64 currents shared between gluon-helicity combinations: share_items(K) items of 24 doubles per event
+// (layout in mg_me_kernel.cuh), computed from the FP64 records of nevt events by K - 1 launches (one per
+// sequence length); launch_me_gluonhel(..., share) then reads them instead of computing them per slot.
+int share_items(int K);
+cudaError_t launch_share(int K, const void* rec, int64_t nevt, const Tables* tab, const MeConst& cst, double* share,
+                         cudaStream_t st);
 int64_t event_record_bytes(int K, bool fp32);
 // The FP32 modes' recomputation of events evlist[0..*nlist) with double-float amplitudes (mg_me_dd.cu):
 // launch_me_gluonhel's contract for prep == NULL, per_hel false, FP32 colour table ctri32.

@@ -15,6 +15,8 @@
 // helicities, or (filter mode) |M_h|^2 of every helicity h separately.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "mg_internal.h"
 #include "mg_kernels.h"
 #include "mg_me_algebra.cuh"
@@ -95,7 +97,8 @@ template <int K, class T, bool PER_HEL>
 static cudaError_t launch_v2(const double* mom, void* prep, int64_t nevt, const Tables* tab, const int* gslots,
                              int maxslot, const int* nslot, const uint32_t* mask, const void* ctri_any,
                              const MeConst& cst, double* out, int64_t stride, float2* jout, MeShape shape,
-                             const uint8_t* skip, const int* evlist, const int* nlist, int rows_out, cudaStream_t st) {
+                             const uint8_t* skip, const int* evlist, const int* nlist, int rows_out, cudaStream_t st,
+                             const double* share) {
   const T* ctri = static_cast<const T*>(ctri_any);
   int tev = shape.tile_ev;
   if (tev != 32 && tev != 64 && tev != 128) tev = 128;
@@ -109,6 +112,19 @@ static cudaError_t launch_v2(const double* mom, void* prep, int64_t nevt, const 
     if (shape.unrolled && me_static_available(K, sizeof(T) == 4))
       return launch_me_static(K, sizeof(T) == 4, rec, nevt, gslots, maxslot, nslot, mask, cst, out, stride, jout, shape,
                               skip, st);
+    if constexpr (std::is_same<T, double>::value) {
+      if (share) {
+        if (jout)
+          v2::k_me_gluonhel<K, T, false, true, true, true><<<grid, kMeThreads, 0, st>>>(
+              mom, rec, nevt, tab, gslots, nslot, mask, ctri, cst, out, stride, jout, tev, sm, nullptr, nullptr, 0, skip,
+              share);
+        else
+          v2::k_me_gluonhel<K, T, false, true, false, true><<<grid, kMeThreads, 0, st>>>(
+              mom, rec, nevt, tab, gslots, nslot, mask, ctri, cst, out, stride, nullptr, tev, sm, nullptr, nullptr, 0,
+              skip, share);
+        return cudaGetLastError();
+      }
+    }
     if (jout)
       v2::k_me_gluonhel<K, T, false, true, true><<<grid, kMeThreads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot, mask,
                                                                              ctri, cst, out, stride, jout, tev, sm, nullptr,
@@ -140,6 +156,47 @@ cudaError_t launch_event_prep(int K, bool fp32, const double* mom, int64_t nevt,
     case 3: return fp32 ? launch_prep<3, float>(mom, nevt, cst, rec, st) : launch_prep<3, double>(mom, nevt, cst, rec, st);
     case 4: return fp32 ? launch_prep<4, float>(mom, nevt, cst, rec, st) : launch_prep<4, double>(mom, nevt, cst, rec, st);
     case 5: return fp32 ? launch_prep<5, float>(mom, nevt, cst, rec, st) : launch_prep<5, double>(mom, nevt, cst, rec, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+template <int K>
+static cudaError_t launch_share_k(const void* rec, int64_t nevt, const Tables* tab, const MeConst& cst, double* share,
+                                  cudaStream_t st) {
+  int s0 = 0;
+  for (int level = 1; level < K; ++level) {
+    int n = 1;   // canonical sequences of `level` gluons: K!/(K-level)!/2 (the K singles for level 1)
+    for (int i = 0; i < level; ++i) n *= K - i;
+    const int count = level == 1 ? K : n / 2;
+    const int64_t threads = nevt * (static_cast<int64_t>(count) << level);
+    if (threads > 0)
+      v2::k_share_level<K><<<static_cast<unsigned>((threads + 127) / 128), 128, 0, st>>>(
+          static_cast<const double*>(rec), nevt, tab, cst, level, s0, s0 + count, share);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    s0 += count;
+  }
+  return cudaSuccess;
+}
+
+int share_items(int K) {
+  int n = 0, total = 0;
+  for (int level = 1; level < K; ++level) {
+    int f = 1;
+    for (int i = 0; i < level; ++i) f *= K - i;
+    n = level == 1 ? K : f / 2;
+    total += n << level;
+  }
+  return total;
+}
+
+cudaError_t launch_share(int K, const void* rec, int64_t nevt, const Tables* tab, const MeConst& cst, double* share,
+                         cudaStream_t st) {
+  switch (K) {
+    case 2: return launch_share_k<2>(rec, nevt, tab, cst, share, st);
+    case 3: return launch_share_k<3>(rec, nevt, tab, cst, share, st);
+    case 4: return launch_share_k<4>(rec, nevt, tab, cst, share, st);
+    case 5: return launch_share_k<5>(rec, nevt, tab, cst, share, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -180,17 +237,18 @@ cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom
                                const Tables* tab, const int* gslots, int maxslot, const int* nslot,
                                const uint32_t* mask, const double* ctri64, const float* ctri32, const MeConst& cst,
                                double* out, int64_t stride, cudaStream_t st, float2* jout, MeShape shape,
-                               const uint8_t* skip, const int* evlist, const int* nlist, int rows_out) {
+                               const uint8_t* skip, const int* evlist, const int* nlist, int rows_out,
+                               const double* share) {
 #define MG_V2_CASE(KK)                                                                                              \
   case KK:                                                                                                          \
     if (per_hel) return fp32 ? launch_v2<KK, float, true>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri32, cst,  \
-                                                          out, stride, jout, shape, skip, evlist, nlist, rows_out, st)                                          \
+                                                          out, stride, jout, shape, skip, evlist, nlist, rows_out, st, share)                                          \
                              : launch_v2<KK, double, true>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri64, cst, \
-                                                           out, stride, jout, shape, skip, evlist, nlist, rows_out, st);                                        \
+                                                           out, stride, jout, shape, skip, evlist, nlist, rows_out, st, share);                                        \
     return fp32 ? launch_v2<KK, float, false>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri32, cst, out, stride, \
-                                              jout, shape, skip, evlist, nlist, rows_out, st)                                                                   \
+                                              jout, shape, skip, evlist, nlist, rows_out, st, share)                                                                   \
                 : launch_v2<KK, double, false>(mom, prep, nevt, tab, gslots, maxslot, nslot, mask, ctri64, cst, out, stride,\
-                                               jout, shape, skip, evlist, nlist, rows_out, st);
+                                               jout, shape, skip, evlist, nlist, rows_out, st, share);
   switch (K) {
     MG_V2_CASE(2)
     MG_V2_CASE(3)

@@ -14,13 +14,19 @@ namespace v2 {
 // JOUT: instead of colour sums, write the jamps of every helicity of the slot as FP32 complex
 // numbers to jout[((e * 4 * 2^K) + slot * 4 + 2 * top + antitop) * ncol + sigma] (zeros for helicities
 // outside the mask), for the tensor-core colour sum.
-template <int K, class T, bool PER_HEL, bool PREP, bool JOUT>
+// SHARED (FP64 with a per-event record): the gluon currents of fewer than all gluons and their (gamma.J) v
+// are not computed here but read from share, where k_share_level left them once per helicity
+// assignment of their own gluons (item tab->share_base[s] + helicity bits of s's gluons, 24 doubles:
+// J, then (gamma.J) v for both antitop helicities).
+template <int K, class T, bool PER_HEL, bool PREP, bool JOUT, bool SHARED = false>
 __global__ void __launch_bounds__(kMeThreads)
 k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab,
               const int* __restrict__ gslots, const int* __restrict__ nslot_dev, const uint32_t* __restrict__ mask,
               const typename ColourT<T>::type* __restrict__ ctri, MeConst cst, double* __restrict__ out, int64_t stride,
               float2* __restrict__ jout, int tile_ev, int slot_major, const int* __restrict__ evlist,
-              const int* __restrict__ nlist, int rows_out, const uint8_t* __restrict__ skip) {
+              const int* __restrict__ nlist, int rows_out, const uint8_t* __restrict__ skip,
+              const double* __restrict__ share = nullptr) {
+  static_assert(!SHARED || (PREP && std::is_same<T, double>::value), "shared currents: FP64 with a record");
   constexpr int npar = K + 2;
   constexpr int NSEQ = Sizes<K>::nseq;
   constexpr int NCOL = Sizes<K>::ncol;
@@ -54,12 +60,14 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
 #pragma unroll
       for (int c = 0; c < 5; ++c) qc[S][c] = __ldg(in + (L::QC + 5 * S + c) * kPage);
     }
+    if constexpr (!SHARED) {
 #pragma unroll
-    for (int g = 0; g < K; ++g) {
-      T pol[5];
+      for (int g = 0; g < K; ++g) {
+        T pol[5];
 #pragma unroll
-      for (int i = 0; i < 5; ++i) pol[i] = __ldg(in + (L::EPS + 5 * g + i) * kPage);
-      ext_gluon(pol, (gc >> g) & 1 ? 1 : -1, g >= 2, J[g]);
+        for (int i = 0; i < 5; ++i) pol[i] = __ldg(in + (L::EPS + 5 * g + i) * kPage);
+        ext_gluon(pol, (gc >> g) & 1 ? 1 : -1, g >= 2, J[g]);
+      }
     }
 #pragma unroll
     for (int l = 0; l < 2; ++l)
@@ -82,7 +90,21 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
   }
 
   // ---- gluon currents (helicities of gc) ----
-  for (int s = K; s < NSEQ; ++s) {
+  constexpr bool kTableX = std::is_same<T, double>::value;
+  cx<T> X[kTableX ? 2 : 1][kTableX ? NSEQ : 1][4];
+  if constexpr (SHARED) {
+    const double* sh = share + static_cast<int64_t>(e) * tab->share_n * 24;
+    for (int s = 0; s < NSEQ; ++s) {
+      const double* it = sh + (tab->share_base[s] + pext_bits(gc, tab->seq_mask[s])) * 24;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) J[s][m] = {it[2 * m], it[2 * m + 1]};
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int m = 0; m < 4; ++m) X[b][s][m] = {it[8 + 8 * b + 2 * m], it[8 + 8 * b + 2 * m + 1]};
+    }
+  }
+  for (int s = K; s < (SHARED ? 0 : NSEQ); ++s) {
     cx<T> acc[4] = {};
     const int n3 = tab->seq_nv3[s];
     for (int k = 0; k < n3; ++k) {
@@ -124,9 +146,7 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
   // instructions); in FP32 and double-float each jamp term forms ubar-side (row spinor x gamma.J) on
   // the fly instead, keeping 2 NSEQ spinors out of the thread's local memory (FP32-pipe arithmetic is
   // cheap, memory is not).
-  constexpr bool kTableX = std::is_same<T, double>::value;
-  cx<T> X[kTableX ? 2 : 1][kTableX ? NSEQ : 1][4];
-  if (kTableX) {
+  if constexpr (kTableX && !SHARED) {
 #pragma unroll
     for (int b = 0; b < 2; ++b)
       for (int s = 0; s < NSEQ; ++s) gamma_col(J[s], vv[b], X[b][s]);
@@ -229,6 +249,89 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
       out[(slot * 4 + 3) * stride + e] = 0.0;
     } else {
       out[slot * stride + e] = total;
+    }
+  }
+}
+
+// Currents shared between gluon-helicity combinations (FP64): every canonical sequence s of `level`
+// gluons, for every helicity assignment h of its own gluons, from the record and the shorter sequences
+// of the same assignment already in share; writes J and (gamma.J) v of both antitop helicities to item
+// share_base[s] + h (the layout k_me_gluonhel<..., SHARED> reads).  One thread per (event, item of the
+// level); levels run in order 1 .. K-1.
+template <int K>
+__global__ void __launch_bounds__(128)
+k_share_level(const double* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab, MeConst cst, int level,
+              int s0, int s1, double* __restrict__ share) {
+  using L = EvLayout<K>;
+  const int per_ev = (s1 - s0) << level;
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= nevt * per_ev) return;
+  const int64_t e = t / per_ev;
+  const int j = static_cast<int>(t - e * per_ev);
+  const int s = s0 + (j >> level), h = j & ((1 << level) - 1);
+  const int msk = tab->seq_mask[s];
+  const int gc = pdep_bits(h, msk);
+  const double* in = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
+  auto ld = [&](int item) -> double { return __ldg(in + item * kPage); };
+  double* sh = share + e * tab->share_n * 24;
+  auto getJ = [&](int slot, cx<double>* J) {
+    const double* it = sh + (tab->share_base[slot] + pext_bits(gc, tab->seq_mask[slot])) * 24;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) J[m] = {it[2 * m], it[2 * m + 1]};
+  };
+  auto getP = [&](int slot, double* P) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) P[m] = ld(L::PT + 4 * tab->seq_mask[slot] + m);
+  };
+  cx<double> J[4];
+  if (level == 1) {
+    double pol[5];
+#pragma unroll
+    for (int i = 0; i < 5; ++i) pol[i] = ld(L::EPS + 5 * s + i);
+    ext_gluon(pol, h ? 1 : -1, s >= 2, J);
+  } else {
+    const double gs = cst.gs;
+    cx<double> acc[4] = {};
+    const int n3 = tab->seq_nv3[s];
+    for (int k = 0; k < n3; ++k) {
+      const int16_t rl = tab->seq_v3[s][k][0], rr = tab->seq_v3[s][k][1];
+      cx<double> JL[4], JR[4];
+      double PL[4], PR[4];
+      getJ(rslot(rl), JL);
+      getJ(rslot(rr), JR);
+      getP(rslot(rl), PL);
+      getP(rslot(rr), PR);
+      v3_acc(acc, JL, JR, PL, PR, rneg(rl) != rneg(rr));
+    }
+    const int n4 = tab->seq_nv4[s];
+    for (int k = 0; k < n4; ++k) {
+      const int16_t ra = tab->seq_v4[s][k][0], rb = tab->seq_v4[s][k][1], rc = tab->seq_v4[s][k][2];
+      cx<double> JA[4], JB[4], JC[4];
+      getJ(rslot(ra), JA);
+      getJ(rslot(rb), JB);
+      getJ(rslot(rc), JC);
+      v4_acc(acc, JA, JB, JC, gs, rneg(ra) ^ rneg(rb) ^ rneg(rc));
+    }
+    const double f = ld(L::GP + msk);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) J[m] = cscale(f, acc[m]);
+  }
+  double* out = sh + (tab->share_base[s] + h) * 24;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    out[2 * m] = J[m].r;
+    out[2 * m + 1] = J[m].i;
+  }
+#pragma unroll
+  for (int b = 0; b < 2; ++b) {
+    cx<double> v[4], X[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) v[q] = {ld(L::VV + (b * 4 + q) * 2), ld(L::VV + (b * 4 + q) * 2 + 1)};
+    gamma_col(J, v, X);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      out[8 + 8 * b + 2 * m] = X[m].r;
+      out[8 + 8 * b + 2 * m + 1] = X[m].i;
     }
   }
 }

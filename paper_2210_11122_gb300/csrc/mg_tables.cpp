@@ -56,6 +56,11 @@ void build_tables(int K, Tables& t) {
       if (s.front() < s.back()) { slot_of[s] = static_cast<int>(seqs.size()); seqs.push_back(s); }
   }
   t.nseq = static_cast<int>(seqs.size());
+  t.share_n = 0;
+  for (int i = 0; i < t.nseq; ++i) {
+    t.share_base[i] = static_cast<int16_t>(t.share_n);
+    t.share_n += 1 << seqs[i].size();
+  }
   auto ref = [&](const std::vector<int>& s) -> int16_t {
     if (s.size() == 1) return pack(s[0], false);
     if (s.front() < s.back()) return pack(slot_of.at(s), false);

@@ -37,7 +37,7 @@ std::string cache_key(mg_ctx* ctx, mg_precision precision) {
 
 int launch_flags(const mg::MeShape& s) {
   return (s.unrolled ? MG_LAUNCH_UNROLLED : 0) | (s.df_redo ? MG_LAUNCH_DF_REDO : 0) | (s.fused ? MG_LAUNCH_FUSED : 0) |
-         (s.warp ? MG_LAUNCH_WARP : 0) | (s.tc_apart ? MG_LAUNCH_TC_APART : 0);
+         (s.warp ? MG_LAUNCH_WARP : 0) | (s.tc_apart ? MG_LAUNCH_TC_APART : 0) | (s.shared ? MG_LAUNCH_SHARED : 0);
 }
 
 bool cache_lookup(const char* path, const std::string& key, mg::MeShape* shape, double* ms) {
@@ -59,6 +59,7 @@ bool cache_lookup(const char* path, const std::string& key, mg::MeShape* shape, 
       shape->fused = (un & MG_LAUNCH_FUSED) != 0;
       shape->warp = (un & MG_LAUNCH_WARP) != 0;
       shape->tc_apart = (un & MG_LAUNCH_TC_APART) != 0;
+      shape->shared = (un & MG_LAUNCH_SHARED) != 0;
       *ms = t;
       found = true;
     }
@@ -153,9 +154,10 @@ extern "C" mg_status mg_autotune(mg_ctx* ctx, mg_precision precision, int64_t ne
       if (rc == MG_OK && t < best_t) { best_t = t; best = s; }
     }
   }
-  if (fp32 && rc == MG_OK) {   // the recomputation arithmetic, on the best shape
+  if ((fp32 || precision == MG_FP64) && rc == MG_OK) {   // recomputation arithmetic / shared currents
     mg::MeShape s = best;
-    s.df_redo = !s.df_redo;
+    if (fp32) s.df_redo = !s.df_redo;
+    else s.shared = !s.shared;
     float t = 1e30f;
     rc = time_shape(s, &t);
     if (rc == MG_OK && t < best_t) { best_t = t; best = s; }
@@ -188,7 +190,8 @@ extern "C" mg_status mg_set_launch_shape(mg_ctx* ctx, mg_precision precision, in
                                          int flags) {
   if (!ctx || precision < MG_FP64 || precision > MG_MIXED) return MG_EINVAL;
   if ((tile_ev != 32 && tile_ev != 64 && tile_ev != 128) || (slot_major != 0 && slot_major != 1) ||
-      (flags & ~(MG_LAUNCH_UNROLLED | MG_LAUNCH_DF_REDO | MG_LAUNCH_FUSED | MG_LAUNCH_WARP | MG_LAUNCH_TC_APART)) != 0)
+      (flags & ~(MG_LAUNCH_UNROLLED | MG_LAUNCH_DF_REDO | MG_LAUNCH_FUSED | MG_LAUNCH_WARP | MG_LAUNCH_TC_APART |
+                 MG_LAUNCH_SHARED)) != 0)
     return MG_EINVAL;
   ctx->shape[precision].tile_ev = tile_ev;
   ctx->shape[precision].slot_major = slot_major != 0;
@@ -197,6 +200,7 @@ extern "C" mg_status mg_set_launch_shape(mg_ctx* ctx, mg_precision precision, in
   ctx->shape[precision].fused = (flags & MG_LAUNCH_FUSED) != 0;
   ctx->shape[precision].warp = (flags & MG_LAUNCH_WARP) != 0;
   ctx->shape[precision].tc_apart = (flags & MG_LAUNCH_TC_APART) != 0;
+  ctx->shape[precision].shared = (flags & MG_LAUNCH_SHARED) != 0;
   return MG_OK;
 }
 

@@ -89,12 +89,12 @@ def test_graph_rejects_shared_context(env):
 def test_launch_shape_set_and_get(env):
     torch, mg = env[0], env[1]
     with mg.Context(1) as ctx:
-        both = mg.LAUNCH_UNROLLED | mg.LAUNCH_DF_REDO | mg.LAUNCH_FUSED
+        both = mg.LAUNCH_UNROLLED | mg.LAUNCH_DF_REDO | mg.LAUNCH_FUSED | mg.LAUNCH_SHARED
         assert ctx.launch_shape(mg.MG_FP32_AMP) == (128, 0, both)
         ctx.set_launch_shape(mg.MG_FP32_AMP, 32, 1, mg.LAUNCH_DF_REDO)
         assert ctx.launch_shape(mg.MG_FP32_AMP) == (32, 1, mg.LAUNCH_DF_REDO)
         assert ctx.launch_shape(mg.MG_FP64) == (128, 0, both)
-        for bad in ((48, 0, 1), (64, 2, 1), (64, 0, 32)):
+        for bad in ((48, 0, 1), (64, 2, 1), (64, 0, 64)):
             with pytest.raises(mg.MGError):
                 ctx.set_launch_shape(mg.MG_FP32_AMP, *bad)
 
