@@ -267,16 +267,19 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
+        n0 = mg.kernel_launches()
         with torch.cuda.stream(stream):
             for k in range(steps):
                 step(precision, evs[k])
                 flush.zero_()
+        nlaunch = mg.kernel_launches() - n0
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
         wall = time.perf_counter() - t0
         step_ms = [e[0].elapsed_time(e[2]) for e in evs]
         me_ms = [e[1].elapsed_time(e[2]) for e in evs]
+        timed.launches = nlaunch
         return statistics.mean(step_ms), statistics.mean(me_ms), wall
 
     if ctx.check(stream) != 0:
@@ -296,6 +299,7 @@ def run_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     ms_step, ms_me, wall = timed(mg.MG_FP64, args.steps, max(3, args.warmup))
+    launches = timed.launches
     clk = clocks.stop()
     nbad = ctx.check(stream)
     ms_step, ms_me = max_over_ranks([ms_step, ms_me], world, "cuda")
@@ -360,7 +364,9 @@ def run_ours(args):
 
     # roofline of the dominant kernel (the FP64 matrix-element kernel, ALU bound on the FP64 pipe)
     mask, ngood = ctx.hel_mask()
-    amp_f, col_f = mg.flops_per_event(ng, mask)
+    flags64 = ctx.launch_shape(mg.MG_FP64)[2]
+    shared64 = bool(flags64 & mg.LAUNCH_SHARED)
+    amp_f, col_f = mg.flops_per_event(ng, mask, mg.MG_FP64, flags64)
     flops = (amp_f + col_f) * nevt
     peak = mg.measure_fma_peak(fp32=False, iters=2048)
     # the other modes against the peak of the pipe their amplitudes run on (FP32 FMA for the FP32-
@@ -369,7 +375,7 @@ def run_ours(args):
     # (the tensor-core colour modes count their amplitude flops only: the colour sums run on the tensor
     # cores, not on that pipe)
     for name, prec in (("fp32_amp", mg.MG_FP32_AMP), ("fp64_tccolor", mg.MG_FP64_TCCOLOR), ("mixed", mg.MG_MIXED)):
-        a, c = mg.flops_per_event(ng, mask, prec)
+        a, c = mg.flops_per_event(ng, mask, prec, ctx.launch_shape(prec)[2])
         if prec in (mg.MG_FP64_TCCOLOR, mg.MG_MIXED):
             c = 0.0
         pk = peak32 if prec in (mg.MG_FP32_AMP, mg.MG_MIXED) else peak
@@ -384,7 +390,8 @@ def run_ours(args):
                                os.path.join(ROOT, "profiles", "k_me_gluonhel_fp64_%s_65536.md" % args.process), nevt)
     roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_event_prep + k_me_gluonhel<%d,double> + k_hel_sum (one mg_sigmakin call)" % (ng + 2),
+                "kernel": "k_event_prep + %sk_me_gluonhel<%d,double> + k_hel_sum (one mg_sigmakin call)"
+                          % ("k_share_level (per sequence length) + " if shared64 else "", ng + 2),
                 "flops_per_event": amp_f + col_f,
                 "peak_source": "measured FP64 DFMA-chain microbenchmark (mg_measure_fma_peak) on this GPU"}
 
@@ -395,9 +402,6 @@ def run_ours(args):
                "sample": "first %d events of the workload (of %d), FP64 ME only, %.1f s on %d threads"
                          % (n, nevt, dt, cores)}
 
-    # rambo; helicity filter (per-helicity ME, helicity sum, ratio maximum, mask, slot list); FP64
-    # sigmakin (per-event record, ME, helicity sum)
-    launches_per_step = 1 + 5 + 3
     line = {"metric": METRIC, "value": value, "unit": "MEs/s", "n_gpus": world, "steps": args.steps,
             "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -407,7 +411,7 @@ def run_ours(args):
             "graph": {"ms_per_step": graph_ms, "value": aggregate_rate(world, nevt, graph_ms), "same_result": graph_same,
                       "what": "the FP64 step captured as one CUDA graph (mg_graph_create) and replayed"},
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
-            "gpu_launches": launches_per_step * args.steps}
+            "gpu_launches": launches}
     print(json.dumps(line))
     ctx.close()
     if world > 1:

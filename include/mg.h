@@ -168,6 +168,13 @@ mg_status mg_check(mg_ctx* ctx, void* stream, int64_t* nbad);
 mg_status mg_flops_per_event(mg_process proc, mg_precision precision, const uint32_t* mask, double* amp_flops,
                              double* colour_flops);
 
+/* As mg_flops_per_event, for the algorithm that the launch flags `flags` (MG_LAUNCH_* bits, as
+ * mg_get_launch_shape returns them) select: with MG_LAUNCH_SHARED the FP64-amplitude modes count the
+ * shared currents once per helicity assignment of their own gluons, without it once per good
+ * gluon-helicity combination.  flags < 0 = the defaults of mg_create.  Host only. */
+mg_status mg_flops_per_event_shape(mg_process proc, mg_precision precision, const uint32_t* mask, int flags,
+                                   double* amp_flops, double* colour_flops);
+
 /* FP64 matrix elements exactly as mg_sigmakin(..., MG_FP64, ...), for callers that must not have
  * the library allocate device memory during the call (an application that hands the engine a
  * fixed memory budget, or whose own pooling allocator must remain the only one): this entry point
@@ -324,6 +331,12 @@ void mg_serve_destroy(mg_server* srv);
  * 8 blocks of 256 threads per SM and returns the measured rate in flop/s (an FMA counts 2) for
  * FP64 (fp32 = 0) or FP32 (fp32 = 1).  Synchronous; 1 <= iters <= 2^20. */
 mg_status mg_measure_fma_peak(int fp32, int iters, double* flops_per_s);
+
+/* Diagnostic: the number of CUDA kernels this library has launched in this process, on every
+ * context, stream and thread (a launch captured into a CUDA graph counts once, at capture; graph
+ * replays do not count).  The difference of two reads brackets the launches of the calls between
+ * them.  Host only; never fails. */
+int64_t mg_kernel_launches(void);
 
 #ifdef __cplusplus
 }

@@ -78,6 +78,8 @@ def lib():
     L.mg_rambo.argtypes = [vp, u64, i64, dbl, vp, vp, vp]
     L.mg_rambo_range.argtypes = [vp, u64, i64, i64, dbl, vp, vp, vp]
     L.mg_measure_fma_peak.argtypes = [i32, i32, P(dbl)]
+    L.mg_kernel_launches.argtypes = []
+    L.mg_kernel_launches.restype = i64
     L.mg_hel_filter.argtypes = [vp, vp, i64, vp]
     L.mg_sigmakin.argtypes = [vp, vp, i64, i32, vp, vp]
     L.mg_sigmakin_host.argtypes = [vp, vp, i64, i32, vp, vp]
@@ -85,6 +87,7 @@ def lib():
     L.mg_hel_mask.argtypes = [vp, P(ctypes.c_uint32), P(i32)]
     L.mg_check.argtypes = [vp, vp, P(ctypes.c_int64)]
     L.mg_flops_per_event.argtypes = [i32, i32, P(ctypes.c_uint32), P(dbl), P(dbl)]
+    L.mg_flops_per_event_shape.argtypes = [i32, i32, P(ctypes.c_uint32), i32, P(dbl), P(dbl)]
     L.mg_autotune.argtypes = [vp, i32, i64, ctypes.c_char_p, P(dbl)]
     L.mg_get_launch_shape.argtypes = [vp, i32, P(i32), P(i32), P(i32)]
     L.mg_set_launch_shape.argtypes = [vp, i32, i32, i32, i32]
@@ -112,7 +115,8 @@ def lib():
         getattr(L, name).restype = i32
     for name in ("mg_process_info", "mg_colour_matrix", "mg_create", "mg_philox", "mg_rambo", "mg_rambo_range",
                  "mg_measure_fma_peak", "mg_hel_filter",
-                 "mg_sigmakin", "mg_sigmakin_host", "mg_sigmakin_noalloc", "mg_hel_mask", "mg_check", "mg_flops_per_event"):
+                 "mg_sigmakin", "mg_sigmakin_host", "mg_sigmakin_noalloc", "mg_hel_mask", "mg_check", "mg_flops_per_event",
+                 "mg_flops_per_event_shape"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -185,15 +189,15 @@ def colour_matrix(process):
     return num, den.value
 
 
-def flops_per_event(process, mask=None, precision=MG_FP64):
+def flops_per_event(process, mask=None, precision=MG_FP64, flags=None):
     """(amplitude flops, colour-sum flops) of one event's ME in the given precision mode for the given
-    helicity mask."""
+    helicity mask, for the algorithm the launch flags select (None: the defaults of a new Context)."""
     a, c = ctypes.c_double(), ctypes.c_double()
     m = None
     if mask is not None:
         m = (ctypes.c_uint32 * len(mask))(*[int(x) for x in mask])
-    _check(lib().mg_flops_per_event(_proc(process), precision, m, ctypes.byref(a), ctypes.byref(c)),
-           "mg_flops_per_event")
+    _check(lib().mg_flops_per_event_shape(_proc(process), precision, m, -1 if flags is None else int(flags),
+                                          ctypes.byref(a), ctypes.byref(c)), "mg_flops_per_event_shape")
     return a.value, c.value
 
 
@@ -222,6 +226,11 @@ def measure_fma_peak(fp32=False, iters=4096):
     r = ctypes.c_double()
     _check(lib().mg_measure_fma_peak(1 if fp32 else 0, iters, ctypes.byref(r)), "mg_measure_fma_peak")
     return r.value
+
+
+def kernel_launches():
+    """CUDA kernels this library has launched in this process so far (all contexts and streams)."""
+    return int(lib().mg_kernel_launches())
 
 
 def philox(seed, nevt, nfinal, words, stream=None):

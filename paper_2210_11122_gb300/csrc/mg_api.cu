@@ -5,6 +5,7 @@
 // No C++ exception crosses the ABI; every entry point returns an mg_status.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -119,6 +120,9 @@ mg_status grow_repair(mg_ctx* ctx, int64_t n) {
 }  // namespace
 
 namespace mg {
+
+static std::atomic<int64_t> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 int64_t share_chunk(int K, int64_t stride) {
   const int64_t per_event = static_cast<int64_t>(share_items(K)) * 24;   // doubles
@@ -243,22 +247,28 @@ mg_status mg_colour_matrix(mg_process proc, int64_t* num, int64_t* den) {
   return MG_OK;
 }
 
-mg_status mg_flops_per_event(mg_process proc, mg_precision precision, const uint32_t* mask, double* amp_flops,
-                             double* colour_flops) {
+mg_status mg_flops_per_event_shape(mg_process proc, mg_precision precision, const uint32_t* mask, int flags,
+                                   double* amp_flops, double* colour_flops) {
   if (!valid_proc(proc) || precision < MG_FP64 || precision > MG_MIXED) return MG_EINVAL;
   mg::Tables* t = new (std::nothrow) mg::Tables;
   if (!t) return MG_ENOMEM;
   mg::build_tables(mg::gluons_of(proc), *t);
   double a, c;
-  // the default algorithm of each mode: FP64 amplitudes share the currents of fewer than all gluons
-  // between gluon-helicity combinations for 1 and 3 final-state gluons (as mg_create's launch shapes)
-  const int K = mg::gluons_of(proc);
   const bool fp32 = precision == MG_FP32_AMP || precision == MG_MIXED;
-  flop_model(*t, mask, fp32, !fp32 && (K == 3 || K == 5), &a, &c);
+  // flags < 0: the default algorithm of each mode (as mg_create's launch shapes): FP64 amplitudes share
+  // the currents of fewer than all gluons between gluon-helicity combinations for 1 and 3 final-state gluons
+  const int K = mg::gluons_of(proc);
+  const bool shared = flags < 0 ? (K == 3 || K == 5) : (flags & MG_LAUNCH_SHARED) != 0;
+  flop_model(*t, mask, fp32, !fp32 && shared, &a, &c);
   delete t;
   if (amp_flops) *amp_flops = a;
   if (colour_flops) *colour_flops = c;
   return MG_OK;
+}
+
+mg_status mg_flops_per_event(mg_process proc, mg_precision precision, const uint32_t* mask, double* amp_flops,
+                             double* colour_flops) {
+  return mg_flops_per_event_shape(proc, precision, mask, -1, amp_flops, colour_flops);
 }
 
 void mg_destroy(mg_ctx* ctx) {
@@ -681,5 +691,7 @@ mg_status mg_check(mg_ctx* ctx, void* stream, int64_t* nbad) {
   if (nbad) *nbad = static_cast<int64_t>(n);
   return n ? MG_ENOCONV : MG_OK;
 }
+
+int64_t mg_kernel_launches(void) { return mg::g_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"

@@ -246,8 +246,8 @@ cudaError_t launch_tc(const float2* jamps, int64_t nevt, int rows_alloc, const i
   const int64_t cap = static_cast<int64_t>(nsm) * per_sm;   // resident blocks; tiles are strided over them
   if (blocks > cap) blocks = cap;
   if (blocks < 1) return cudaSuccess;
-  k_colour_tc<NCOL><<<static_cast<unsigned>(blocks), 128, smem, st>>>(jamps, nevt, rows_alloc, nrows, cmat, scale, out,
-                                                                       stride, skip);
+  { k_colour_tc<NCOL><<<static_cast<unsigned>(blocks), 128, smem, st>>>(jamps, nevt, rows_alloc, nrows, cmat, scale, out,
+                                                                       stride, skip); mg::note_launch(); }
   return cudaGetLastError();
 }
 

@@ -13,6 +13,9 @@ constexpr int kMaxNcol = 120;      // 5!
 constexpr int kMaxSeq = 105;       // canonical gluon sequences of length 1..K-1 for K = 5
 constexpr int kPage = 32;          // AoSoA page: events per page
 
+// Count one kernel launch of this library (process-wide, thread-safe; read by mg_kernel_launches).
+void note_launch();
+
 inline int gluons_of(mg_process p) { return static_cast<int>(p) + 2; }
 inline int npar_of(mg_process p) { return static_cast<int>(p) + 4; }
 inline int factorial(int n) { int f = 1; for (int i = 2; i <= n; ++i) f *= i; return f; }

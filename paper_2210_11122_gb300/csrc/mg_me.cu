@@ -429,7 +429,7 @@ static cudaError_t launch_me_t(const double* mom, int64_t nevt, const Tables* ta
                                cudaStream_t st) {
   dim3 grid(static_cast<unsigned>((nevt + kMeThreads - 1) / kMeThreads), static_cast<unsigned>(maxslot));
   if (grid.x == 0 || grid.y == 0) return cudaSuccess;
-  k_me_helicity<K, T><<<grid, kMeThreads, 0, st>>>(mom, nevt, tab, hels, nslot, ctri, cst, out, stride);
+  { k_me_helicity<K, T><<<grid, kMeThreads, 0, st>>>(mom, nevt, tab, hels, nslot, ctri, cst, out, stride); mg::note_launch(); }
   return cudaGetLastError();
 }
 
@@ -454,14 +454,14 @@ cudaError_t launch_hel_sum(const double* part, const int* nslot, int64_t nevt, i
   const int threads = 256;
   const unsigned blocks = static_cast<unsigned>((nevt + threads - 1) / threads);
   if (blocks == 0) return cudaSuccess;
-  k_hel_sum<<<blocks, threads, 0, st>>>(part, nslot, nevt, stride, norm, me);
+  { k_hel_sum<<<blocks, threads, 0, st>>>(part, nslot, nevt, stride, norm, me); mg::note_launch(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_hel_mask(const double* part, const double* tot, int nhel, int64_t nevt, int64_t stride, double tau,
                             double* maxr, uint32_t* mask, int* good, int* ngood, cudaStream_t st) {
-  k_hel_ratio_max<<<nhel, 256, 0, st>>>(part, tot, nevt, stride, maxr);
-  k_hel_mask<<<1, 128, 0, st>>>(maxr, nhel, tau, mask, good, ngood);
+  { k_hel_ratio_max<<<nhel, 256, 0, st>>>(part, tot, nevt, stride, maxr); mg::note_launch(); }
+  { k_hel_mask<<<1, 128, 0, st>>>(maxr, nhel, tau, mask, good, ngood); mg::note_launch(); }
   return cudaGetLastError();
 }
 

@@ -89,7 +89,7 @@ __global__ void k_gluon_slots(const uint32_t* __restrict__ mask, int K, int* __r
 }  // namespace v2
 
 cudaError_t launch_gluon_slots(const uint32_t* mask, int K, int* gslots, int* n, int* nrows, cudaStream_t st) {
-  v2::k_gluon_slots<<<1, 32, 0, st>>>(mask, K, gslots, n, nrows);
+  { v2::k_gluon_slots<<<1, 32, 0, st>>>(mask, K, gslots, n, nrows); mg::note_launch(); }
   return cudaGetLastError();
 }
 
@@ -115,29 +115,29 @@ static cudaError_t launch_v2(const double* mom, void* prep, int64_t nevt, const 
     if constexpr (std::is_same<T, double>::value) {
       if (share) {
         if (jout)
-          v2::k_me_gluonhel<K, T, false, true, true, true><<<grid, kMeThreads, 0, st>>>(
+          { v2::k_me_gluonhel<K, T, false, true, true, true><<<grid, kMeThreads, 0, st>>>(
               mom, rec, nevt, tab, gslots, nslot, mask, ctri, cst, out, stride, jout, tev, sm, nullptr, nullptr, 0, skip,
-              share);
+              share); mg::note_launch(); }
         else
-          v2::k_me_gluonhel<K, T, false, true, false, true><<<grid, kMeThreads, 0, st>>>(
+          { v2::k_me_gluonhel<K, T, false, true, false, true><<<grid, kMeThreads, 0, st>>>(
               mom, rec, nevt, tab, gslots, nslot, mask, ctri, cst, out, stride, nullptr, tev, sm, nullptr, nullptr, 0,
-              skip, share);
+              skip, share); mg::note_launch(); }
         return cudaGetLastError();
       }
     }
     if (jout)
-      v2::k_me_gluonhel<K, T, false, true, true><<<grid, kMeThreads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot, mask,
+      { v2::k_me_gluonhel<K, T, false, true, true><<<grid, kMeThreads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot, mask,
                                                                              ctri, cst, out, stride, jout, tev, sm, nullptr,
-                                                                             nullptr, 0, skip);
+                                                                             nullptr, 0, skip); mg::note_launch(); }
     else
-      v2::k_me_gluonhel<K, T, false, true, false><<<grid, kMeThreads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot,
+      { v2::k_me_gluonhel<K, T, false, true, false><<<grid, kMeThreads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot,
                                                                               mask, ctri, cst, out, stride, nullptr, tev,
-                                                                              sm, nullptr, nullptr, 0, skip);
+                                                                              sm, nullptr, nullptr, 0, skip); mg::note_launch(); }
   } else {
-    v2::k_me_gluonhel<K, T, PER_HEL, false, false><<<grid, kMeThreads, 0, st>>>(mom, nullptr, nevt, tab, gslots, nslot,
+    { v2::k_me_gluonhel<K, T, PER_HEL, false, false><<<grid, kMeThreads, 0, st>>>(mom, nullptr, nevt, tab, gslots, nslot,
                                                                                  mask, ctri, cst, out, stride, nullptr,
                                                                                  tev, sm, evlist, nlist, rows_out,
-                                                                                 nullptr);
+                                                                                 nullptr); mg::note_launch(); }
   }
   return cudaGetLastError();
 }
@@ -145,7 +145,7 @@ static cudaError_t launch_v2(const double* mom, void* prep, int64_t nevt, const 
 template <int K, class T>
 static cudaError_t launch_prep(const double* mom, int64_t nevt, const MeConst& cst, void* rec, cudaStream_t st) {
   if (nevt <= 0) return cudaSuccess;
-  v2::k_event_prep<K, T><<<static_cast<unsigned>((nevt + 127) / 128), 128, 0, st>>>(mom, nevt, cst, static_cast<T*>(rec));
+  { v2::k_event_prep<K, T><<<static_cast<unsigned>((nevt + 127) / 128), 128, 0, st>>>(mom, nevt, cst, static_cast<T*>(rec)); mg::note_launch(); }
   return cudaGetLastError();
 }
 
@@ -170,8 +170,8 @@ static cudaError_t launch_share_k(const void* rec, int64_t nevt, const Tables* t
     const int count = level == 1 ? K : n / 2;
     const int64_t threads = nevt * (static_cast<int64_t>(count) << level);
     if (threads > 0)
-      v2::k_share_level<K><<<static_cast<unsigned>((threads + 127) / 128), 128, 0, st>>>(
-          static_cast<const double*>(rec), nevt, tab, cst, level, s0, s0 + count, share);
+      { v2::k_share_level<K><<<static_cast<unsigned>((threads + 127) / 128), 128, 0, st>>>(
+          static_cast<const double*>(rec), nevt, tab, cst, level, s0, s0 + count, share); mg::note_launch(); }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     s0 += count;
@@ -205,8 +205,8 @@ template <int K>
 static cudaError_t launch_flags(const double* mom, int64_t nevt, const MeConst& cst, int* repair, int* nrepair,
                                 uint8_t* flag, cudaStream_t st) {
   if (nevt <= 0) return cudaSuccess;
-  v2::k_event_flags<K><<<static_cast<unsigned>((nevt + 127) / 128), 128, 0, st>>>(
-      mom, nevt, static_cast<float>(cst.mt), static_cast<float>(cst.fp32_tau), repair, nrepair, flag);
+  { v2::k_event_flags<K><<<static_cast<unsigned>((nevt + 127) / 128), 128, 0, st>>>(
+      mom, nevt, static_cast<float>(cst.mt), static_cast<float>(cst.fp32_tau), repair, nrepair, flag); mg::note_launch(); }
   return cudaGetLastError();
 }
 

@@ -314,11 +314,11 @@ static cudaError_t launch_static(const void* rec, int64_t nevt, const int* gslot
   const dim3 grid = sm ? dim3(nsl_t, nev_t) : dim3(nev_t, nsl_t);
   const T* r = static_cast<const T*>(rec);
   if (jout)
-    st::k_me_static<K, T, true><<<grid, kMeThreads, 0, stream>>>(r, nevt, gslots, nslot, mask, cst, out, stride, jout,
-                                                                 tev, sm, skip);
+    { st::k_me_static<K, T, true><<<grid, kMeThreads, 0, stream>>>(r, nevt, gslots, nslot, mask, cst, out, stride, jout,
+                                                                 tev, sm, skip); mg::note_launch(); }
   else
-    st::k_me_static<K, T, false><<<grid, kMeThreads, 0, stream>>>(r, nevt, gslots, nslot, mask, cst, out, stride,
-                                                                  nullptr, tev, sm, skip);
+    { st::k_me_static<K, T, false><<<grid, kMeThreads, 0, stream>>>(r, nevt, gslots, nslot, mask, cst, out, stride,
+                                                                  nullptr, tev, sm, skip); mg::note_launch(); }
   return cudaGetLastError();
 }
 
@@ -329,11 +329,11 @@ static cudaError_t launch_fused(const double* mom, int64_t nevt, const int* gslo
   const unsigned blocks = static_cast<unsigned>((nevt + 31) / 32);
   if (blocks == 0) return cudaSuccess;
   if (jout)
-    st::k_me_fused<K, T, true><<<blocks, kMeThreads, 0, stream>>>(mom, nevt, gslots, nslot, mask, cst, out, stride, jout,
-                                                                  skip);
+    { st::k_me_fused<K, T, true><<<blocks, kMeThreads, 0, stream>>>(mom, nevt, gslots, nslot, mask, cst, out, stride, jout,
+                                                                  skip); mg::note_launch(); }
   else
-    st::k_me_fused<K, T, false><<<blocks, kMeThreads, 0, stream>>>(mom, nevt, gslots, nslot, mask, cst, out, stride,
-                                                                   nullptr, skip);
+    { st::k_me_fused<K, T, false><<<blocks, kMeThreads, 0, stream>>>(mom, nevt, gslots, nslot, mask, cst, out, stride,
+                                                                   nullptr, skip); mg::note_launch(); }
   return cudaGetLastError();
 }
 

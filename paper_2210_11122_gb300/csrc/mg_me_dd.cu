@@ -19,9 +19,9 @@ static cudaError_t launch_dd(const double* mom, int64_t nevt, const Tables* tab,
   const int tsl = kMeThreads / tev;
   const unsigned nev_t = static_cast<unsigned>((nevt + tev - 1) / tev), nsl_t = static_cast<unsigned>((maxslot + tsl - 1) / tsl);
   if (nev_t == 0 || nsl_t == 0) return cudaSuccess;
-  v2::k_me_gluonhel<K, dd::df, false, false, false><<<dim3(nev_t, nsl_t), kMeThreads, 0, st>>>(
+  { v2::k_me_gluonhel<K, dd::df, false, false, false><<<dim3(nev_t, nsl_t), kMeThreads, 0, st>>>(
       mom, nullptr, nevt, tab, gslots, nslot, mask, ctri32, cst, out, stride, nullptr, tev, 0, evlist, nlist, rows_out,
-      nullptr);
+      nullptr); mg::note_launch(); }
   return cudaGetLastError();
 }
 

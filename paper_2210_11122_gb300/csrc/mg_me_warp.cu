@@ -431,14 +431,14 @@ static cudaError_t launch_k(const void* rec, int64_t nevt, const Tables* tab, co
     configured = true;
   }
   if (epi == kJamps)
-    k_me_warp<K, kJamps><<<grid, kWarps * 32, smem, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, c16, cst, out,
-                                                          stride, jout, skip);
+    { k_me_warp<K, kJamps><<<grid, kWarps * 32, smem, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, c16, cst, out,
+                                                          stride, jout, skip); mg::note_launch(); }
   else if (epi == kMma)
-    k_me_warp<K, kMma><<<grid, kWarps * 32, smem, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, c16, cst, out, stride,
-                                                        nullptr, skip);
+    { k_me_warp<K, kMma><<<grid, kWarps * 32, smem, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, c16, cst, out, stride,
+                                                        nullptr, skip); mg::note_launch(); }
   else
-    k_me_warp<K, kSimt><<<grid, kWarps * 32, smem, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, c16, cst, out,
-                                                         stride, nullptr, skip);
+    { k_me_warp<K, kSimt><<<grid, kWarps * 32, smem, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, c16, cst, out,
+                                                         stride, nullptr, skip); mg::note_launch(); }
   return cudaGetLastError();
 }
 

@@ -136,7 +136,7 @@ cudaError_t launch_philox(uint64_t seed, int64_t nevt, int nfinal, uint32_t* wor
   const int64_t n = nevt * nfinal;
   const int threads = 256;
   const int64_t blocks = (n + threads - 1) / threads;
-  if (blocks > 0) k_philox<<<static_cast<unsigned>(blocks), threads, 0, st>>>(seed, nevt, nfinal, words);
+  if (blocks > 0) { k_philox<<<static_cast<unsigned>(blocks), threads, 0, st>>>(seed, nevt, nfinal, words); mg::note_launch(); }
   return cudaGetLastError();
 }
 
@@ -146,10 +146,10 @@ cudaError_t launch_rambo(int K, uint64_t seed, int64_t e0, int64_t nevt, double 
   const unsigned blocks = static_cast<unsigned>((nevt + threads - 1) / threads);
   if (blocks == 0) return cudaSuccess;
   switch (K) {
-    case 2: k_rambo<2><<<blocks, threads, 0, st>>>(seed, e0, nevt, sqrts, mt, w0, mom, wgt, nbad); break;
-    case 3: k_rambo<3><<<blocks, threads, 0, st>>>(seed, e0, nevt, sqrts, mt, w0, mom, wgt, nbad); break;
-    case 4: k_rambo<4><<<blocks, threads, 0, st>>>(seed, e0, nevt, sqrts, mt, w0, mom, wgt, nbad); break;
-    case 5: k_rambo<5><<<blocks, threads, 0, st>>>(seed, e0, nevt, sqrts, mt, w0, mom, wgt, nbad); break;
+    case 2: { k_rambo<2><<<blocks, threads, 0, st>>>(seed, e0, nevt, sqrts, mt, w0, mom, wgt, nbad); mg::note_launch(); } break;
+    case 3: { k_rambo<3><<<blocks, threads, 0, st>>>(seed, e0, nevt, sqrts, mt, w0, mom, wgt, nbad); mg::note_launch(); } break;
+    case 4: { k_rambo<4><<<blocks, threads, 0, st>>>(seed, e0, nevt, sqrts, mt, w0, mom, wgt, nbad); mg::note_launch(); } break;
+    case 5: { k_rambo<5><<<blocks, threads, 0, st>>>(seed, e0, nevt, sqrts, mt, w0, mom, wgt, nbad); mg::note_launch(); } break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -103,6 +103,16 @@ def test_flop_model(mg):
         a32, c32 = mg.flops_per_event(proc, None, mg.MG_FP32_AMP)
         assert c32 == col and a32 != amp
         assert mg.flops_per_event(proc, None, mg.MG_MIXED) == (a32, c32)
+        # FP64 amplitudes with the currents shared between gluon-helicity combinations: fewer flops with
+        # every helicity good from 1 final-state gluon on, the same colour sums; the default for
+        # gg->ttg and gg->ttggg; no effect on the FP32-amplitude modes
+        sh = mg.flops_per_event(proc, None, mg.MG_FP64, mg.LAUNCH_SHARED)
+        plain = mg.flops_per_event(proc, None, mg.MG_FP64, 0)
+        assert sh[1] == plain[1] == col
+        if proc != "ggtt":
+            assert sh[0] < plain[0]
+        assert (amp, col) == (sh if proc in ("ggttg", "ggttggg") else plain)
+        assert mg.flops_per_event(proc, None, mg.MG_FP32_AMP, mg.LAUNCH_SHARED) == (a32, c32)
     with pytest.raises(mg.MGError):
         mg.flops_per_event("ggttg", None, 7)
 

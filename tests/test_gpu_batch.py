@@ -121,3 +121,26 @@ def test_graph_batch_fp32_modes(env, precision):
     g.close()
     for c in ctxs.values():
         c.close()
+
+
+def test_kernel_launch_counter(env):
+    # mg_kernel_launches brackets the kernels of the calls between two reads: an FP64 gg->ttg call is
+    # the per-event record, the matrix elements and the helicity sum, plus one pass per sequence length
+    # (1 and 2 gluons) with the shared currents
+    torch, mg = env
+    n = 4096
+    with mg.Context("ggttg") as ctx:
+        mom = torch.zeros(ctx.mom_count(n), dtype=torch.float64, device="cuda")
+        me = torch.zeros(n, dtype=torch.float64, device="cuda")
+        c0 = mg.kernel_launches()
+        ctx.rambo(2, n, SQRTS, mom)
+        assert mg.kernel_launches() > c0
+        ctx.hel_filter(mom, 1024)
+        counts = {}
+        for flags in (mg.LAUNCH_UNROLLED | mg.LAUNCH_FUSED | mg.LAUNCH_SHARED, mg.LAUNCH_UNROLLED | mg.LAUNCH_FUSED):
+            ctx.set_launch_shape(mg.MG_FP64, 128, 0, flags)
+            c0 = mg.kernel_launches()
+            ctx.sigmakin(mom, n, me, mg.MG_FP64)
+            counts[flags] = mg.kernel_launches() - c0
+        torch.cuda.synchronize()
+    assert list(counts.values()) == [5, 3]
