@@ -133,6 +133,13 @@ static cudaError_t launch_v2(const double* mom, void* prep, int64_t nevt, const 
       { v2::k_me_gluonhel<K, T, false, true, false><<<grid, kMeThreads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot,
                                                                               mask, ctri, cst, out, stride, nullptr, tev,
                                                                               sm, nullptr, nullptr, 0, skip); mg::note_launch(); }
+  } else if (PER_HEL) {
+    // the helicity filter: a few thousand threads, so blocks of one warp (32 events of one slot) spread
+    // them evenly over every SM; 128-thread blocks left a third of the SMs with twice the work
+    const dim3 g1(static_cast<unsigned>((nevt + 31) / 32), static_cast<unsigned>(maxslot));
+    { v2::k_me_gluonhel<K, T, PER_HEL, false, false><<<g1, 32, 0, st>>>(mom, nullptr, nevt, tab, gslots, nslot, mask,
+                                                                       ctri, cst, out, stride, nullptr, 32, 0, evlist,
+                                                                       nlist, rows_out, nullptr); mg::note_launch(); }
   } else {
     { v2::k_me_gluonhel<K, T, PER_HEL, false, false><<<grid, kMeThreads, 0, st>>>(mom, nullptr, nevt, tab, gslots, nslot,
                                                                                  mask, ctri, cst, out, stride, nullptr,

@@ -32,7 +32,7 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
   constexpr int NCOL = Sizes<K>::ncol;
   constexpr int NFULL = Sizes<K>::nfull;
   constexpr int NSUB = 1 << K;
-  const int tile_sl = kMeThreads / tile_ev;
+  const int tile_sl = static_cast<int>(blockDim.x) / tile_ev;   // slots per block
   const unsigned bev = slot_major ? blockIdx.y : blockIdx.x, bsl = slot_major ? blockIdx.x : blockIdx.y;
   const int64_t et = static_cast<int64_t>(bev) * tile_ev + threadIdx.x % tile_ev;
   const int slot = static_cast<int>(bsl) * tile_sl + static_cast<int>(threadIdx.x) / tile_ev;

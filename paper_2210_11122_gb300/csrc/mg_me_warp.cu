@@ -319,6 +319,94 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
       if (good[h]) total += static_cast<double>(s) * cst.colour_scale;
     }
     if (lane == 0) out[slot * stride + e] = total;
+  } else if constexpr (GPW == 1) {
+    // colour sums on the tensor cores, one slot per warp (5 gluons): Y = C a for the slot's 8 vectors
+    // a_n (helicity n/2, real part for even n, imaginary for odd) as D = C B, MMA rows = colour index x
+    // (row-major A = C, exact FP16 integers), columns = the 8 vectors, k = colour index y, so every row
+    // and column of every MMA is used.  Each vector is scaled by a power of two and split hi + lo 2^-11
+    // in FP16 (B fragments, built once); FP32 accumulation; the quadratic form a_n . Y_n takes the FP32
+    // jamps themselves.
+    __syncwarp();
+    if (!active) return;
+    constexpr int KP = (NCOL + 15) / 16 * 16, KS = KP / 16, MT = KP / 16, LDH = KP + 8;
+    static_assert(MT % 2 == 0, "row tiles in pairs");
+    const int lw = threadIdx.x & 31, gq = lw >> 2, q = lw & 3;
+    // B fragments of vector n = gq: k = 16 ks + 2q (+1) and + 8 (+9)
+    const float2* av = S.A[gq >> 1];
+    const bool im = gq & 1;
+    auto comp = [&](int y) -> float {
+      if (y >= NCOL) return 0.f;
+      const float2 v = av[y];
+      return im ? v.y : v.x;
+    };
+    float mx = 0.f;
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) mx = fmaxf(mx, fabsf(comp(ks * 16 + 2 * q + (j & 1) + (j >> 1) * 8)));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 1));
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, 2));
+    int ex = 0;
+    if (mx > 0.f) frexpf(mx, &ex);
+    const float sc = ldexpf(1.f, -ex);
+    uint32_t bh[KS][2], bl[KS][2];
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int y = ks * 16 + 2 * q + 8 * half;
+        const float x0 = comp(y) * sc, x1 = comp(y + 1) * sc;
+        const __half h0 = __float2half_rn(x0), h1 = __float2half_rn(x1);
+        const __half l0 = __float2half_rn((x0 - __half2float(h0)) * 2048.f);
+        const __half l1 = __float2half_rn((x1 - __half2float(h1)) * 2048.f);
+        bh[ks][half] = pack_h2(h0, h1);
+        bl[ks][half] = pack_h2(l0, l1);
+      }
+    // this thread's D columns are vectors 2q (real part) and 2q + 1 (imaginary part) of helicity q, at
+    // rows x = 16 mt + gq and + 8
+    const float2* aq = S.A[q];
+    float sr = 0.f, si = 0.f;
+    const unsigned int* cw = reinterpret_cast<const unsigned int*>(cmat16);
+#pragma unroll
+    for (int mt = 0; mt < MT; mt += 2) {
+      float dh[2][4] = {}, dl[2][4] = {};
+#pragma unroll
+      for (int ks = 0; ks < KS; ++ks)
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int x0 = (mt + u) * 16 + gq, y0 = ks * 16 + 2 * q;
+          uint32_t af[4];
+          af[0] = x0 < NCOL ? __ldg(cw + (x0 * LDH + y0) / 2) : 0u;
+          af[1] = x0 + 8 < NCOL ? __ldg(cw + ((x0 + 8) * LDH + y0) / 2) : 0u;
+          af[2] = x0 < NCOL ? __ldg(cw + (x0 * LDH + y0 + 8) / 2) : 0u;
+          af[3] = x0 + 8 < NCOL ? __ldg(cw + ((x0 + 8) * LDH + y0 + 8) / 2) : 0u;
+          mma16816(dh[u], af, bh[ks]);
+          mma16816(dl[u], af, bl[ks]);
+        }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int x = (mt + u) * 16 + gq + 8 * r;
+          if (x < NCOL) {
+            const float2 a = aq[x];
+            sr = fmaf(a.x, fmaf(dl[u][2 * r], 1.f / 2048.f, dh[u][2 * r]), sr);
+            si = fmaf(a.y, fmaf(dl[u][2 * r + 1], 1.f / 2048.f, dh[u][2 * r + 1]), si);
+          }
+        }
+    }
+    // sum over the rows (lanes with the same q), undo the vector scales (exact powers of two: the
+    // exponent of vector n sits in lanes 4n .. 4n + 3), then sum the four helicities
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      si += __shfl_xor_sync(0xffffffffu, si, o);
+    }
+    const int exr = __shfl_sync(0xffffffffu, ex, 8 * q), exi = __shfl_sync(0xffffffffu, ex, 8 * q + 4);
+    double v = static_cast<double>(sr) * pow2d(exr) + static_cast<double>(si) * pow2d(exi);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    if (lw == 0) out[slot * stride + e] = v * cst.colour_scale;
   } else {
     // colour sums on the tensor cores, the warp's slots together: MMA rows = (slot, helicity, Re/Im),
     // 8 per slot; each row scaled by a power of two and split hi + lo 2^-11 in FP16 against the exact
