@@ -240,8 +240,8 @@ mg_status mg_autotune(mg_ctx* ctx, mg_precision precision, int64_t nevt, const c
 
 /* The launch shape mg_sigmakin(precision) uses on this context (default: 128 events per block,
  * event-tile-major, flags MG_LAUNCH_UNROLLED | MG_LAUNCH_DF_REDO | MG_LAUNCH_FUSED, plus MG_LAUNCH_SHARED
- * for gg -> t tbar g and t tbar g g g and MG_LAUNCH_WARP for t tbar g g and t tbar g g g).  Any
- * out-pointer may be NULL. */
+ * for gg -> t tbar g and t tbar g g g, MG_LAUNCH_WARP for t tbar g g and t tbar g g g, and
+ * MG_LAUNCH_TC_APART for t tbar g g g).  Any out-pointer may be NULL. */
 mg_status mg_get_launch_shape(mg_ctx* ctx, mg_precision precision, int* tile_ev, int* slot_major, int* flags);
 
 /* Set the launch shape of mg_sigmakin(precision) by hand: tile_ev in {32, 64, 128}, slot_major 0 or 1,

@@ -395,6 +395,9 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
     // state does not fit on chip); the autotuner can change it
     if (c->K >= 4)
       for (int p = 0; p < 4; ++p) c->shape[p].warp = true;
+    // five gluons, FP32 amplitudes + tensor-core colour: the separate colour pass (measured 2 % faster
+    // than the in-kernel one there); the autotuner can change it
+    if (c->K == 5) c->shape[MG_MIXED].tc_apart = true;
     // FP64 amplitudes: share the currents of fewer than all gluons between gluon-helicity combinations
     // where that was measured faster (1 and 3 final-state gluons); the autotuner can change it
     for (int p = 0; p < 4; ++p) c->shape[p].shared = c->K == 3 || c->K == 5;

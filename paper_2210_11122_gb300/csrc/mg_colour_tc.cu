@@ -13,7 +13,9 @@
 //     the current one, whose A fragments are built once in registers for all column tiles.
 // Relative error per (event, helicity) ~1e-7 (the colour matrices are well conditioned: kappa <= 16).
 // Rows: jamps[(e * rows_alloc + r) * ncol + sigma] (FP32 complex), r < *nrows_dev; output:
-// out[r * stride + e] = colour sum * scale, in FP64.
+// out[r * stride + e] = colour sum * scale, in FP64.  rows_alloc is a power of two (the helicity count),
+// so the kernel walks the padded row index q = e * rows_alloc + r with shifts and masks: a tile of 8
+// consecutive q is 8 rows of one event, and rows r >= *nrows_dev are zero-filled, never read.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -79,7 +81,7 @@ __device__ __forceinline__ float unsplit(uint32_t h, uint32_t l, int k) {
 // current one is computed; the current tile's A fragments (hi and lo) are built once, in registers, and
 // serve every column tile of Y = C a and the row's quadratic form a . Y.
 template <int NCOL>
-__global__ void __launch_bounds__(128) k_colour_tc(const float2* __restrict__ jamps, int64_t nevt, int rows_alloc,
+__global__ void __launch_bounds__(128) k_colour_tc(const float2* __restrict__ jamps, int64_t nevt, int rows_log2,
                                                    const int* __restrict__ nrows_dev, const __half* __restrict__ cmat,
                                                    double scale, double* __restrict__ out, int64_t stride,
                                                    const uint8_t* __restrict__ skip) {
@@ -94,8 +96,8 @@ __global__ void __launch_bounds__(128) k_colour_tc(const float2* __restrict__ ja
   __syncthreads();
 
   const int nrows = *nrows_dev;
-  const int64_t npairs = nevt * nrows;
-  const int64_t ntiles = (npairs + 7) / 8;
+  const int64_t rmask = (int64_t(1) << rows_log2) - 1;
+  const int64_t ntiles = ((nevt << rows_log2) + 7) / 8;
   const int64_t tstep = static_cast<int64_t>(gridDim.x) * S::WARPS;
   const int g = lane >> 2, q = lane & 3;
 
@@ -106,11 +108,11 @@ __global__ void __launch_bounds__(128) k_colour_tc(const float2* __restrict__ ja
       const int64_t qq = tile * 8 + p;
       const float2* src = jamps;
       bool valid = false;
-      if (tile < ntiles && qq < npairs) {
-        const int64_t e = qq / nrows;
-        const int r = static_cast<int>(qq - e * nrows);
-        valid = !skip || !skip[e];   // skipped events: no jamps (zeros)
-        src = jamps + (e * rows_alloc + r) * NCOL + 2 * w;
+      if (tile < ntiles) {
+        const int64_t e = qq >> rows_log2;
+        // rows past the last good one, and skipped events: no jamps (zeros)
+        valid = (qq & rmask) < nrows && (!skip || !skip[e]);
+        src = jamps + qq * NCOL + 2 * w;
       }
       cp_async16(dst + p * NCOL + 2 * w, src, valid);
     }
@@ -212,13 +214,10 @@ __global__ void __launch_bounds__(128) k_colour_tc(const float2* __restrict__ ja
     const double w1 = v1d + __shfl_xor_sync(0xffffffffu, v1d, 4);
     if (q == 0 && (g & 1) == 0) {
       const int64_t qa = tile * 8 + g / 2, qb = tile * 8 + 4 + g / 2;
-      if (qa < npairs) {
-        const int64_t e = qa / nrows;
-        if (!skip || !skip[e]) out[(qa - e * nrows) * stride + e] = w0 * scale;
-      }
-      if (qb < npairs) {
-        const int64_t e = qb / nrows;
-        if (!skip || !skip[e]) out[(qb - e * nrows) * stride + e] = w1 * scale;
+      const int64_t e = qa >> rows_log2;   // the tile's 8 rows belong to one event
+      if (!skip || !skip[e]) {
+        if ((qa & rmask) < nrows) out[(qa & rmask) * stride + e] = w0 * scale;
+        if ((qb & rmask) < nrows) out[(qb & rmask) * stride + e] = w1 * scale;
       }
     }
   }
@@ -229,6 +228,9 @@ template <int NCOL>
 cudaError_t launch_tc(const float2* jamps, int64_t nevt, int rows_alloc, const int* nrows, const __half* cmat,
                       double scale, double* out, int64_t stride, const uint8_t* skip, cudaStream_t st) {
   using S = TcShape<NCOL>;
+  int rows_log2 = 0;   // rows_alloc: a power of two, at least one tile (8 rows)
+  while ((1 << rows_log2) < rows_alloc) ++rows_log2;
+  if ((1 << rows_log2) != rows_alloc || rows_alloc < 8) return cudaErrorInvalidValue;
   const size_t smem = S::smem_bytes();
   static bool configured = false;
   if (!configured) {
@@ -246,7 +248,7 @@ cudaError_t launch_tc(const float2* jamps, int64_t nevt, int rows_alloc, const i
   const int64_t cap = static_cast<int64_t>(nsm) * per_sm;   // resident blocks; tiles are strided over them
   if (blocks > cap) blocks = cap;
   if (blocks < 1) return cudaSuccess;
-  { k_colour_tc<NCOL><<<static_cast<unsigned>(blocks), 128, smem, st>>>(jamps, nevt, rows_alloc, nrows, cmat, scale, out,
+  { k_colour_tc<NCOL><<<static_cast<unsigned>(blocks), 128, smem, st>>>(jamps, nevt, rows_log2, nrows, cmat, scale, out,
                                                                        stride, skip); mg::note_launch(); }
   return cudaGetLastError();
 }
