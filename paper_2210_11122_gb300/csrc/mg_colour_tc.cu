@@ -25,9 +25,36 @@
 namespace mg {
 namespace {
 
-// 2^k as a double, built from its exponent bits (exact; |k| < 1000): undoes a power-of-two row scale
-// with one multiplication instead of an FP64 division
-__device__ __forceinline__ double pow2d(int k) { return __longlong_as_double(static_cast<long long>(1023 + k) << 52); }
+// 2^k as a float from its exponent bits (exact), 0 below the normal range; k <= 0 here
+__device__ __forceinline__ float pow2f_neg(int k) {
+  return k >= -126 ? __uint_as_float(static_cast<unsigned>(127 + k) << 23) : 0.f;
+}
+
+// s 2^E as a double, built from the IEEE 754 fields of the float s (exact: the mantissa is copied and
+// the exponent moved).  No FP64 instruction for normal s: the FP64 pipe is 1/64 of the FP32 one, and
+// this kernel's epilogue would otherwise spend most of its time there.  Zero and FP32 subnormals (never
+// seen for these colour sums) take the FP64 route.
+__device__ __forceinline__ double f32_times_pow2(float s, int E) {
+  const unsigned u = __float_as_uint(s);
+  const unsigned ef = (u >> 23) & 0xffu;
+  if ((u & 0x7fffffffu) == 0) return 0.0;   // E may be a placeholder here
+  if (ef == 0) return static_cast<double>(s) * __longlong_as_double(static_cast<long long>(1023 + E) << 52);
+  const unsigned long long bits = (static_cast<unsigned long long>(u >> 31) << 63) |
+                                  (static_cast<unsigned long long>(static_cast<int>(ef) - 127 + E + 1023) << 52) |
+                                  (static_cast<unsigned long long>(u & 0x7fffffu) << 29);
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
+// (a 2^ea + b 2^eb) scale: the colour sums of a vector's real and imaginary rows, each under its own
+// power-of-two row scale; summed in FP32 at the larger exponent of the nonzero rows (C is positive
+// definite, so a row's sum is 0 only for a zero row, whose exponent means nothing), then widened exactly
+__device__ __forceinline__ double combine_rows(float a, int ea, float b, int eb, float scale) {
+  if (a == 0.f) return f32_times_pow2(b * scale, eb);
+  if (b == 0.f) return f32_times_pow2(a * scale, ea);
+  const int E = ea > eb ? ea : eb;
+  const float t = fmaf(a, pow2f_neg(ea - E), b * pow2f_neg(eb - E)) * scale;
+  return f32_times_pow2(t, E);
+}
 
 __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, const uint32_t* b) {
   asm volatile(
@@ -95,6 +122,7 @@ __global__ void __launch_bounds__(128) k_colour_tc(const float2* __restrict__ ja
   for (int i = threadIdx.x; i < NP * LDH; i += blockDim.x) sC[i] = cmat[i];
   __syncthreads();
 
+  const float scale_f = static_cast<float>(scale);
   const int nrows = *nrows_dev;
   const int64_t rmask = (int64_t(1) << rows_log2) - 1;
   const int64_t ntiles = ((nevt << rows_log2) + 7) / 8;
@@ -206,18 +234,16 @@ __global__ void __launch_bounds__(128) k_colour_tc(const float2* __restrict__ ja
     s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
     s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
     s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
-    // undo the row scales (exact powers of two)
-    const double v0d = static_cast<double>(s0) * pow2d(2 * ex0);
-    const double v1d = static_cast<double>(s1) * pow2d(2 * ex1);
-    // the real and imaginary rows of a vector sit in quads g and g^1 (lanes 4 apart)
-    const double w0 = v0d + __shfl_xor_sync(0xffffffffu, v0d, 4);
-    const double w1 = v1d + __shfl_xor_sync(0xffffffffu, v1d, 4);
+    // the real and imaginary rows of a vector sit in quads g and g^1 (lanes 4 apart): their sums and
+    // row exponents, combined in the writing lanes
+    const float t0 = __shfl_xor_sync(0xffffffffu, s0, 4), t1 = __shfl_xor_sync(0xffffffffu, s1, 4);
+    const int f0 = __shfl_xor_sync(0xffffffffu, ex0, 4), f1 = __shfl_xor_sync(0xffffffffu, ex1, 4);
     if (q == 0 && (g & 1) == 0) {
       const int64_t qa = tile * 8 + g / 2, qb = tile * 8 + 4 + g / 2;
       const int64_t e = qa >> rows_log2;   // the tile's 8 rows belong to one event
       if (!skip || !skip[e]) {
-        if ((qa & rmask) < nrows) out[(qa & rmask) * stride + e] = w0 * scale;
-        if ((qb & rmask) < nrows) out[(qb & rmask) * stride + e] = w1 * scale;
+        if ((qa & rmask) < nrows) out[(qa & rmask) * stride + e] = combine_rows(s0, 2 * ex0, t0, 2 * f0, scale_f);
+        if ((qb & rmask) < nrows) out[(qb & rmask) * stride + e] = combine_rows(s1, 2 * ex1, t1, 2 * f1, scale_f);
       }
     }
   }

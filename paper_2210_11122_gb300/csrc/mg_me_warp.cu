@@ -63,6 +63,25 @@ enum Epi { kSimt = 0, kJamps = 1, kMma = 2 };
 // with one multiplication instead of an FP64 division
 __device__ __forceinline__ double pow2d(int k) { return __longlong_as_double(static_cast<long long>(1023 + k) << 52); }
 
+// 2^k as a float from its exponent bits (exact), 0 below the normal range; k <= 0 here
+__device__ __forceinline__ float pow2f_neg(int k) {
+  return k >= -126 ? __uint_as_float(static_cast<unsigned>(127 + k) << 23) : 0.f;
+}
+
+// s 2^E as a double, built from the IEEE 754 fields of the float s (exact: the mantissa is copied and
+// the exponent moved), without an FP64 instruction for normal s; zero and FP32 subnormals take the
+// FP64 route
+__device__ __forceinline__ double f32_times_pow2(float s, int E) {
+  const unsigned u = __float_as_uint(s);
+  const unsigned ef = (u >> 23) & 0xffu;
+  if ((u & 0x7fffffffu) == 0) return 0.0;   // E may be a placeholder here
+  if (ef == 0) return static_cast<double>(s) * pow2d(E);
+  const unsigned long long bits = (static_cast<unsigned long long>(u >> 31) << 63) |
+                                  (static_cast<unsigned long long>(static_cast<int>(ef) - 127 + E + 1023) << 52) |
+                                  (static_cast<unsigned long long>(u & 0x7fffffu) << 29);
+  return __longlong_as_double(static_cast<long long>(bits));
+}
+
 __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, const uint32_t* b) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -301,7 +320,7 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
         }
       }
     }
-    double total = 0.0;
+    float total = 0.f;   // summed in FP32 (these are FP32 colour sums), widened exactly at the end
 #pragma unroll
     for (int h = 0; h < 4; ++h) {   // jamps of helicities outside the mask are zero: no branch needed
       float s = 0.f;
@@ -316,9 +335,9 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
       }
 #pragma unroll
       for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, G);
-      if (good[h]) total += static_cast<double>(s) * cst.colour_scale;
+      if (good[h]) total += s;
     }
-    if (lane == 0) out[slot * stride + e] = total;
+    if (lane == 0) out[slot * stride + e] = f32_times_pow2(total * static_cast<float>(cst.colour_scale), 0);
   } else if constexpr (GPW == 1) {
     // colour sums on the tensor cores, one slot per warp (5 gluons): Y = C a for the slot's 8 vectors
     // a_n (helicity n/2, real part for even n, imaginary for odd) as D = C B, MMA rows = colour index x
@@ -481,18 +500,28 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
       s0 += __shfl_xor_sync(0xffffffffu, s0, 2);
       s1 += __shfl_xor_sync(0xffffffffu, s1, 1);
       s1 += __shfl_xor_sync(0xffffffffu, s1, 2);
-      // unscale (exact powers of two), then sum the 8 rows of a slot: rows gq = 0..7 sit in lanes 4 gq
-      double v0 = static_cast<double>(s0) * pow2d(2 * ex0);
-      double v1 = static_cast<double>(s1) * pow2d(2 * ex1);
+      // sum the 8 rows of a slot (rows gq = 0..7 sit in lanes 4 gq) in FP32 at the largest exponent of
+      // its nonzero rows (C is positive definite: a row's sum is 0 only for a zero row), then widen
+      // exactly to FP64 (no FP64 instruction: that pipe runs at 1/64 of the FP32 rate)
+      constexpr int kNone = -100000;
+      int E0 = s0 != 0.f ? 2 * ex0 : kNone, E1 = s1 != 0.f ? 2 * ex1 : kNone;
 #pragma unroll
       for (int o = 4; o < 32; o <<= 1) {
-        v0 += __shfl_xor_sync(0xffffffffu, v0, o);
-        v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+        E0 = max(E0, __shfl_xor_sync(0xffffffffu, E0, o));
+        E1 = max(E1, __shfl_xor_sync(0xffffffffu, E1, o));
+      }
+      float u0 = s0 != 0.f ? s0 * pow2f_neg(2 * ex0 - E0) : 0.f;
+      float u1 = s1 != 0.f ? s1 * pow2f_neg(2 * ex1 - E1) : 0.f;
+#pragma unroll
+      for (int o = 4; o < 32; o <<= 1) {
+        u0 += __shfl_xor_sync(0xffffffffu, u0, o);
+        u1 += __shfl_xor_sync(0xffffffffu, u1, o);
       }
       if (lw == 0) {
+        const float csf = static_cast<float>(cst.colour_scale);
         const int sa = 2 * t, sb = 2 * t + 1;   // the slots of rows 0-7 and 8-15 of this tile
-        if (sa < GPW && slot0 + sa < nslot) out[(slot0 + sa) * stride + e] = v0 * cst.colour_scale;
-        if (sb < GPW && slot0 + sb < nslot) out[(slot0 + sb) * stride + e] = v1 * cst.colour_scale;
+        if (sa < GPW && slot0 + sa < nslot) out[(slot0 + sa) * stride + e] = f32_times_pow2(u0 * csf, E0);
+        if (sb < GPW && slot0 + sb < nslot) out[(slot0 + sb) * stride + e] = f32_times_pow2(u1 * csf, E1);
       }
     }
   }
