@@ -16,6 +16,8 @@
 // out[r * stride + e] = colour sum * scale, in FP64.  rows_alloc is a power of two (the helicity count),
 // so the kernel walks the padded row index q = e * rows_alloc + r with shifts and masks: a tile of 8
 // consecutive q is 8 rows of one event, and rows r >= *nrows_dev are zero-filled, never read.
+#include <atomic>
+
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -258,14 +260,16 @@ cudaError_t launch_tc(const float2* jamps, int64_t nevt, int rows_alloc, const i
   while ((1 << rows_log2) < rows_alloc) ++rows_log2;
   if ((1 << rows_log2) != rows_alloc || rows_alloc < 8) return cudaErrorInvalidValue;
   const size_t smem = S::smem_bytes();
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(k_colour_tc<NCOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
   int dev = 0, nsm = 0, per_sm = 0;
   cudaGetDevice(&dev);
+  // the shared-memory opt-in, once per device (a bit per device; racing first calls both set it)
+  static std::atomic<unsigned long long> configured{0};
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(configured.load(std::memory_order_acquire) & bit)) {
+    cudaError_t e = cudaFuncSetAttribute(k_colour_tc<NCOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    configured.fetch_or(bit, std::memory_order_release);
+  }
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_colour_tc<NCOL>, 128, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;

@@ -13,6 +13,8 @@
 //   * the colour sums of the four helicities together: rows of C A per lane (register-blocked over
 //     rows and helicities), then sums over the group; or (jamp output) the jamps are written out for
 //     the tensor-core colour sum.
+#include <atomic>
+
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -539,13 +541,18 @@ static cudaError_t launch_k(const void* rec, int64_t nevt, const Tables* tab, co
   const float* r = static_cast<const float*>(rec);
   const __half* c16 = static_cast<const __half*>(cmat16);
   constexpr size_t smem = SmemLayout<K>::bytes;
-  static bool configured = false;   // opt in to more than 48 KB of dynamic shared memory, once
-  if (!configured) {
+  // opt in to more than 48 KB of dynamic shared memory, once per device (a bit per device; racing
+  // first calls both set it)
+  static std::atomic<unsigned long long> configured{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(configured.load(std::memory_order_acquire) & bit)) {
     cudaError_t e = cudaFuncSetAttribute(k_me_warp<K, kJamps>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_me_warp<K, kMma>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_me_warp<K, kSimt>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     if (e != cudaSuccess) return e;
-    configured = true;
+    configured.fetch_or(bit, std::memory_order_release);
   }
   if (epi == kJamps)
     { k_me_warp<K, kJamps><<<grid, kWarps * 32, smem, st>>>(r, nevt, tab, gslots, nslot, mask, cfull, c16, cst, out,
