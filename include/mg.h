@@ -53,7 +53,7 @@ typedef enum {
   MG_EAGAIN = 5,   /* not ready yet (serving) */
   MG_ETIMEOUT = 6, /* a bounded wait expired */
   MG_EBUSY = 7,    /* resource busy (serving admission) */
-  MG_ENOTSUP = 8   /* valid request that this build does not implement */
+  MG_ENOTSUP = 8   /* valid request that this library does not implement */
 } mg_status;
 
 typedef enum { MG_GG_TT = 0, MG_GG_TTG = 1, MG_GG_TTGG = 2, MG_GG_TTGGG = 3 } mg_process;
