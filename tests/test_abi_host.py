@@ -125,6 +125,11 @@ def test_invalid_arguments_rejected_without_gpu(mg):
     assert L.mg_philox(1, -1, 2, None, None) == 1
     assert L.mg_create(9, None, ctypes.byref(ctypes.c_void_p())) == 1
     assert L.mg_create(0, None, None) == 1
+    # rejected calls launch nothing: the process-wide launch count does not move
+    n0 = mg.kernel_launches()
+    assert L.mg_sigmakin(None, None, 10, 0, None, None) == 1
+    assert L.mg_philox(1, -1, 2, None, None) == 1
+    assert mg.kernel_launches() == n0 >= 0
 
 
 def test_serve_footprint_host(mg):
