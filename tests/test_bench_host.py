@@ -1,0 +1,28 @@
+"""bench.py's host-side measurement logic, without a GPU: the DRAM traffic read from a committed ncu
+summary only while the kernel sources hash to the captured ones, scaled by the events of a launch;
+the workload table and the per-rank bookkeeping."""
+import hashlib
+
+import bench
+
+def _write(path, text):
+    with open(path, "w") as f:
+        f.write(text)
+
+
+def test_profiled_traffic_follows_the_source_hash(tmp_path):
+    src = tmp_path / "k.cuh"
+    _write(src, "kernel v1\n")
+    sha = hashlib.sha256(b"kernel v1\n").hexdigest()[:16]
+    md = tmp_path / "p.md"
+    _write(md, "# k\n\nsource_sha256_16: %s   (k.cuh)\ntraffic_bytes_per_event: 1000  (per event)\n" % sha)
+    assert bench.profiled_traffic([str(src)], str(md), 524288) == 1000.0 * 524288
+    _write(src, "kernel v2\n")   # the kernel changed since the capture: no traffic figure
+    assert bench.profiled_traffic([str(src)], str(md), 524288) is None
+    assert bench.profiled_traffic([str(src)], str(tmp_path / "missing.md"), 1) is None
+
+
+def test_workloads_and_rank_bookkeeping():
+    assert {w["nevt"] for w in bench.WORKLOADS.values()} == {16384, 524288, 262144, 65536}
+    assert bench.rank_first_event(3, 1000) == 3000
+    assert bench.aggregate_rate(2, 1000, 10.0) == 2000 / 10e-3
