@@ -5,6 +5,7 @@ import hashlib
 
 import bench
 
+
 def _write(path, text):
     with open(path, "w") as f:
         f.write(text)
