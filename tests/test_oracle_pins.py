@@ -177,6 +177,59 @@ def test_full_colour_brute_force(orc, ng, nev, hels):
                 assert abs(mh[h] / ref - 1) < 1e-11
 
 
+def _mdot(a, b):
+    return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3]
+
+
+@pytest.mark.parametrize("ng", [0, 1, 2, 3])
+def test_massless_colour_ordered_amplitudes_parke_taylor(orc, ng):
+    """Massless limit (m_t = 0) against the Parke-Taylor closed form (Phys. Rev. Lett. 56 (1986) 2459;
+    with one quark line, Mangano-Parke, Phys. Rep. 200 (1991) 301, Sec. 3), all particles outgoing
+    (incoming gluons: momentum and helicity reversed):
+      * a quark line of equal helicities, or gluons all of one helicity: every A(sigma) vanishes;
+      * exactly one gluon j of helicity -1 (or exactly one of +1): for every ordering sigma
+        |A(sigma)|^2 = (2 g^2)^K s_{a j}^3 s_{b j} / (s_{t s1} s_{s1 s2} ... s_{sK tbar} s_{tbar t}),
+        s_{xy} = |2 p_x.p_y|, (a, b) = (negative, positive) quark for the one negative gluon and
+        (positive, negative) quark for the one positive gluon; the factor 2^K is the sqrt(2) per
+        gluon of Tr(T^a T^b) = delta^ab / 2.
+    A closed form for every colour-ordered amplitude of these helicities, normalisation included."""
+    K, npar = ng + 2, ng + 4
+    g2 = 4 * math.pi * AS
+    gpart = [0, 1] + [4 + i for i in range(ng)]   # particle of gluon label 0..K-1 (order g1 g2 t tbar g3 ..)
+    perms = list(permutations(range(K)))          # jamp index = lexicographic rank of the ordering
+    mom, _, _ = orc.events(ng, 70 + ng, 2, mt=0.0)
+    checked = 0
+    for p in mom:
+        mh, J = orc.me_hel(ng, p, mt=0.0, want_jamps=True)
+        scale = np.abs(J).max()
+
+        def s(a, b):
+            return abs(2 * _mdot(p[a], p[b]))
+
+        for h in range(1 << npar):
+            lam = [1 if (h >> (npar - 1 - i)) & 1 else -1 for i in range(npar)]
+            out = [-lam[0], -lam[1]] + lam[2:]    # all outgoing
+            gl = [out[q] for q in gpart]
+            nneg = gl.count(-1)
+            if out[2] == out[3] or nneg in (0, K):
+                assert np.abs(J[h]).max() <= 1e-10 * scale
+                continue
+            if nneg != 1 and nneg != K - 1:
+                continue                          # beyond MHV: no one-line closed form
+            odd = -1 if nneg == 1 else 1
+            j = gpart[gl.index(odd)]
+            qneg = 2 if out[2] < 0 else 3
+            qpos = 5 - qneg
+            a, b = (qneg, qpos) if odd < 0 else (qpos, qneg)
+            for c, sig in enumerate(perms):
+                chain = [2] + [gpart[g] for g in sig] + [3]
+                den = np.prod([s(chain[i], chain[i + 1]) for i in range(len(chain) - 1)]) * s(3, 2)
+                want = (2 * g2) ** K * s(a, j) ** 3 * s(b, j) / den
+                assert abs(abs(J[h, c]) ** 2 / want - 1) <= 1e-10
+                checked += 1
+    assert checked >= 2 * math.factorial(K) * 2 * K   # at least the one-negative and one-positive sets
+
+
 @pytest.mark.parametrize("ng", [0, 1, 2, 3])
 def test_gauge_invariance(orc, ng):
     """epsilon_g -> k_g for any one gluon makes every colour-ordered amplitude vanish."""
