@@ -230,6 +230,77 @@ def test_massless_colour_ordered_amplitudes_parke_taylor(orc, ng):
     assert checked >= 2 * math.factorial(K) * 2 * K   # at least the one-negative and one-positive sets
 
 
+def _with_soft_gluon(p, lam, nhat):
+    """The event p plus an outgoing gluon k = lam (sqrt(s)/2) (1, nhat), momentum conserved: the beams
+    rescaled to E = k0 + sqrt(s + k0^2) and the final state boosted to total momentum (E - k0, -k)."""
+    s = _mdot(p[0] + p[1], p[0] + p[1])
+    k0 = lam * math.sqrt(s) / 2
+    k = np.array([k0, *(k0 * nhat)])
+    E = k0 + math.sqrt(s + k0 * k0)
+    beta = -k[1:] / (E - k0)
+    b2 = beta @ beta
+    g = 1 / math.sqrt(1 - b2)
+    out = np.zeros((p.shape[0] + 1, 4))
+    out[0] = [E / 2, 0, 0, E / 2]
+    out[1] = [E / 2, 0, 0, -E / 2]
+    for i in range(2, p.shape[0]):
+        bp = beta @ p[i, 1:]
+        out[i, 0] = g * (p[i, 0] + bp)
+        out[i, 1:] = p[i, 1:] + ((g - 1) * bp / b2) * beta + g * p[i, 0] * beta
+    out[-1] = k
+    return out
+
+
+@pytest.mark.parametrize("ng", [0, 1, 2])
+def test_soft_gluon_limit_of_colour_ordered_amplitudes(orc, ng):
+    """Soft-gluon theorem for colour-ordered amplitudes (e.g. Mangano-Parke, Phys. Rep. 200 (1991)
+    301, Sec. 3; Dixon, TASI'95): a gluon k inserted between colour neighbours a and b of the ordering
+    (the quark line's ends included) factorises as k -> 0,
+        sum over its helicities |A_{n+1}(.. a, k, b ..)|^2 -> g^2 (-J^2) |A_n(.. a, b ..)|^2,
+        J = p_a / (p_a.k) - p_b / (p_b.k),
+    massive tops included, for every helicity of the n other particles, every ordering and every
+    insertion.  The deviation falls linearly with the soft scale: this ties each process to the one
+    with a gluon less (gg->ttggg to gg->ttgg, which the brute-force Feynman-rule test pins)."""
+    K, npar = ng + 2, ng + 4
+    g2 = 4 * math.pi * AS
+    p, _, _ = orc.events(ng, 80 + ng, 1)
+    p = p[0]
+    nhat = np.random.default_rng(5).normal(size=3)
+    nhat /= np.linalg.norm(nhat)
+    _, Jn = orc.me_hel(ng, p, want_jamps=True)
+    gpart = [0, 1] + [4 + i for i in range(ng)] + [4 + ng]   # particle of gluon label; label K = the soft one
+    perms_n = list(permutations(range(K)))
+    rank_m = {sg: i for i, sg in enumerate(permutations(range(K + 1)))}
+    big = np.abs(Jn) ** 2 >= 1e-3 * (np.abs(Jn) ** 2).max()
+
+    def worst(lam):
+        q = _with_soft_gluon(p, lam, nhat)
+        assert np.abs(q[0] + q[1] - q[2:].sum(0)).max() <= 1e-9
+        _, Jm = orc.me_hel(ng + 1, q, want_jamps=True)
+        k = q[-1]
+        dev, n = 0.0, 0
+        for h in range(1 << npar):
+            for c, sig in enumerate(perms_n):
+                if not big[h, c]:
+                    continue
+                chain = [2] + [gpart[x] for x in sig] + [3]
+                for pos in range(K + 1):
+                    a, b = chain[pos], chain[pos + 1]
+                    J = q[a] / _mdot(q[a], k) - q[b] / _mdot(q[b], k)
+                    sm = list(sig)
+                    sm.insert(pos, K)
+                    cm = rank_m[tuple(sm)]
+                    num = abs(Jm[2 * h, cm]) ** 2 + abs(Jm[2 * h + 1, cm]) ** 2   # soft gluon: last helicity bit
+                    dev = max(dev, abs(num / (g2 * -_mdot(J, J) * abs(Jn[h, c]) ** 2) - 1))
+                    n += 1
+        return dev, n
+
+    d4, n = worst(1e-4)
+    d5, _ = worst(1e-5)
+    assert n >= (1 << npar) * (K + 1)
+    assert d5 <= 1e-3 and d5 <= 0.2 * d4   # the limit is reached, linearly in the soft scale
+
+
 @pytest.mark.parametrize("ng", [0, 1, 2, 3])
 def test_gauge_invariance(orc, ng):
     """epsilon_g -> k_g for any one gluon makes every colour-ordered amplitude vanish."""
