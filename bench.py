@@ -169,6 +169,18 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------
 # CPU oracle timing (cpu_baseline and the reference arm)
 # ------------------------------------------------------------------------------------------
+def rejected_clocks(clk):
+    """A timed region whose clock record disqualifies it: a hardware or thermal slowdown was active, or
+    the SM clock sat well below its maximum with no reason given (a leftover clock lock).  A power cap
+    alone is kept (and shows in the record)."""
+    if not clk:
+        return False
+    if set(clk.get("reasons") or []) & {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}:
+        return True
+    sm, mx = clk.get("sm_mhz"), clk.get("sm_max_mhz")
+    return bool(sm and mx and sm < 0.8 * mx and not clk.get("reasons"))
+
+
 def oracle_rate(ng, seed, nevt, target_s=15.0):
     """Events/s of the FP64 oracle's ME on all host cores, over a bounded sample of the workload."""
     import oracle
@@ -301,6 +313,17 @@ def run_ours(args):
     ms_step, ms_me, wall = timed(mg.MG_FP64, args.steps, max(3, args.warmup))
     launches = timed.launches
     clk = clocks.stop()
+    # measured again, once, if any rank's clock record disqualifies it (decided by all ranks together:
+    # the timed region holds barriers); the first record is kept beside the second
+    if max_over_ranks([1.0 if rejected_clocks(clk) else 0.0], world, "cuda")[0] > 0:
+        first = clk
+        clocks = ClockSampler(local)
+        clocks.start()
+        ms_step, ms_me, wall = timed(mg.MG_FP64, args.steps, max(3, args.warmup))
+        launches = timed.launches
+        clk = clocks.stop()
+        if clk is not None:
+            clk["remeasured_after"] = first
     nbad = ctx.check(stream)
     ms_step, ms_me = max_over_ranks([ms_step, ms_me], world, "cuda")
     value = aggregate_rate(world, nevt, ms_step)

@@ -27,3 +27,13 @@ def test_workloads_and_rank_bookkeeping():
     assert {w["nevt"] for w in bench.WORKLOADS.values()} == {16384, 524288, 262144, 65536}
     assert bench.rank_first_event(3, 1000) == 3000
     assert bench.aggregate_rate(2, 1000, 10.0) == 2000 / 10e-3
+
+
+def test_clock_records_that_disqualify_a_timed_region():
+    ok = {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": [], "samples": 3}
+    assert not bench.rejected_clocks(ok)
+    assert not bench.rejected_clocks(None)
+    assert not bench.rejected_clocks(dict(ok, reasons=["sw_power_cap"], sm_mhz=1500.0))   # kept, noted
+    for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
+        assert bench.rejected_clocks(dict(ok, reasons=[r]))
+    assert bench.rejected_clocks(dict(ok, sm_mhz=1000.0))   # well below max with no reason: a clock lock
