@@ -32,6 +32,17 @@ def test_header_declares_the_boundary():
         assert name in syms
 
 
+def test_binding_constants_match_the_header(mg):
+    """The Python binding's enum values and launch flags are the header's."""
+    src = open(os.path.join(ROOT, "include", "mg.h")).read()
+    flags = dict((k, int(v)) for k, v in re.findall(r"#define MG_LAUNCH_([A-Z_]+)\s+(\d+)", src))
+    assert flags and all(getattr(mg, "LAUNCH_" + k) == v for k, v in flags.items())
+    enums = dict((k, int(v)) for k, v in re.findall(r"\b(MG_[A-Z0-9_]+)\s*=\s*(\d+)", src))
+    for name in ("MG_FP64", "MG_FP32_AMP", "MG_FP64_TCCOLOR", "MG_MIXED", "MG_GG_TT", "MG_GG_TTG", "MG_GG_TTGG",
+                 "MG_GG_TTGGG"):
+        assert getattr(mg, name) == enums[name], name
+
+
 def test_library_exports_every_declared_symbol(mg):
     L = ctypes.CDLL(mg.library_path())
     missing = [s for s in declared_symbols() if not hasattr(L, s)]
