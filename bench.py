@@ -120,13 +120,26 @@ def config_of(args, nevt, extra=None):
 # ------------------------------------------------------------------------------------------
 # clocks sampled during the timed region
 # ------------------------------------------------------------------------------------------
+def nvsmi_gpu_id(props):
+    """nvidia-smi's -i argument for a torch device: its UUID ("GPU-<uuid>").  nvidia-smi ignores
+    CUDA_VISIBLE_DEVICES and numbers the GPUs physically, so a visible-device index could name another
+    GPU of the machine; the UUID names this one.  None when torch gives no UUID."""
+    u = getattr(props, "uuid", None)
+    if u is None:
+        return None
+    u = str(u).strip()
+    if not u:
+        return None
+    return u if u.startswith("GPU-") else "GPU-" + u
+
+
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
-        self.index = index
+    def __init__(self, gpu_id):
+        self.index = gpu_id
         self.proc = None
         self.path = None
 
@@ -163,7 +176,7 @@ class ClockSampler:
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+                "reasons": reasons, "samples": len(rows), "gpu": self.index}
 
 
 # ------------------------------------------------------------------------------------------
@@ -308,7 +321,8 @@ def run_ours(args):
                             "warp": bool(fl & mg.LAUNCH_WARP), "tc_apart": bool(fl & mg.LAUNCH_TC_APART),
                             "shared": bool(fl & mg.LAUNCH_SHARED)}
 
-    clocks = ClockSampler(local)
+    gpu_id = nvsmi_gpu_id(torch.cuda.get_device_properties(local)) or str(local)
+    clocks = ClockSampler(gpu_id)
     clocks.start()
     ms_step, ms_me, wall = timed(mg.MG_FP64, args.steps, max(3, args.warmup))
     launches = timed.launches
@@ -317,7 +331,7 @@ def run_ours(args):
     # the timed region holds barriers); the first record is kept beside the second
     if max_over_ranks([1.0 if rejected_clocks(clk) else 0.0], world, "cuda")[0] > 0:
         first = clk
-        clocks = ClockSampler(local)
+        clocks = ClockSampler(gpu_id)
         clocks.start()
         ms_step, ms_me, wall = timed(mg.MG_FP64, args.steps, max(3, args.warmup))
         launches = timed.launches

@@ -190,7 +190,12 @@ mg_status mg_flops_per_event_shape(mg_process proc, mg_precision precision, cons
  *     element a call reads is written by that call first).  Calls whose work can overlap on the
  *     GPU (different streams without ordering, several host threads) race on it: serialise them.
  *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress with
- *     that device current); make that first call before any stream capture. */
+ *     that device current); make that first call before any stream capture.
+ *   - The library allocates nothing, but the CUDA driver itself may enlarge the context's
+ *     per-thread local-memory reservation the first time a kernel with a large stack runs in the
+ *     process (the five-gluon kernel keeps ~28 KB of local arrays per thread), which is a device
+ *     allocation and a device-wide synchronisation made by the driver.  To keep that out of the
+ *     caller's steady state, make one warm-up call per device and process at set-up. */
 mg_status mg_sigmakin_noalloc(mg_ctx* ctx, const double* mom_dev, int64_t nevt, double* me_dev, void* stream);
 
 /* ---------------------------------------------------------------------------------------------

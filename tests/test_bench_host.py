@@ -37,3 +37,17 @@ def test_clock_records_that_disqualify_a_timed_region():
     for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"):
         assert bench.rejected_clocks(dict(ok, reasons=[r]))
     assert bench.rejected_clocks(dict(ok, sm_mhz=1000.0))   # well below max with no reason: a clock lock
+
+
+def test_clock_sampler_names_the_gpu_by_uuid():
+    """nvidia-smi numbers GPUs physically and ignores CUDA_VISIBLE_DEVICES: the sampler is given the
+    device's UUID, as torch reports it, in nvidia-smi's "GPU-<uuid>" form."""
+    class Props:
+        def __init__(self, uuid):
+            self.uuid = uuid
+
+    u = "6b1c0e52-7a3d-4f0e-9c1a-2b3c4d5e6f70"
+    assert bench.nvsmi_gpu_id(Props(u)) == "GPU-" + u
+    assert bench.nvsmi_gpu_id(Props("GPU-" + u)) == "GPU-" + u
+    assert bench.nvsmi_gpu_id(Props("")) is None
+    assert bench.nvsmi_gpu_id(object()) is None

@@ -34,13 +34,11 @@ def env():
 def test_partial_helicity_mask_every_mode(env, ng):
     """A helicity threshold between the oracle's per-helicity maximum ratios keeps about half of the
     helicities: fewer gluon-helicity slots than combinations, slots with only some good top helicities,
-    and tensor-core rows past the last good slot.  The mask equals the oracle's at that threshold; FP64
-    matches the oracle with that mask; the other modes (and kernel variants) stay within their bounds
-    of FP64.  Errors are relative to the event's full matrix element.  The FP64 bar is 1e-11 (as for
-    the full-size sampled test), not the 1e-12 of the physical sums: leaving helicities out also
-    removes the partial cancellation between the rounding errors of different helicities (measured: an
-    event at 1.06e-12 of its full matrix element for gg->ttgg), while an error in the masking machinery
-    would show at O(1)."""
+    and tensor-core rows past the last good slot.  The GPU gets the oracle's own momenta, so both sides
+    see identical inputs.  The mask equals the oracle's at that threshold; plain FP64 matches the oracle
+    with that mask within 1e-12 per event, relative to the partial (masked) sum itself, which is a sum of
+    positive per-helicity terms; the other modes (and kernel variants) stay within their bounds of FP64,
+    relative to the event's full matrix element."""
     torch, mg, orc = env
     seed = WORKLOADS[ng][0]
     n = 131 if ng == 3 else 257   # the filter's warm-up is the whole (ragged) batch
@@ -57,14 +55,21 @@ def test_partial_helicity_mask_every_mode(env, ng):
     ref = orc.me_batch(ng, evs, mask=ref_mask, nthreads=NTHREADS)
     full = orc.me_batch(ng, evs, nthreads=NTHREADS)
     with mg.Context(ng, hel_warmup=n, hel_tau=tau) as ctx:
-        mom = torch.zeros(ctx.mom_count(n), dtype=torch.float64, device="cuda")
-        ctx.rambo(seed, n, SQRTS, mom)
-        me = torch.zeros(n, dtype=torch.float64, device="cuda")
+        mom = torch.from_numpy(mg.to_aosoa(evs)).cuda()
+        me = torch.full((n,), -1.0, dtype=torch.float64, device="cuda")
+        ctx.hel_filter(mom, n)
         ctx.sigmakin(mom, n, me, mg.MG_FP64)
         gmask, ngood = ctx.hel_mask()
         assert np.array_equal(gmask, ref_mask) and ngood == ngood_ref
         fp64 = me.cpu().numpy()
-        assert np.max(np.abs(fp64 - ref) / full) <= 1e-11
+        assert np.all(fp64 > 0)
+        rel = np.abs(fp64 / ref - 1)
+        assert rel.max() <= 1e-12, (rel.max(), int(np.argmax(rel)))
+        for flags in (39, 7):   # FP64 with and without the currents shared between slots
+            ctx.set_launch_shape(mg.MG_FP64, 128, 0, flags)
+            ctx.sigmakin(mom, n, me, mg.MG_FP64)
+            rel = np.abs(me.cpu().numpy() / ref - 1)
+            assert rel.max() <= 1e-12, (flags, rel.max(), int(np.argmax(rel)))
         variants = [(mg.MG_FP64_TCCOLOR, None, 1e-6), (mg.MG_FP32_AMP, None, 1e-5), (mg.MG_MIXED, None, 1e-5)]
         if ng >= 2:   # lane-group kernel: in-kernel and separate tensor-core colour sums
             variants += [(mg.MG_MIXED, 15, 1e-5), (mg.MG_MIXED, 31, 1e-5)]
