@@ -81,6 +81,10 @@ def parse():
                     help="precision of the served form: fp64, fp32_amp, fp64_tccolor or mixed; a comma-separated "
                          "list serves each in turn against one one-at-a-time FP64 baseline")
     ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--no-processes", action="store_true", help="time the configured process only")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg of the default run")
+    ap.add_argument("--serve-requests", type=int, default=500,
+                    help="requests of the default run's serving leg (the first ones of the 20,000-request trace)")
     return ap.parse_args()
 
 
@@ -111,7 +115,8 @@ def config_of(args, nevt, extra=None):
                      % (LABEL[args.process], nevt, w["seed"]),
          "process": args.process, "events_per_gpu": nevt, "seed": w["seed"],
          "step": "philox+rambo -> helicity filter (1024 warm-up events) -> FP64 matrix elements",
-         "l2": "256 MB memset between timed steps, outside the per-step CUDA events"}
+         "l2": "256 MB memset between timed steps, outside the per-step CUDA events",
+         "parallelism": "dp%d (disjoint event ranges)" % args.gpus}
     if extra:
         c.update(extra)
     return c
@@ -236,7 +241,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "MEs/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(args, nevt, {"reference": "FP64 CPU oracle (oracle/me_oracle.cpp) on the host cores"}),
+            "config": config_of(args, nevt), "reference": "FP64 CPU oracle (oracle/me_oracle.cpp) on the host cores",
             "cpu_baseline": {"value": value, "unit": "MEs/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "MEs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -244,8 +249,208 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------------------------------
+# roofline inputs
+# ------------------------------------------------------------------------------------------
+MODES = (("fp64", 0), ("fp32_amp", 1), ("fp64_tccolor", 2), ("mixed", 3))
+# timed steps of a process leg at most (a five-gluon FP64 step takes about a second)
+LEG_STEPS = {"ggtt": 20, "ggttg": 20, "ggttgg": 5, "ggttggg": 3}
+# events of the autotuner's probe batch per process
+TUNE_EVENTS = {"ggtt": 16384, "ggttg": 65536, "ggttgg": 16384, "ggttggg": 4096}
+ORACLE_FLOPS = os.path.join(ROOT, "tests", "golden", "oracle_flops.txt")
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_TC_TFLOPS = 1900.0
+
+
+def oracle_flops_table(path=ORACLE_FLOPS):
+    """{process: (good helicities, flops per event)} of the FP64 oracle's instrumented count, as stored
+    by tests/golden/make_oracle_flops.py (a script that calls only the oracle)."""
+    out = {}
+    try:
+        for line in open(path):
+            if line.strip() and not line.startswith("#"):
+                f = line.split()
+                out[f[0]] = (int(f[2]), int(f[9]))
+    except OSError:
+        pass
+    return out
+
+
+def tensor_peak(path=PEAKS_FILE):
+    """Dense FP16 (FP32 accumulate) tensor-core rate in flop/s and where it comes from: the measured bf16
+    burst rate of the GB300s (FP16 and bf16 have the same nominal dense rate), else the fallback."""
+    try:
+        v = float(json.load(open(path))["bf16_tflops"])
+        return v * 1e12, "measured bf16 cuBLAS burst (MEASURED_PEAKS.json) x 1 (nominal f16/bf16 ratio)"
+    except (OSError, KeyError, ValueError, TypeError):
+        return FALLBACK_TC_TFLOPS * 1e12, "fallback 1.9 PFLOP/s bf16 burst x 1 (nominal f16/bf16 ratio)"
+
+
+def colour_tc_flops(ncol, good):
+    """Tensor-core work of the split-FP16 colour sum per event: for each good helicity the real and
+    imaginary jamp rows, each as a hi and a lo FP16 row, times the ncol x ncol matrix (2 ncol^2 flops)."""
+    return good * 2 * 2 * 2 * ncol * ncol
+
+
+def time_roofline(parts, me_ms):
+    """Time-based roofline of a kernel mix: T_min = sum over parts of flops / peak (each on its own
+    pipe); frac = T_min / measured time."""
+    tmin = sum(f / pk for _, f, pk, _ in parts)
+    return {"bound": "time", "t_min_ms": tmin * 1e3, "t_ms": me_ms, "frac": tmin / (me_ms * 1e-3),
+            "parts": [{"pipe": n, "flops_per_call": f, "peak_tflops": pk / 1e12, "peak_source": src}
+                      for n, f, pk, src in parts]}
+
+
+def fp64_roofline(model_flops, oracle_flops, nevt, me_ms, peak, traffic, kernel):
+    """ALU roofline of the FP64 path on the FP64 pipe.  achieved counts the flops of the engine's own
+    algorithm (its flop model, pinned to the hardware's FP64 instruction counts); the oracle-count
+    figures count the FP64 oracle's instrumented operations (plain recursion per helicity) for the same
+    events in the same time, and count_ratio = oracle / engine flops per event."""
+    ach = model_flops * nevt / (me_ms * 1e-3)
+    r = {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s", "frac": ach / peak,
+         "traffic": traffic, "kernel": kernel, "flops_per_event": model_flops,
+         "peak_source": "measured FP64 DFMA-chain microbenchmark (mg_measure_fma_peak) on this GPU"}
+    if oracle_flops:
+        ach_o = oracle_flops * nevt / (me_ms * 1e-3)
+        r.update({"oracle_flops_per_event": oracle_flops, "oracle_count_achieved": ach_o / 1e12,
+                  "oracle_count_frac": ach_o / peak, "count_ratio": oracle_flops / model_flops})
+    return r
+
+
+def profile_for(process):
+    """The committed ncu summary of the FP64 matrix-element kernel of a process, if any."""
+    import glob
+    c = sorted(glob.glob(os.path.join(ROOT, "profiles", "k_me_gluonhel_fp64_%s_*.md" % process)))
+    return c[0] if c else None
+
+
+# ------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------
+class Leg:
+    """One process at its workload size on this rank's GPU: context, momenta and ME buffers, the step
+    (Philox + RAMBO -> helicity filter on the first 1,024 events -> matrix elements) and its timing."""
+
+    def __init__(self, mg, torch, process, nevt, rank, stream, flush, autotune):
+        w = WORKLOADS[process]
+        self.mg, self.torch, self.process, self.nevt = mg, torch, process, nevt
+        self.ng, self.seed = w["ng"], w["seed"]
+        self.e0 = rank_first_event(rank, nevt)
+        self.stream, self.flush = stream, flush
+        self.ctx = mg.Context(self.ng, mt=MT, alphas=ALPHAS)
+        self.mom = torch.zeros(self.ctx.mom_count(nevt), dtype=torch.float64, device="cuda")
+        self.me = torch.zeros(nevt, dtype=torch.float64, device="cuda")
+        self.me_x = torch.zeros(nevt, dtype=torch.float64, device="cuda")
+        self.nwarm = min(nevt, 1024)
+        self.shapes = {}
+        self.ctx.rambo_range(self.seed, self.e0, nevt, SQRTS, self.mom, stream=stream)
+        if self.ctx.check(stream) != 0:
+            raise RuntimeError("RAMBO did not converge")
+        if autotune:   # launch shape of the matrix-element kernel per precision (setup, untimed)
+            for name, prec in MODES:
+                self.ctx.autotune(prec, nevt=min(nevt, TUNE_EVENTS[process]))
+        for name, prec in MODES:
+            tev, slm, fl = self.ctx.launch_shape(prec)
+            self.shapes[name] = {"tile_ev": tev, "slot_major": slm, "flags": fl,
+                                 "unrolled": bool(fl & mg.LAUNCH_UNROLLED), "df_redo": bool(fl & mg.LAUNCH_DF_REDO),
+                                 "fused": bool(fl & mg.LAUNCH_FUSED), "warp": bool(fl & mg.LAUNCH_WARP),
+                                 "tc_apart": bool(fl & mg.LAUNCH_TC_APART), "shared": bool(fl & mg.LAUNCH_SHARED)}
+
+    def step(self, precision, ev):
+        ev[0].record(self.stream)
+        self.ctx.rambo_range(self.seed, self.e0, self.nevt, SQRTS, self.mom, stream=self.stream)
+        self.ctx.hel_filter(self.mom, self.nwarm, stream=self.stream)
+        ev[1].record(self.stream)
+        self.ctx.sigmakin(self.mom, self.nevt, self.me if precision == self.mg.MG_FP64 else self.me_x, precision,
+                          stream=self.stream)
+        ev[2].record(self.stream)
+
+    def timed(self, precision, steps, warmup, world):
+        """Mean step and matrix-element times (CUDA events on the launching stream, L2 flushed between
+        steps outside the events), wall time of the timed region, and the library's kernel launches in it."""
+        torch, dist = self.torch, None
+        if world > 1:
+            import torch.distributed as dist
+        mk = lambda: [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        evs = [mk() for _ in range(steps)]
+        with torch.cuda.stream(self.stream):
+            for _ in range(warmup):
+                self.step(precision, mk())
+                self.flush.zero_()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        n0 = self.mg.kernel_launches()
+        with torch.cuda.stream(self.stream):
+            for k in range(steps):
+                self.step(precision, evs[k])
+                self.flush.zero_()
+        nlaunch = self.mg.kernel_launches() - n0
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        wall = time.perf_counter() - t0
+        return (statistics.mean(e[0].elapsed_time(e[2]) for e in evs),
+                statistics.mean(e[1].elapsed_time(e[2]) for e in evs), wall, nlaunch)
+
+    def rel_err(self):
+        rel = ((self.me_x / self.me) - 1).abs().cpu()
+        return {"max": float(rel.max()), "p99": float(rel.quantile(0.99) if rel.numel() <= 1 << 24 else rel.max()),
+                "median": float(rel.median())}
+
+    def rooflines(self, name, precision, me_ms, peaks, oracle_flops, world):
+        """FP64 path: the ALU roofline on the FP64 pipe (engine count, with the oracle-count figures).
+        The other modes: the time-based roofline over the pipes their parts run on."""
+        mg = self.mg
+        mask, ngood = self.ctx.hel_mask()
+        flags = self.shapes[name]["flags"]
+        amp, col = mg.flops_per_event(self.ng, mask, precision, flags)
+        nev = self.nevt
+        p64, p32, (ptc, tc_src) = peaks
+        src64 = "measured FP64 DFMA-chain microbenchmark (mg_measure_fma_peak)"
+        src32 = "measured FP32 FFMA-chain microbenchmark (mg_measure_fma_peak)"
+        ncol = math.factorial(self.ng + 2)
+        if precision == mg.MG_FP64:
+            csrc = os.path.join(ROOT, "paper_2210_11122_gb300", "csrc")
+            prof = profile_for(self.process)
+            traffic = profiled_traffic([os.path.join(csrc, f) for f in ("mg_me_kernel.cuh", "mg_me_algebra.cuh")],
+                                       prof, nev) if prof else None
+            shared = self.shapes[name]["shared"]
+            kernel = ("k_event_prep + %sk_me_gluonhel<%d,double> + k_hel_sum (one mg_sigmakin call)"
+                      % ("k_share_level (per sequence length) + " if shared else "", self.ng + 2))
+            return fp64_roofline(amp + col, oracle_flops, nev, me_ms, p64, traffic, kernel)
+        if precision == mg.MG_FP64_TCCOLOR:
+            return time_roofline([("fp64", amp * nev, p64, src64),
+                                  ("tensor_f16", colour_tc_flops(ncol, ngood) * nev, ptc, tc_src)], me_ms)
+        # FP32 amplitudes: the per-event FP64 record is the amplitude count with no good helicity
+        rec64, _ = mg.flops_per_event(self.ng, [0] * len(mask), precision, flags)
+        if precision == mg.MG_FP32_AMP:
+            return time_roofline([("fp32", (amp - rec64 + col) * nev, p32, src32), ("fp64", rec64 * nev, p64, src64)],
+                                 me_ms)
+        return time_roofline([("fp32", (amp - rec64) * nev, p32, src32), ("fp64", rec64 * nev, p64, src64),
+                              ("tensor_f16", colour_tc_flops(ncol, ngood) * nev, ptc, tc_src)], me_ms)
+
+    def close(self):
+        self.ctx.close()
+
+
+def measure_leg(leg, steps, warmup, world, peaks, oracle_flops, modes=MODES):
+    """Every precision mode of one process: rates of the whole step and of mg_sigmakin alone, the
+    per-event error against the FP64 result of the same events, and the rooflines."""
+    out = {}
+    for name, prec in modes:
+        ms, me_ms, wall, nl = leg.timed(prec, steps, warmup, world)
+        ms, me_ms = max_over_ranks([ms, me_ms], world, "cuda")
+        r = {"value": aggregate_rate(world, leg.nevt, ms), "ms_per_step": ms, "me_kernel_ms": me_ms,
+             "value_me_only": aggregate_rate(world, leg.nevt, me_ms), "steps": steps, "launches_per_step": nl / steps,
+             "roofline": leg.rooflines(name, prec, me_ms, peaks, oracle_flops, world)}
+        if prec != leg.mg.MG_FP64:
+            r["rel_err_vs_fp64"] = leg.rel_err()
+        out[name] = r
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -261,71 +466,19 @@ def run_ours(args):
     mgbuild.build()
     import paper_2210_11122_gb300 as mg
 
-    w = WORKLOADS[args.process]
-    ng, seed = w["ng"], w["seed"]
-    nevt = args.nevt or w["nevt"]
-    e0 = rank_first_event(rank, nevt)
+    nevt = args.nevt or WORKLOADS[args.process]["nevt"]
     stream = torch.cuda.Stream()
-    ctx = mg.Context(ng, mt=MT, alphas=ALPHAS)
-    mom = torch.zeros(ctx.mom_count(nevt), dtype=torch.float64, device="cuda")
-    me = torch.zeros(nevt, dtype=torch.float64, device="cuda")
-    me32 = torch.zeros(nevt, dtype=torch.float64, device="cuda")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
-    nwarm = min(nevt, 1024)
+    oflops = oracle_flops_table()
+    peaks = (mg.measure_fma_peak(fp32=False, iters=2048), mg.measure_fma_peak(fp32=True, iters=2048), tensor_peak())
+    warm = max(3, args.warmup)
 
-    def step(precision, ev):
-        ev[0].record(stream)
-        ctx.rambo_range(seed, e0, nevt, SQRTS, mom, stream=stream)
-        ctx.hel_filter(mom, nwarm, stream=stream)
-        ev[1].record(stream)
-        ctx.sigmakin(mom, nevt, me if precision == mg.MG_FP64 else me32, precision, stream=stream)
-        ev[2].record(stream)
-
-    def timed(precision, steps, warmup):
-        evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
-        with torch.cuda.stream(stream):
-            for _ in range(warmup):
-                step(precision, [torch.cuda.Event(enable_timing=True) for _ in range(3)])
-                flush.zero_()
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        n0 = mg.kernel_launches()
-        with torch.cuda.stream(stream):
-            for k in range(steps):
-                step(precision, evs[k])
-                flush.zero_()
-        nlaunch = mg.kernel_launches() - n0
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        wall = time.perf_counter() - t0
-        step_ms = [e[0].elapsed_time(e[2]) for e in evs]
-        me_ms = [e[1].elapsed_time(e[2]) for e in evs]
-        timed.launches = nlaunch
-        return statistics.mean(step_ms), statistics.mean(me_ms), wall
-
-    if ctx.check(stream) != 0:
-        raise RuntimeError("RAMBO did not converge")
-    # launch shape of the matrix-element kernel per precision, picked by the autotuner (setup, untimed)
-    shapes = {}
-    if not args.no_autotune:
-        for name, prec in (("fp64", mg.MG_FP64), ("fp32_amp", mg.MG_FP32_AMP), ("fp64_tccolor", mg.MG_FP64_TCCOLOR),
-                           ("mixed", mg.MG_MIXED)):
-            ctx.autotune(prec, nevt=min(nevt, 65536))
-            tev, slm, fl = ctx.launch_shape(prec)
-            shapes[name] = {"tile_ev": tev, "slot_major": slm, "unrolled": bool(fl & mg.LAUNCH_UNROLLED),
-                            "df_redo": bool(fl & mg.LAUNCH_DF_REDO), "fused": bool(fl & mg.LAUNCH_FUSED),
-                            "warp": bool(fl & mg.LAUNCH_WARP), "tc_apart": bool(fl & mg.LAUNCH_TC_APART),
-                            "shared": bool(fl & mg.LAUNCH_SHARED)}
-
+    # ---- headline: the configured process, FP64 step, clocks sampled during the timed region ----
+    leg = Leg(mg, torch, args.process, nevt, rank, stream, flush, not args.no_autotune)
     gpu_id = nvsmi_gpu_id(torch.cuda.get_device_properties(local)) or str(local)
     clocks = ClockSampler(gpu_id)
     clocks.start()
-    ms_step, ms_me, wall = timed(mg.MG_FP64, args.steps, max(3, args.warmup))
-    launches = timed.launches
+    ms_step, ms_me, wall, launches = leg.timed(mg.MG_FP64, args.steps, warm, world)
     clk = clocks.stop()
     # measured again, once, if any rank's clock record disqualifies it (decided by all ranks together:
     # the timed region holds barriers); the first record is kept beside the second
@@ -333,35 +486,29 @@ def run_ours(args):
         first = clk
         clocks = ClockSampler(gpu_id)
         clocks.start()
-        ms_step, ms_me, wall = timed(mg.MG_FP64, args.steps, max(3, args.warmup))
-        launches = timed.launches
+        ms_step, ms_me, wall, launches = leg.timed(mg.MG_FP64, args.steps, warm, world)
         clk = clocks.stop()
         if clk is not None:
             clk["remeasured_after"] = first
-    nbad = ctx.check(stream)
+    nbad = leg.ctx.check(stream)
     ms_step, ms_me = max_over_ranks([ms_step, ms_me], world, "cuda")
     value = aggregate_rate(world, nevt, ms_step)
+    ref64 = leg.me.clone()
+    _, ngood = leg.ctx.hel_mask()
+    roofline = leg.rooflines("fp64", mg.MG_FP64, ms_me, peaks, oflops.get(args.process, (0, 0))[1], world)
 
-    # the other arithmetic modes on the same step: FP32 amplitudes; FP64 or FP32 amplitudes with the
-    # colour sum on the tensor cores
-    ref64 = me.double().cpu()
-    variants = {}
-    for name, prec in (("fp32_amp", mg.MG_FP32_AMP), ("fp64_tccolor", mg.MG_FP64_TCCOLOR), ("mixed", mg.MG_MIXED)):
-        msv, msv_me, _ = timed(prec, max(3, args.steps // 2), 3)
-        torch.cuda.synchronize()
-        msv, msv_me = max_over_ranks([msv, msv_me], world, "cuda")
-        rel = ((me32.double().cpu() / ref64) - 1).abs()
-        variants[name] = {"value": aggregate_rate(world, nevt, msv), "ms_per_step": msv, "me_kernel_ms": msv_me,
-                          "rel_err_vs_fp64": {"max": float(rel.max()), "p99": float(rel.quantile(0.99)),
-                                              "median": float(rel.median())}}
+    # the other arithmetic modes on the same step
+    variants = measure_leg(leg, max(3, args.steps // 2), 3, world, peaks, oflops.get(args.process, (0, 0))[1],
+                           modes=MODES[1:])
+    leg.me.copy_(ref64)
 
     # the same FP64 step captured once as a CUDA graph and replayed (one launch per step)
-    gmom = torch.zeros_like(mom)
-    gme = torch.zeros_like(me)
-    gctx = mg.Context(ng, mt=MT, alphas=ALPHAS)
-    if not args.no_autotune:
-        gctx.autotune(mg.MG_FP64, nevt=min(nevt, 65536))
-    graph = mg.GraphBatch([(gctx, seed, e0, nevt, SQRTS, gmom, gme, mg.MG_FP64)])
+    gmom = torch.zeros_like(leg.mom)
+    gme = torch.zeros_like(leg.me)
+    gctx = mg.Context(leg.ng, mt=MT, alphas=ALPHAS)
+    gctx.set_launch_shape(mg.MG_FP64, leg.shapes["fp64"]["tile_ev"], leg.shapes["fp64"]["slot_major"],
+                          leg.shapes["fp64"]["flags"])
+    graph = mg.GraphBatch([(gctx, leg.seed, leg.e0, nevt, SQRTS, gmom, gme, mg.MG_FP64)])
     gev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
     with torch.cuda.stream(stream):
         for _ in range(3):
@@ -375,82 +522,83 @@ def run_ours(args):
     torch.cuda.synchronize()
     graph_ms = statistics.mean(gev[2 * k].elapsed_time(gev[2 * k + 1]) for k in range(args.steps))
     graph_ms = max_over_ranks([graph_ms], world, "cuda")[0]
-    graph_same = bool(torch.equal(gme, me))
+    graph_same = bool(torch.equal(gme, leg.me))
     graph.close()
     gctx.close()
 
-    # end to end through the host-buffer entry point (pinned momenta in, MEs out, copies timed)
-    host_mom = mom.cpu().pin_memory()
+    # end to end through the host-buffer entry point (pinned momenta in, MEs out, copies timed), FP64
+    # and MIXED
+    host_mom = leg.mom.cpu().pin_memory()
     host_me = torch.zeros(nevt, dtype=torch.float64).pin_memory()
-    ne2e = max(3, args.steps // 2)
-    for _ in range(2):
-        ctx.sigmakin_host(host_mom, nevt, host_me, mg.MG_FP64, stream=stream)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(ne2e):
-        ctx.sigmakin_host(host_mom, nevt, host_me, mg.MG_FP64, stream=stream)
-    e2e_s = max_over_ranks([(time.perf_counter() - t0) / ne2e], world, "cuda")[0]
+
+    def e2e_of(prec, reps):
+        for _ in range(2):
+            leg.ctx.sigmakin_host(host_mom, nevt, host_me, prec, stream=stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            leg.ctx.sigmakin_host(host_mom, nevt, host_me, prec, stream=stream)
+        return max_over_ranks([(time.perf_counter() - t0) / reps], world, "cuda")[0]
+
+    e2e_s = e2e_of(mg.MG_FP64, max(3, args.steps // 2))
+    e2e_mixed_s = e2e_of(mg.MG_MIXED, max(3, args.steps))
     e2e = {"value": aggregate_rate(world, nevt, e2e_s * 1e3), "unit": "MEs/s", "h2d_bytes_per_step": int(host_mom.numel() * 8),
            "d2h_bytes_per_step": int(nevt * 8),
-           "api": "mg_sigmakin_host: pinned AoSoA momenta -> device -> FP64 MEs -> host"}
+           "api": "mg_sigmakin_host: pinned AoSoA momenta -> device -> FP64 MEs -> host (chunked, copies overlapped)",
+           "mixed": {"value": aggregate_rate(world, nevt, e2e_mixed_s * 1e3), "ms_per_call": e2e_mixed_s * 1e3,
+                     "device_me_ms": variants["mixed"]["me_kernel_ms"]}}
+    headline = {"fp64": {"value": value, "ms_per_step": ms_step, "me_kernel_ms": ms_me,
+                         "value_me_only": aggregate_rate(world, nevt, ms_me), "steps": args.steps,
+                         "roofline": roofline}}
+    headline.update(variants)
+    shapes = leg.shapes
+    leg.close()
+
+    # ---- every other process of the workloads at its own size: FP64 and the three other modes ----
+    processes = {args.process: {"events_per_gpu": nevt, "seed": WORKLOADS[args.process]["seed"],
+                                "good_helicities": ngood, "modes": headline, "launch_shapes": shapes}}
+    if not args.no_processes:
+        for p in ("ggtt", "ggttg", "ggttgg", "ggttggg"):
+            if p == args.process:
+                continue
+            n = WORKLOADS[p]["nevt"]
+            lg = Leg(mg, torch, p, n, rank, stream, flush, not args.no_autotune)
+            steps = min(args.steps, LEG_STEPS[p])
+            modes = measure_leg(lg, steps, 3, world, peaks, oflops.get(p, (0, 0))[1])
+            _, g = lg.ctx.hel_mask()
+            processes[p] = {"events_per_gpu": n, "seed": WORKLOADS[p]["seed"], "good_helicities": g, "modes": modes,
+                            "launch_shapes": lg.shapes}
+            lg.close()
+            torch.cuda.empty_cache()
+
+    # ---- serving: a bounded sample of the request trace, 80 % load (rank 0, one GPU) ----
+    serving = None
+    if not args.no_serve and world == 1:
+        serving = serve_leg(mg, torch, args.serve_requests, args.slots, ["fp64", "mixed"])
 
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel (the FP64 matrix-element kernel, ALU bound on the FP64 pipe)
-    mask, ngood = ctx.hel_mask()
-    flags64 = ctx.launch_shape(mg.MG_FP64)[2]
-    shared64 = bool(flags64 & mg.LAUNCH_SHARED)
-    amp_f, col_f = mg.flops_per_event(ng, mask, mg.MG_FP64, flags64)
-    flops = (amp_f + col_f) * nevt
-    peak = mg.measure_fma_peak(fp32=False, iters=2048)
-    # the other modes against the peak of the pipe their amplitudes run on (FP32 FMA for the FP32-
-    # amplitude modes, whose colour sums run on the FP32 pipe or the tensor cores; FP64 otherwise)
-    peak32 = mg.measure_fma_peak(fp32=True, iters=2048)
-    # (the tensor-core colour modes count their amplitude flops only: the colour sums run on the tensor
-    # cores, not on that pipe)
-    for name, prec in (("fp32_amp", mg.MG_FP32_AMP), ("fp64_tccolor", mg.MG_FP64_TCCOLOR), ("mixed", mg.MG_MIXED)):
-        a, c = mg.flops_per_event(ng, mask, prec, ctx.launch_shape(prec)[2])
-        if prec in (mg.MG_FP64_TCCOLOR, mg.MG_MIXED):
-            c = 0.0
-        pk = peak32 if prec in (mg.MG_FP32_AMP, mg.MG_MIXED) else peak
-        ach = (a + c) * nevt / (variants[name]["me_kernel_ms"] * 1e-3)
-        variants[name]["roofline"] = {"bound": "alu", "achieved": ach / 1e12, "peak": pk / 1e12, "unit": "TFLOP/s",
-                                      "frac": ach / pk, "flops_per_event": a + c,
-                                      "peak_source": "measured %s FMA-chain microbenchmark (mg_measure_fma_peak)"
-                                                     % ("FP32" if pk is peak32 else "FP64")}
-    achieved = flops / (ms_me * 1e-3)
-    csrc = os.path.join(ROOT, "paper_2210_11122_gb300", "csrc")
-    traffic = profiled_traffic([os.path.join(csrc, f) for f in ("mg_me_kernel.cuh", "mg_me_algebra.cuh")],
-                               os.path.join(ROOT, "profiles", "k_me_gluonhel_fp64_%s_65536.md" % args.process), nevt)
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_event_prep + %sk_me_gluonhel<%d,double> + k_hel_sum (one mg_sigmakin call)"
-                          % ("k_share_level (per sequence length) + " if shared64 else "", ng + 2),
-                "flops_per_event": amp_f + col_f,
-                "peak_source": "measured FP64 DFMA-chain microbenchmark (mg_measure_fma_peak) on this GPU"}
-
     cpu = None
     if not args.no_cpu_baseline:
-        rate, cores, n, dt = oracle_rate(ng, seed, nevt)
+        rate, cores, n, dt = oracle_rate(WORKLOADS[args.process]["ng"], WORKLOADS[args.process]["seed"], nevt)
         cpu = {"value": rate, "unit": "MEs/s", "cores": cores, "kind": "oracle",
                "sample": "first %d events of the workload (of %d), FP64 ME only, %.1f s on %d threads"
                          % (n, nevt, dt, cores)}
 
     line = {"metric": METRIC, "value": value, "unit": "MEs/s", "n_gpus": world, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": warm, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_of(args, nevt, {"parallelism": "dp%d (disjoint event ranges)" % world}),
+            "config": config_of(args, nevt),
             "me_kernel_ms": ms_me, "wall_s": wall, "nonconverged_events": nbad, "good_helicities": ngood,
-            "modes": variants, "launch_shapes": shapes,
+            "modes": variants, "launch_shapes": shapes, "processes": processes, "serving": serving,
             "graph": {"ms_per_step": graph_ms, "value": aggregate_rate(world, nevt, graph_ms), "same_result": graph_same,
                       "what": "the FP64 step captured as one CUDA graph (mg_graph_create) and replayed"},
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": launches}
     print(json.dumps(line))
-    ctx.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -491,6 +639,37 @@ def run_trace(mg, srv, proc, nevt, expo, rate):
     lat = np.array([srv.wait(t)[1] for t in tickets])
     span = time.perf_counter() - t0
     return span, lat
+
+
+def serve_leg(mg, torch, nreq, slots, names):
+    """Short serving measurement of the default run: the first nreq requests of the trace, each served
+    form closed loop (capacity) and at Poisson arrivals of 80 % of that capacity, against one-at-a-time
+    FP64 on the same requests."""
+    import numpy as np
+    table = {"fp64": mg.MG_FP64, "fp32_amp": mg.MG_FP32_AMP, "fp64_tccolor": mg.MG_FP64_TCCOLOR, "mixed": mg.MG_MIXED}
+    proc, nevt, expo = serve_trace(mg, torch, nreq)
+    total = int(nevt.sum())
+    runs = [("served_" + n, slots, table[n]) for n in names] + [("one_at_a_time_fp64", 1, mg.MG_FP64)]
+    out = {}
+    for label, sl, precision in runs:
+        with mg.Server(slots=sl, precision=precision) as srv:
+            w = [srv.submit(p, 10**9 + p, 2048) for p in range(4)]       # warm-up
+            for t in w:
+                srv.wait(t)
+            span, _ = run_trace(mg, srv, proc, nevt, expo, None)
+            cap = len(proc) / span
+            span2, lat = run_trace(mg, srv, proc, nevt, expo, 0.8 * cap)
+            out[label] = {"slots": sl, "capacity_req_per_s": cap, "closed_loop_MEs_per_s": total / span,
+                          "open_loop_rate_req_per_s": 0.8 * cap, "open_loop_MEs_per_s": total / span2,
+                          "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                          "peak": srv.stats()}
+    base = out["one_at_a_time_fp64"]["closed_loop_MEs_per_s"]
+    for n in names:
+        out["served_" + n]["speedup_closed_loop_vs_one_at_a_time_fp64"] = out["served_" + n]["closed_loop_MEs_per_s"] / base
+    out["workload"] = ("first %d requests of the serving trace (gg->tt/ttg/ttgg/ttggg with p=0.4/0.3/0.2/0.1, nevt "
+                       "log-uniform in [32, 65536], seed = request id), %d events; Poisson arrivals at 80%% of each "
+                       "form's measured capacity; HBM admission cap 64 GiB" % (nreq, total))
+    return out
 
 
 def run_serve(args):

@@ -143,7 +143,11 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
 
 /* The same, through host buffers: copies mom_host (AoSoA, mg_mom_count doubles) to the device,
  * computes, and copies the MEs back to me_host; returns after the results are in me_host.
- * Device staging buffers are owned by the context and grown on demand. */
+ * Batches of 32,768 events or more are split into up to 4 chunks of whole 32-event pages (each of at
+ * least 16,384 events): the momenta of later chunks are copied in and the MEs of earlier ones copied
+ * out (on two copy streams of the context) while a chunk's MEs are computed on `stream`.  The results
+ * are those of one mg_sigmakin call over the batch.  Pinned host buffers are needed for the copies to
+ * overlap.  Device staging buffers are owned by the context and grown on demand. */
 mg_status mg_sigmakin_host(mg_ctx* ctx, const double* mom_host, int64_t nevt, mg_precision precision,
                            double* me_host, void* stream);
 

@@ -304,6 +304,12 @@ void mg_destroy(mg_ctx* ctx) {
   if (ctx->side) cudaStreamDestroy(ctx->side);
   cudaFree(ctx->d_mom_stage);
   cudaFree(ctx->d_me_stage);
+  for (int c = 0; c < mg_ctx::kHostChunks; ++c) {
+    if (ctx->ev_in[c]) cudaEventDestroy(ctx->ev_in[c]);
+    if (ctx->ev_done[c]) cudaEventDestroy(ctx->ev_done[c]);
+  }
+  if (ctx->cp_in) cudaStreamDestroy(ctx->cp_in);
+  if (ctx->cp_out) cudaStreamDestroy(ctx->cp_out);
   delete ctx;
 }
 
@@ -664,12 +670,54 @@ mg_status mg_sigmakin_host(mg_ctx* ctx, const double* mom_host, int64_t nevt, mg
     }
     ctx->stage_cap = nmom + pad32(nevt);
   }
+  if (!ctx->cp_in) {
+    if (cudaStreamCreateWithFlags(&ctx->cp_in, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->cp_out, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      return MG_ECUDA;
+    }
+    for (int c = 0; c < mg_ctx::kHostChunks; ++c)
+      if (cudaEventCreateWithFlags(&ctx->ev_in[c], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&ctx->ev_done[c], cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return MG_ECUDA;
+      }
+  }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  MG_CUDA(cudaMemcpyAsync(ctx->d_mom_stage, mom_host, nmom * sizeof(double), cudaMemcpyHostToDevice, st));
-  mg_status s = mg_sigmakin(ctx, ctx->d_mom_stage, nevt, precision, ctx->d_me_stage, stream);
-  if (s != MG_OK) return s;
-  MG_CUDA(cudaMemcpyAsync(me_host, ctx->d_me_stage, nevt * sizeof(double), cudaMemcpyDeviceToHost, st));
-  MG_CUDA(cudaStreamSynchronize(st));
+  // up to kHostChunks chunks of whole 32-event pages, each of at least 16,384 events: the copies in run
+  // on cp_in, the matrix elements of chunk c on st once its momenta are in, its results go out on cp_out.
+  // Per-event results do not depend on the chunking (the helicity filter of a first call sees the same
+  // first events, a chunk holding at least 16,384 of them).
+  int64_t nch = nevt / 16384;
+  if (nch < 1) nch = 1;
+  if (nch > mg_ctx::kHostChunks) nch = mg_ctx::kHostChunks;
+  const int64_t chunk = pad32((nevt + nch - 1) / nch);
+  const int64_t per_page = static_cast<int64_t>(ctx->npar) * 4 * mg::kPage;
+  int nc = 0;
+  for (int64_t e0 = 0; e0 < nevt; e0 += chunk, ++nc) {
+    const int64_t n = nevt - e0 < chunk ? nevt - e0 : chunk;
+    const int64_t off = e0 / mg::kPage * per_page;
+    MG_CUDA(cudaMemcpyAsync(ctx->d_mom_stage + off, mom_host + off, pad32(n) / mg::kPage * per_page * sizeof(double),
+                            cudaMemcpyHostToDevice, ctx->cp_in));
+    MG_CUDA(cudaEventRecord(ctx->ev_in[nc], ctx->cp_in));
+  }
+  nc = 0;
+  for (int64_t e0 = 0; e0 < nevt; e0 += chunk, ++nc) {
+    const int64_t n = nevt - e0 < chunk ? nevt - e0 : chunk;
+    const int64_t off = e0 / mg::kPage * per_page;
+    MG_CUDA(cudaStreamWaitEvent(st, ctx->ev_in[nc], 0));
+    mg_status s = mg_sigmakin(ctx, ctx->d_mom_stage + off, n, precision, ctx->d_me_stage + e0, stream);
+    if (s != MG_OK) {
+      cudaStreamSynchronize(ctx->cp_in);
+      cudaStreamSynchronize(ctx->cp_out);
+      return s;
+    }
+    MG_CUDA(cudaEventRecord(ctx->ev_done[nc], st));
+    MG_CUDA(cudaStreamWaitEvent(ctx->cp_out, ctx->ev_done[nc], 0));
+    MG_CUDA(cudaMemcpyAsync(me_host + e0, ctx->d_me_stage + e0, n * sizeof(double), cudaMemcpyDeviceToHost,
+                            ctx->cp_out));
+  }
+  MG_CUDA(cudaStreamSynchronize(ctx->cp_out));
   return MG_OK;
 }
 

@@ -48,6 +48,11 @@ struct mg_ctx {
   double* d_mom_stage = nullptr;
   double* d_me_stage = nullptr;
   int64_t stage_cap = 0;
+  // mg_sigmakin_host: copy streams and per-chunk events (host->device copies of later chunks and
+  // device->host copies of earlier ones overlap the matrix elements of the chunk in between)
+  static constexpr int kHostChunks = 4;
+  cudaStream_t cp_in = nullptr, cp_out = nullptr;
+  cudaEvent_t ev_in[kHostChunks] = {}, ev_done[kHostChunks] = {};
   bool mask_ready = false;
   mg::MeShape shape[4];       // launch shape of the matrix-element kernel per precision (autotuned)
   cudaStream_t last = nullptr;

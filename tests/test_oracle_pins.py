@@ -511,3 +511,91 @@ def test_flop_counter_colour_part(orc, ng):
     nh = 1 << (ng + 4)
     assert c["colour"]["add"] + c["colour"]["mul"] == nh * (4 * ncol * ncol + 4 * ncol)
     assert c["amp"]["add"] + c["amp"]["mul"] > 0
+
+
+# ------------------------------------------------------------------------------------------
+# The oracle's amplitude operation counter, pinned to a count derived by hand from the algorithm:
+# per helicity, the external wavefunctions, every off-shell gluon current J(seq) once per ordered
+# sequence of distinct gluons (length L = 2..k: k!/(k-L)! of them), every quark-line prefix
+# Psibar(prefix) once per ordered prefix (length 1..k-1), and k terms per colour ordering (k! of them).
+# Costs per primitive, with a complex add = 2 adds and a complex multiply = 4 mul + 2 add:
+#   dot_cc 16 mul 14 add; dot_cr 8 mul 6 add; dot_rr 4 mul 3 add;
+#   row spinor x (gamma.J): the two J1 -+ i J2 (8 mul 4 add), eight complex sums or differences
+#   (16 add), four outputs of two complex products and a sum (32 mul 24 add) -> 40 mul 44 add;
+#   row spinor x (Qslash + m): 40 mul 44 add + 4 (scale, complex add) -> 48 mul 52 add.
+# ------------------------------------------------------------------------------------------
+def _hand_amp_count(k, mt_nonzero=True):
+    """(add, mul) per helicity of the oracle's colour-ordered recursion for k gluons (massive tops,
+    incoming gluons along the beam, final-state gluons off the axis)."""
+    from math import comb, factorial
+    nseq = lambda L: factorial(k) // factorial(k - L)
+    add = mul = 0
+    # ubar(p_t) and v(p_tbar): |p| (3 mul 2 add), E + |p| (1 add), m*m (1 mul), the helicity
+    # spinor chi (3 mul 2 add for pt^2 and |p|, one add for |p| + pz, 2 mul for 2|p|(|p| + pz),
+    # 3 mul for its components), four scaled components (8 mul)
+    add += 2 * (2 + 1 + 3)
+    mul += 2 * (3 + 1 + 8 + 8)
+    # gluon polarisations: kt (2 mul 1 add), |k| (3 mul 2 add), 1/sqrt(2) scalings (6 mul); off the
+    # beam axis also e_theta, e_phi (4 mul)
+    for g in range(k):
+        add += 3
+        mul += 2 + 3 + 6 + (4 if g >= 2 else 0)
+    mul += 1                                                      # g_s = sqrt(4 pi alpha_s)
+    for L in range(2, k + 1):                                     # off-shell gluon currents
+        n3, n4 = L - 1, comb(L - 1, 2)
+        # momentum sum 4L add; three-gluon split: dot_cc, d / a1 / a2 (8 mul 12 add), two dot_cr,
+        # four components of (scale + 2 complex products, 3 complex sums, g scaling) = 88 mul 78 add;
+        # four-gluon split: three dot_cc, four components of (3 complex products, 2 scalings, 2 sums,
+        # g*g, g^2 scaling, accumulation) = 116 mul 90 add; propagator dot_rr + 4 scalings
+        add += nseq(L) * (4 * L + 78 * n3 + 90 * n4 + 3)
+        mul += nseq(L) * (88 * n3 + 116 * n4 + 4 + 8)
+    for ln in range(1, k):                                        # quark-line prefixes
+        # per attached current: row x gamma.J + i g scaling and accumulation (48 mul 52 add); momentum
+        # Q (4 len add); (Qslash + m) (48 mul 52 add); Q^2 - m^2 (5 mul 4 add), m w (1 mul), the
+        # propagator's 1/|d|^2 (2 mul 1 add) and its two components (2 mul); times the spinor (16 mul 8 add)
+        add += nseq(ln) * (52 * ln + 4 * ln + 52 + 4 + 1 + 8)
+        mul += nseq(ln) * (48 * ln + 48 + 5 + 1 + 2 + 2 + 16)
+    # amplitude terms: row x gamma.J, the product with v (16 mul 14 add), i g scaling and sum (2 mul 2 add)
+    add += factorial(k) * k * (44 + 14 + 2)
+    mul += factorial(k) * k * (40 + 16 + 2)
+    return add, mul
+
+
+@pytest.mark.parametrize("ng", [0, 1, 2, 3])
+def test_flop_counter_amplitude_part_hand_count(orc, ng):
+    """The oracle's amplitude counts equal the count derived by hand from the algorithm (every add and
+    multiply of the recursion, exact), for one helicity and for every helicity of a mask: the count
+    scales with the number of good helicities and nothing else."""
+    mom, _, _ = orc.events(ng, 7, 1)
+    add1, mul1 = _hand_amp_count(ng + 2)
+    nhel = 1 << (ng + 4)
+    one = np.zeros((nhel + 31) // 32, dtype=np.uint32)
+    one[0] = 1
+    c1 = orc.flops(ng, mom[0], mask=one)
+    assert (c1["amp"]["add"], c1["amp"]["mul"]) == (add1, mul1)
+    rng = np.random.default_rng(ng)
+    hs = rng.choice(nhel, size=nhel // 3 + 1, replace=False)
+    m = np.zeros_like(one)
+    for h in hs:
+        m[h >> 5] |= np.uint32(1 << (int(h) & 31))
+    c = orc.flops(ng, mom[0], mask=m)
+    assert (c["amp"]["add"], c["amp"]["mul"]) == (len(hs) * add1, len(hs) * mul1)
+    ncol = math.factorial(ng + 2)
+    assert c["colour"]["add"] == c["colour"]["mul"] == len(hs) * (2 * ncol * ncol + 2 * ncol)
+
+
+def test_oracle_flops_golden_is_the_oracles_count(orc):
+    """tests/golden/oracle_flops.txt (the roofline numerator bench.py reads) is what the oracle counts
+    now, and each amplitude count is good helicities x the hand-derived per-helicity count."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("mk", os.path.join(os.path.dirname(__file__), "golden",
+                                                                     "make_oracle_flops.py"))
+    mk = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mk)
+    stored = [ln.split() for ln in open(mk.OUT) if ln.strip() and not ln.startswith("#")]
+    fresh = [[str(x) for x in r] for r in mk.rows()]
+    assert stored == fresh
+    for r in fresh:
+        ng, good, add, mul = int(r[1]), int(r[2]), int(r[3]), int(r[4])
+        a1, m1 = _hand_amp_count(ng + 2)
+        assert (add, mul) == (good * a1, good * m1)
