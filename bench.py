@@ -255,7 +255,7 @@ MODES = (("fp64", 0), ("fp32_amp", 1), ("fp64_tccolor", 2), ("mixed", 3))
 # timed steps of a process leg at most (a five-gluon FP64 step takes about a second)
 LEG_STEPS = {"ggtt": 20, "ggttg": 20, "ggttgg": 5, "ggttggg": 3}
 # events of the autotuner's probe batch per process
-TUNE_EVENTS = {"ggtt": 16384, "ggttg": 65536, "ggttgg": 16384, "ggttggg": 4096}
+TUNE_EVENTS = {"ggtt": 16384, "ggttg": 65536, "ggttgg": 65536, "ggttggg": 8192}
 ORACLE_FLOPS = os.path.join(ROOT, "tests", "golden", "oracle_flops.txt")
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_TC_TFLOPS = 1900.0

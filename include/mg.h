@@ -203,6 +203,47 @@ mg_status mg_flops_per_event_shape(mg_process proc, mg_precision precision, cons
 mg_status mg_sigmakin_noalloc(mg_ctx* ctx, const double* mom_dev, int64_t nevt, double* me_dev, void* stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Event-level epilogues (the paper's Sec. 4: event-by-event helicities and leading colours are the two
+ * pieces its GPU matrix elements still lacked for unweighted-event (LHE) files; Sec. 2: the running of
+ * the QCD coupling alpha_s is a feature the engine gained).  FP64 matrix elements.
+ * --------------------------------------------------------------------------------------------- */
+
+/* FP64 matrix elements (as mg_sigmakin(..., MG_FP64, ...), summed over the good helicities in ascending
+ * helicity index) with, per event e:
+ *   - hel_dev[e] (if not NULL): the helicity chosen with probability |M_h|^2 / sum_h' |M_h'|^2 -- the
+ *     smallest good h whose running sum over good helicities (ascending h) of the colour-summed |M_h|^2
+ *     exceeds rnd_hel_dev[e] times the total; index convention of this header;
+ *   - col_dev[e] (if not NULL): the leading-colour flow chosen with probability w_sigma / sum w, where
+ *     w_sigma = sum over good helicities of |J_sigma(h)|^2 (the colour-ordered amplitude of flow sigma,
+ *     the lexicographic rank of the gluon ordering along the quark line, see mg_colour_flow) -- the
+ *     smallest sigma whose running sum of w exceeds rnd_col_dev[e] times the total;
+ *   - running_alphas = 1: the matrix element at the one-loop running coupling alpha_s(mu_e), mu_e = H_T/2
+ *     (half the sum over t, tbar and the final-state gluons of sqrt(m^2 + px^2 + py^2)),
+ *     alpha_s(mu) = a / (1 + a b0 ln(mu^2 / M_Z^2)), a = params.alphas taken as alpha_s(M_Z),
+ *     M_Z = 91.1876 GeV, b0 = (33 - 2 n_f)/(12 pi), n_f = 5 -- i.e. the fixed-coupling matrix element
+ *     times (alpha_s(mu_e)/a)^(n_g+2), every tree diagram carrying g_s^(n_g+2); running_alphas = 0: the
+ *     fixed coupling params.alphas.  alphas_dev[e] (if not NULL) receives the coupling used.
+ * rnd_hel_dev / rnd_col_dev: caller-supplied uniform numbers in [0, 1), one per event (device, FP64;
+ * needed when the matching output is requested, else MG_EINVAL).  hel_dev / col_dev: int32 per event.
+ * Every buffer holds nevt entries.  Zero top width only (MG_ENOTSUP otherwise).  Scratch: per-slot sums of
+ * |J_sigma|^2 (events processed in chunks that keep it within 1 GiB), owned by the context.  If no helicity
+ * mask exists yet, the call first runs mg_hel_filter on its own first events. */
+mg_status mg_sigmakin_lhe(mg_ctx* ctx, const double* mom_dev, int64_t nevt, const double* rnd_hel_dev,
+                          const double* rnd_col_dev, int running_alphas, double* me_dev, int* hel_dev, int* col_dev,
+                          double* alphas_dev, void* stream);
+
+/* Running coupling for matrix elements of any precision mode, in place: me_dev[e] *= (alpha_s(mu_e)/a)^(n_g+2)
+ * with mu_e, alpha_s(mu) and a as in mg_sigmakin_lhe; alphas_dev (may be NULL) receives alpha_s(mu_e).
+ * mom_dev: the events' AoSoA momenta. */
+mg_status mg_alphas_running(mg_ctx* ctx, const double* mom_dev, int64_t nevt, double* me_dev, double* alphas_dev,
+                            void* stream);
+
+/* The gluon ordering of colour flow `flow` (0 <= flow < (n_g+2)!): order[i] = gluon label (0 = g1, 1 = g2,
+ * 2.. = final-state gluons g3..) at position i along the quark line, flow = lexicographic rank of the
+ * permutation; the flow's colour factor is (T^{a_order[0]} ... T^{a_order[K-1]})_{i_t j_tbar}.  Host only. */
+mg_status mg_colour_flow(mg_process proc, int flow, int* order);
+
+/* ---------------------------------------------------------------------------------------------
  * Launch-shape autotuner and CUDA-graph batches (no counterpart in the paper; its Sec. 4 and
  * Fig. 2 show the throughput depending on how many events one launch holds).
  * --------------------------------------------------------------------------------------------- */

@@ -84,6 +84,9 @@ def lib():
     L.mg_sigmakin.argtypes = [vp, vp, i64, i32, vp, vp]
     L.mg_sigmakin_host.argtypes = [vp, vp, i64, i32, vp, vp]
     L.mg_sigmakin_noalloc.argtypes = [vp, vp, i64, vp, vp]
+    L.mg_sigmakin_lhe.argtypes = [vp, vp, i64, vp, vp, i32, vp, vp, vp, vp, vp]
+    L.mg_alphas_running.argtypes = [vp, vp, i64, vp, vp, vp]
+    L.mg_colour_flow.argtypes = [i32, i32, P(i32)]
     L.mg_hel_mask.argtypes = [vp, P(ctypes.c_uint32), P(i32)]
     L.mg_check.argtypes = [vp, vp, P(ctypes.c_int64)]
     L.mg_flops_per_event.argtypes = [i32, i32, P(ctypes.c_uint32), P(dbl), P(dbl)]
@@ -115,7 +118,8 @@ def lib():
         getattr(L, name).restype = i32
     for name in ("mg_process_info", "mg_colour_matrix", "mg_create", "mg_philox", "mg_rambo", "mg_rambo_range",
                  "mg_measure_fma_peak", "mg_hel_filter",
-                 "mg_sigmakin", "mg_sigmakin_host", "mg_sigmakin_noalloc", "mg_hel_mask", "mg_check", "mg_flops_per_event",
+                 "mg_sigmakin", "mg_sigmakin_host", "mg_sigmakin_noalloc", "mg_sigmakin_lhe", "mg_alphas_running",
+                 "mg_colour_flow", "mg_hel_mask", "mg_check", "mg_flops_per_event",
                  "mg_flops_per_event_shape"):
         getattr(L, name).restype = i32
     _lib = L
@@ -187,6 +191,14 @@ def colour_matrix(process):
     _check(lib().mg_colour_matrix(_proc(process), num.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                   ctypes.byref(den)), "mg_colour_matrix")
     return num, den.value
+
+
+def colour_flow(process, flow):
+    """Gluon labels along the quark line of colour flow `flow` (mg_colour_flow)."""
+    n = process_info(process)["npar"] - 2
+    out = (ctypes.c_int * n)()
+    _check(lib().mg_colour_flow(_proc(process), flow, out), "mg_colour_flow")
+    return list(out)
 
 
 def flops_per_event(process, mask=None, precision=MG_FP64, flags=None):
@@ -293,6 +305,18 @@ class Context:
     def sigmakin_noalloc(self, mom, nevt, me, stream=None):
         """FP64 MEs without any device allocation (fixed 16 MiB library scratch; see mg.h)."""
         _check(lib().mg_sigmakin_noalloc(self._h, _ptr(mom), nevt, _ptr(me), _stream(stream)), "mg_sigmakin_noalloc")
+
+    def sigmakin_lhe(self, mom, nevt, me, rnd_hel=None, rnd_col=None, hel=None, col=None, running_alphas=False,
+                     alphas=None, stream=None):
+        """FP64 MEs with the per-event helicity and leading-colour choices (int32 outputs, from the
+        caller's uniforms) and optionally the one-loop running coupling at mu = H_T/2 (see mg.h)."""
+        _check(lib().mg_sigmakin_lhe(self._h, _ptr(mom), nevt, _ptr(rnd_hel), _ptr(rnd_col), 1 if running_alphas else 0,
+                                     _ptr(me), _ptr(hel), _ptr(col), _ptr(alphas), _stream(stream)), "mg_sigmakin_lhe")
+
+    def alphas_running(self, mom, nevt, me, alphas=None, stream=None):
+        """In place: me[e] *= (alpha_s(H_T/2)/alpha_s)^(n_g+2), one-loop running (see mg.h)."""
+        _check(lib().mg_alphas_running(self._h, _ptr(mom), nevt, _ptr(me), _ptr(alphas), _stream(stream)),
+               "mg_alphas_running")
 
     def autotune(self, precision=MG_FP64, nevt=65536, cache_path=None):
         """Pick the fastest launch shape of the ME kernel for this context; returns (tile_ev, slot_major, ms)."""

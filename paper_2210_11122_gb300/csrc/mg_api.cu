@@ -48,7 +48,11 @@ mg_status grow(double** buf, int64_t* cap, int64_t need) {
 // helicity combination with a good helicity; per thread the gluon currents once, (gamma.J) v per
 // antitop helicity, a depth-first walk of the quark-line prefixes per top helicity, the jamps and
 // the colour sum per good helicity.  mask == NULL means every helicity is good.
-void flop_model(const mg::Tables& t, const uint32_t* mask, bool fp32, bool shared, double* amp, double* col) {
+// warp_simt: the FP32 lane-group kernel's SIMT colour epilogue, which multiplies the full ncol x ncol matrix
+// into the jamps of all four helicities of a slot (4 ncol^2 + 4 ncol each, good or not) instead of the
+// packed triangle per good helicity.
+void flop_model(const mg::Tables& t, const uint32_t* mask, bool fp32, bool shared, bool warp_simt, double* amp,
+                double* col) {
   const int K = t.K, nsub = 1 << K, npar = K + 2;
   // three-gluon vertex in the current-conserving form: d (4) + JL.JR (30) + JL.PR, JR.PL (2 x 14) +
   // two scalings (4) + 4 x (real-complex and two complex multiply-adds) (80)
@@ -92,7 +96,10 @@ void flop_model(const mg::Tables& t, const uint32_t* mask, bool fp32, bool share
     a += per_slot;
     for (int top = 0; top < 2; ++top)
       if (good[2 * top] || good[2 * top + 1]) a += walk;
-    for (int k = 0; k < 4; ++k) c += good[k] ? colour : 0.0;
+    if (warp_simt)
+      c += 4.0 * (4.0 * t.ncol * t.ncol + 4.0 * t.ncol);
+    else
+      for (int k = 0; k < 4; ++k) c += good[k] ? colour : 0.0;
   }
   *amp = a;
   *col = c;
@@ -259,7 +266,11 @@ mg_status mg_flops_per_event_shape(mg_process proc, mg_precision precision, cons
   // the currents of fewer than all gluons between gluon-helicity combinations for 1 and 3 final-state gluons
   const int K = mg::gluons_of(proc);
   const bool shared = flags < 0 ? (K == 3 || K == 5) : (flags & MG_LAUNCH_SHARED) != 0;
-  flop_model(*t, mask, fp32, !fp32 && shared, &a, &c);
+  // the lane-group kernel (FP32 amplitudes, 3..5 gluons; the default for 4 and 5) with its SIMT colour
+  // epilogue: MG_FP32_AMP, or MG_MIXED whose colour sums then run on the tensor cores (not counted here)
+  const bool warp = flags < 0 ? K >= 4 : (flags & MG_LAUNCH_WARP) != 0;
+  const bool warp_simt = precision == MG_FP32_AMP && warp && mg::me_warp_available(K, true);
+  flop_model(*t, mask, fp32, !fp32 && shared, warp_simt, &a, &c);
   delete t;
   if (amp_flops) *amp_flops = a;
   if (colour_flops) *colour_flops = c;
@@ -299,6 +310,7 @@ void mg_destroy(mg_ctx* ctx) {
   cudaFree(ctx->d_nrepair);
   cudaFree(ctx->d_flag);
   cudaFree(ctx->d_share);
+  cudaFree(ctx->d_j2);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->side) cudaStreamDestroy(ctx->side);

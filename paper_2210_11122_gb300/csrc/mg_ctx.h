@@ -39,6 +39,8 @@ struct mg_ctx {
   int* d_nrepair = nullptr;
   uint8_t* d_flag = nullptr;  // FP32 modes: 1 for the events in d_repair (the FP32 launches skip them)
   int64_t repair_cap = 0;
+  double* d_j2 = nullptr;      // mg_sigmakin_lhe: per-slot sums of |jamp|^2 over good helicities (one chunk)
+  int64_t j2_cap = 0;         // in doubles
   double* d_share = nullptr;   // FP64: currents shared between gluon-helicity combinations (one chunk of events)
   int64_t share_cap = 0;      // in doubles
   cudaStream_t side = nullptr;         // FP32 modes: the FP64 recomputation runs here, beside the FP32 launches

@@ -18,15 +18,20 @@ namespace v2 {
 // are not computed here but read from share, where k_share_level left them once per helicity
 // assignment of their own gluons (item tab->share_base[s] + helicity bits of s's gluons, 24 doubles:
 // J, then (gamma.J) v for both antitop helicities).
-template <int K, class T, bool PER_HEL, bool PREP, bool JOUT, bool SHARED = false>
+// LHE (FP64 with a per-event record, for the event-level epilogues): the colour sum of every helicity of
+// the slot in its own row, out[(slot * 4 + 2 top + antitop) * stride + e] (zero for helicities outside
+// the mask), and the slot's sum over its good helicities of every |jamp|^2,
+// j2[(slot * ncol + sigma) * stride + e].
+template <int K, class T, bool PER_HEL, bool PREP, bool JOUT, bool SHARED = false, bool LHE = false>
 __global__ void __launch_bounds__(kMeThreads)
 k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab,
               const int* __restrict__ gslots, const int* __restrict__ nslot_dev, const uint32_t* __restrict__ mask,
               const typename ColourT<T>::type* __restrict__ ctri, MeConst cst, double* __restrict__ out, int64_t stride,
               float2* __restrict__ jout, int tile_ev, int slot_major, const int* __restrict__ evlist,
               const int* __restrict__ nlist, int rows_out, const uint8_t* __restrict__ skip,
-              const double* __restrict__ share = nullptr) {
+              const double* __restrict__ share = nullptr, double* __restrict__ j2 = nullptr) {
   static_assert(!SHARED || (PREP && std::is_same<T, double>::value), "shared currents: FP64 with a record");
+  static_assert(!LHE || (PREP && !PER_HEL && !JOUT && std::is_same<T, double>::value), "LHE rows: FP64 with a record");
   constexpr int npar = K + 2;
   constexpr int NSEQ = Sizes<K>::nseq;
   constexpr int NCOL = Sizes<K>::ncol;
@@ -160,6 +165,9 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
   const int bit_t = 1 << (npar - 3), bit_tb = 1 << (npar - 4);
 
   double total = 0.0;
+  double jsum[LHE ? NCOL : 1];
+  if constexpr (LHE)
+    for (int c = 0; c < NCOL; ++c) jsum[c] = 0.0;
   for (int a = 0; a < 2; ++a) {
     const int h0 = hbase | (a ? bit_t : 0), h1 = h0 | bit_tb;
     const bool good0 = PER_HEL || ((mask[h0 >> 5] >> (h0 & 31)) & 1u);
@@ -168,6 +176,10 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
       if (JOUT) {
         float2* row = jout + (e * (4 << K) + slot * 4 + 2 * a) * NCOL;
         for (int c = 0; c < 2 * NCOL; ++c) row[c] = make_float2(0.f, 0.f);
+      }
+      if (LHE) {
+        out[(slot * 4 + 2 * a) * stride + e] = 0.0;
+        out[(slot * 4 + 2 * a + 1) * stride + e] = 0.0;
       }
       continue;
     }
@@ -230,16 +242,26 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
       for (int b = 0; b < 2; ++b) {
         const int h = b ? h1 : h0;
         const bool good = b ? good1 : good0;
-        if (!good) continue;
+        if (!good) {
+          if (LHE) out[(slot * 4 + 2 * a + b) * stride + e] = 0.0;
+          continue;
+        }
         double v;
         if constexpr (std::is_same<T, dd::df>::value)
           v = static_cast<double>(colour_sum_hi<NCOL>(A[b], ctri)) * cst.colour_scale;
         else
           v = static_cast<double>(colour_sum<NCOL, T>(A[b], ctri)) * cst.colour_scale;
         if (PER_HEL) out[h * stride + e] = v;
+        else if (LHE) out[(slot * 4 + 2 * a + b) * stride + e] = v;
         else total += v;
+        if constexpr (LHE)
+          for (int c = 0; c < NCOL; ++c) jsum[c] = fma(A[b][c].r, A[b][c].r, fma(A[b][c].i, A[b][c].i, jsum[c]));
       }
     }
+  }
+  if constexpr (LHE) {
+    for (int c = 0; c < NCOL; ++c) j2[(static_cast<int64_t>(slot) * NCOL + c) * stride + e] = jsum[c];
+    return;
   }
   if (!PER_HEL && !JOUT) {
     if (rows_out) {   // tensor-core row layout: slot*4 + (2 top + antitop); the slot total in the first row

@@ -156,3 +156,14 @@ def test_serve_footprint_host(mg):
         assert ftc - f64 == n * nhel * ncol * 8
         assert mg.serve_footprint(proc, 1000, mg.MG_FP64) > f64
     assert mg.serve_footprint(9, 10, 0) == -1
+
+
+def test_colour_flow_is_the_lexicographic_permutation(mg):
+    """Colour flow index = lexicographic rank of the gluon ordering along the quark line (the jamp index
+    of mg_sigmakin_lhe's colour choice); out-of-range flows are rejected."""
+    from itertools import permutations
+    for proc, k in (("ggtt", 2), ("ggttg", 3), ("ggttgg", 4), ("ggttggg", 5)):
+        for c, perm in enumerate(permutations(range(k))):
+            assert mg.colour_flow(proc, c) == list(perm)
+        with pytest.raises(mg.MGError):
+            mg.colour_flow(proc, len(list(permutations(range(k)))))
