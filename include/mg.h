@@ -131,8 +131,10 @@ mg_status mg_rambo_range(mg_ctx* ctx, uint64_t seed, int64_t e0, int64_t nevt, d
                          double* wgt_dev, void* stream);
 
 /* Helicity filter: recompute the context's helicity mask from the first min(nevt, hel_warmup)
- * events of mom_dev (AoSoA).  good(h) <=> max_e |M_h|^2 / sum_h' |M_h'|^2 > hel_tau, evaluated in
- * FP64.  Stream-ordered; the mask is used by every later mg_sigmakin on this context. */
+ * events of mom_dev (AoSoA).  good(h) <=> max_e |M_h|^2 / sum_h' |M_h'|^2 > hel_tau, the ratios taken in
+ * FP64 from FP32-amplitude colour sums (zero top width; FP64 otherwise): with the default hel_tau the kept
+ * and the vanishing helicities of these processes are at least six decades apart, so FP32 rounding cannot
+ * change the mask.  Stream-ordered; the mask is used by every later mg_sigmakin on this context. */
 mg_status mg_hel_filter(mg_ctx* ctx, const double* mom_dev, int64_t nevt, void* stream);
 
 /* Matrix elements: me_dev[e] = ME of event e of mom_dev (AoSoA), e < nevt.  If no helicity mask
@@ -155,9 +157,10 @@ mg_status mg_sigmakin_host(mg_ctx* ctx, const double* mom_host, int64_t nevt, mg
  * number of good helicities to *ngood.  Synchronises the context's last stream. */
 mg_status mg_hel_mask(mg_ctx* ctx, uint32_t* mask_host, int* ngood);
 
-/* Wait for the context's work on stream and report device-side conditions: MG_ENOCONV if any
+/* Wait for the context's work on stream and report device-side conditions: MG_ETIMEOUT if a bounded
+ * wait inside the tensor-memory colour kernel gave up (its results are then invalid), MG_ENOCONV if any
  * event since the last mg_check failed to converge in RAMBO (the count goes to *nbad if not
- * NULL), MG_ECUDA on an asynchronous CUDA error, else MG_OK.  Clears the condition. */
+ * NULL), MG_ECUDA on an asynchronous CUDA error, else MG_OK.  Clears the conditions. */
 mg_status mg_check(mg_ctx* ctx, void* stream, int64_t* nbad);
 
 /* Floating-point operations of one event's matrix element in this engine's algorithm for the given
@@ -268,13 +271,17 @@ mg_status mg_colour_flow(mg_process proc, int flow, int* order);
  *   MG_LAUNCH_SHARED    MG_FP64: the gluon currents of fewer than all gluons (and their products with the
  *                       antitop spinors) are computed once per helicity assignment of their own gluons, by
  *                       a pass before the matrix-element kernel, instead of once per gluon-helicity
- *                       combination. */
+ *                       combination;
+ *   MG_LAUNCH_TC_SYNC   the separate tensor-core colour pass (MG_FP64_TCCOLOR, and MG_MIXED where the jamps
+ *                       are written out) on warp-level mma.sync instead of the default fifth-generation
+ *                       tensor-core kernel (tcgen05.mma with the accumulators in tensor memory). */
 #define MG_LAUNCH_UNROLLED 1
 #define MG_LAUNCH_DF_REDO 2
 #define MG_LAUNCH_FUSED 4
 #define MG_LAUNCH_WARP 8
 #define MG_LAUNCH_TC_APART 16
 #define MG_LAUNCH_SHARED 32
+#define MG_LAUNCH_TC_SYNC 64
 
 /* Time mg_sigmakin(precision) of nevt probe events (this context's process, fixed seed) for each
  * launch shape of the matrix-element kernel -- 32, 64 or 128 events per 128-thread block (the other
@@ -333,7 +340,9 @@ void mg_graph_destroy(mg_graph* g);
  * Serving: continuous batching of matrix-element requests (no counterpart in the paper, which runs
  * one batch at a time; the paper's Sec. 4 notes that 8k-event batches underfill a GPU).
  * A request (process, seed, nevt) returns the MEs of events 0..nevt-1 of the seed's Philox stream
- * (mg_rambo_range + mg_hel_filter on the request's own first events + mg_sigmakin).  A scheduler
+ * (mg_rambo_range + mg_sigmakin) with the server's resident helicity mask of the process: computed once,
+ * when the server is created, by mg_hel_filter on the first params.hel_warmup events of Philox seed
+ * MG_SERVE_MASK_SEED (at cfg.sqrts), and shared by every slot.  A scheduler
  * thread admits queued requests in FIFO order when a slot is free and the sum of the in-flight
  * requests' device footprints (mg_serve_footprint) stays within hbm_cap_bytes; each slot is a CUDA
  * stream with its own pre-reserved contexts and buffers, so admitted requests run concurrently on
@@ -350,6 +359,9 @@ typedef struct {
 } mg_serve_cfg;
 
 typedef struct mg_server mg_server;
+
+/* Philox seed of the warm-up events from which a server computes its helicity masks. */
+#define MG_SERVE_MASK_SEED 0x4D47u
 
 void mg_serve_default_cfg(mg_serve_cfg* cfg);
 

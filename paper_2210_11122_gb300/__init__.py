@@ -18,6 +18,8 @@ MG_GG_TT, MG_GG_TTG, MG_GG_TTGG, MG_GG_TTGGG = 0, 1, 2, 3
 PROCESSES = {"ggtt": 0, "ggttg": 1, "ggttgg": 2, "ggttggg": 3}
 MG_FP64, MG_FP32_AMP, MG_FP64_TCCOLOR, MG_MIXED = 0, 1, 2, 3
 LAUNCH_UNROLLED, LAUNCH_DF_REDO, LAUNCH_FUSED, LAUNCH_WARP, LAUNCH_TC_APART, LAUNCH_SHARED = 1, 2, 4, 8, 16, 32
+LAUNCH_TC_SYNC = 64
+SERVE_MASK_SEED = 0x4D47   # mg.h MG_SERVE_MASK_SEED
 PAGE = 32
 
 STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "MG_ENOCONV", 5: "MG_EAGAIN",

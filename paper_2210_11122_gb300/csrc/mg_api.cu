@@ -180,6 +180,20 @@ mg_status ctx_reserve(mg_ctx* ctx, int64_t nevt, mg_precision precision) {
   return s;
 }
 
+mg_status ctx_copy_mask(mg_ctx* dst, const mg_ctx* src, cudaStream_t st) {
+  if (!dst || !src || dst->proc != src->proc) return MG_EINVAL;
+  auto cp = [&](void* d, const void* s, size_t n) {
+    return cudaMemcpyAsync(d, s, n, cudaMemcpyDeviceToDevice, st) == cudaSuccess;
+  };
+  const bool ok = cp(dst->d_mask, src->d_mask, 4 * sizeof(uint32_t)) && cp(dst->d_good, src->d_good, 128 * sizeof(int)) &&
+                  cp(dst->d_ngood, src->d_ngood, sizeof(int)) && cp(dst->d_maxr, src->d_maxr, 128 * sizeof(double)) &&
+                  cp(dst->d_gslots, src->d_gslots, 32 * sizeof(int)) && cp(dst->d_ngslots, src->d_ngslots, sizeof(int)) &&
+                  cp(dst->d_nrows, src->d_nrows, sizeof(int));
+  if (!ok) { cudaGetLastError(); return MG_ECUDA; }
+  dst->mask_ready = true;
+  return MG_OK;
+}
+
 // Device bytes one sigmakin call of nevt events touches (momenta, MEs, scratch): the serving
 // loop's admission footprint.
 int64_t footprint_bytes(mg_process proc, int64_t nevt, mg_precision precision) {
@@ -300,6 +314,8 @@ void mg_destroy(mg_ctx* ctx) {
   cudaFree(ctx->d_allg);
   cudaFree(ctx->d_nrows);
   cudaFree(ctx->d_cmat);
+  cudaFree(ctx->d_cumma);
+  cudaFree(ctx->d_tcerr);
   cudaFree(ctx->d_jamps);
   cudaFree(ctx->d_nallg);
   cudaFree(ctx->d_nbad);
@@ -383,6 +399,14 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
     {
       std::vector<uint16_t> halves(mg::colour_tc_cmat_halves(c->ncol));
       mg::colour_tc_pack(c->ncol, num.data(), halves.data());
+      std::vector<uint16_t> uh(mg::colour_umma_halves(c->ncol));
+      mg::colour_umma_pack(c->ncol, num.data(), uh.data());
+      if (cudaMalloc(&c->d_cumma, uh.size() * sizeof(uint16_t)) != cudaSuccess ||
+          cudaMemcpy(c->d_cumma, uh.data(), uh.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMalloc(&c->d_tcerr, sizeof(int)) != cudaSuccess || cudaMemset(c->d_tcerr, 0, sizeof(int)) != cudaSuccess) {
+        st = MG_ENOMEM;
+        break;
+      }
       if (cudaMalloc(&c->d_cmat, halves.size() * sizeof(uint16_t)) != cudaSuccess ||
           cudaMemcpy(c->d_cmat, halves.data(), halves.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess ||
           cudaMalloc(&c->d_nrows, sizeof(int)) != cudaSuccess || cudaMemset(c->d_nrows, 0, sizeof(int)) != cudaSuccess) {
@@ -487,7 +511,10 @@ mg_status mg_hel_filter(mg_ctx* ctx, const double* mom_dev, int64_t nevt, void* 
   ctx->last = st;
   const mg::MeConst cst = me_const(ctx);
   if (ctx->prm.wt == 0.0) {
-    MG_CUDA(mg::launch_me_gluonhel(ctx->K, false, true, mom_dev, nullptr, w, ctx->d_tab, ctx->d_allg, 1 << ctx->K,
+    // FP32 amplitudes: the accepted and rejected helicities' ratios are at least six decades apart (the
+    // kept ones >= 1e-6, the vanishing ones <= 1e-25 in FP64), far more than FP32 rounding can move a
+    // ratio, so the mask is the one FP64 gives, at the FP32 pipe's rate
+    MG_CUDA(mg::launch_me_gluonhel(ctx->K, true, true, mom_dev, nullptr, w, ctx->d_tab, ctx->d_allg, 1 << ctx->K,
                                    ctx->d_nallg, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, stride, st));
   } else {
     MG_CUDA(mg::launch_me_helicity(ctx->K, false, mom_dev, w, ctx->d_tab, ctx->d_allhel, ctx->nhel, ctx->d_nhel,
@@ -605,8 +632,12 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
         MG_CUDA(mg::launch_me_gluonhel(ctx->K, fp32, false, mom_c, ctx->d_prep, n, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
                                        ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, cst_stride,
                                        st, ctx->d_jamps, ctx->shape[precision], fp32 ? ctx->d_flag : nullptr));
-      MG_CUDA(mg::launch_colour_tc(ctx->ncol, ctx->d_jamps, n, ctx->nhel, ctx->d_nrows, ctx->d_cmat, cst.colour_scale,
-                                   ctx->d_part, cst_stride, st, fp32 ? ctx->d_flag : nullptr));
+      if (ctx->shape[precision].tc_sync)
+        MG_CUDA(mg::launch_colour_tc(ctx->ncol, ctx->d_jamps, n, ctx->nhel, ctx->d_nrows, ctx->d_cmat, cst.colour_scale,
+                                     ctx->d_part, cst_stride, st, fp32 ? ctx->d_flag : nullptr));
+      else
+        MG_CUDA(mg::launch_colour_umma(ctx->ncol, ctx->d_jamps, n, ctx->nhel, ctx->d_nrows, ctx->d_cumma, cst.colour_scale,
+                                       ctx->d_part, cst_stride, st, fp32 ? ctx->d_flag : nullptr, ctx->d_tcerr));
       if (fp32) MG_CUDA(join_repair(ctx, st));
       MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_nrows, n, cst_stride, norm, me_dev + e0, st));
     }
@@ -747,9 +778,13 @@ mg_status mg_check(mg_ctx* ctx, void* stream, int64_t* nbad) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (cudaStreamSynchronize(st) != cudaSuccess) { cudaGetLastError(); return MG_ECUDA; }
   unsigned long long n = 0;
+  int tcerr = 0;
   MG_CUDA(cudaMemcpy(&n, ctx->d_nbad, sizeof(n), cudaMemcpyDeviceToHost));
   MG_CUDA(cudaMemset(ctx->d_nbad, 0, sizeof(n)));
+  MG_CUDA(cudaMemcpy(&tcerr, ctx->d_tcerr, sizeof(int), cudaMemcpyDeviceToHost));
+  MG_CUDA(cudaMemset(ctx->d_tcerr, 0, sizeof(int)));
   if (nbad) *nbad = static_cast<int64_t>(n);
+  if (tcerr) return MG_ETIMEOUT;
   return n ? MG_ENOCONV : MG_OK;
 }
 

@@ -283,6 +283,331 @@ cudaError_t launch_tc(const float2* jamps, int64_t nevt, int rows_alloc, const i
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------------------------------
+// The same colour sums on the fifth-generation tensor cores (tcgen05.mma, accumulators in tensor memory).
+//
+// One persistent CTA of 8 warps per SM walks "stages" of VECS = 64 S jamp vectors (128 S real rows, S
+// M=128 MMA tiles; S NP = 128 accumulator columns in TMEM, NP = the padded colour count):
+//   1. the stage's FP32 jamps, prefetched into registers with coalesced 16-byte loads during the previous
+//      stage, go to a padded staging buffer in shared memory (row pitch 2 NCOL + 2 floats: the per-row
+//      accesses below are free of bank conflicts);
+//   2. each row (real or imaginary part of one vector) is scaled by a power of two to max |t| in
+//      [1/2, 1) and split t = hi + lo (two FP16 values, lo = fp16(t - hi) keeps t to ~2^-24 absolute),
+//      written as the MMA's A operand in the no-swizzle K-major layout (8-row x 16-byte core matrices,
+//      k-chunks 128 bytes apart, 8-row groups 16 (K/8) + 16 bytes apart: the extra 16 bytes spread the
+//      16-byte stores of the 32 lanes, each a different vector, evenly over the banks);
+//   3. one thread issues S x (K/16) x 2 MMAs (M = 128, N = NP, K = 16; hi, then lo, into the same FP32
+//      accumulator: Y = C hi + C lo) against the exact integer colour matrix C (FP16, resident in shared
+//      memory for the whole kernel) and commits them to an mbarrier;
+//   4. the 8 warps read Y back (tcgen05.ld, warp w: TMEM lanes 32 (w % 4) .. +31, columns 64 (w / 4) ..
+//      +63) and form each row's quadratic form t . Y with the exact scaled FP32 t from the staging buffer;
+//      the real and imaginary rows of a vector are combined and unscaled exactly, as in k_colour_tc.
+// Every wait is bounded: a wait that gives up records the stage in *err, and the CTA frees its tensor
+// memory and returns.
+template <int NCOL>
+struct Umma {
+  static constexpr int KP = (NCOL + 15) / 16 * 16;   // contraction length padded to the MMA K
+  static constexpr int NP = KP;                       // C is square: N = K (a multiple of 16)
+  static constexpr int S = 128 / NP;                  // MMA tiles per stage: S NP = 128 TMEM columns
+  static constexpr int ROWS = 128 * S;
+  static constexpr int VECS = ROWS / 2;
+  static constexpr int PITCH = 2 * NCOL + 2;          // staging floats per vector
+  static constexpr int CH = (NCOL + 7) / 8;           // 8-element k chunks holding data
+  static constexpr int KC = KP / 8;                   // k chunks per row, padding included
+  static constexpr int SBO_A = KC * 128 + 16;         // bytes between 8-row groups of A
+  static constexpr int SBO_B = KC * 128;              // bytes between 8-row groups of B = C
+  static constexpr int A_BYTES = (ROWS / 8) * SBO_A;  // hi or lo
+  static constexpr int B_BYTES = (NP / 8) * SBO_B;
+  static constexpr int STG_BYTES = VECS * PITCH * 4;
+  static constexpr int F4 = VECS * NCOL * 2 / 4;      // 16-byte pieces of a stage
+  static constexpr int THREADS = 256;
+  static constexpr int PF = (F4 + THREADS - 1) / THREADS;   // prefetched pieces per thread
+  static constexpr int VPL = CH <= 4 ? 32 : 8;        // vectors per warp in the conversion
+  static constexpr int CPL = VPL == 32 ? CH : (CH + 3) / 4;   // k chunks per lane
+  static constexpr int PASSES = VECS / (8 * VPL);
+  // shared memory: A hi | A lo | B | staging | partial sums [2][S][128] | row exponents [S][128] | mbarrier, TMEM address
+  static constexpr int OFF_ALO = (A_BYTES + 1023) / 1024 * 1024;
+  static constexpr int OFF_B = OFF_ALO + (A_BYTES + 1023) / 1024 * 1024;
+  static constexpr int OFF_STG = OFF_B + (B_BYTES + 1023) / 1024 * 1024;
+  static constexpr int OFF_PART = OFF_STG + (STG_BYTES + 15) / 16 * 16;
+  static constexpr int OFF_EXP = OFF_PART + 2 * S * 128 * 4;
+  static constexpr int OFF_BAR = OFF_EXP + S * 128 * 4;
+  static constexpr int SMEM = OFF_BAR + 64 + 1024;    // + 1024: the dynamic buffer is aligned up to 1 KB
+  static constexpr uint32_t IDESC = (1u << 4) | (static_cast<uint32_t>(NP >> 3) << 17) | (static_cast<uint32_t>(128 >> 4) << 24);
+  static_assert(S * NP == 128 && PASSES * 8 * VPL == VECS && (2 * NCOL) % 4 == 0, "stage shape");
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
+
+// shared-memory matrix descriptor, no swizzle: start, leading (k-chunk) and stride (8-row group) byte offsets
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4) | (static_cast<uint64_t>(lbo >> 4) << 16) |
+         (static_cast<uint64_t>(sbo >> 4) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t accum) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accum)
+      : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]),
+        "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+        "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+
+// FP16 bits of hi and lo for one value t (|t| < 1)
+__device__ __forceinline__ void split_bits(float t, uint32_t& hb, uint32_t& lb) {
+  const __half h = __float2half_rn(t);
+  const __half l = __float2half_rn(t - __half2float(h));
+  hb = __half_as_ushort(h);
+  lb = __half_as_ushort(l);
+}
+
+constexpr long long kUmmaSpin = 1ll << 22;   // bounded waits (the MMAs of a stage take about a microsecond)
+
+template <int NCOL>
+__global__ void __launch_bounds__(256, 1)
+k_colour_umma(const float2* __restrict__ jamps, int64_t nevt, int rows_log2, const int* __restrict__ nrows_dev,
+              const uint16_t* __restrict__ cumma, double scale, double* __restrict__ out, int64_t stride,
+              const uint8_t* __restrict__ skip, int* __restrict__ err) {
+  using U = Umma<NCOL>;
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sAhi = smem;
+  unsigned char* sAlo = smem + U::OFF_ALO;
+  unsigned char* sB = smem + U::OFF_B;
+  float* stg = reinterpret_cast<float*>(smem + U::OFF_STG);
+  float* part = reinterpret_cast<float*>(smem + U::OFF_PART);
+  int* rexp = reinterpret_cast<int*>(smem + U::OFF_EXP);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + U::OFF_BAR);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + U::OFF_BAR + 8);
+  int* abort_flag = reinterpret_cast<int*>(smem + U::OFF_BAR + 16);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // operands at rest: A's padding chunks stay zero; C in the canonical layout
+  for (int i = tid; i < (U::OFF_B - 0) / 16; i += U::THREADS) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < U::B_BYTES / 16; i += U::THREADS)
+    reinterpret_cast<uint4*>(sB)[i] = reinterpret_cast<const uint4*>(cumma)[i];
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    *abort_flag = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_addr(tmem_slot)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  const int nrows = *nrows_dev;
+  const int64_t rmask = (int64_t(1) << rows_log2) - 1;
+  const int64_t nvec = nevt << rows_log2;                      // vectors in the buffer
+  const int64_t nstage = (nvec + U::VECS - 1) / U::VECS;
+  const float scale_f = static_cast<float>(scale);
+  auto vec_valid = [&](int64_t q) -> bool {
+    return q < nvec && (q & rmask) < nrows && (!skip || !skip[q >> rows_log2]);
+  };
+
+  float4 pf[U::PF];
+  auto prefetch = [&](int64_t st) {
+    const float4* src = reinterpret_cast<const float4*>(jamps) + st * (U::F4);
+    const int64_t lim = (nvec - st * U::VECS) * (NCOL * 2 / 4);   // pieces left in the buffer
+#pragma unroll
+    for (int j = 0; j < U::PF; ++j) {
+      const int i = tid + U::THREADS * j;
+      pf[j] = (st < nstage && i < U::F4 && i < lim) ? __ldg(src + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  };
+
+  uint32_t phase = 0;
+  int64_t st = blockIdx.x;
+  prefetch(st);
+  for (; st < nstage; st += gridDim.x) {
+    const int64_t q0 = st * U::VECS;
+    // 1. staging <- prefetched registers; prefetch the next stage
+#pragma unroll
+    for (int j = 0; j < U::PF; ++j) {
+      const int i = tid + U::THREADS * j;
+      if (i < U::F4) {
+        const int f = 4 * i, v = f / (2 * NCOL), o = f - v * 2 * NCOL;
+        float* d = stg + v * U::PITCH + o;
+        *reinterpret_cast<float2*>(d) = make_float2(pf[j].x, pf[j].y);
+        *reinterpret_cast<float2*>(d + 2) = make_float2(pf[j].z, pf[j].w);
+      }
+    }
+    prefetch(st + gridDim.x);
+    __syncthreads();
+
+    // 2. rows -> scaled hi/lo FP16 A operand
+#pragma unroll 1
+    for (int pass = 0; pass < U::PASSES; ++pass) {
+      const int v = pass * 8 * U::VPL + warp * U::VPL + (lane % U::VPL);
+      const int b = lane / U::VPL;
+      const bool ok = vec_valid(q0 + v);
+      float2 val[U::CPL][8];
+      float mre = 0.f, mim = 0.f;
+#pragma unroll
+      for (int i = 0; i < U::CPL; ++i) {
+        const int c = U::VPL == 32 ? i : b + 4 * i;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int k = 8 * c + j;
+          float2 x = make_float2(0.f, 0.f);
+          if (ok && c < U::CH && k < NCOL) x = *reinterpret_cast<const float2*>(stg + v * U::PITCH + 2 * k);
+          val[i][j] = x;
+          mre = fmaxf(mre, fabsf(x.x));
+          mim = fmaxf(mim, fabsf(x.y));
+        }
+      }
+      if (U::VPL == 8) {
+        mre = fmaxf(mre, __shfl_xor_sync(0xffffffffu, mre, 8));
+        mre = fmaxf(mre, __shfl_xor_sync(0xffffffffu, mre, 16));
+        mim = fmaxf(mim, __shfl_xor_sync(0xffffffffu, mim, 8));
+        mim = fmaxf(mim, __shfl_xor_sync(0xffffffffu, mim, 16));
+      }
+      int ere = 0, eim = 0;
+      if (mre > 0.f) frexpf(mre, &ere);
+      if (mim > 0.f) frexpf(mim, &eim);
+      const float sre = ldexpf(1.f, -ere), sim = ldexpf(1.f, -eim);
+      if (b == 0) {
+        rexp[2 * v] = ere;
+        rexp[2 * v + 1] = eim;
+      }
+#pragma unroll
+      for (int i = 0; i < U::CPL; ++i) {
+        const int c = U::VPL == 32 ? i : b + 4 * i;
+        if (c >= U::CH) continue;
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          uint32_t hw[4], lw[4];
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            uint32_t h0, l0, h1, l1;
+            split_bits((p ? val[i][2 * j].y : val[i][2 * j].x) * (p ? sim : sre), h0, l0);
+            split_bits((p ? val[i][2 * j + 1].y : val[i][2 * j + 1].x) * (p ? sim : sre), h1, l1);
+            hw[j] = h0 | (h1 << 16);
+            lw[j] = l0 | (l1 << 16);
+          }
+          const int m = 2 * v + p;
+          const int off = (m & 7) * 16 + (m >> 3) * U::SBO_A + c * 128;
+          *reinterpret_cast<uint4*>(sAhi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+          *reinterpret_cast<uint4*>(sAlo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        }
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+
+    // 3. one thread issues the MMAs of the stage
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ahi = smem_addr(sAhi), alo = smem_addr(sAlo), bb = smem_addr(sB);
+#pragma unroll 1
+      for (int s = 0; s < U::S; ++s)
+#pragma unroll 1
+        for (int ks = 0; ks < U::KP / 16; ++ks)
+#pragma unroll
+          for (int hl = 0; hl < 2; ++hl) {
+            const uint32_t a = (hl ? alo : ahi) + s * 16 * U::SBO_A + ks * 256;
+            umma_f16(tmem + s * U::NP, umma_desc(a, 128, U::SBO_A), umma_desc(bb + ks * 256, 128, U::SBO_B), U::IDESC,
+                     (ks | hl) != 0);
+          }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                   : "memory");
+    }
+    // wait for the accumulators (bounded)
+    {
+      long long n = 0;
+      bool done = false;
+      while (!(done = mbar_try_wait(smem_addr(bar), phase)) && ++n < kUmmaSpin) {
+      }
+      if (!done) *abort_flag = 1;
+    }
+    phase ^= 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (*abort_flag) {
+      if (tid == 0) atomicCAS(err, 0, static_cast<int>(st % 1000000) + 1);
+      break;
+    }
+
+    // 4. quadratic forms t . Y (warp: TMEM lane quarter warp % 4, column half warp / 4)
+    {
+      const int qw = warp & 3, hf = warp >> 2;
+      const int m = 32 * qw + lane;                          // row within each MMA tile
+      float acc[U::S], rs[U::S];
+#pragma unroll
+      for (int s = 0; s < U::S; ++s) {
+        acc[s] = 0.f;
+        rs[s] = ldexpf(1.f, -rexp[2 * (64 * s + (m >> 1)) + (m & 1)]);   // the row's power-of-two scale
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        uint32_t y[32];
+        const int c0 = 64 * hf + 32 * h;
+        tmem_ld32(tmem + (static_cast<uint32_t>(32 * qw) << 16) + c0, y);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int c = c0 + j, s = c / U::NP, n = c % U::NP;
+          if (n < NCOL) {
+            const int v = 64 * s + (m >> 1);
+            const float t = stg[v * U::PITCH + 2 * n + (m & 1)] * rs[s];
+            acc[s] = fmaf(t, __uint_as_float(y[j]), acc[s]);
+          }
+        }
+      }
+#pragma unroll
+      for (int s = 0; s < U::S; ++s) part[(hf * U::S + s) * 128 + m] = acc[s];
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp < 4) {
+      const int m = 32 * warp + lane;
+#pragma unroll
+      for (int s = 0; s < U::S; ++s) {
+        const float tot = part[s * 128 + m] + part[(U::S + s) * 128 + m];
+        const int e = rexp[2 * (64 * s + (m >> 1)) + (m & 1)];
+        const float other = __shfl_xor_sync(0xffffffffu, tot, 1);
+        const int eo = __shfl_xor_sync(0xffffffffu, e, 1);
+        if ((m & 1) == 0) {
+          const int64_t q = q0 + 64 * s + (m >> 1);
+          if (vec_valid(q))
+            out[(q & rmask) * stride + (q >> rows_log2)] = combine_rows(tot, 2 * e, other, 2 * eo, scale_f);
+        }
+      }
+    }
+    __syncthreads();   // staging, exponents and partial sums are rewritten by the next stage
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+}
+
 }  // namespace
 
 int colour_tc_cmat_halves(int ncol) {
@@ -323,6 +648,75 @@ cudaError_t launch_colour_tc(int ncol, const float2* jamps, int64_t nevt, int ro
     case 6: return launch_tc<6>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, st);
     case 24: return launch_tc<24>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, st);
     case 120: return launch_tc<120>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+
+// ---- tensor-memory (tcgen05) colour kernel: host side ----
+int colour_umma_halves(int ncol) {
+  switch (ncol) {
+    case 2: return Umma<2>::B_BYTES / 2;
+    case 6: return Umma<6>::B_BYTES / 2;
+    case 24: return Umma<24>::B_BYTES / 2;
+    case 120: return Umma<120>::B_BYTES / 2;
+    default: return 0;
+  }
+}
+
+// C (integer numerators) as the MMA's B operand: no-swizzle K-major canonical layout, element (n, k) at
+// byte (n % 8) 16 + (n / 8) SBO_B + (k / 8) 128 + (k % 8) 2, zero padding up to NP x KP.
+void colour_umma_pack(int ncol, const int64_t* num, uint16_t* out_halves) {
+  const int total = colour_umma_halves(ncol);
+  if (!total) return;
+  const int kp = (ncol + 15) / 16 * 16, sbo = kp / 8 * 128;
+  for (int i = 0; i < total; ++i) out_halves[i] = 0;
+  for (int n = 0; n < ncol; ++n)
+    for (int k = 0; k < ncol; ++k) {
+      const int byte = (n % 8) * 16 + (n / 8) * sbo + (k / 8) * 128 + (k % 8) * 2;
+      out_halves[byte / 2] = __half_as_ushort(__float2half_rn(static_cast<float>(num[static_cast<size_t>(n) * ncol + k])));
+    }
+}
+
+template <int NCOL>
+static cudaError_t launch_umma(const float2* jamps, int64_t nevt, int rows_alloc, const int* nrows, const uint16_t* cumma,
+                               double scale, double* out, int64_t stride, const uint8_t* skip, int* err, cudaStream_t st) {
+  using U = Umma<NCOL>;
+  int rows_log2 = 0;
+  while ((1 << rows_log2) < rows_alloc) ++rows_log2;
+  if ((1 << rows_log2) != rows_alloc) return cudaErrorInvalidValue;
+  int dev = 0, nsm = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  static std::atomic<unsigned long long> configured{0};
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(configured.load(std::memory_order_acquire) & bit)) {
+    cudaError_t e = cudaFuncSetAttribute(k_colour_umma<NCOL>, cudaFuncAttributeMaxDynamicSharedMemorySize, U::SMEM);
+    if (e != cudaSuccess) return e;
+    configured.fetch_or(bit, std::memory_order_release);
+  }
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_colour_umma<NCOL>, U::THREADS, U::SMEM) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  if (per_sm > 4) per_sm = 4;   // 4 x 128 TMEM columns per SM
+  const int64_t nstage = ((nevt << rows_log2) + U::VECS - 1) / U::VECS;
+  int64_t blocks = static_cast<int64_t>(nsm) * per_sm;
+  if (blocks > nstage) blocks = nstage;
+  if (blocks < 1) return cudaSuccess;
+  { k_colour_umma<NCOL><<<static_cast<unsigned>(blocks), U::THREADS, U::SMEM, st>>>(jamps, nevt, rows_log2, nrows, cumma, scale,
+                                                                                  out, stride, skip, err); mg::note_launch(); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_colour_umma(int ncol, const float2* jamps, int64_t nevt, int rows_alloc, const int* nrows,
+                               const void* cumma, double scale, double* out, int64_t stride, cudaStream_t st,
+                               const uint8_t* skip, int* err) {
+  const uint16_t* c = static_cast<const uint16_t*>(cumma);
+  switch (ncol) {
+    case 2: return launch_umma<2>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, err, st);
+    case 6: return launch_umma<6>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, err, st);
+    case 24: return launch_umma<24>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, err, st);
+    case 120: return launch_umma<120>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, err, st);
     default: return cudaErrorInvalidValue;
   }
 }

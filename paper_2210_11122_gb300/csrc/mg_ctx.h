@@ -26,6 +26,8 @@ struct mg_ctx {
   int* d_ngslots = nullptr;
   int* d_nrows = nullptr;     // 4 * (number of gluon combinations): jamp rows per event
   void* d_cmat = nullptr;     // colour matrix numerators as the packed FP16 tensor-core operand
+  void* d_cumma = nullptr;    // the same as the tcgen05 B operand (canonical no-swizzle K-major layout)
+  int* d_tcerr = nullptr;     // nonzero: a bounded wait of the tcgen05 colour kernel gave up
   float2* d_jamps = nullptr;  // FP32 jamps of the tensor-core colour path
   int64_t jamp_cap = 0;       // in float2
   int* d_allg = nullptr;      // 0..2^K-1
@@ -67,5 +69,8 @@ int64_t share_chunk(int K, int64_t stride);
 // MG_MIXED on the lane-group kernel: colour sums on the tensor cores inside it, per-slot outputs
 bool mixed_in_kernel(const mg_ctx* ctx, mg_precision precision);
 mg_status ctx_reserve(mg_ctx* ctx, int64_t nevt, mg_precision precision);
+// Give dst (same process) the helicity mask of src: mask words, good-helicity and gluon-slot lists,
+// stream-ordered on st (device-to-device copies), then dst->mask_ready.
+mg_status ctx_copy_mask(mg_ctx* dst, const mg_ctx* src, cudaStream_t st);
 int64_t footprint_bytes(mg_process proc, int64_t nevt, mg_precision precision);
 }  // namespace mg

@@ -37,6 +37,7 @@ struct MeShape {
   bool warp = false;
   bool tc_apart = false;
   bool shared = true;   // FP64 amplitudes: currents of fewer than all gluons shared between slots
+  bool tc_sync = false;  // separate colour pass on mma.sync (k_colour_tc) instead of tcgen05 (k_colour_umma)
 };
 
 cudaError_t launch_philox(uint64_t seed, int64_t nevt, int nfinal, uint32_t* words, cudaStream_t st);
@@ -107,6 +108,14 @@ cudaError_t launch_me_fused(int K, bool fp32, const double* mom, int64_t nevt, c
 // for the jamp rows jamps[(e * rows_alloc + r) * ncol ...], r < *nrows; events with skip[e] != 0 (skip
 // optional) are not written.
 int colour_tc_cmat_halves(int ncol);
+// The separate tensor-core colour pass on the fifth-generation tensor cores (tcgen05.mma, accumulators in
+// tensor memory): same rows, outputs and skip list as launch_colour_tc; cumma = colour_umma_pack's operand;
+// a bounded wait that gives up leaves a nonzero stage code in *err (read by mg_check).
+int colour_umma_halves(int ncol);
+void colour_umma_pack(int ncol, const int64_t* num, uint16_t* out_halves);
+cudaError_t launch_colour_umma(int ncol, const float2* jamps, int64_t nevt, int rows_alloc, const int* nrows,
+                               const void* cumma, double scale, double* out, int64_t stride, cudaStream_t st,
+                               const uint8_t* skip, int* err);
 void colour_tc_pack(int ncol, const int64_t* num, uint16_t* out_halves);
 cudaError_t launch_colour_tc(int ncol, const float2* jamps, int64_t nevt, int rows_alloc, const int* nrows,
                              const void* cmat, double scale, double* out, int64_t stride, cudaStream_t st,

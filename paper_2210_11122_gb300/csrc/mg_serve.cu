@@ -17,9 +17,11 @@
 //     so their thread blocks are dispatched ahead of a large request's pending blocks; large
 //     requests use the low-priority slots; a small request may pass a large one that waits for a
 //     slot.
-// A request's result depends only on (process, seed, nevt): its helicity mask is computed from its
-// own first events and every kernel sums in a fixed order, so a request gives the same bits alone
-// and in any mix.  Requests larger than max_nevt run as consecutive chunks on one slot.
+// Helicity masks are resident: one per process, computed when the server is created from the first
+// params.hel_warmup events of Philox seed MG_SERVE_MASK_SEED and copied into every slot's context, so no
+// request runs the filter.  A request's result depends only on (process, seed, nevt) and that mask, and
+// every kernel sums in a fixed order, so a request gives the same bits alone and in any mix.  Requests
+// larger than max_nevt run as consecutive chunks on one slot.
 #include <cuda_runtime.h>
 
 #include <chrono>
@@ -96,7 +98,6 @@ mg_status launch_chunk(mg_server* srv, Slot& s) {
   s.chunk_n = n;
   mg_ctx* ctx = s.ctx[r->proc];
   mg_status st = mg_rambo_range(ctx, r->seed, r->next, n, srv->cfg.sqrts, s.mom, nullptr, s.stream);
-  if (st == MG_OK && r->next == 0) st = mg_hel_filter(ctx, s.mom, n, s.stream);
   if (st == MG_OK) st = mg_sigmakin(ctx, s.mom, n, srv->cfg.precision, s.me, s.stream);
   if (st != MG_OK) return st;
   if (cudaMemcpyAsync(s.host, s.me, n * sizeof(double), cudaMemcpyDeviceToHost, s.stream) != cudaSuccess ||
@@ -253,6 +254,17 @@ mg_status mg_serve_create(const mg_serve_cfg* cfg_in, mg_server** out) {
       if (st == MG_OK) st = mg::ctx_reserve(s.ctx[p], nmax, cfg.precision);
     }
     if (st != MG_OK) break;
+  }
+  // resident helicity masks: computed once per process on slot 0's context from the fixed warm-up sample,
+  // copied to the other slots' contexts
+  for (int p = 0; p < 4 && st == MG_OK; ++p) {
+    Slot& s0 = srv->slots[0];
+    const int64_t nw = cfg.params.hel_warmup < nmax ? cfg.params.hel_warmup : nmax;
+    st = mg_rambo(s0.ctx[p], MG_SERVE_MASK_SEED, nw, cfg.sqrts, s0.mom, nullptr, s0.stream);
+    if (st == MG_OK) st = mg_hel_filter(s0.ctx[p], s0.mom, nw, s0.stream);
+    for (size_t i = 1; i < srv->slots.size() && st == MG_OK; ++i) st = mg::ctx_copy_mask(srv->slots[i].ctx[p], s0.ctx[p], s0.stream);
+    if (st == MG_OK && cudaStreamSynchronize(s0.stream) != cudaSuccess) { cudaGetLastError(); st = MG_ECUDA; }
+    if (st == MG_OK && mg_check(s0.ctx[p], s0.stream, nullptr) != MG_OK) st = MG_ENOCONV;
   }
   if (st == MG_OK && cudaDeviceSynchronize() != cudaSuccess) { cudaGetLastError(); st = MG_ECUDA; }
   if (st != MG_OK) {

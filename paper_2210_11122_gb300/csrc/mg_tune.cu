@@ -37,7 +37,8 @@ std::string cache_key(mg_ctx* ctx, mg_precision precision) {
 
 int launch_flags(const mg::MeShape& s) {
   return (s.unrolled ? MG_LAUNCH_UNROLLED : 0) | (s.df_redo ? MG_LAUNCH_DF_REDO : 0) | (s.fused ? MG_LAUNCH_FUSED : 0) |
-         (s.warp ? MG_LAUNCH_WARP : 0) | (s.tc_apart ? MG_LAUNCH_TC_APART : 0) | (s.shared ? MG_LAUNCH_SHARED : 0);
+         (s.warp ? MG_LAUNCH_WARP : 0) | (s.tc_apart ? MG_LAUNCH_TC_APART : 0) | (s.shared ? MG_LAUNCH_SHARED : 0) |
+         (s.tc_sync ? MG_LAUNCH_TC_SYNC : 0);
 }
 
 bool cache_lookup(const char* path, const std::string& key, mg::MeShape* shape, double* ms) {
@@ -60,6 +61,7 @@ bool cache_lookup(const char* path, const std::string& key, mg::MeShape* shape, 
       shape->warp = (un & MG_LAUNCH_WARP) != 0;
       shape->tc_apart = (un & MG_LAUNCH_TC_APART) != 0;
       shape->shared = (un & MG_LAUNCH_SHARED) != 0;
+      shape->tc_sync = (un & MG_LAUNCH_TC_SYNC) != 0;
       *ms = t;
       found = true;
     }
@@ -191,7 +193,7 @@ extern "C" mg_status mg_set_launch_shape(mg_ctx* ctx, mg_precision precision, in
   if (!ctx || precision < MG_FP64 || precision > MG_MIXED) return MG_EINVAL;
   if ((tile_ev != 32 && tile_ev != 64 && tile_ev != 128) || (slot_major != 0 && slot_major != 1) ||
       (flags & ~(MG_LAUNCH_UNROLLED | MG_LAUNCH_DF_REDO | MG_LAUNCH_FUSED | MG_LAUNCH_WARP | MG_LAUNCH_TC_APART |
-                 MG_LAUNCH_SHARED)) != 0)
+                 MG_LAUNCH_SHARED | MG_LAUNCH_TC_SYNC)) != 0)
     return MG_EINVAL;
   ctx->shape[precision].tile_ev = tile_ev;
   ctx->shape[precision].slot_major = slot_major != 0;
@@ -201,6 +203,7 @@ extern "C" mg_status mg_set_launch_shape(mg_ctx* ctx, mg_precision precision, in
   ctx->shape[precision].warp = (flags & MG_LAUNCH_WARP) != 0;
   ctx->shape[precision].tc_apart = (flags & MG_LAUNCH_TC_APART) != 0;
   ctx->shape[precision].shared = (flags & MG_LAUNCH_SHARED) != 0;
+  ctx->shape[precision].tc_sync = (flags & MG_LAUNCH_TC_SYNC) != 0;
   return MG_OK;
 }
 
@@ -238,7 +241,9 @@ mg_status check_jobs(const mg_job* jobs, int njobs) {
     if (s != MG_OK) return s;
     if (jobs[i].precision == MG_FP64_TCCOLOR || jobs[i].precision == MG_MIXED)
       if (mg::launch_colour_tc(jobs[i].ctx->ncol, nullptr, 0, jobs[i].ctx->nhel, nullptr, nullptr, 0.0, nullptr, 0,
-                               nullptr) != cudaSuccess) {
+                               nullptr) != cudaSuccess ||
+          mg::launch_colour_umma(jobs[i].ctx->ncol, nullptr, 0, jobs[i].ctx->nhel, nullptr, nullptr, 0.0, nullptr, 0,
+                                 nullptr, nullptr, nullptr) != cudaSuccess) {
         cudaGetLastError();
         return MG_ECUDA;
       }

@@ -1,7 +1,7 @@
 """Serving loop (continuous batching) on the GPU through the C ABI.
 
 Each request's result must be the same alone and in a concurrent mix (bit-identical in FP64: the
-per-request helicity mask comes from the request's own events and every sum has a fixed order),
+server's helicity masks are resident, one per process, and every sum has a fixed order),
 admission must respect the device-memory cap, and waits are bounded.
 """
 import numpy as np
@@ -24,11 +24,15 @@ def env():
 
 
 def alone(torch, mg, proc, seed, nevt, precision):
+    """The request computed by hand with the server's resident helicity mask (the filter on the first
+    1,024 events of Philox seed SERVE_MASK_SEED)."""
     with mg.Context(proc) as ctx:
+        warm = torch.zeros(ctx.mom_count(1024), dtype=torch.float64, device="cuda")
+        ctx.rambo(mg.SERVE_MASK_SEED, 1024, SQRTS, warm)
+        ctx.hel_filter(warm, 1024)
         mom = torch.zeros(ctx.mom_count(nevt), dtype=torch.float64, device="cuda")
         me = torch.zeros(nevt, dtype=torch.float64, device="cuda")
         ctx.rambo_range(seed, 0, nevt, SQRTS, mom)
-        ctx.hel_filter(mom, nevt)
         ctx.sigmakin(mom, nevt, me, precision)
         return me.cpu().numpy()
 
@@ -100,6 +104,20 @@ def test_served_results_match_oracle(env):
         t = srv.submit("ggtt", 77, 333)
         me, _ = srv.wait(t)
     mom, _, _ = oracle.events(0, 77, 333)
-    mask, _ = oracle.hel_mask(0, mom)
+    warm, _, _ = oracle.events(0, mg.SERVE_MASK_SEED, 1024)     # the server's warm-up sample
+    mask, _ = oracle.hel_mask(0, warm)
     ref = oracle.me_batch(0, mom, mask=mask)
     assert np.max(np.abs(me / ref - 1)) <= 1e-12
+
+
+def test_server_masks_are_resident(env):
+    """The server computes each process's helicity mask once, at creation: a request of one event gets
+    the same mask as a request of thousands (no per-request filter), and its result equals the one
+    computed by hand with that mask."""
+    torch, mg = env
+    with mg.Server(slots=2) as srv:
+        one = srv.wait(srv.submit("ggtt", 5, 1))[0]
+        many = srv.wait(srv.submit("ggtt", 5, 2048))[0]
+    assert one[0] == many[0]
+    assert np.array_equal(one, alone(torch, mg, "ggtt", 5, 1, mg.MG_FP64))
+
