@@ -288,8 +288,8 @@ mg_status mg_colour_flow(mg_process proc, int flow, int* order);
  * threads of a block take further helicity combinations of the same events), grid dispatched
  * event-tile-major or helicity-tile-major, with and without MG_LAUNCH_UNROLLED where that kernel
  * exists, MG_LAUNCH_UNROLLED | MG_LAUNCH_FUSED, MG_LAUNCH_WARP and (MG_MIXED) MG_LAUNCH_WARP | MG_LAUNCH_TC_APART
- * -- then the fastest with MG_LAUNCH_DF_REDO (FP32 modes) or MG_LAUNCH_SHARED (MG_FP64) toggled, and keep
- * the fastest
+ * -- then the fastest with MG_LAUNCH_DF_REDO (FP32 modes) or MG_LAUNCH_SHARED (MG_FP64) toggled, and for the
+ * tensor-core colour modes with MG_LAUNCH_TC_SYNC toggled, and keep the fastest
  * for this context and precision.  cache_path (may be NULL): text file of
  * "gpu|process|precision tile_ev slot_major flags ms" lines; an existing entry is used without timing,
  * a new result is appended.  *best_ms may be NULL.  Synchronous; allocates probe buffers; nevt >= 32. */

@@ -287,10 +287,10 @@ cudaError_t launch_tc(const float2* jamps, int64_t nevt, int rows_alloc, const i
 // The same colour sums on the fifth-generation tensor cores (tcgen05.mma, accumulators in tensor memory).
 //
 // One persistent CTA of 8 warps per SM walks "stages" of VECS = 64 S jamp vectors (128 S real rows, S
-// M=128 MMA tiles; S NP = 128 accumulator columns in TMEM, NP = the padded colour count):
+// M=128 MMA tiles; S NP = 128 accumulator columns in TMEM, NP = the padded colour count).  Per stage:
 //   1. the stage's FP32 jamps, prefetched into registers with coalesced 16-byte loads during the previous
 //      stage, go to a padded staging buffer in shared memory (row pitch 2 NCOL + 2 floats: the per-row
-//      accesses below are free of bank conflicts);
+//      reads below are free of bank conflicts);
 //   2. each row (real or imaginary part of one vector) is scaled by a power of two to max |t| in
 //      [1/2, 1) and split t = hi + lo (two FP16 values, lo = fp16(t - hi) keeps t to ~2^-24 absolute),
 //      written as the MMA's A operand in the no-swizzle K-major layout (8-row x 16-byte core matrices,
@@ -298,10 +298,11 @@ cudaError_t launch_tc(const float2* jamps, int64_t nevt, int rows_alloc, const i
 //      16-byte stores of the 32 lanes, each a different vector, evenly over the banks);
 //   3. one thread issues S x (K/16) x 2 MMAs (M = 128, N = NP, K = 16; hi, then lo, into the same FP32
 //      accumulator: Y = C hi + C lo) against the exact integer colour matrix C (FP16, resident in shared
-//      memory for the whole kernel) and commits them to an mbarrier;
-//   4. the 8 warps read Y back (tcgen05.ld, warp w: TMEM lanes 32 (w % 4) .. +31, columns 64 (w / 4) ..
-//      +63) and form each row's quadratic form t . Y with the exact scaled FP32 t from the staging buffer;
-//      the real and imaginary rows of a vector are combined and unscaled exactly, as in k_colour_tc.
+//      memory for the whole kernel) and commits them to the stage's mbarrier;
+//   4. meanwhile the 8 warps finish the PREVIOUS stage (A and the accumulators are double-buffered):
+//      they read its Y back (tcgen05.ld, warp w: TMEM lanes 32 (w % 4) .. +31, one half of the columns)
+//      and form each row's quadratic form t . Y with t = hi + lo from its A buffer; the real and
+//      imaginary rows of a vector are combined and unscaled exactly, as in k_colour_tc.
 // Every wait is bounded: a wait that gives up records the stage in *err, and the CTA frees its tensor
 // memory and returns.
 template <int NCOL>
@@ -316,7 +317,7 @@ struct Umma {
   static constexpr int KC = KP / 8;                   // k chunks per row, padding included
   static constexpr int SBO_A = KC * 128 + 16;         // bytes between 8-row groups of A
   static constexpr int SBO_B = KC * 128;              // bytes between 8-row groups of B = C
-  static constexpr int A_BYTES = (ROWS / 8) * SBO_A;  // hi or lo
+  static constexpr int A_BYTES = (ROWS / 8) * SBO_A;  // one of hi / lo
   static constexpr int B_BYTES = (NP / 8) * SBO_B;
   static constexpr int STG_BYTES = VECS * PITCH * 4;
   static constexpr int F4 = VECS * NCOL * 2 / 4;      // 16-byte pieces of a stage
@@ -325,16 +326,21 @@ struct Umma {
   static constexpr int VPL = CH <= 4 ? 32 : 8;        // vectors per warp in the conversion
   static constexpr int CPL = VPL == 32 ? CH : (CH + 3) / 4;   // k chunks per lane
   static constexpr int PASSES = VECS / (8 * VPL);
-  // shared memory: A hi | A lo | B | staging | partial sums [2][S][128] | row exponents [S][128] | mbarrier, TMEM address
-  static constexpr int OFF_ALO = (A_BYTES + 1023) / 1024 * 1024;
-  static constexpr int OFF_B = OFF_ALO + (A_BYTES + 1023) / 1024 * 1024;
-  static constexpr int OFF_STG = OFF_B + (B_BYTES + 1023) / 1024 * 1024;
-  static constexpr int OFF_PART = OFF_STG + (STG_BYTES + 15) / 16 * 16;
+  static constexpr int CHALF = S == 1 ? (CH + 1) / 2 : 0;     // S = 1: data chunks of the first column half
+  // shared memory (128-byte aligned pieces): A hi, lo for two buffers | B | staging | partial sums
+  // [2][S][128] | row exponents [2][S][128] | 2 mbarriers, TMEM address, abort flag
+  static constexpr int A_PAD = (A_BYTES + 127) / 128 * 128;
+  static constexpr int OFF_B = 4 * A_PAD;
+  static constexpr int OFF_STG = OFF_B + (B_BYTES + 127) / 128 * 128;
+  static constexpr int OFF_PART = OFF_STG + (STG_BYTES + 127) / 128 * 128;
   static constexpr int OFF_EXP = OFF_PART + 2 * S * 128 * 4;
-  static constexpr int OFF_BAR = OFF_EXP + S * 128 * 4;
-  static constexpr int SMEM = OFF_BAR + 64 + 1024;    // + 1024: the dynamic buffer is aligned up to 1 KB
+  static constexpr int OFF_VAL = OFF_EXP + 2 * S * 128 * 4;
+  static constexpr int OFF_BAR = OFF_VAL + (2 * VECS + 127) / 128 * 128;
+  static constexpr int VPT = (VECS + THREADS - 1) / THREADS;   // vector validity flags prefetched per thread
+  static constexpr int SMEM = OFF_BAR + 64 + 128;     // + 128: the dynamic buffer is aligned up to 128 bytes
   static constexpr uint32_t IDESC = (1u << 4) | (static_cast<uint32_t>(NP >> 3) << 17) | (static_cast<uint32_t>(128 >> 4) << 24);
   static_assert(S * NP == 128 && PASSES * 8 * VPL == VECS && (2 * NCOL) % 4 == 0, "stage shape");
+  static_assert(SMEM <= 232448, "shared memory");
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
@@ -373,12 +379,36 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
       : "r"(taddr));
 }
 
-// FP16 bits of hi and lo for one value t (|t| < 1)
-__device__ __forceinline__ void split_bits(float t, uint32_t& hb, uint32_t& lb) {
-  const __half h = __float2half_rn(t);
-  const __half l = __float2half_rn(t - __half2float(h));
-  hb = __half_as_ushort(h);
-  lb = __half_as_ushort(l);
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+        "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr));
+}
+
+// FP16x2 hi and lo words of the value pair (a, b), |a|, |b| < 1: hi = fp16(a), fp16(b); lo = fp16 of
+// the remainders (exact in FP32)
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t& hw, uint32_t& lw) {
+  const __half2 h = __floats2half2_rn(a, b);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+  hw = *reinterpret_cast<const uint32_t*>(&h);
+  lw = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// t . y over 8 k values: t = hi + lo from the 16-byte hi and lo chunks, y from the accumulator columns
+__device__ __forceinline__ float dot8(uint4 h, uint4 l, const uint32_t* y, float acc) {
+  const uint32_t hv[4] = {h.x, h.y, h.z, h.w}, lv[4] = {l.x, l.y, l.z, l.w};
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&hv[j]));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&lv[j]));
+    acc = fmaf(a.x + b.x, __uint_as_float(y[2 * j]), acc);
+    acc = fmaf(a.y + b.y, __uint_as_float(y[2 * j + 1]), acc);
+  }
+  return acc;
 }
 
 constexpr long long kUmmaSpin = 1ll << 22;   // bounded waits (the MMAs of a stage take about a microsecond)
@@ -390,29 +420,31 @@ k_colour_umma(const float2* __restrict__ jamps, int64_t nevt, int rows_log2, con
               const uint8_t* __restrict__ skip, int* __restrict__ err) {
   using U = Umma<NCOL>;
   extern __shared__ unsigned char smem_raw[];
-  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* sAhi = smem;
-  unsigned char* sAlo = smem + U::OFF_ALO;
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
   unsigned char* sB = smem + U::OFF_B;
   float* stg = reinterpret_cast<float*>(smem + U::OFF_STG);
   float* part = reinterpret_cast<float*>(smem + U::OFF_PART);
-  int* rexp = reinterpret_cast<int*>(smem + U::OFF_EXP);
+  int* rexp_all = reinterpret_cast<int*>(smem + U::OFF_EXP);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + U::OFF_BAR);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + U::OFF_BAR + 8);
-  int* abort_flag = reinterpret_cast<int*>(smem + U::OFF_BAR + 16);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + U::OFF_BAR + 16);
+  int* abort_flag = reinterpret_cast<int*>(smem + U::OFF_BAR + 24);
+  uint8_t* vval_all = smem + U::OFF_VAL;                    // [2][VECS]: vector holds a row to compute
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  auto a_hi = [&](int buf) { return smem + (2 * buf) * U::A_PAD; };
+  auto a_lo = [&](int buf) { return smem + (2 * buf + 1) * U::A_PAD; };
 
   // operands at rest: A's padding chunks stay zero; C in the canonical layout
-  for (int i = tid; i < (U::OFF_B - 0) / 16; i += U::THREADS) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < U::OFF_B / 16; i += U::THREADS) reinterpret_cast<uint4*>(smem)[i] = make_uint4(0, 0, 0, 0);
   for (int i = tid; i < U::B_BYTES / 16; i += U::THREADS)
     reinterpret_cast<uint4*>(sB)[i] = reinterpret_cast<const uint4*>(cumma)[i];
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar + 1)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     *abort_flag = 0;
   }
   if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_addr(tmem_slot)) : "memory");
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(tmem_slot)) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -431,7 +463,13 @@ k_colour_umma(const float2* __restrict__ jamps, int64_t nevt, int rows_log2, con
   };
 
   float4 pf[U::PF];
+  bool pv[U::VPT];
   auto prefetch = [&](int64_t st) {
+#pragma unroll
+    for (int j = 0; j < U::VPT; ++j) {
+      const int v = tid + U::THREADS * j;
+      pv[j] = st < nstage && v < U::VECS && vec_valid(st * U::VECS + v);
+    }
     const float4* src = reinterpret_cast<const float4*>(jamps) + st * (U::F4);
     const int64_t lim = (nvec - st * U::VECS) * (NCOL * 2 / 4);   // pieces left in the buffer
 #pragma unroll
@@ -441,12 +479,8 @@ k_colour_umma(const float2* __restrict__ jamps, int64_t nevt, int rows_log2, con
     }
   };
 
-  uint32_t phase = 0;
-  int64_t st = blockIdx.x;
-  prefetch(st);
-  for (; st < nstage; st += gridDim.x) {
-    const int64_t q0 = st * U::VECS;
-    // 1. staging <- prefetched registers; prefetch the next stage
+  // stage st (buffer buf): rows -> A; one thread issues its MMAs
+  auto produce = [&](int64_t st, int buf) {
 #pragma unroll
     for (int j = 0; j < U::PF; ++j) {
       const int i = tid + U::THREADS * j;
@@ -457,15 +491,20 @@ k_colour_umma(const float2* __restrict__ jamps, int64_t nevt, int rows_log2, con
         *reinterpret_cast<float2*>(d + 2) = make_float2(pf[j].z, pf[j].w);
       }
     }
+    uint8_t* vval = vval_all + buf * U::VECS;
+#pragma unroll
+    for (int j = 0; j < U::VPT; ++j)
+      if (tid + U::THREADS * j < U::VECS) vval[tid + U::THREADS * j] = pv[j] ? 1 : 0;
     prefetch(st + gridDim.x);
     __syncthreads();
-
-    // 2. rows -> scaled hi/lo FP16 A operand
+    unsigned char* ahi = a_hi(buf);
+    unsigned char* alo = a_lo(buf);
+    int* rexp = rexp_all + buf * U::ROWS;
 #pragma unroll 1
     for (int pass = 0; pass < U::PASSES; ++pass) {
       const int v = pass * 8 * U::VPL + warp * U::VPL + (lane % U::VPL);
       const int b = lane / U::VPL;
-      const bool ok = vec_valid(q0 + v);
+      const bool ok = vval[v] != 0;
       float2 val[U::CPL][8];
       float mre = 0.f, mim = 0.f;
 #pragma unroll
@@ -490,7 +529,7 @@ k_colour_umma(const float2* __restrict__ jamps, int64_t nevt, int rows_log2, con
       int ere = 0, eim = 0;
       if (mre > 0.f) frexpf(mre, &ere);
       if (mim > 0.f) frexpf(mim, &eim);
-      const float sre = ldexpf(1.f, -ere), sim = ldexpf(1.f, -eim);
+      const float sre = pow2f_neg(-ere), sim = pow2f_neg(-eim);   // 2^-e (exact for |e| <= 126)
       if (b == 0) {
         rexp[2 * v] = ere;
         rexp[2 * v + 1] = eim;
@@ -499,113 +538,157 @@ k_colour_umma(const float2* __restrict__ jamps, int64_t nevt, int rows_log2, con
       for (int i = 0; i < U::CPL; ++i) {
         const int c = U::VPL == 32 ? i : b + 4 * i;
         if (c >= U::CH) continue;
+        uint32_t hr[4], lr[4], hi_[4], li_[4];
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
-          uint32_t hw[4], lw[4];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            uint32_t h0, l0, h1, l1;
-            split_bits((p ? val[i][2 * j].y : val[i][2 * j].x) * (p ? sim : sre), h0, l0);
-            split_bits((p ? val[i][2 * j + 1].y : val[i][2 * j + 1].x) * (p ? sim : sre), h1, l1);
-            hw[j] = h0 | (h1 << 16);
-            lw[j] = l0 | (l1 << 16);
-          }
-          const int m = 2 * v + p;
-          const int off = (m & 7) * 16 + (m >> 3) * U::SBO_A + c * 128;
-          *reinterpret_cast<uint4*>(sAhi + off) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
-          *reinterpret_cast<uint4*>(sAlo + off) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+        for (int j = 0; j < 4; ++j) {
+          split_pair(val[i][2 * j].x * sre, val[i][2 * j + 1].x * sre, hr[j], lr[j]);
+          split_pair(val[i][2 * j].y * sim, val[i][2 * j + 1].y * sim, hi_[j], li_[j]);
         }
+        const int m = 2 * v;   // real row; the imaginary row m + 1 is 16 bytes further
+        const int off = (m & 7) * 16 + (m >> 3) * U::SBO_A + c * 128;
+        *reinterpret_cast<uint4*>(ahi + off) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+        *reinterpret_cast<uint4*>(alo + off) = make_uint4(lr[0], lr[1], lr[2], lr[3]);
+        *reinterpret_cast<uint4*>(ahi + off + 16) = make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
+        *reinterpret_cast<uint4*>(alo + off + 16) = make_uint4(li_[0], li_[1], li_[2], li_[3]);
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-
-    // 3. one thread issues the MMAs of the stage
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t ahi = smem_addr(sAhi), alo = smem_addr(sAlo), bb = smem_addr(sB);
+      const uint32_t h = smem_addr(ahi), l = smem_addr(alo), bb = smem_addr(sB);
+      const uint32_t d = tmem + buf * 128;
 #pragma unroll 1
       for (int s = 0; s < U::S; ++s)
 #pragma unroll 1
         for (int ks = 0; ks < U::KP / 16; ++ks)
 #pragma unroll
           for (int hl = 0; hl < 2; ++hl) {
-            const uint32_t a = (hl ? alo : ahi) + s * 16 * U::SBO_A + ks * 256;
-            umma_f16(tmem + s * U::NP, umma_desc(a, 128, U::SBO_A), umma_desc(bb + ks * 256, 128, U::SBO_B), U::IDESC,
+            const uint32_t a = (hl ? l : h) + s * 16 * U::SBO_A + ks * 256;
+            umma_f16(d + s * U::NP, umma_desc(a, 128, U::SBO_A), umma_desc(bb + ks * 256, 128, U::SBO_B), U::IDESC,
                      (ks | hl) != 0);
           }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar + buf))
                    : "memory");
     }
-    // wait for the accumulators (bounded)
+  };
+
+  // stage st (buffer buf), whose MMAs were committed: quadratic forms and outputs
+  uint32_t phases = 0;   // bit b: parity of the next completion of buffer b's mbarrier
+  auto consume = [&](int64_t st, int buf) -> bool {
     {
       long long n = 0;
       bool done = false;
-      while (!(done = mbar_try_wait(smem_addr(bar), phase)) && ++n < kUmmaSpin) {
+      while (!(done = mbar_try_wait(smem_addr(bar + buf), (phases >> buf) & 1u)) && ++n < kUmmaSpin) {
       }
       if (!done) *abort_flag = 1;
     }
-    phase ^= 1;
+    phases ^= 1u << buf;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
-    if (*abort_flag) {
-      if (tid == 0) atomicCAS(err, 0, static_cast<int>(st % 1000000) + 1);
-      break;
-    }
-
-    // 4. quadratic forms t . Y (warp: TMEM lane quarter warp % 4, column half warp / 4)
-    {
-      const int qw = warp & 3, hf = warp >> 2;
-      const int m = 32 * qw + lane;                          // row within each MMA tile
-      float acc[U::S], rs[U::S];
-#pragma unroll
-      for (int s = 0; s < U::S; ++s) {
-        acc[s] = 0.f;
-        rs[s] = ldexpf(1.f, -rexp[2 * (64 * s + (m >> 1)) + (m & 1)]);   // the row's power-of-two scale
-      }
+    if (*abort_flag) return false;
+    const int64_t q0 = st * U::VECS;
+    const unsigned char* ahi = a_hi(buf);
+    const unsigned char* alo = a_lo(buf);
+    const int* rexp = rexp_all + buf * U::ROWS;
+    const uint8_t* vval = vval_all + buf * U::VECS;
+    const int qw = warp & 3, hf = warp >> 2;
+    const int m = 32 * qw + lane;                          // row within each MMA tile
+    const uint32_t taddr = tmem + buf * 128 + (static_cast<uint32_t>(32 * qw) << 16);
+    if constexpr (U::S == 1) {
+      // one tile: this half's 64 columns = k chunks 8 hf .. 8 hf + 7
+      float acc = 0.f;
+      const int row_off = (m & 7) * 16 + (m >> 3) * U::SBO_A;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         uint32_t y[32];
-        const int c0 = 64 * hf + 32 * h;
-        tmem_ld32(tmem + (static_cast<uint32_t>(32 * qw) << 16) + c0, y);
+        tmem_ld32(taddr + 64 * hf + 32 * h, y);
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int c = c0 + j, s = c / U::NP, n = c % U::NP;
-          if (n < NCOL) {
-            const int v = 64 * s + (m >> 1);
-            const float t = stg[v * U::PITCH + 2 * n + (m & 1)] * rs[s];
-            acc[s] = fmaf(t, __uint_as_float(y[j]), acc[s]);
+        for (int cc = 0; cc < 4; ++cc) {
+          const int c = 8 * hf + 4 * h + cc;
+          if (c < U::CH) {
+            const uint4 hv = *reinterpret_cast<const uint4*>(ahi + row_off + c * 128);
+            const uint4 lv = *reinterpret_cast<const uint4*>(alo + row_off + c * 128);
+            acc = dot8(hv, lv, y + 8 * cc, acc);
           }
         }
       }
+      part[hf * 128 + m] = acc;
+    } else {
+      // this half's S/2 tiles, NP columns each
 #pragma unroll
-      for (int s = 0; s < U::S; ++s) part[(hf * U::S + s) * 128 + m] = acc[s];
+      for (int i = 0; i < U::S / 2; ++i) {
+        const int s = hf * (U::S / 2) + i;
+        const int mm = 128 * s + m;                        // row of the stage
+        const int row_off = (mm & 7) * 16 + (mm >> 3) * U::SBO_A;
+        float acc = 0.f;
+        if constexpr (U::NP == 16) {
+          uint32_t y[16];
+          tmem_ld16(taddr + s * U::NP, y);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          acc = dot8(*reinterpret_cast<const uint4*>(ahi + row_off), *reinterpret_cast<const uint4*>(alo + row_off), y, acc);
+          if (U::CH > 1)
+            acc = dot8(*reinterpret_cast<const uint4*>(ahi + row_off + 128), *reinterpret_cast<const uint4*>(alo + row_off + 128),
+                       y + 8, acc);
+        } else {
+          uint32_t y[32];
+          tmem_ld32(taddr + s * U::NP, y);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int c = 0; c < U::CH; ++c)
+            acc = dot8(*reinterpret_cast<const uint4*>(ahi + row_off + c * 128),
+                       *reinterpret_cast<const uint4*>(alo + row_off + c * 128), y + 8 * c, acc);
+        }
+        part[s * 128 + m] = acc;
+      }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp < 4) {
-      const int m = 32 * warp + lane;
+      const int m2 = 32 * warp + lane;
 #pragma unroll
       for (int s = 0; s < U::S; ++s) {
-        const float tot = part[s * 128 + m] + part[(U::S + s) * 128 + m];
-        const int e = rexp[2 * (64 * s + (m >> 1)) + (m & 1)];
+        const float tot = U::S == 1 ? part[m2] + part[128 + m2] : part[s * 128 + m2];
+        const int e = rexp[128 * s + m2];
         const float other = __shfl_xor_sync(0xffffffffu, tot, 1);
         const int eo = __shfl_xor_sync(0xffffffffu, e, 1);
-        if ((m & 1) == 0) {
-          const int64_t q = q0 + 64 * s + (m >> 1);
-          if (vec_valid(q))
+        if ((m2 & 1) == 0) {
+          const int64_t q = q0 + 64 * s + (m2 >> 1);
+          if (vval[64 * s + (m2 >> 1)])
             out[(q & rmask) * stride + (q >> rows_log2)] = combine_rows(tot, 2 * e, other, 2 * eo, scale_f);
         }
       }
     }
-    __syncthreads();   // staging, exponents and partial sums are rewritten by the next stage
+    return true;
+  };
+
+  int64_t st = blockIdx.x;
+  prefetch(st);
+  int buf = 0;
+  int64_t prev = -1;
+  for (;; st += gridDim.x, buf ^= 1) {
+    if (st < nstage) produce(st, buf);
+    if (prev >= 0) {
+      if (!consume(prev, buf ^ 1)) {
+        if (tid == 0) atomicCAS(err, 0, static_cast<int>(prev % 1000000) + 1);
+        if (st < nstage) {   // the stage just issued: let its MMAs finish (bounded) before the memory goes
+          long long n = 0;
+          while (!mbar_try_wait(smem_addr(bar + buf), (phases >> buf) & 1u) && ++n < kUmmaSpin) {
+          }
+        }
+        break;
+      }
+    }
+    if (st >= nstage) break;
+    prev = st;
+    __syncthreads();   // the next produce() rewrites the validity flags the combine step above just read
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
 }
 
 }  // namespace
@@ -698,7 +781,7 @@ static cudaError_t launch_umma(const float2* jamps, int64_t nevt, int rows_alloc
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_colour_umma<NCOL>, U::THREADS, U::SMEM) != cudaSuccess ||
       per_sm < 1)
     per_sm = 1;
-  if (per_sm > 4) per_sm = 4;   // 4 x 128 TMEM columns per SM
+  if (per_sm > 2) per_sm = 2;   // 2 x 256 TMEM columns per SM
   const int64_t nstage = ((nevt << rows_log2) + U::VECS - 1) / U::VECS;
   int64_t blocks = static_cast<int64_t>(nsm) * per_sm;
   if (blocks > nstage) blocks = nstage;

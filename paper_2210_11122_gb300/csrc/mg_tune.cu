@@ -164,6 +164,13 @@ extern "C" mg_status mg_autotune(mg_ctx* ctx, mg_precision precision, int64_t ne
     rc = time_shape(s, &t);
     if (rc == MG_OK && t < best_t) { best_t = t; best = s; }
   }
+  if ((precision == MG_FP64_TCCOLOR || precision == MG_MIXED) && rc == MG_OK) {   // colour-pass kernel
+    mg::MeShape s = best;
+    s.tc_sync = !s.tc_sync;
+    float t = 1e30f;
+    rc = time_shape(s, &t);
+    if (rc == MG_OK && t < best_t) { best_t = t; best = s; }
+  }
   ctx->shape[precision] = rc == MG_OK ? best : saved;
   if (rc == MG_OK) {
     cache_store(cache_path, key, best, best_t);

@@ -94,7 +94,7 @@ def test_launch_shape_set_and_get(env):
         ctx.set_launch_shape(mg.MG_FP32_AMP, 32, 1, mg.LAUNCH_DF_REDO)
         assert ctx.launch_shape(mg.MG_FP32_AMP) == (32, 1, mg.LAUNCH_DF_REDO)
         assert ctx.launch_shape(mg.MG_FP64) == (128, 0, both)
-        for bad in ((48, 0, 1), (64, 2, 1), (64, 0, 64)):
+        for bad in ((48, 0, 1), (64, 2, 1), (64, 0, 128)):
             with pytest.raises(mg.MGError):
                 ctx.set_launch_shape(mg.MG_FP32_AMP, *bad)
 
