@@ -22,32 +22,19 @@ namespace v2 {
 // the slot in its own row, out[(slot * 4 + 2 top + antitop) * stride + e] (zero for helicities outside
 // the mask), and the slot's sum over its good helicities of every |jamp|^2,
 // j2[(slot * ncol + sigma) * stride + e].
+// The work of one thread: event e, gluon-helicity slot `slot` with gluon helicities gc (bit g = helicity +1
+// of gluon g).  Called by k_me_gluonhel below and by the persistent multi-process kernel (mg_persist.cu).
 template <int K, class T, bool PER_HEL, bool PREP, bool JOUT, bool SHARED = false, bool LHE = false>
-__global__ void __launch_bounds__(kMeThreads)
-k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab,
-              const int* __restrict__ gslots, const int* __restrict__ nslot_dev, const uint32_t* __restrict__ mask,
-              const typename ColourT<T>::type* __restrict__ ctri, MeConst cst, double* __restrict__ out, int64_t stride,
-              float2* __restrict__ jout, int tile_ev, int slot_major, const int* __restrict__ evlist,
-              const int* __restrict__ nlist, int rows_out, const uint8_t* __restrict__ skip,
-              const double* __restrict__ share = nullptr, double* __restrict__ j2 = nullptr) {
-  static_assert(!SHARED || (PREP && std::is_same<T, double>::value), "shared currents: FP64 with a record");
-  static_assert(!LHE || (PREP && !PER_HEL && !JOUT && std::is_same<T, double>::value), "LHE rows: FP64 with a record");
+__device__ __forceinline__ void me_slot(const double* __restrict__ mom, const T* __restrict__ rec, int64_t e, int slot,
+                                        int gc, const Tables* __restrict__ tab, const uint32_t* __restrict__ mask,
+                                        const typename ColourT<T>::type* __restrict__ ctri, const MeConst& cst,
+                                        double* __restrict__ out, int64_t stride, float2* __restrict__ jout, int rows_out,
+                                        const double* __restrict__ share, double* __restrict__ j2) {
   constexpr int npar = K + 2;
   constexpr int NSEQ = Sizes<K>::nseq;
   constexpr int NCOL = Sizes<K>::ncol;
   constexpr int NFULL = Sizes<K>::nfull;
   constexpr int NSUB = 1 << K;
-  const int tile_sl = static_cast<int>(blockDim.x) / tile_ev;   // slots per block
-  const unsigned bev = slot_major ? blockIdx.y : blockIdx.x, bsl = slot_major ? blockIdx.x : blockIdx.y;
-  const int64_t et = static_cast<int64_t>(bev) * tile_ev + threadIdx.x % tile_ev;
-  const int slot = static_cast<int>(bsl) * tile_sl + static_cast<int>(threadIdx.x) / tile_ev;
-  if (et >= nevt || slot >= *nslot_dev) return;
-  // evlist: the thread works on event evlist[et] of the batch (et < *nlist), else on event et
-  if (evlist && et >= *nlist) return;
-  const int64_t e = evlist ? static_cast<int64_t>(evlist[et]) : et;
-  if (PREP && skip && skip[e]) return;   // recomputed by another launch
-  const int gc = gslots[slot];   // bit g = helicity (+1) of gluon g
-
   const T gs = static_cast<T>(cst.gs);
   T PT[NSUB][4];
   T gprop[NSUB];
@@ -273,6 +260,31 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
       out[slot * stride + e] = total;
     }
   }
+}
+
+template <int K, class T, bool PER_HEL, bool PREP, bool JOUT, bool SHARED = false, bool LHE = false>
+__global__ void __launch_bounds__(kMeThreads)
+k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab,
+              const int* __restrict__ gslots, const int* __restrict__ nslot_dev, const uint32_t* __restrict__ mask,
+              const typename ColourT<T>::type* __restrict__ ctri, MeConst cst, double* __restrict__ out, int64_t stride,
+              float2* __restrict__ jout, int tile_ev, int slot_major, const int* __restrict__ evlist,
+              const int* __restrict__ nlist, int rows_out, const uint8_t* __restrict__ skip,
+              const double* __restrict__ share = nullptr, double* __restrict__ j2 = nullptr) {
+  static_assert(!SHARED || (PREP && std::is_same<T, double>::value), "shared currents: FP64 with a record");
+  static_assert(!LHE || (PREP && !PER_HEL && !JOUT && std::is_same<T, double>::value), "LHE rows: FP64 with a record");
+  const int tile_sl = static_cast<int>(blockDim.x) / tile_ev;   // slots per block
+  const unsigned bev = slot_major ? blockIdx.y : blockIdx.x, bsl = slot_major ? blockIdx.x : blockIdx.y;
+  const int64_t et = static_cast<int64_t>(bev) * tile_ev + threadIdx.x % tile_ev;
+  const int slot = static_cast<int>(bsl) * tile_sl + static_cast<int>(threadIdx.x) / tile_ev;
+  if (et >= nevt || slot >= *nslot_dev) return;
+  // evlist: the thread works on event evlist[et] of the batch (et < *nlist), else on event et
+  if (evlist && et >= *nlist) return;
+  const int64_t e = evlist ? static_cast<int64_t>(evlist[et]) : et;
+  if (PREP && skip && skip[e]) return;   // recomputed by another launch
+  const int gc = gslots[slot];   // bit g = helicity (+1) of gluon g
+
+  me_slot<K, T, PER_HEL, PREP, JOUT, SHARED, LHE>(mom, rec, e, slot, gc, tab, mask, ctri, cst, out, stride, jout, rows_out,
+                                                share, j2);
 }
 
 // Currents shared between gluon-helicity combinations (FP64): every canonical sequence s of `level`
