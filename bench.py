@@ -83,6 +83,8 @@ def parse():
     ap.add_argument("--slots", type=int, default=8)
     ap.add_argument("--no-processes", action="store_true", help="time the configured process only")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg of the default run")
+    ap.add_argument("--batch-requests", type=int, default=48,
+                    help="jobs of the default run's graph-batch leg (the first requests of the serving trace)")
     ap.add_argument("--serve-requests", type=int, default=500,
                     help="requests of the default run's serving leg (the first ones of the 20,000-request trace)")
     return ap.parse_args()
@@ -571,6 +573,11 @@ def run_ours(args):
             lg.close()
             torch.cuda.empty_cache()
 
+    # ---- many small jobs of all processes: per-job launches vs graph branches vs one persistent launch ----
+    graph_batch = None
+    if not args.no_serve and world == 1:
+        graph_batch = batch_leg(mg, torch, stream, flush, args.batch_requests)
+
     # ---- serving: a bounded sample of the request trace, 80 % load (rank 0, one GPU) ----
     serving = None
     if not args.no_serve and world == 1:
@@ -594,6 +601,7 @@ def run_ours(args):
             "config": config_of(args, nevt),
             "me_kernel_ms": ms_me, "wall_s": wall, "nonconverged_events": nbad, "good_helicities": ngood,
             "modes": variants, "launch_shapes": shapes, "processes": processes, "serving": serving,
+            "graph_batch": graph_batch,
             "graph": {"ms_per_step": graph_ms, "value": aggregate_rate(world, nevt, graph_ms), "same_result": graph_same,
                       "what": "the FP64 step captured as one CUDA graph (mg_graph_create) and replayed"},
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
@@ -639,6 +647,66 @@ def run_trace(mg, srv, proc, nevt, expo, rate):
     lat = np.array([srv.wait(t)[1] for t in tickets])
     span = time.perf_counter() - t0
     return span, lat
+
+
+def batch_leg(mg, torch, stream, flush, nreq, reps=3):
+    """The first nreq requests of the serving trace as one batch of FP64 jobs (seed = request id), timed
+    three ways with CUDA events: one launch sequence per job on one stream (Philox + RAMBO, helicity filter,
+    matrix elements), the CUDA graph with every job on its own branch, and the graph whose matrix elements
+    all run in one persistent launch (mg_graph_create_ex, MG_GRAPH_PERSISTENT)."""
+    proc, nevt, _ = serve_trace(mg, torch, nreq)
+    total = int(nevt.sum())
+
+    def make(persistent):
+        jobs = []
+        for r in range(nreq):
+            c = mg.Context(int(proc[r]), mt=MT, alphas=ALPHAS)
+            if persistent:
+                c.set_launch_shape(mg.MG_FP64, 128, 0, 7)
+            n = int(nevt[r])
+            mom = torch.zeros(c.mom_count(n), dtype=torch.float64, device="cuda")
+            me = torch.zeros(n, dtype=torch.float64, device="cuda")
+            jobs.append((c, r, 0, n, SQRTS, mom, me, mg.MG_FP64))
+        return jobs
+
+    def time_it(fn):
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * reps)]
+        with torch.cuda.stream(stream):
+            fn()
+            flush.zero_()
+            for k in range(reps):
+                ev[2 * k].record(stream)
+                fn()
+                ev[2 * k + 1].record(stream)
+                flush.zero_()
+        torch.cuda.synchronize()
+        return statistics.mean(ev[2 * k].elapsed_time(ev[2 * k + 1]) for k in range(reps))
+
+    counts = [int((proc == p).sum()) for p in range(4)]
+    out = {"workload": "first %d requests of the serving trace as one batch of FP64 jobs: %d events; gg->tt, ttg, "
+                       "ttgg, ttggg jobs: %s" % (nreq, total, counts), "events": total}
+    jobs = make(False)
+
+    def seq():
+        for c, seed, e0, n, q, mom, me, prec in jobs:
+            c.rambo_range(seed, e0, n, q, mom, stream=stream)
+            c.hel_filter(mom, n, stream=stream)
+            c.sigmakin(mom, n, me, prec, stream=stream)
+    ms = time_it(seq)
+    out["one_launch_sequence_per_job"] = {"ms": ms, "MEs_per_s": total / (ms * 1e-3)}
+    g = mg.GraphBatch(jobs)
+    ms = time_it(lambda: g.launch(stream))
+    out["graph_branches"] = {"ms": ms, "MEs_per_s": total / (ms * 1e-3), "nodes": g.nodes()}
+    g.close()
+    pj = make(True)
+    gp = mg.GraphBatch(pj, persistent=True)
+    ms = time_it(lambda: gp.launch(stream))
+    out["graph_persistent"] = {"ms": ms, "MEs_per_s": total / (ms * 1e-3), "nodes": gp.nodes()}
+    gp.close()
+    for j in jobs + pj:
+        j[0].close()
+    out["speedup_persistent_vs_sequence"] = out["graph_persistent"]["MEs_per_s"] / out["one_launch_sequence_per_job"]["MEs_per_s"]
+    return out
 
 
 def serve_leg(mg, torch, nreq, slots, names):

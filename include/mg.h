@@ -320,9 +320,36 @@ typedef struct {
 
 typedef struct mg_graph mg_graph;
 
+/* One job of mg_sigmakin_batch: the FP64 matrix elements of nevt events (AoSoA momenta) on ctx. */
+typedef struct {
+  mg_ctx* ctx;
+  const double* mom_dev;
+  int64_t nevt;
+  double* me_dev;
+} mg_batch_job;
+
+/* FP64 matrix elements of njobs jobs (1..64, any mix of processes, one context each, zero top width) with
+ * ONE persistent kernel launch for all their matrix elements: its thread blocks drain a queue of (job,
+ * gluon-helicity slot, 128-event tile) work items (the jobs with more gluons first) from an atomic counter,
+ * so many small jobs fill the GPU together (the paper's Sec. 4: throughput keeps growing up to batches of
+ * ~16k events).  Per job, as mg_sigmakin(MG_FP64): the helicity filter on its own first events if its
+ * context has no mask yet, the per-event records, and the helicity sums after the shared launch.  Results
+ * are bit-identical to mg_sigmakin(MG_FP64) with a launch shape without MG_LAUNCH_SHARED.  Stream-ordered,
+ * graph-capturable once each context's scratch is large enough (mg_graph_create reserves it). */
+mg_status mg_sigmakin_batch(const mg_batch_job* jobs, int njobs, void* stream);
+
+/* Flags of mg_graph_create_ex. */
+#define MG_GRAPH_PERSISTENT 1   /* FP64 jobs: every job's matrix elements in one mg_sigmakin_batch launch */
+
 /* Capture the steps of njobs jobs (any mix of processes) into ONE CUDA graph, each job on its own
  * parallel branch; all scratch is reserved first, so launching the graph allocates nothing. */
 mg_status mg_graph_create(const mg_job* jobs, int njobs, mg_graph** out);
+
+/* As mg_graph_create; flags = MG_GRAPH_PERSISTENT (every job MG_FP64 with zero top width, at most 64 jobs,
+ * else MG_ENOTSUP / MG_EINVAL): each job's mg_rambo_range and mg_hel_filter on its own branch, then the
+ * matrix elements of all jobs in one persistent launch (mg_sigmakin_batch) and the helicity sums.
+ * mg_graph_update, _launch, _nodes and _destroy apply unchanged. */
+mg_status mg_graph_create_ex(const mg_job* jobs, int njobs, int flags, mg_graph** out);
 
 /* Replace the jobs' parameters (seeds, event ranges, sizes of an identical topology) in place
  * (cudaGraphExecUpdate); MG_EINVAL if the new jobs do not fit the captured topology. */

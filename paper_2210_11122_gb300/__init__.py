@@ -20,6 +20,7 @@ MG_FP64, MG_FP32_AMP, MG_FP64_TCCOLOR, MG_MIXED = 0, 1, 2, 3
 LAUNCH_UNROLLED, LAUNCH_DF_REDO, LAUNCH_FUSED, LAUNCH_WARP, LAUNCH_TC_APART, LAUNCH_SHARED = 1, 2, 4, 8, 16, 32
 LAUNCH_TC_SYNC = 64
 SERVE_MASK_SEED = 0x4D47   # mg.h MG_SERVE_MASK_SEED
+GRAPH_PERSISTENT = 1       # mg.h MG_GRAPH_PERSISTENT
 PAGE = 32
 
 STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "MG_ENOCONV", 5: "MG_EAGAIN",
@@ -41,6 +42,10 @@ class Job(ctypes.Structure):
     _fields_ = [("ctx", ctypes.c_void_p), ("seed", ctypes.c_uint64), ("e0", ctypes.c_int64), ("nevt", ctypes.c_int64),
                 ("sqrts", ctypes.c_double), ("mom_dev", ctypes.c_void_p), ("me_dev", ctypes.c_void_p),
                 ("precision", ctypes.c_int)]
+
+
+class BatchJob(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("mom_dev", ctypes.c_void_p), ("nevt", ctypes.c_int64), ("me_dev", ctypes.c_void_p)]
 
 
 class ServeCfg(ctypes.Structure):
@@ -97,13 +102,15 @@ def lib():
     L.mg_get_launch_shape.argtypes = [vp, i32, P(i32), P(i32), P(i32)]
     L.mg_set_launch_shape.argtypes = [vp, i32, i32, i32, i32]
     L.mg_graph_create.argtypes = [P(Job), i32, P(vp)]
+    L.mg_graph_create_ex.argtypes = [P(Job), i32, i32, P(vp)]
+    L.mg_sigmakin_batch.argtypes = [P(BatchJob), i32, vp]
     L.mg_graph_update.argtypes = [vp, P(Job), i32]
     L.mg_graph_launch.argtypes = [vp, vp]
     L.mg_graph_nodes.argtypes = [vp, P(i32)]
     L.mg_graph_destroy.argtypes = [vp]
     L.mg_graph_destroy.restype = None
-    for name in ("mg_autotune", "mg_get_launch_shape", "mg_set_launch_shape", "mg_graph_create", "mg_graph_update", "mg_graph_launch",
-                 "mg_graph_nodes"):
+    for name in ("mg_autotune", "mg_get_launch_shape", "mg_set_launch_shape", "mg_graph_create", "mg_graph_create_ex",
+                 "mg_graph_update", "mg_graph_launch", "mg_graph_nodes", "mg_sigmakin_batch"):
         getattr(L, name).restype = i32
     L.mg_serve_default_cfg.argtypes = [P(ServeCfg)]
     L.mg_serve_default_cfg.restype = None
@@ -430,14 +437,25 @@ class Server:
 # ------------------------------------------------------------------------------------------
 # graph batches
 # ------------------------------------------------------------------------------------------
+def sigmakin_batch(jobs, stream=None):
+    """FP64 MEs of several jobs in one persistent launch (mg_sigmakin_batch).
+    jobs: list of (Context, mom_tensor, nevt, me_tensor)."""
+    arr = (BatchJob * len(jobs))()
+    for i, (ctx, mom, nevt, me) in enumerate(jobs):
+        arr[i] = BatchJob(ctx._h, _ptr(mom), nevt, _ptr(me))
+    _check(lib().mg_sigmakin_batch(arr, len(jobs), _stream(stream)), "mg_sigmakin_batch")
+
+
 class GraphBatch:
-    """One CUDA graph running the full step of several jobs on parallel branches (mg_graph_*).
+    """One CUDA graph running the full step of several jobs on parallel branches (mg_graph_*), or with
+    persistent=True (FP64 jobs) all their matrix elements in one persistent launch (mg_graph_create_ex).
     jobs: list of (Context, seed, e0, nevt, sqrts, mom_tensor, me_tensor, precision)."""
 
-    def __init__(self, jobs):
+    def __init__(self, jobs, persistent=False):
         arr = self._jobs(jobs)
         h = ctypes.c_void_p()
-        _check(lib().mg_graph_create(arr, len(jobs), ctypes.byref(h)), "mg_graph_create")
+        _check(lib().mg_graph_create_ex(arr, len(jobs), GRAPH_PERSISTENT if persistent else 0, ctypes.byref(h)),
+               "mg_graph_create_ex")
         self._h = h
 
     @staticmethod

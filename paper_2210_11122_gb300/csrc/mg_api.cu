@@ -316,6 +316,7 @@ void mg_destroy(mg_ctx* ctx) {
   cudaFree(ctx->d_cmat);
   cudaFree(ctx->d_cumma);
   cudaFree(ctx->d_tcerr);
+  cudaFree(ctx->d_tiles);
   cudaFree(ctx->d_jamps);
   cudaFree(ctx->d_nallg);
   cudaFree(ctx->d_nbad);
@@ -403,7 +404,8 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
       mg::colour_umma_pack(c->ncol, num.data(), uh.data());
       if (cudaMalloc(&c->d_cumma, uh.size() * sizeof(uint16_t)) != cudaSuccess ||
           cudaMemcpy(c->d_cumma, uh.data(), uh.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess ||
-          cudaMalloc(&c->d_tcerr, sizeof(int)) != cudaSuccess || cudaMemset(c->d_tcerr, 0, sizeof(int)) != cudaSuccess) {
+          cudaMalloc(&c->d_tcerr, sizeof(int)) != cudaSuccess || cudaMemset(c->d_tcerr, 0, sizeof(int)) != cudaSuccess ||
+          cudaMalloc(&c->d_tiles, sizeof(unsigned long long)) != cudaSuccess) {
         st = MG_ENOMEM;
         break;
       }

@@ -221,6 +221,7 @@ struct mg_graph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int launches = 0;
+  int flags = 0;
 };
 
 extern "C" void mg_graph_destroy(mg_graph* g) {
@@ -260,7 +261,7 @@ mg_status check_jobs(const mg_job* jobs, int njobs) {
 
 // Capture the jobs into a new graph: a fork from one origin stream, each job's step on its own
 // branch, a join back.
-mg_status capture(const mg_job* jobs, int njobs, cudaGraph_t* out) {
+mg_status capture(const mg_job* jobs, int njobs, cudaGraph_t* out, bool persistent = false) {
   std::vector<cudaStream_t> streams(njobs, nullptr);
   std::vector<cudaEvent_t> done(njobs, nullptr);
   cudaStream_t origin = nullptr;
@@ -282,10 +283,15 @@ mg_status capture(const mg_job* jobs, int njobs, cudaGraph_t* out) {
     if (cudaStreamWaitEvent(streams[i], fork, 0) != cudaSuccess) { rc = MG_ECUDA; break; }
     rc = mg_rambo_range(j.ctx, j.seed, j.e0, j.nevt, j.sqrts, j.mom_dev, nullptr, streams[i]);
     if (rc == MG_OK) rc = mg_hel_filter(j.ctx, j.mom_dev, j.nevt, streams[i]);
-    if (rc == MG_OK) rc = mg_sigmakin(j.ctx, j.mom_dev, j.nevt, j.precision, j.me_dev, streams[i]);
+    if (rc == MG_OK && !persistent) rc = mg_sigmakin(j.ctx, j.mom_dev, j.nevt, j.precision, j.me_dev, streams[i]);
     if (rc == MG_OK && (cudaEventRecord(done[i], streams[i]) != cudaSuccess ||
                         cudaStreamWaitEvent(origin, done[i], 0) != cudaSuccess))
       rc = MG_ECUDA;
+  }
+  if (rc == MG_OK && persistent) {   // after every branch: all matrix elements in one persistent launch
+    std::vector<mg_batch_job> b(njobs);
+    for (int i = 0; i < njobs; ++i) b[i] = {jobs[i].ctx, jobs[i].mom_dev, jobs[i].nevt, jobs[i].me_dev};
+    rc = mg_sigmakin_batch(b.data(), njobs, origin);
   }
   cudaGraph_t graph = nullptr;
   if (capturing && cudaStreamEndCapture(origin, &graph) != cudaSuccess && rc == MG_OK) rc = MG_ECUDA;
@@ -308,13 +314,25 @@ mg_status capture(const mg_job* jobs, int njobs, cudaGraph_t* out) {
 }  // namespace
 
 extern "C" mg_status mg_graph_create(const mg_job* jobs, int njobs, mg_graph** out) {
+  return mg_graph_create_ex(jobs, njobs, 0, out);
+}
+
+extern "C" mg_status mg_graph_create_ex(const mg_job* jobs, int njobs, int flags, mg_graph** out) {
   if (!out) return MG_EINVAL;
   *out = nullptr;
+  if (flags & ~MG_GRAPH_PERSISTENT) return MG_EINVAL;
+  const bool persistent = (flags & MG_GRAPH_PERSISTENT) != 0;
   mg_status rc = check_jobs(jobs, njobs);
   if (rc != MG_OK) return rc;
+  if (persistent) {
+    if (njobs > 64) return MG_EINVAL;
+    for (int i = 0; i < njobs; ++i)
+      if (jobs[i].precision != MG_FP64 || jobs[i].ctx->prm.wt != 0.0) return MG_ENOTSUP;
+  }
   mg_graph* g = new (std::nothrow) mg_graph;
   if (!g) return MG_ENOMEM;
-  rc = capture(jobs, njobs, &g->graph);
+  g->flags = flags;
+  rc = capture(jobs, njobs, &g->graph, persistent);
   if (rc == MG_OK && cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess) { cudaGetLastError(); rc = MG_ECUDA; }
   if (rc == MG_OK) {
     size_t n = 0;
@@ -332,8 +350,11 @@ extern "C" mg_status mg_graph_update(mg_graph* g, const mg_job* jobs, int njobs)
   if (!g || !g->exec) return MG_EINVAL;
   mg_status rc = check_jobs(jobs, njobs);
   if (rc != MG_OK) return rc;
+  if (g->flags & MG_GRAPH_PERSISTENT)
+    for (int i = 0; i < njobs; ++i)
+      if (jobs[i].precision != MG_FP64 || jobs[i].ctx->prm.wt != 0.0) return MG_ENOTSUP;
   cudaGraph_t ng = nullptr;
-  rc = capture(jobs, njobs, &ng);
+  rc = capture(jobs, njobs, &ng, (g->flags & MG_GRAPH_PERSISTENT) != 0);
   if (rc != MG_OK) return rc;
   cudaGraphExecUpdateResultInfo info;
   if (cudaGraphExecUpdate(g->exec, ng, &info) != cudaSuccess) {
