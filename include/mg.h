@@ -241,6 +241,27 @@ mg_status mg_sigmakin_lhe(mg_ctx* ctx, const double* mom_dev, int64_t nevt, cons
 mg_status mg_alphas_running(mg_ctx* ctx, const double* mom_dev, int64_t nevt, double* me_dev, double* alphas_dev,
                             void* stream);
 
+/* Single-diagram-enhancement channel weights (MadEvent's phase-space channels; the paper's Sec. 2 lists the
+ * algorithm among the engine's features).  Channel d is a Feynman diagram built from three-point vertices
+ * only (3 / 15 / 105 / 945 for n_g = 0..3; a diagram with a four-gluon vertex has no propagator structure of
+ * its own and is no channel): an ordered list of binary gluon trees attached along the quark line from the
+ * top to the antitop, the trees' gluons partitioning the gluons.  Per event e (FP64):
+ *     w_dev[d * nevt + e] = sum_h |A_d(h)|^2 / sum_d' sum_h |A_d'(h)|^2   (good helicities h),
+ * A_d the diagram's amplitude with its colour factor stripped (Feynman-gauge vertices and propagators; the
+ * couplings and phases, common to all channels, cancel).  w_dev holds nchannels * nevt doubles.  Zero top
+ * width (MG_ENOTSUP otherwise); if no helicity mask exists yet, the call first runs mg_hel_filter on its
+ * own first events.  Scratch (events in chunks of at most 2 GiB of per-channel sums) is owned by the context. */
+mg_status mg_sde_weights(mg_ctx* ctx, const double* mom_dev, int64_t nevt, double* w_dev, void* stream);
+
+/* Number of channels of a process.  Host only. */
+mg_status mg_sde_channels(mg_process proc, int* nchannels);
+
+/* The channel's diagram as text into key (keylen bytes, NUL-terminated; MG_EINVAL if too short): its gluon
+ * trees in quark-line order from the top, joined by "|"; a tree is a gluon label (1, 2 the incoming gluons,
+ * 3.. the final-state ones) or "(A,B)", the child holding the smaller label first.  E.g. for gg -> t tbar:
+ * "1|2", "2|1", "(1,2)".  Host only. */
+mg_status mg_sde_channel_key(mg_process proc, int channel, char* key, int keylen);
+
 /* The gluon ordering of colour flow `flow` (0 <= flow < (n_g+2)!): order[i] = gluon label (0 = g1, 1 = g2,
  * 2.. = final-state gluons g3..) at position i along the quark line, flow = lexicographic rank of the
  * permutation; the flow's colour factor is (T^{a_order[0]} ... T^{a_order[K-1]})_{i_t j_tbar}.  Host only. */

@@ -94,6 +94,9 @@ def lib():
     L.mg_sigmakin_lhe.argtypes = [vp, vp, i64, vp, vp, i32, vp, vp, vp, vp, vp]
     L.mg_alphas_running.argtypes = [vp, vp, i64, vp, vp, vp]
     L.mg_colour_flow.argtypes = [i32, i32, P(i32)]
+    L.mg_sde_weights.argtypes = [vp, vp, i64, vp, vp]
+    L.mg_sde_channels.argtypes = [i32, P(i32)]
+    L.mg_sde_channel_key.argtypes = [i32, i32, ctypes.c_char_p, i32]
     L.mg_hel_mask.argtypes = [vp, P(ctypes.c_uint32), P(i32)]
     L.mg_check.argtypes = [vp, vp, P(ctypes.c_int64)]
     L.mg_flops_per_event.argtypes = [i32, i32, P(ctypes.c_uint32), P(dbl), P(dbl)]
@@ -128,7 +131,7 @@ def lib():
     for name in ("mg_process_info", "mg_colour_matrix", "mg_create", "mg_philox", "mg_rambo", "mg_rambo_range",
                  "mg_measure_fma_peak", "mg_hel_filter",
                  "mg_sigmakin", "mg_sigmakin_host", "mg_sigmakin_noalloc", "mg_sigmakin_lhe", "mg_alphas_running",
-                 "mg_colour_flow", "mg_hel_mask", "mg_check", "mg_flops_per_event",
+                 "mg_colour_flow", "mg_sde_weights", "mg_sde_channels", "mg_sde_channel_key", "mg_hel_mask", "mg_check", "mg_flops_per_event",
                  "mg_flops_per_event_shape"):
         getattr(L, name).restype = i32
     _lib = L
@@ -200,6 +203,18 @@ def colour_matrix(process):
     _check(lib().mg_colour_matrix(_proc(process), num.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                   ctypes.byref(den)), "mg_colour_matrix")
     return num, den.value
+
+
+def sde_channels(process):
+    """Keys of the single-diagram-enhancement channels of a process, in channel order (mg_sde_channel_key)."""
+    n = ctypes.c_int()
+    _check(lib().mg_sde_channels(_proc(process), ctypes.byref(n)), "mg_sde_channels")
+    buf = ctypes.create_string_buffer(256)
+    out = []
+    for c in range(n.value):
+        _check(lib().mg_sde_channel_key(_proc(process), c, buf, 256), "mg_sde_channel_key")
+        out.append(buf.value.decode())
+    return out
 
 
 def colour_flow(process, flow):
@@ -321,6 +336,10 @@ class Context:
         caller's uniforms) and optionally the one-loop running coupling at mu = H_T/2 (see mg.h)."""
         _check(lib().mg_sigmakin_lhe(self._h, _ptr(mom), nevt, _ptr(rnd_hel), _ptr(rnd_col), 1 if running_alphas else 0,
                                      _ptr(me), _ptr(hel), _ptr(col), _ptr(alphas), _stream(stream)), "mg_sigmakin_lhe")
+
+    def sde_weights(self, mom, nevt, w, stream=None):
+        """Single-diagram-enhancement weights w[channel * nevt + e] (mg_sde_weights)."""
+        _check(lib().mg_sde_weights(self._h, _ptr(mom), nevt, _ptr(w), _stream(stream)), "mg_sde_weights")
 
     def alphas_running(self, mom, nevt, me, alphas=None, stream=None):
         """In place: me[e] *= (alpha_s(H_T/2)/alpha_s)^(n_g+2), one-loop running (see mg.h)."""

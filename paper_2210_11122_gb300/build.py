@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libmg.so")
-SOURCES = ["mg_api.cu", "mg_rambo.cu", "mg_me.cu", "mg_me2.cu", "mg_me3.cu", "mg_me3_k23.cu", "mg_me3_k4s.cu", "mg_me3_k4f.cu", "mg_me_dd.cu", "mg_me_warp.cu", "mg_colour_tc.cu", "mg_peak.cu", "mg_noalloc.cu", "mg_lhe.cu", "mg_persist.cu", "mg_serve.cu", "mg_tune.cu", "mg_colour.cpp", "mg_tables.cpp"]
+SOURCES = ["mg_api.cu", "mg_rambo.cu", "mg_me.cu", "mg_me2.cu", "mg_me3.cu", "mg_me3_k23.cu", "mg_me3_k4s.cu", "mg_me3_k4f.cu", "mg_me_dd.cu", "mg_me_warp.cu", "mg_colour_tc.cu", "mg_peak.cu", "mg_noalloc.cu", "mg_lhe.cu", "mg_persist.cu", "mg_sde.cu", "mg_serve.cu", "mg_tune.cu", "mg_colour.cpp", "mg_tables.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -328,6 +328,8 @@ void mg_destroy(mg_ctx* ctx) {
   cudaFree(ctx->d_flag);
   cudaFree(ctx->d_share);
   cudaFree(ctx->d_j2);
+  cudaFree(ctx->d_sdetab);
+  cudaFree(ctx->d_sde);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->side) cudaStreamDestroy(ctx->side);

@@ -44,6 +44,9 @@ struct mg_ctx {
   int64_t repair_cap = 0;
   double* d_j2 = nullptr;      // mg_sigmakin_lhe: per-slot sums of |jamp|^2 over good helicities (one chunk)
   int64_t j2_cap = 0;         // in doubles
+  void* d_sdetab = nullptr;    // mg_sde_weights: trees and walk of the channels (uploaded on first use)
+  double* d_sde = nullptr;     // per-slot channel sums (one chunk of events)
+  int64_t sde_cap = 0;         // in doubles
   double* d_share = nullptr;   // FP64: currents shared between gluon-helicity combinations (one chunk of events)
   int64_t share_cap = 0;      // in doubles
   cudaStream_t side = nullptr;         // FP32 modes: the FP64 recomputation runs here, beside the FP32 launches

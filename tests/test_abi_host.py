@@ -174,3 +174,13 @@ def test_colour_flow_is_the_lexicographic_permutation(mg):
             assert mg.colour_flow(proc, c) == list(perm)
         with pytest.raises(mg.MGError):
             mg.colour_flow(proc, len(list(permutations(range(k)))))
+
+
+def test_sde_channel_keys_equal_the_oracles(mg):
+    """The library's single-diagram-enhancement channels (its own enumeration) are the oracle's, key for
+    key (3 / 15 / 105 / 945 three-point-vertex diagrams)."""
+    from oracle import sde
+    for ng, proc in enumerate(("ggtt", "ggttg", "ggttgg", "ggttggg")):
+        keys = mg.sde_channels(proc)
+        assert len(keys) == len(set(keys)) == [3, 15, 105, 945][ng]
+        assert set(keys) == {sde.key(d) for d in sde.diagrams(ng)}
