@@ -130,16 +130,18 @@ mg_status mg_rambo(mg_ctx* ctx, uint64_t seed, int64_t nevt, double sqrts, doubl
 mg_status mg_rambo_range(mg_ctx* ctx, uint64_t seed, int64_t e0, int64_t nevt, double sqrts, double* mom_dev,
                          double* wgt_dev, void* stream);
 
-/* Helicity filter: recompute the context's helicity mask from the first min(nevt, hel_warmup)
- * events of mom_dev (AoSoA).  good(h) <=> max_e |M_h|^2 / sum_h' |M_h'|^2 > hel_tau, the ratios taken in
+/* Helicity filter (the paper's Sec. 2: the engine sums only the helicities that contribute; which ones do
+ * is found once from a sample of events): recompute the context's helicity mask from the first
+ * min(nevt, hel_warmup) events of mom_dev (AoSoA).  good(h) <=> max_e |M_h|^2 / sum_h' |M_h'|^2 > hel_tau, the ratios taken in
  * FP64 from FP32-amplitude colour sums (zero top width; FP64 otherwise): with the default hel_tau the kept
  * and the vanishing helicities of these processes are at least six decades apart, so FP32 rounding cannot
  * change the mask.  Stream-ordered; the mask is used by every later mg_sigmakin on this context. */
 mg_status mg_hel_filter(mg_ctx* ctx, const double* mom_dev, int64_t nevt, void* stream);
 
-/* Matrix elements: me_dev[e] = ME of event e of mom_dev (AoSoA), e < nevt.  If no helicity mask
- * has been computed yet, the first call runs mg_hel_filter on its own first events.  precision
- * selects the arithmetic (MG_ENOTSUP if not built). */
+/* Matrix elements (the per-event hot path of the paper's Sec. 2, its "sigmaKin": every tree diagram,
+ * colour sum and helicity sum of one event; throughput N_events / t_MEs, Tables 1-2): me_dev[e] = ME of
+ * event e of mom_dev (AoSoA), e < nevt.  If no helicity mask has been computed yet, the first call runs
+ * mg_hel_filter on its own first events.  precision selects the arithmetic (MG_ENOTSUP if not built). */
 mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_precision precision, double* me_dev,
                       void* stream);
 
@@ -153,11 +155,14 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
 mg_status mg_sigmakin_host(mg_ctx* ctx, const double* mom_host, int64_t nevt, mg_precision precision,
                            double* me_host, void* stream);
 
-/* Copy the current helicity mask (ceil(nhel/32) words, bit h of word h/32) to mask_host and the
- * number of good helicities to *ngood.  Synchronises the context's last stream. */
+/* The helicity mask of the filter above (paper Sec. 2; a test and diagnostics hook): copy the current mask
+ * (ceil(nhel/32) words, bit h of word h/32) to mask_host and the number of good helicities to *ngood.
+ * Synchronises the context's last stream. */
 mg_status mg_hel_mask(mg_ctx* ctx, uint32_t* mask_host, int* ngood);
 
-/* Wait for the context's work on stream and report device-side conditions: MG_ETIMEOUT if a bounded
+/* Device-side conditions of the random numbers -> momenta -> ME workflow (paper Sec. 1, Fig. 1) that a
+ * stream-ordered call cannot return synchronously.
+ * Wait for the context's work on stream and report device-side conditions: MG_ETIMEOUT if a bounded
  * wait inside the tensor-memory colour kernel gave up (its results are then invalid), MG_ENOCONV if any
  * event since the last mg_check failed to converge in RAMBO (the count goes to *nbad if not
  * NULL), MG_ECUDA on an asynchronous CUDA error, else MG_OK.  Clears the conditions. */

@@ -17,8 +17,11 @@ has n_g + 2 vertices, so g and the phases are common to all and cancel in w_d):
 A diagram is the ordered list of gluon trees attached along the quark line from the top (ubar) to the
 antitop (v); each tree is a binary tree over a subset of the gluons, the subsets partitioning them.
 
-Written directly from those rules with 4x4 gamma matrices and the angle-based wavefunctions of
-fullcolour.py, independently of me_oracle.cpp.  Channel keys: a gluon tree is its leaf label (1-based
+Written directly from those rules with the 4x4 gamma matrices of fullcolour.py and wavefunctions of its
+own (the HELAS helicity states in the chiral basis, from the momentum components: cos(theta/2) and
+sin(theta/2) as square roots of (|p| +- pz) / 2|p|, the form of |p| + pz without cancellation for pz < 0,
+so every component keeps full FP64 precision near the beam axis, where angles from acos do not),
+independently of me_oracle.cpp.  Channel keys: a gluon tree is its leaf label (1-based
 gluon index: 1, 2 incoming, 3.. outgoing) or "(A,B)" with the child holding the smaller label first;
 a diagram joins its trees with "|" in quark-line order.
 """
@@ -101,6 +104,55 @@ def _v3(jl, pl, jr, pr):
     return _dot(jl, jr) * (pl - pr) + _dot(jl, pl + 2 * pr) * jr - _dot(jr, 2 * pl + pr) * jl
 
 
+def _chi(p3, lam):
+    """Two-component helicity eigenspinor (sigma.p) chi = lam |p| chi: chi_+ = (cos t/2, e^{i phi} sin t/2),
+    chi_- = (-e^{-i phi} sin t/2, cos t/2), from the components (the theta -> pi limit at phi = 0 on -z)."""
+    px, py, pz = p3
+    pt2 = px * px + py * py
+    pp = math.sqrt(pt2 + pz * pz)
+    ppz = pp + pz if pz >= 0 else pt2 / (pp - pz)          # |p| + pz
+    if ppz <= 0:
+        return np.array([0, 1], dtype=complex) if lam > 0 else np.array([-1, 0], dtype=complex)
+    n = 1 / math.sqrt(2 * pp * ppz)
+    c, sp = ppz * n, complex(px, py) * n                   # cos t/2, e^{i phi} sin t/2
+    return np.array([c, sp]) if lam > 0 else np.array([-sp.conjugate(), c])
+
+
+def _ubar(p, m, lam):
+    """ubar = u^dagger gamma^0, u = (sqrt(E - lam|p|) chi_lam ; sqrt(E + lam|p|) chi_lam)."""
+    pp = math.sqrt(p[1] ** 2 + p[2] ** 2 + p[3] ** 2)
+    wp = math.sqrt(p[0] + pp)
+    wm = m / wp if m > 0 else 0.0                          # sqrt(E - |p|) = m / sqrt(E + |p|)
+    c = _chi(p[1:], lam)
+    u = np.concatenate([(wm if lam > 0 else wp) * c, (wp if lam > 0 else wm) * c])
+    return u.conj() @ fc.GAMMA0
+
+
+def _v(p, m, lam):
+    """Outgoing antifermion of physical helicity lam: (-lam sqrt(E + lam|p|) chi_-lam ; lam sqrt(E - lam|p|) chi_-lam)."""
+    pp = math.sqrt(p[1] ** 2 + p[2] ** 2 + p[3] ** 2)
+    wp = math.sqrt(p[0] + pp)
+    wm = m / wp if m > 0 else 0.0
+    c = _chi(p[1:], -lam)
+    return np.concatenate([(-wp if lam > 0 else wm) * c, (wm if lam > 0 else -wp) * c])
+
+
+def _eps(k, lam):
+    """epsilon(k, lam) = (0, (-lam e_theta - i e_phi)/sqrt 2) from the components (phi = 0 on the z axis)."""
+    kx, ky, kz = k[1], k[2], k[3]
+    kt = math.sqrt(kx * kx + ky * ky)
+    kk = math.sqrt(kt * kt + kz * kz)
+    if kt > 0:
+        e_th = np.array([kx * kz / (kk * kt), ky * kz / (kk * kt), -kt / kk])
+        e_ph = np.array([-ky / kt, kx / kt, 0.0])
+    else:
+        e_th = np.array([1.0 if kz >= 0 else -1.0, 0.0, 0.0])
+        e_ph = np.array([0.0, 1.0, 0.0])
+    e = np.zeros(4, dtype=complex)
+    e[1:] = (-lam * e_th - 1j * e_ph) / math.sqrt(2)
+    return e
+
+
 def externals(ng, p, hel, mt):
     npar = ng + 4
     lam = [1 if (hel >> (npar - 1 - i)) & 1 else -1 for i in range(npar)]
@@ -108,10 +160,10 @@ def externals(ng, p, hel, mt):
     q = [np.array(p[part[g]], dtype=float) if g < 2 else -np.array(p[part[g]], dtype=float) for g in range(ng + 2)]
     eps = []
     for g in range(ng + 2):
-        e = fc.polarisation(np.array(p[part[g]], dtype=float), lam[part[g]])
+        e = _eps(np.array(p[part[g]], dtype=float), lam[part[g]])
         eps.append(e if g < 2 else e.conj())
-    ub = fc.spinor_ubar(np.array(p[2], dtype=float), mt, lam[2])
-    v = fc.spinor_v(np.array(p[3], dtype=float), mt, lam[3])
+    ub = _ubar(np.array(p[2], dtype=float), mt, lam[2])
+    v = _v(np.array(p[3], dtype=float), mt, lam[3])
     return q, eps, ub, v
 
 

@@ -25,6 +25,21 @@
 namespace mg {
 namespace wk {
 
+// Two FP32 values in one 64-bit register pair, and the paired fused multiply-add d = a b + c of each half
+// (Blackwell's FFMA2: one instruction for two FP32 FMAs)
+__device__ __forceinline__ uint64_t pack2(float2 v) {
+  return (static_cast<uint64_t>(__float_as_uint(v.y)) << 32) | __float_as_uint(v.x);
+}
+__device__ __forceinline__ float2 unpack2(uint64_t v) {
+  return make_float2(__uint_as_float(static_cast<uint32_t>(v)), __uint_as_float(static_cast<uint32_t>(v >> 32)));
+}
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+
 using v2::cx;
 
 constexpr int kWarps = 4;   // warps per block; a block holds slots of one event
@@ -305,36 +320,38 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
   } else if constexpr (EPI == kSimt) {
     // colour sums of the four helicities at once: lane l forms rows x = l, l + G, ... of w_h = C A_h
     // (C symmetric: row y of C read along x, coalesced; each C value feeds 8 FMAs), then A_h^* . w_h
+    // (real, imaginary) pairs on Blackwell's paired FP32 FMA: one instruction per colour-matrix entry
+    // and helicity instead of two
     constexpr int XR = (NCOL + G - 1) / G;   // rows per lane
-    float wr[4][XR] = {}, wi[4][XR] = {};
-    for (int y = 0; y < NCOL; ++y) {
-      float2 ay[4];
+    uint64_t w2[4][XR];
 #pragma unroll
-      for (int h = 0; h < 4; ++h) ay[h] = S.A[h][y];
+    for (int h = 0; h < 4; ++h)
+#pragma unroll
+      for (int k = 0; k < XR; ++k) w2[h][k] = 0ull;
+    for (int y = 0; y < NCOL; ++y) {
+      uint64_t ay[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) ay[h] = pack2(S.A[h][y]);
 #pragma unroll
       for (int k = 0; k < XR; ++k) {
         const int x = lane + G * k;
         const float cxy = x < NCOL ? __ldg(cfull + y * NCOL + x) : 0.f;
+        const uint64_t cc = pack2(make_float2(cxy, cxy));
 #pragma unroll
-        for (int h = 0; h < 4; ++h) {
-          wr[h][k] = fmaf(cxy, ay[h].x, wr[h][k]);
-          wi[h][k] = fmaf(cxy, ay[h].y, wi[h][k]);
-        }
+        for (int h = 0; h < 4; ++h) w2[h][k] = ffma2(cc, ay[h], w2[h][k]);
       }
     }
     float total = 0.f;   // summed in FP32 (these are FP32 colour sums), widened exactly at the end
 #pragma unroll
     for (int h = 0; h < 4; ++h) {   // jamps of helicities outside the mask are zero: no branch needed
-      float s = 0.f;
+      uint64_t s2 = 0ull;
 #pragma unroll
       for (int k = 0; k < XR; ++k) {
         const int x = lane + G * k;
-        if (x < NCOL) {
-          const float2 ax = S.A[h][x];
-          s = fmaf(ax.x, wr[h][k], s);
-          s = fmaf(ax.y, wi[h][k], s);
-        }
+        if (x < NCOL) s2 = ffma2(pack2(S.A[h][x]), w2[h][k], s2);
       }
+      const float2 sp = unpack2(s2);
+      float s = sp.x + sp.y;
 #pragma unroll
       for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, G);
       if (good[h]) total += s;
