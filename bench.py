@@ -437,6 +437,40 @@ class Leg:
         self.ctx.close()
 
 
+def epilogue_leg(leg, reps=2):
+    """Event-level epilogues on the leg's momenta (one call = all events; CUDA events): FP64 matrix elements
+    with the per-event helicity and colour choices and the running coupling (mg_sigmakin_lhe), and the
+    single-diagram-enhancement weights of every channel (mg_sde_weights), beside plain FP64 mg_sigmakin."""
+    torch, mg = leg.torch, leg.mg
+    n = leg.nevt
+    gen = torch.Generator(device="cuda").manual_seed(12345)
+    rh = torch.rand(n, dtype=torch.float64, device="cuda", generator=gen)
+    rc = torch.rand(n, dtype=torch.float64, device="cuda", generator=gen)
+    hel = torch.zeros(n, dtype=torch.int32, device="cuda")
+    col = torch.zeros(n, dtype=torch.int32, device="cuda")
+    nch = len(mg.sde_channels(leg.ng))
+    w = torch.zeros(nch * n, dtype=torch.float64, device="cuda")
+
+    def t(fn):
+        with torch.cuda.stream(leg.stream):
+            fn()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(leg.stream)
+            for _ in range(reps):
+                fn()
+            ev[1].record(leg.stream)
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / reps
+
+    lhe = t(lambda: leg.ctx.sigmakin_lhe(leg.mom, n, leg.me_x, rh, rc, hel, col, True, None, stream=leg.stream))
+    sde = t(lambda: leg.ctx.sde_weights(leg.mom, n, w, stream=leg.stream))
+    return {"lhe_ms": lhe, "lhe_MEs_per_s": n / (lhe * 1e-3), "sde_ms": sde, "sde_events_per_s": n / (sde * 1e-3),
+            "sde_channels": nch,
+            "what": "mg_sigmakin_lhe (FP64 MEs + helicity and leading-colour choices + one-loop running alpha_s at "
+                    "H_T/2) and mg_sde_weights (single-diagram-enhancement weights of every channel), one call "
+                    "over the workload's events"}
+
+
 def measure_leg(leg, steps, warmup, world, peaks, oracle_flops, modes=MODES):
     """Every precision mode of one process: rates of the whole step and of mg_sigmakin alone, the
     per-event error against the FP64 result of the same events, and the rooflines."""
@@ -554,11 +588,13 @@ def run_ours(args):
                          "roofline": roofline}}
     headline.update(variants)
     shapes = leg.shapes
+    epi = epilogue_leg(leg)
     leg.close()
 
     # ---- every other process of the workloads at its own size: FP64 and the three other modes ----
     processes = {args.process: {"events_per_gpu": nevt, "seed": WORKLOADS[args.process]["seed"],
-                                "good_helicities": ngood, "modes": headline, "launch_shapes": shapes}}
+                                "good_helicities": ngood, "modes": headline, "launch_shapes": shapes,
+                                "epilogues": epi}}
     if not args.no_processes:
         for p in ("ggtt", "ggttg", "ggttgg", "ggttggg"):
             if p == args.process:
@@ -569,7 +605,7 @@ def run_ours(args):
             modes = measure_leg(lg, steps, 3, world, peaks, oflops.get(p, (0, 0))[1])
             _, g = lg.ctx.hel_mask()
             processes[p] = {"events_per_gpu": n, "seed": WORKLOADS[p]["seed"], "good_helicities": g, "modes": modes,
-                            "launch_shapes": lg.shapes}
+                            "launch_shapes": lg.shapes, "epilogues": epilogue_leg(lg)}
             lg.close()
             torch.cuda.empty_cache()
 
