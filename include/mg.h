@@ -453,6 +453,12 @@ mg_status mg_measure_fma_peak(int fp32, int iters, double* flops_per_s);
  * them.  Host only; never fails. */
 int64_t mg_kernel_launches(void);
 
+/* Diagnostics of the failure path (no counterpart in the paper): with on = 1 the tensor-memory colour
+ * pass on this context issues no MMAs, so each CTA's bounded mbarrier wait runs out (after 0.2 s): the
+ * kernel records it, frees its tensor memory and returns; mg_check then reports MG_ETIMEOUT and the
+ * context stays usable.  on = 0 restores normal operation.  Host only; no fault, trap or hang. */
+mg_status mg_diag_tc_stall(mg_ctx* ctx, int on);
+
 #ifdef __cplusplus
 }
 #endif

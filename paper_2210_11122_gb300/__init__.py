@@ -86,6 +86,8 @@ def lib():
     L.mg_rambo_range.argtypes = [vp, u64, i64, i64, dbl, vp, vp, vp]
     L.mg_measure_fma_peak.argtypes = [i32, i32, P(dbl)]
     L.mg_kernel_launches.argtypes = []
+    L.mg_diag_tc_stall.argtypes = [vp, i32]
+    L.mg_diag_tc_stall.restype = i32
     L.mg_kernel_launches.restype = i64
     L.mg_hel_filter.argtypes = [vp, vp, i64, vp]
     L.mg_sigmakin.argtypes = [vp, vp, i64, i32, vp, vp]
@@ -371,6 +373,10 @@ class Context:
         n = ctypes.c_int()
         _check(lib().mg_hel_mask(self._h, m, ctypes.byref(n)), "mg_hel_mask")
         return np.array(list(m), dtype=np.uint32), n.value
+
+    def diag_tc_stall(self, on):
+        """Diagnostics: the tensor-memory colour pass issues no MMAs, so its bounded waits run out."""
+        _check(lib().mg_diag_tc_stall(self._h, 1 if on else 0), "mg_diag_tc_stall")
 
     def check(self, stream=None):
         """Returns the number of RAMBO events that failed to converge since the last check."""

@@ -641,7 +641,8 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
                                      ctx->d_part, cst_stride, st, fp32 ? ctx->d_flag : nullptr));
       else
         MG_CUDA(mg::launch_colour_umma(ctx->ncol, ctx->d_jamps, n, ctx->nhel, ctx->d_nrows, ctx->d_cumma, cst.colour_scale,
-                                       ctx->d_part, cst_stride, st, fp32 ? ctx->d_flag : nullptr, ctx->d_tcerr));
+                                       ctx->d_part, cst_stride, st, fp32 ? ctx->d_flag : nullptr, ctx->d_tcerr,
+                                       ctx->tc_stall));
       if (fp32) MG_CUDA(join_repair(ctx, st));
       MG_CUDA(mg::launch_hel_sum(ctx->d_part, ctx->d_nrows, n, cst_stride, norm, me_dev + e0, st));
     }
@@ -793,5 +794,11 @@ mg_status mg_check(mg_ctx* ctx, void* stream, int64_t* nbad) {
 }
 
 int64_t mg_kernel_launches(void) { return mg::g_launches.load(std::memory_order_relaxed); }
+
+mg_status mg_diag_tc_stall(mg_ctx* ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) return MG_EINVAL;
+  ctx->tc_stall = on;
+  return MG_OK;
+}
 
 }  // extern "C"

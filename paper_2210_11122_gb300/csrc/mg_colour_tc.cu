@@ -411,13 +411,30 @@ __device__ __forceinline__ float dot8(uint4 h, uint4 l, const uint32_t* y, float
   return acc;
 }
 
-constexpr long long kUmmaSpin = 1ll << 22;   // bounded waits (the MMAs of a stage take about a microsecond)
+constexpr long long kUmmaSpin = 1ll << 22;      // bounded waits (the MMAs of a stage take about a microsecond):
+constexpr unsigned long long kUmmaWaitNs = 200000000ull;   // give up after 2^22 polls or 0.2 s, whichever first
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait for the completion of parity `parity` of the mbarrier at shared address bar, bounded.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = globaltimer_ns();
+  for (long long n = 0; n < kUmmaSpin; ++n) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((n & 255) == 255 && globaltimer_ns() - t0 > kUmmaWaitNs) return false;
+  }
+  return false;
+}
 
 template <int NCOL>
 __global__ void __launch_bounds__(256, 1)
 k_colour_umma(const float2* __restrict__ jamps, int64_t nevt, int rows_log2, const int* __restrict__ nrows_dev,
               const uint16_t* __restrict__ cumma, double scale, double* __restrict__ out, int64_t stride,
-              const uint8_t* __restrict__ skip, int* __restrict__ err) {
+              const uint8_t* __restrict__ skip, int* __restrict__ err, int stall) {
   using U = Umma<NCOL>;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -555,7 +572,7 @@ k_colour_umma(const float2* __restrict__ jamps, int64_t nevt, int rows_log2, con
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && !stall) {   // (stall: the diagnostics mode that lets the bounded wait run out)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t h = smem_addr(ahi), l = smem_addr(alo), bb = smem_addr(sB);
       const uint32_t d = tmem + buf * 128;
@@ -577,13 +594,7 @@ k_colour_umma(const float2* __restrict__ jamps, int64_t nevt, int rows_log2, con
   // stage st (buffer buf), whose MMAs were committed: quadratic forms and outputs
   uint32_t phases = 0;   // bit b: parity of the next completion of buffer b's mbarrier
   auto consume = [&](int64_t st, int buf) -> bool {
-    {
-      long long n = 0;
-      bool done = false;
-      while (!(done = mbar_try_wait(smem_addr(bar + buf), (phases >> buf) & 1u)) && ++n < kUmmaSpin) {
-      }
-      if (!done) *abort_flag = 1;
-    }
+    if (!mbar_wait_bounded(smem_addr(bar + buf), (phases >> buf) & 1u)) *abort_flag = 1;
     phases ^= 1u << buf;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
@@ -673,11 +684,8 @@ k_colour_umma(const float2* __restrict__ jamps, int64_t nevt, int rows_log2, con
     if (prev >= 0) {
       if (!consume(prev, buf ^ 1)) {
         if (tid == 0) atomicCAS(err, 0, static_cast<int>(prev % 1000000) + 1);
-        if (st < nstage) {   // the stage just issued: let its MMAs finish (bounded) before the memory goes
-          long long n = 0;
-          while (!mbar_try_wait(smem_addr(bar + buf), (phases >> buf) & 1u) && ++n < kUmmaSpin) {
-          }
-        }
+        if (st < nstage && !stall)   // the stage just issued: let its MMAs finish (bounded) before the memory goes
+          mbar_wait_bounded(smem_addr(bar + buf), (phases >> buf) & 1u);
         break;
       }
     }
@@ -763,7 +771,8 @@ void colour_umma_pack(int ncol, const int64_t* num, uint16_t* out_halves) {
 
 template <int NCOL>
 static cudaError_t launch_umma(const float2* jamps, int64_t nevt, int rows_alloc, const int* nrows, const uint16_t* cumma,
-                               double scale, double* out, int64_t stride, const uint8_t* skip, int* err, cudaStream_t st) {
+                               double scale, double* out, int64_t stride, const uint8_t* skip, int* err, int stall,
+                               cudaStream_t st) {
   using U = Umma<NCOL>;
   int rows_log2 = 0;
   while ((1 << rows_log2) < rows_alloc) ++rows_log2;
@@ -787,21 +796,20 @@ static cudaError_t launch_umma(const float2* jamps, int64_t nevt, int rows_alloc
   if (blocks > nstage) blocks = nstage;
   if (blocks < 1) return cudaSuccess;
   { k_colour_umma<NCOL><<<static_cast<unsigned>(blocks), U::THREADS, U::SMEM, st>>>(jamps, nevt, rows_log2, nrows, cumma, scale,
-                                                                                  out, stride, skip, err); mg::note_launch(); }
+                                                                                  out, stride, skip, err, stall); mg::note_launch(); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_colour_umma(int ncol, const float2* jamps, int64_t nevt, int rows_alloc, const int* nrows,
                                const void* cumma, double scale, double* out, int64_t stride, cudaStream_t st,
-                               const uint8_t* skip, int* err) {
+                               const uint8_t* skip, int* err, int stall) {
   const uint16_t* c = static_cast<const uint16_t*>(cumma);
   switch (ncol) {
-    case 2: return launch_umma<2>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, err, st);
-    case 6: return launch_umma<6>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, err, st);
-    case 24: return launch_umma<24>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, err, st);
-    case 120: return launch_umma<120>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, err, st);
+    case 2: return launch_umma<2>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, err, stall, st);
+    case 6: return launch_umma<6>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, err, stall, st);
+    case 24: return launch_umma<24>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, err, stall, st);
+    case 120: return launch_umma<120>(jamps, nevt, rows_alloc, nrows, c, scale, out, stride, skip, err, stall, st);
     default: return cudaErrorInvalidValue;
   }
 }
-
 }  // namespace mg

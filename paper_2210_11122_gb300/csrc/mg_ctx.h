@@ -28,6 +28,7 @@ struct mg_ctx {
   void* d_cmat = nullptr;     // colour matrix numerators as the packed FP16 tensor-core operand
   void* d_cumma = nullptr;    // the same as the tcgen05 B operand (canonical no-swizzle K-major layout)
   int* d_tcerr = nullptr;     // nonzero: a bounded wait of the tcgen05 colour kernel gave up
+  int tc_stall = 0;           // diagnostics (mg_diag_tc_stall): the tcgen05 colour kernel issues no MMAs
   unsigned long long* d_tiles = nullptr;   // mg_sigmakin_batch: tile counter of the persistent launch
   float2* d_jamps = nullptr;  // FP32 jamps of the tensor-core colour path
   int64_t jamp_cap = 0;       // in float2

@@ -115,7 +115,7 @@ int colour_umma_halves(int ncol);
 void colour_umma_pack(int ncol, const int64_t* num, uint16_t* out_halves);
 cudaError_t launch_colour_umma(int ncol, const float2* jamps, int64_t nevt, int rows_alloc, const int* nrows,
                                const void* cumma, double scale, double* out, int64_t stride, cudaStream_t st,
-                               const uint8_t* skip, int* err);
+                               const uint8_t* skip, int* err, int stall = 0);
 void colour_tc_pack(int ncol, const int64_t* num, uint16_t* out_halves);
 cudaError_t launch_colour_tc(int ncol, const float2* jamps, int64_t nevt, int rows_alloc, const int* nrows,
                              const void* cmat, double scale, double* out, int64_t stride, cudaStream_t st,

@@ -140,6 +140,7 @@ def test_invalid_arguments_rejected_without_gpu(mg):
     assert L.mg_rambo(None, 1, 10, 1500.0, None, None, None) == 1
     assert L.mg_sigmakin(None, None, 10, 0, None, None) == 1
     assert L.mg_hel_mask(None, None, None) == 1
+    assert L.mg_diag_tc_stall(None, 1) == 1
     assert L.mg_philox(1, -1, 2, None, None) == 1
     assert L.mg_create(9, None, ctypes.byref(ctypes.c_void_p())) == 1
     assert L.mg_create(0, None, None) == 1

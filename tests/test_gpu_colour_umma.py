@@ -70,3 +70,31 @@ def test_umma_colour_pass_full_size(env):
         assert ctx.check() == 0
         rel = (b / a - 1).abs().max().item()
     assert rel <= 1e-6, rel
+
+
+def test_umma_bounded_wait_reports_timeout_and_context_recovers(env):
+    """The failure path of the tensor-memory colour pass without a fault: with MMAs withheld
+    (mg_diag_tc_stall) every CTA's bounded mbarrier wait runs out after 0.2 s; the kernel records it,
+    frees its tensor memory and returns; mg_check reports MG_ETIMEOUT once; then, back to normal, the
+    same context gives the same values as before."""
+    torch, mg, orc = env
+    n = 4096
+    with mg.Context("ggttgg") as ctx:
+        mom = torch.zeros(ctx.mom_count(n), dtype=torch.float64, device="cuda")
+        ctx.rambo(9, n, SQRTS, mom)
+        ctx.set_launch_shape(mg.MG_FP64_TCCOLOR, 128, 0, 7)
+        a = torch.zeros(n, dtype=torch.float64, device="cuda")
+        ctx.sigmakin(mom, n, a, mg.MG_FP64_TCCOLOR)
+        assert ctx.check() == 0
+        ctx.diag_tc_stall(True)
+        b = torch.zeros(n, dtype=torch.float64, device="cuda")
+        ctx.sigmakin(mom, n, b, mg.MG_FP64_TCCOLOR)
+        with pytest.raises(mg.MGError) as e:
+            ctx.check()
+        assert e.value.status == 6
+        assert ctx.check() == 0                     # the flag was read and cleared
+        ctx.diag_tc_stall(False)
+        c = torch.zeros(n, dtype=torch.float64, device="cuda")
+        ctx.sigmakin(mom, n, c, mg.MG_FP64_TCCOLOR)
+        assert ctx.check() == 0
+        assert torch.equal(a, c)
