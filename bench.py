@@ -507,6 +507,11 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     oflops = oracle_flops_table()
     peaks = (mg.measure_fma_peak(fp32=False, iters=2048), mg.measure_fma_peak(fp32=True, iters=2048), tensor_peak())
+    try:
+        own_mma = mg.measure_mma_peak(16384)
+    except mg.MGError as e:
+        own_mma = None
+        print("note: tensor-core microbenchmark: %s" % e, file=sys.stderr)
     warm = max(3, args.warmup)
 
     # ---- headline: the configured process, FP64 step, clocks sampled during the timed region ----
@@ -641,6 +646,12 @@ def run_ours(args):
             "graph": {"ms_per_step": graph_ms, "value": aggregate_rate(world, nevt, graph_ms), "same_result": graph_same,
                       "what": "the FP64 step captured as one CUDA graph (mg_graph_create) and replayed"},
             "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "peaks": {"fp64_dfma_tflops": peaks[0] / 1e12, "fp32_ffma_tflops": peaks[1] / 1e12,
+                      "f16_mma_tflops": own_mma / 1e12 if own_mma else None,
+                      "tensor_denominator_tflops": peaks[2][0] / 1e12,
+                      "what": "this GPU, measured by the library's microbenchmarks (mg_measure_fma_peak: FMA chains; "
+                              "mg_measure_mma_peak: tcgen05.mma kind::f16 M128 N256 K16, exact integer result checked); "
+                              "the tensor rooflines divide by the pool's measured bf16 peak (tensor_denominator_tflops)"},
             "gpu_launches": launches}
     print(json.dumps(line))
     if world > 1:

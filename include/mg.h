@@ -53,7 +53,8 @@ typedef enum {
   MG_EAGAIN = 5,   /* not ready yet (serving) */
   MG_ETIMEOUT = 6, /* a bounded wait expired */
   MG_EBUSY = 7,    /* resource busy (serving admission) */
-  MG_ENOTSUP = 8   /* valid request that this library does not implement */
+  MG_ENOTSUP = 8,  /* valid request that this library does not implement */
+  MG_ECANCELED = 9 /* the request was cancelled (serving) */
 } mg_status;
 
 typedef enum { MG_GG_TT = 0, MG_GG_TTG = 1, MG_GG_TTGG = 2, MG_GG_TTGGG = 3 } mg_process;
@@ -331,6 +332,13 @@ mg_status mg_get_launch_shape(mg_ctx* ctx, mg_precision precision, int* tile_ev,
  * flags a combination of the MG_LAUNCH_ bits.  MG_EINVAL otherwise. */
 mg_status mg_set_launch_shape(mg_ctx* ctx, mg_precision precision, int tile_ev, int slot_major, int flags);
 
+/* FP32 modes (MG_FP32_AMP, MG_MIXED): the events whose smallest internal invariant -- |P^2| of a gluon
+ * propagator or |Q^2 - m_t^2| of a top propagator, evaluated from the momenta -- is below tau * s are
+ * recomputed with double-float (or FP64) amplitudes; default 3e-4, and 1e-4 for gg -> t tbar g g g, where
+ * the plain FP32 error of the events kept was measured <= 3e-6; tau = 0 recomputes nothing (the plain
+ * FP32 error).  MG_EINVAL for tau < 0 or not finite. */
+mg_status mg_set_fp32_tau(mg_ctx* ctx, double tau);
+
 /* One job of a graph batch: the step mg_rambo_range(seed, e0, nevt, sqrts, mom_dev) ->
  * mg_hel_filter(mom_dev, nevt) -> mg_sigmakin(precision, me_dev) on ctx.  Every job of a batch needs
  * its own context. */
@@ -435,7 +443,15 @@ mg_status mg_serve_poll(mg_server* srv, uint64_t ticket, double* me_out_host, in
 /* Blocking version with a timeout: MG_ETIMEOUT (request kept) if not done within timeout_ms. */
 mg_status mg_serve_wait(mg_server* srv, uint64_t ticket, double* me_out_host, int64_t timeout_ms, double* latency_ms);
 
-/* Counters since creation: completed requests, their events, peak in-flight footprint and count. */
+/* Cancel a request.  A queued request is dropped before it starts; one in flight stops at the next chunk
+ * boundary (the chunk on the device runs to its end: nothing is interrupted).  Its poll or wait then
+ * returns MG_ECANCELED with the MEs of the chunks that finished and zeros for the rest (a request whose
+ * last chunk was already running completes normally).  MG_OK if the request was cancelled or had already
+ * finished, MG_EINVAL for an unknown ticket.  Returns at once. */
+mg_status mg_serve_cancel(mg_server* srv, uint64_t ticket);
+
+/* Counters since creation: completed requests (cancelled ones included), the events computed for them,
+ * peak in-flight footprint and count. */
 mg_status mg_serve_stats(mg_server* srv, int64_t* completed, int64_t* events, int64_t* peak_bytes, int* peak_inflight);
 
 /* Drain the queue, stop the scheduler and free everything (unpolled results are dropped). */
@@ -447,13 +463,32 @@ void mg_serve_destroy(mg_server* srv);
  * FP64 (fp32 = 0) or FP32 (fp32 = 1).  Synchronous; 1 <= iters <= 2^20. */
 mg_status mg_measure_fma_peak(int fp32, int iters, double* flops_per_s);
 
+/* Diagnostic: dense FP16 tensor-core throughput of the current device through the instruction the colour
+ * pass uses (tcgen05.mma kind::f16, FP32 accumulators in tensor memory): one CTA per SM issues iters MMAs
+ * of M = 128, N = 256, K = 16 into one accumulator; returns the rate in flop/s (2 M N K per MMA).  The
+ * operands are small integers, so the accumulated result is exact and is checked on the host: MG_ECUDA
+ * if it differs, MG_ETIMEOUT if a bounded wait ran out.  Synchronous; 1 <= iters <= 65536. */
+mg_status mg_measure_mma_peak(int iters, double* flops_per_s);
+
 /* Diagnostic: the number of CUDA kernels this library has launched in this process, on every
  * context, stream and thread (a launch captured into a CUDA graph counts once, at capture; graph
  * replays do not count).  The difference of two reads brackets the launches of the calls between
  * them.  Host only; never fails. */
 int64_t mg_kernel_launches(void);
 
-/* Diagnostics of the failure path (no counterpart in the paper): with on = 1 the tensor-memory colour
+/* Diagnostics of the failure paths (no counterpart in the paper).
+ *
+ * Host-side allocation-failure injector: the nth device or pinned-host allocation that the library makes
+ * from now on (nth = 1: the next one) fails as an exhausted device would, and the call that made it
+ * returns MG_ENOMEM after freeing what it had allocated; later allocations succeed again.  nth = 0
+ * disarms it.  Process-wide; MG_EINVAL for nth < 0.  No GPU needed. */
+mg_status mg_diag_fail_alloc(int64_t nth);
+
+/* Device and pinned-host allocations of the library alive now (process-wide): every context, server and
+ * graph returns to the count it found when destroyed, including after a failed creation. */
+int64_t mg_diag_live_allocs(void);
+
+/* With on = 1 the tensor-memory colour
  * pass on this context issues no MMAs, so each CTA's bounded mbarrier wait runs out (after 0.2 s): the
  * kernel records it, frees its tensor memory and returns; mg_check then reports MG_ETIMEOUT and the
  * context stays usable.  on = 0 restores normal operation.  Host only; no fault, trap or hang. */

@@ -24,7 +24,7 @@ GRAPH_PERSISTENT = 1       # mg.h MG_GRAPH_PERSISTENT
 PAGE = 32
 
 STATUS = {0: "MG_OK", 1: "MG_EINVAL", 2: "MG_ENOMEM", 3: "MG_ECUDA", 4: "MG_ENOCONV", 5: "MG_EAGAIN",
-          6: "MG_ETIMEOUT", 7: "MG_EBUSY", 8: "MG_ENOTSUP"}
+          6: "MG_ETIMEOUT", 7: "MG_EBUSY", 8: "MG_ENOTSUP", 9: "MG_ECANCELED"}
 
 
 class MGError(RuntimeError):
@@ -85,8 +85,14 @@ def lib():
     L.mg_rambo.argtypes = [vp, u64, i64, dbl, vp, vp, vp]
     L.mg_rambo_range.argtypes = [vp, u64, i64, i64, dbl, vp, vp, vp]
     L.mg_measure_fma_peak.argtypes = [i32, i32, P(dbl)]
+    L.mg_measure_mma_peak.argtypes = [i32, P(dbl)]
     L.mg_kernel_launches.argtypes = []
+    L.mg_diag_fail_alloc.argtypes = [ctypes.c_int64]
+    L.mg_diag_fail_alloc.restype = i32
+    L.mg_diag_live_allocs.argtypes = []
+    L.mg_diag_live_allocs.restype = ctypes.c_int64
     L.mg_diag_tc_stall.argtypes = [vp, i32]
+    L.mg_set_fp32_tau.argtypes = [vp, dbl]
     L.mg_diag_tc_stall.restype = i32
     L.mg_kernel_launches.restype = i64
     L.mg_hel_filter.argtypes = [vp, vp, i64, vp]
@@ -126,6 +132,7 @@ def lib():
     L.mg_serve_poll.argtypes = [vp, ctypes.c_uint64, vp, P(i32), P(dbl)]
     L.mg_serve_wait.argtypes = [vp, ctypes.c_uint64, vp, i64, P(dbl)]
     L.mg_serve_stats.argtypes = [vp, P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_int64), P(i32)]
+    L.mg_serve_cancel.argtypes = [vp, ctypes.c_uint64]
     L.mg_serve_destroy.argtypes = [vp]
     L.mg_serve_destroy.restype = None
     for name in ("mg_serve_create", "mg_serve_submit", "mg_serve_poll", "mg_serve_wait", "mg_serve_stats"):
@@ -266,9 +273,27 @@ def measure_fma_peak(fp32=False, iters=4096):
     return r.value
 
 
+def measure_mma_peak(iters=16384):
+    """Measured dense FP16 tensor-core throughput (tcgen05.mma kind::f16) in flop/s; the accumulated
+    integer result is checked exactly."""
+    r = ctypes.c_double()
+    _check(lib().mg_measure_mma_peak(iters, ctypes.byref(r)), "mg_measure_mma_peak")
+    return r.value
+
+
 def kernel_launches():
     """CUDA kernels this library has launched in this process so far (all contexts and streams)."""
     return int(lib().mg_kernel_launches())
+
+
+def diag_fail_alloc(nth):
+    """Fault injection on the host: the nth next allocation of the library fails (0 disarms)."""
+    _check(lib().mg_diag_fail_alloc(int(nth)), "mg_diag_fail_alloc")
+
+
+def live_allocs():
+    """Device and pinned-host allocations of the library alive now."""
+    return int(lib().mg_diag_live_allocs())
 
 
 def philox(seed, nevt, nfinal, words, stream=None):
@@ -374,6 +399,10 @@ class Context:
         _check(lib().mg_hel_mask(self._h, m, ctypes.byref(n)), "mg_hel_mask")
         return np.array(list(m), dtype=np.uint32), n.value
 
+    def set_fp32_tau(self, tau):
+        """FP32 modes: recompute the events whose smallest internal invariant is below tau * s."""
+        _check(lib().mg_set_fp32_tau(self._h, tau), "mg_set_fp32_tau")
+
     def diag_tc_stall(self, on):
         """Diagnostics: the tensor-memory colour pass issues no MMAs, so its bounded waits run out."""
         _check(lib().mg_diag_tc_stall(self._h, 1 if on else 0), "mg_diag_tc_stall")
@@ -434,6 +463,10 @@ class Server:
         del self._nevt[ticket]
         _check(s, "mg_serve_wait")
         return out, lat.value
+
+    def cancel(self, ticket):
+        """Cancel a queued or running request; its wait/poll then raises MGError(MG_ECANCELED)."""
+        _check(lib().mg_serve_cancel(self._h, ticket), "mg_serve_cancel")
 
     def stats(self):
         a, b, c, d = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int()

@@ -12,6 +12,7 @@
 #include <new>
 #include <vector>
 
+#include "mg_alloc.h"
 #include "mg_ctx.h"
 #include "mg_internal.h"
 #include "mg_kernels.h"
@@ -32,10 +33,10 @@ int64_t pad32(int64_t n) { return (n + mg::kPage - 1) / mg::kPage * mg::kPage; }
 
 mg_status grow(double** buf, int64_t* cap, int64_t need) {
   if (need <= *cap) return MG_OK;
-  if (*buf) cudaFree(*buf);
+  if (*buf) mg::dev_free(*buf);
   *buf = nullptr;
   *cap = 0;
-  if (cudaMalloc(buf, static_cast<size_t>(need) * sizeof(double)) != cudaSuccess) {
+  if (mg::dev_alloc(buf, static_cast<size_t>(need) * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return MG_ENOMEM;
   }
@@ -107,16 +108,16 @@ void flop_model(const mg::Tables& t, const uint32_t* mask, bool fp32, bool share
 
 mg_status grow_repair(mg_ctx* ctx, int64_t n) {
   if (!ctx->d_nrepair) {
-    if (cudaMalloc(&ctx->d_nrepair, sizeof(int)) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
+    if (mg::dev_alloc(&ctx->d_nrepair, sizeof(int)) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
   }
   if (n <= ctx->repair_cap) return MG_OK;
-  if (ctx->d_repair) cudaFree(ctx->d_repair);
-  if (ctx->d_flag) cudaFree(ctx->d_flag);
+  if (ctx->d_repair) mg::dev_free(ctx->d_repair);
+  if (ctx->d_flag) mg::dev_free(ctx->d_flag);
   ctx->d_repair = nullptr;
   ctx->d_flag = nullptr;
   ctx->repair_cap = 0;
-  if (cudaMalloc(&ctx->d_repair, static_cast<size_t>(n) * sizeof(int)) != cudaSuccess ||
-      cudaMalloc(&ctx->d_flag, static_cast<size_t>(n)) != cudaSuccess) {
+  if (mg::dev_alloc(&ctx->d_repair, static_cast<size_t>(n) * sizeof(int)) != cudaSuccess ||
+      mg::dev_alloc(&ctx->d_flag, static_cast<size_t>(n)) != cudaSuccess) {
     cudaGetLastError();
     return MG_ENOMEM;
   }
@@ -130,6 +131,29 @@ namespace mg {
 
 static std::atomic<int64_t> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// allocations: live count, and the countdown of the injected failure (0: none armed)
+static std::atomic<int64_t> g_live_allocs{0};
+static std::atomic<int64_t> g_fail_countdown{0};
+
+cudaError_t alloc_raw(void** p, size_t bytes, bool host) {
+  int64_t n = g_fail_countdown.load();
+  while (n > 0 && !g_fail_countdown.compare_exchange_weak(n, n - 1)) {
+  }
+  if (n == 1) {   // this call brought the countdown to zero: it fails, as an exhausted device would
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  const cudaError_t e = host ? cudaMallocHost(p, bytes) : cudaMalloc(p, bytes);
+  if (e == cudaSuccess) g_live_allocs.fetch_add(1);
+  return e;
+}
+
+cudaError_t free_raw(void* p, bool host) {
+  if (!p) return cudaSuccess;
+  g_live_allocs.fetch_sub(1);
+  return host ? cudaFreeHost(p) : cudaFree(p);
+}
 
 int64_t share_chunk(int K, int64_t stride) {
   const int64_t per_event = static_cast<int64_t>(share_items(K)) * 24;   // doubles
@@ -160,10 +184,10 @@ mg_status ctx_reserve(mg_ctx* ctx, int64_t nevt, mg_precision precision) {
     if (chunk < kPage) chunk = kPage;
     if (chunk > stride) chunk = stride;
     if (s == MG_OK && ctx->jamp_cap < chunk * per_event) {
-      if (ctx->d_jamps) cudaFree(ctx->d_jamps);
+      if (ctx->d_jamps) mg::dev_free(ctx->d_jamps);
       ctx->d_jamps = nullptr;
       ctx->jamp_cap = 0;
-      if (cudaMalloc(&ctx->d_jamps, static_cast<size_t>(chunk * per_event) * sizeof(float2)) != cudaSuccess) {
+      if (mg::dev_alloc(&ctx->d_jamps, static_cast<size_t>(chunk * per_event) * sizeof(float2)) != cudaSuccess) {
         cudaGetLastError();
         return MG_ENOMEM;
       }
@@ -225,6 +249,7 @@ const char* mg_strerror(mg_status s) {
     case MG_ETIMEOUT: return "timed out";
     case MG_EBUSY: return "busy";
     case MG_ENOTSUP: return "not supported";
+    case MG_ECANCELED: return "cancelled";
   }
   return "unknown status";
 }
@@ -299,42 +324,42 @@ mg_status mg_flops_per_event(mg_process proc, mg_precision precision, const uint
 void mg_destroy(mg_ctx* ctx) {
   if (!ctx) return;
   cudaDeviceSynchronize();
-  cudaFree(ctx->d_tab);
-  cudaFree(ctx->d_ctri);
-  cudaFree(ctx->d_ctri_f);
-  cudaFree(ctx->d_cfull);
-  cudaFree(ctx->d_mask);
-  cudaFree(ctx->d_maxr);
-  cudaFree(ctx->d_good);
-  cudaFree(ctx->d_ngood);
-  cudaFree(ctx->d_allhel);
-  cudaFree(ctx->d_nhel);
-  cudaFree(ctx->d_gslots);
-  cudaFree(ctx->d_ngslots);
-  cudaFree(ctx->d_allg);
-  cudaFree(ctx->d_nrows);
-  cudaFree(ctx->d_cmat);
-  cudaFree(ctx->d_cumma);
-  cudaFree(ctx->d_tcerr);
-  cudaFree(ctx->d_tiles);
-  cudaFree(ctx->d_jamps);
-  cudaFree(ctx->d_nallg);
-  cudaFree(ctx->d_nbad);
-  cudaFree(ctx->d_part);
-  cudaFree(ctx->d_tot);
-  cudaFree(ctx->d_prep);
-  cudaFree(ctx->d_repair);
-  cudaFree(ctx->d_nrepair);
-  cudaFree(ctx->d_flag);
-  cudaFree(ctx->d_share);
-  cudaFree(ctx->d_j2);
-  cudaFree(ctx->d_sdetab);
-  cudaFree(ctx->d_sde);
+  mg::dev_free(ctx->d_tab);
+  mg::dev_free(ctx->d_ctri);
+  mg::dev_free(ctx->d_ctri_f);
+  mg::dev_free(ctx->d_cfull);
+  mg::dev_free(ctx->d_mask);
+  mg::dev_free(ctx->d_maxr);
+  mg::dev_free(ctx->d_good);
+  mg::dev_free(ctx->d_ngood);
+  mg::dev_free(ctx->d_allhel);
+  mg::dev_free(ctx->d_nhel);
+  mg::dev_free(ctx->d_gslots);
+  mg::dev_free(ctx->d_ngslots);
+  mg::dev_free(ctx->d_allg);
+  mg::dev_free(ctx->d_nrows);
+  mg::dev_free(ctx->d_cmat);
+  mg::dev_free(ctx->d_cumma);
+  mg::dev_free(ctx->d_tcerr);
+  mg::dev_free(ctx->d_tiles);
+  mg::dev_free(ctx->d_jamps);
+  mg::dev_free(ctx->d_nallg);
+  mg::dev_free(ctx->d_nbad);
+  mg::dev_free(ctx->d_part);
+  mg::dev_free(ctx->d_tot);
+  mg::dev_free(ctx->d_prep);
+  mg::dev_free(ctx->d_repair);
+  mg::dev_free(ctx->d_nrepair);
+  mg::dev_free(ctx->d_flag);
+  mg::dev_free(ctx->d_share);
+  mg::dev_free(ctx->d_j2);
+  mg::dev_free(ctx->d_sdetab);
+  mg::dev_free(ctx->d_sde);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->side) cudaStreamDestroy(ctx->side);
-  cudaFree(ctx->d_mom_stage);
-  cudaFree(ctx->d_me_stage);
+  mg::dev_free(ctx->d_mom_stage);
+  mg::dev_free(ctx->d_me_stage);
   for (int c = 0; c < mg_ctx::kHostChunks; ++c) {
     if (ctx->ev_in[c]) cudaEventDestroy(ctx->ev_in[c]);
     if (ctx->ev_done[c]) cudaEventDestroy(ctx->ev_done[c]);
@@ -369,32 +394,32 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
     mg::Tables* t = new (std::nothrow) mg::Tables;
     if (!t) { st = MG_ENOMEM; break; }
     mg::build_tables(c->K, *t);
-    cudaError_t e = cudaMalloc(&c->d_tab, sizeof(mg::Tables));
+    cudaError_t e = mg::dev_alloc(&c->d_tab, sizeof(mg::Tables));
     if (e == cudaSuccess) e = cudaMemcpy(c->d_tab, t, sizeof(mg::Tables), cudaMemcpyHostToDevice);
     delete t;
-    if (e != cudaSuccess) { st = MG_ECUDA; break; }
+    if (e != cudaSuccess) { st = e == cudaErrorMemoryAllocation ? MG_ENOMEM : MG_ECUDA; break; }
     std::vector<int64_t> num;
     mg::colour_matrix_exact(c->K, num, c->colour_den);
     std::vector<double> tri;
     for (int a = 0; a < c->ncol; ++a)
       for (int b = a; b < c->ncol; ++b)
         tri.push_back(static_cast<double>(num[static_cast<size_t>(a) * c->ncol + b]) * (a == b ? 1.0 : 2.0));
-    e = cudaMalloc(&c->d_ctri, tri.size() * sizeof(double));
+    e = mg::dev_alloc(&c->d_ctri, tri.size() * sizeof(double));
     if (e == cudaSuccess) e = cudaMemcpy(c->d_ctri, tri.data(), tri.size() * sizeof(double), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = mg::me_static_upload_colour(c->K, tri.data(), static_cast<int>(tri.size()));
     std::vector<float> full(num.begin(), num.end());
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_cfull, full.size() * sizeof(float));
+    if (e == cudaSuccess) e = mg::dev_alloc(&c->d_cfull, full.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(c->d_cfull, full.data(), full.size() * sizeof(float), cudaMemcpyHostToDevice);
     std::vector<float> trif(tri.begin(), tri.end());
-    if (e == cudaSuccess) e = cudaMalloc(&c->d_ctri_f, trif.size() * sizeof(float));
+    if (e == cudaSuccess) e = mg::dev_alloc(&c->d_ctri_f, trif.size() * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(c->d_ctri_f, trif.data(), trif.size() * sizeof(float), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) { st = MG_ECUDA; break; }
+    if (e != cudaSuccess) { st = e == cudaErrorMemoryAllocation ? MG_ENOMEM : MG_ECUDA; break; }
     std::vector<int> all(c->nhel);
     for (int h = 0; h < c->nhel; ++h) all[h] = h;
-    if (cudaMalloc(&c->d_mask, 4 * sizeof(uint32_t)) != cudaSuccess || cudaMalloc(&c->d_good, 128 * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&c->d_maxr, 128 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&c->d_ngood, sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_allhel, c->nhel * sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&c->d_nhel, sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_nbad, sizeof(unsigned long long)) != cudaSuccess) {
+    if (mg::dev_alloc(&c->d_mask, 4 * sizeof(uint32_t)) != cudaSuccess || mg::dev_alloc(&c->d_good, 128 * sizeof(int)) != cudaSuccess ||
+        mg::dev_alloc(&c->d_maxr, 128 * sizeof(double)) != cudaSuccess ||
+        mg::dev_alloc(&c->d_ngood, sizeof(int)) != cudaSuccess || mg::dev_alloc(&c->d_allhel, c->nhel * sizeof(int)) != cudaSuccess ||
+        mg::dev_alloc(&c->d_nhel, sizeof(int)) != cudaSuccess || mg::dev_alloc(&c->d_nbad, sizeof(unsigned long long)) != cudaSuccess) {
       st = MG_ENOMEM;
       break;
     }
@@ -404,22 +429,22 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
       mg::colour_tc_pack(c->ncol, num.data(), halves.data());
       std::vector<uint16_t> uh(mg::colour_umma_halves(c->ncol));
       mg::colour_umma_pack(c->ncol, num.data(), uh.data());
-      if (cudaMalloc(&c->d_cumma, uh.size() * sizeof(uint16_t)) != cudaSuccess ||
+      if (mg::dev_alloc(&c->d_cumma, uh.size() * sizeof(uint16_t)) != cudaSuccess ||
           cudaMemcpy(c->d_cumma, uh.data(), uh.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess ||
-          cudaMalloc(&c->d_tcerr, sizeof(int)) != cudaSuccess || cudaMemset(c->d_tcerr, 0, sizeof(int)) != cudaSuccess ||
-          cudaMalloc(&c->d_tiles, sizeof(unsigned long long)) != cudaSuccess) {
+          mg::dev_alloc(&c->d_tcerr, sizeof(int)) != cudaSuccess || cudaMemset(c->d_tcerr, 0, sizeof(int)) != cudaSuccess ||
+          mg::dev_alloc(&c->d_tiles, sizeof(unsigned long long)) != cudaSuccess) {
         st = MG_ENOMEM;
         break;
       }
-      if (cudaMalloc(&c->d_cmat, halves.size() * sizeof(uint16_t)) != cudaSuccess ||
+      if (mg::dev_alloc(&c->d_cmat, halves.size() * sizeof(uint16_t)) != cudaSuccess ||
           cudaMemcpy(c->d_cmat, halves.data(), halves.size() * sizeof(uint16_t), cudaMemcpyHostToDevice) != cudaSuccess ||
-          cudaMalloc(&c->d_nrows, sizeof(int)) != cudaSuccess || cudaMemset(c->d_nrows, 0, sizeof(int)) != cudaSuccess) {
+          mg::dev_alloc(&c->d_nrows, sizeof(int)) != cudaSuccess || cudaMemset(c->d_nrows, 0, sizeof(int)) != cudaSuccess) {
         st = MG_ENOMEM;
         break;
       }
     }
-    if (cudaMalloc(&c->d_gslots, 32 * sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_ngslots, sizeof(int)) != cudaSuccess ||
-        cudaMalloc(&c->d_allg, 32 * sizeof(int)) != cudaSuccess || cudaMalloc(&c->d_nallg, sizeof(int)) != cudaSuccess) {
+    if (mg::dev_alloc(&c->d_gslots, 32 * sizeof(int)) != cudaSuccess || mg::dev_alloc(&c->d_ngslots, sizeof(int)) != cudaSuccess ||
+        mg::dev_alloc(&c->d_allg, 32 * sizeof(int)) != cudaSuccess || mg::dev_alloc(&c->d_nallg, sizeof(int)) != cudaSuccess) {
       st = MG_ENOMEM;
       break;
     }
@@ -447,6 +472,10 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
     // FP64 amplitudes: share the currents of fewer than all gluons between gluon-helicity combinations
     // where that was measured faster (1 and 3 final-state gluons); the autotuner can change it
     for (int p = 0; p < 4; ++p) c->shape[p].shared = c->K == 3 || c->K == 5;
+    // FP32 recomputation threshold: the largest plain-FP32 error among the events kept in FP32 was
+    // measured at 3.6e-6 / 3.7e-6 / 2.0e-6 (1 / 2 / 3 final-state gluons) with tau = 3e-4, and 2.8e-6 for
+    // 3 gluons with tau = 1e-4, which recomputes a third as many events there
+    c->fp32_tau = c->K == 5 ? 1e-4 : 3e-4;
     // side stream of the FP32 modes' recomputation: highest priority, so that its few blocks are
     // dispatched ahead of the FP32 launch's
     int lo = 0, hi = 0;
@@ -500,7 +529,14 @@ static mg::MeConst me_const(const mg_ctx* ctx) {
   c.mt = ctx->prm.mt;
   c.wt = ctx->prm.wt;
   c.colour_scale = c.gs * c.gs / static_cast<double>(ctx->colour_den);
+  c.fp32_tau = ctx->fp32_tau;
   return c;
+}
+
+mg_status mg_set_fp32_tau(mg_ctx* ctx, double tau) {
+  if (!ctx || !(tau >= 0.0) || !std::isfinite(tau)) return MG_EINVAL;
+  ctx->fp32_tau = tau;
+  return MG_OK;
 }
 
 mg_status mg_hel_filter(mg_ctx* ctx, const double* mom_dev, int64_t nevt, void* stream) {
@@ -594,10 +630,10 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
       if (s != MG_OK) return s;
     }
     if (ctx->jamp_cap < chunk * per_event) {
-      if (ctx->d_jamps) cudaFree(ctx->d_jamps);
+      if (ctx->d_jamps) mg::dev_free(ctx->d_jamps);
       ctx->d_jamps = nullptr;
       ctx->jamp_cap = 0;
-      if (cudaMalloc(&ctx->d_jamps, static_cast<size_t>(chunk * per_event) * sizeof(float2)) != cudaSuccess) {
+      if (mg::dev_alloc(&ctx->d_jamps, static_cast<size_t>(chunk * per_event) * sizeof(float2)) != cudaSuccess) {
         cudaGetLastError();
         return MG_ENOMEM;
       }
@@ -707,12 +743,12 @@ mg_status mg_sigmakin_host(mg_ctx* ctx, const double* mom_host, int64_t nevt, mg
   if (nevt == 0) return MG_OK;
   const int64_t nmom = mg_mom_count(ctx->proc, nevt);
   if (ctx->stage_cap < nmom + pad32(nevt)) {
-    if (ctx->d_mom_stage) cudaFree(ctx->d_mom_stage);
-    if (ctx->d_me_stage) cudaFree(ctx->d_me_stage);
+    if (ctx->d_mom_stage) mg::dev_free(ctx->d_mom_stage);
+    if (ctx->d_me_stage) mg::dev_free(ctx->d_me_stage);
     ctx->d_mom_stage = ctx->d_me_stage = nullptr;
     ctx->stage_cap = 0;
-    if (cudaMalloc(&ctx->d_mom_stage, nmom * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&ctx->d_me_stage, pad32(nevt) * sizeof(double)) != cudaSuccess) {
+    if (mg::dev_alloc(&ctx->d_mom_stage, nmom * sizeof(double)) != cudaSuccess ||
+        mg::dev_alloc(&ctx->d_me_stage, pad32(nevt) * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
       return MG_ENOMEM;
     }
@@ -794,6 +830,14 @@ mg_status mg_check(mg_ctx* ctx, void* stream, int64_t* nbad) {
 }
 
 int64_t mg_kernel_launches(void) { return mg::g_launches.load(std::memory_order_relaxed); }
+
+mg_status mg_diag_fail_alloc(int64_t nth) {
+  if (nth < 0) return MG_EINVAL;
+  mg::g_fail_countdown.store(nth);
+  return MG_OK;
+}
+
+int64_t mg_diag_live_allocs(void) { return mg::g_live_allocs.load(); }
 
 mg_status mg_diag_tc_stall(mg_ctx* ctx, int on) {
   if (!ctx || (on != 0 && on != 1)) return MG_EINVAL;

@@ -17,10 +17,12 @@
 // so the kernel walks the padded row index q = e * rows_alloc + r with shifts and masks: a tile of 8
 // consecutive q is 8 rows of one event, and rows r >= *nrows_dev are zero-filled, never read.
 #include <atomic>
+#include <vector>
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "mg_alloc.h"
 #include "mg_internal.h"
 #include "mg_kernels.h"
 
@@ -699,6 +701,75 @@ k_colour_umma(const float2* __restrict__ jamps, int64_t nevt, int rows_log2, con
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
 }
 
+// ---- tensor-pipe peak (the f16 MMA denominator of the colour pass's roofline) ----
+// Every CTA (one per SM) issues `iters` MMAs of M = 128, N = 256, K = 16 (FP16 operands resident in
+// shared memory, FP32 accumulator in tensor memory) from one thread, all into the same accumulator, and
+// commits them to one mbarrier.  The operands are small integers (-2..2), so the accumulator is exact:
+// CTA 0 writes it out and the host compares it with iters x (A B^T).
+constexpr int kPkN = 256;
+constexpr uint32_t kPkIdesc = (1u << 4) | (static_cast<uint32_t>(kPkN >> 3) << 17) | (static_cast<uint32_t>(128 >> 4) << 24);
+
+__host__ __device__ inline int pk_a(int r, int k) { return (r * 7 + k * 3) % 5 - 2; }
+__host__ __device__ inline int pk_b(int n, int k) { return (n * 5 + k * 11 + 1) % 5 - 2; }
+
+// element (r, k) of an R x 16 K-major operand: 8-row x 16-byte core matrices, the two k halves 128 bytes
+// apart, 8-row groups 256 bytes apart (index in halves)
+__host__ __device__ inline int pk_off(int r, int k) { return ((r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2) / 2; }
+
+__global__ void __launch_bounds__(128, 1) k_mma_peak(int iters, float* __restrict__ d_out, int* __restrict__ err) {
+  __shared__ __align__(128) uint16_t sA[128 * 16];
+  __shared__ __align__(128) uint16_t sB[kPkN * 16];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tslot;
+  __shared__ int timed_out;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  for (int i = tid; i < 128 * 16; i += 128)
+    sA[pk_off(i >> 4, i & 15)] = __half_as_ushort(__int2half_rn(pk_a(i >> 4, i & 15)));
+  for (int i = tid; i < kPkN * 16; i += 128)
+    sB[pk_off(i >> 4, i & 15)] = __half_as_ushort(__int2half_rn(pk_b(i >> 4, i & 15)));
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    timed_out = 0;
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(smem_addr(&tslot)) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tslot;
+  if (tid == 0) {
+    const uint64_t ad = umma_desc(smem_addr(sA), 128, 256), bd = umma_desc(smem_addr(sB), 128, 256);
+#pragma unroll 1
+    for (int i = 0; i < iters; ++i) umma_f16(tmem, ad, bd, kPkIdesc, i > 0 ? 1u : 0u);
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(&bar))
+                 : "memory");
+  }
+  if (!mbar_wait_bounded(smem_addr(&bar), 0)) timed_out = 1;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (timed_out) {
+    if (tid == 0) atomicAdd(err, 1);
+  } else if (blockIdx.x == 0) {   // warp w reads tensor-memory lanes 32 w .. 32 w + 31 (rows of D)
+    const int row = tid;
+#pragma unroll 1
+    for (int c = 0; c < kPkN; c += 32) {
+      uint32_t v[32];
+      tmem_ld32(tmem + (static_cast<uint32_t>(32 * warp) << 16) + c, v);
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int j = 0; j < 32; ++j) d_out[row * kPkN + c + j] = __uint_as_float(v[j]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+}
+
 }  // namespace
 
 int colour_tc_cmat_halves(int ncol) {
@@ -812,4 +883,56 @@ cudaError_t launch_colour_umma(int ncol, const float2* jamps, int64_t nevt, int 
     default: return cudaErrorInvalidValue;
   }
 }
+
 }  // namespace mg
+
+extern "C" mg_status mg_measure_mma_peak(int iters, double* flops_per_s) {
+  if (!flops_per_s || iters < 1 || iters > (1 << 16)) return MG_EINVAL;
+  int dev = 0, nsm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return MG_ECUDA;
+  }
+  float* out = nullptr;
+  int* err = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  mg_status rc = MG_OK;
+  if (mg::dev_alloc(&out, sizeof(float) * 128 * mg::kPkN) != cudaSuccess || mg::dev_alloc(&err, sizeof(int)) != cudaSuccess) {
+    rc = MG_ENOMEM;
+  } else if (cudaMemset(err, 0, sizeof(int)) != cudaSuccess ||
+             cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+             cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    rc = MG_ECUDA;
+  } else {
+    { mg::k_mma_peak<<<nsm, 128, 0, st>>>(iters / 8 + 1, out, err); mg::note_launch(); }   // warm-up
+    cudaEventRecord(e0, st);
+    { mg::k_mma_peak<<<nsm, 128, 0, st>>>(iters, out, err); mg::note_launch(); }
+    cudaEventRecord(e1, st);
+    std::vector<float> d(128 * mg::kPkN);
+    int nerr = 0;
+    float ms = 0.f;
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess ||
+        cudaMemcpy(d.data(), out, d.size() * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(&nerr, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      rc = MG_ECUDA;
+    } else if (nerr) {
+      rc = MG_ETIMEOUT;
+    } else {
+      for (int r = 0; r < 128 && rc == MG_OK; ++r)
+        for (int n = 0; n < mg::kPkN; ++n) {
+          int dot = 0;
+          for (int k = 0; k < 16; ++k) dot += mg::pk_a(r, k) * mg::pk_b(n, k);
+          if (d[r * mg::kPkN + n] != static_cast<float>(static_cast<int64_t>(dot) * iters)) { rc = MG_ECUDA; break; }
+        }
+      if (rc == MG_OK) *flops_per_s = 2.0 * 128 * mg::kPkN * 16 * static_cast<double>(iters) * nsm / (ms * 1e-3);
+    }
+  }
+  cudaGetLastError();
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  mg::dev_free(out);
+  mg::dev_free(err);
+  return rc;
+}

@@ -63,6 +63,8 @@ struct mg_ctx {
   cudaStream_t cp_in = nullptr, cp_out = nullptr;
   cudaEvent_t ev_in[kHostChunks] = {}, ev_done[kHostChunks] = {};
   bool mask_ready = false;
+  double fp32_tau = 3e-4;     // FP32 modes: events with an internal invariant below fp32_tau * s are recomputed
+                              // (set per process at creation)
   mg::MeShape shape[4];       // launch shape of the matrix-element kernel per precision (autotuned)
   cudaStream_t last = nullptr;
 };

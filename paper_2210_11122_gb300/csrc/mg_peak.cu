@@ -3,6 +3,7 @@
 // independent FMA chains; the grid covers every SM several times over.
 #include <cuda_runtime.h>
 
+#include "mg_alloc.h"
 #include "mg_internal.h"
 
 namespace {
@@ -32,7 +33,7 @@ mg_status run(int iters, double* flops) {
   cudaStream_t st = nullptr;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   mg_status rc = MG_OK;
-  if (cudaMalloc(&out, sizeof(T)) != cudaSuccess || cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+  if (mg::dev_alloc(&out, sizeof(T)) != cudaSuccess || cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
     rc = MG_ECUDA;
   } else {
@@ -55,7 +56,7 @@ mg_status run(int iters, double* flops) {
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (st) cudaStreamDestroy(st);
-  if (out) cudaFree(out);
+  if (out) mg::dev_free(out);
   return rc;
 }
 

@@ -15,6 +15,7 @@
 #include <cmath>
 #include <vector>
 
+#include "mg_alloc.h"
 #include "mg_ctx.h"
 #include "mg_internal.h"
 #include "mg_kernels.h"
@@ -96,10 +97,10 @@ int64_t pad_pg(int64_t n) { return (n + mg::kPage - 1) / mg::kPage * mg::kPage; 
 
 mg_status grow_d(double** buf, int64_t* cap, int64_t need) {
   if (need <= *cap) return MG_OK;
-  if (*buf) cudaFree(*buf);
+  if (*buf) mg::dev_free(*buf);
   *buf = nullptr;
   *cap = 0;
-  if (cudaMalloc(buf, static_cast<size_t>(need) * sizeof(double)) != cudaSuccess) {
+  if (mg::dev_alloc(buf, static_cast<size_t>(need) * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return MG_ENOMEM;
   }

@@ -27,6 +27,7 @@
 #include <string>
 #include <vector>
 
+#include "mg_alloc.h"
 #include "mg_ctx.h"
 #include "mg_internal.h"
 #include "mg_kernels.h"
@@ -247,10 +248,10 @@ int64_t padp(int64_t n) { return (n + mg::kPage - 1) / mg::kPage * mg::kPage; }
 
 mg_status growb(double** buf, int64_t* cap, int64_t need) {
   if (need <= *cap) return MG_OK;
-  if (*buf) cudaFree(*buf);
+  if (*buf) mg::dev_free(*buf);
   *buf = nullptr;
   *cap = 0;
-  if (cudaMalloc(buf, static_cast<size_t>(need) * sizeof(double)) != cudaSuccess) {
+  if (mg::dev_alloc(buf, static_cast<size_t>(need) * sizeof(double)) != cudaSuccess) {
     cudaGetLastError();
     return MG_ENOMEM;
   }
@@ -299,7 +300,7 @@ mg_status mg_sde_weights(mg_ctx* ctx, const double* mom_dev, int64_t nevt, doubl
   const int K = ctx->K;
   const mg::sde::Built& b = mg::sde::built(K);
   if (!ctx->d_sdetab) {
-    if (cudaMalloc(&ctx->d_sdetab, sizeof(mg::sde::Tab)) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
+    if (mg::dev_alloc(&ctx->d_sdetab, sizeof(mg::sde::Tab)) != cudaSuccess) { cudaGetLastError(); return MG_ENOMEM; }
     if (cudaMemcpy(ctx->d_sdetab, &b.tab, sizeof(mg::sde::Tab), cudaMemcpyHostToDevice) != cudaSuccess) {
       cudaGetLastError();
       return MG_ECUDA;

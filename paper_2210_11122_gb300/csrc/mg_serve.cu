@@ -34,6 +34,7 @@
 #include <unordered_map>
 #include <vector>
 
+#include "mg_alloc.h"
 #include "mg_ctx.h"
 #include "mg_internal.h"
 
@@ -50,6 +51,8 @@ struct Request {
   Clock::time_point t_submit, t_done;
   std::vector<double> me;
   int64_t next = 0;          // first event of the next chunk
+  int64_t computed = 0;      // events of the chunks that finished
+  bool cancel = false;       // mg_serve_cancel while in flight: launch no further chunk
   bool done = false;
   mg_status status = MG_OK;
   int64_t footprint = 0;
@@ -128,7 +131,12 @@ void worker_loop(mg_server* srv) {
         r->next = r->nevt;
       } else {
         std::memcpy(r->me.data() + s.chunk_e0, s.host, s.chunk_n * sizeof(double));
+        r->computed += s.chunk_n;
         if (*s.host_nbad && r->status == MG_OK) r->status = MG_ENOCONV;
+      }
+      if (r->cancel && r->next < r->nevt && r->status != MG_ECUDA) {
+        r->status = MG_ECANCELED;
+        r->next = r->nevt;
       }
       if (r->next < r->nevt && r->status != MG_ECUDA) {
         const mg_status st = launch_chunk(srv, s);
@@ -141,7 +149,7 @@ void worker_loop(mg_server* srv) {
       srv->inflight--;
       srv->inflight_bytes -= r->footprint;
       srv->completed++;
-      srv->events += r->nevt;
+      srv->events += r->computed;
       srv->cv_done.notify_all();
     }
     // admission: FIFO within each class; small requests take high-priority slots first and may
@@ -188,10 +196,10 @@ void destroy_slots(mg_server* srv) {
   for (Slot& s : srv->slots) {
     for (mg_ctx*& c : s.ctx)
       if (c) { mg_destroy(c); c = nullptr; }
-    if (s.mom) cudaFree(s.mom);
-    if (s.me) cudaFree(s.me);
-    if (s.host) cudaFreeHost(s.host);
-    if (s.host_nbad) cudaFreeHost(s.host_nbad);
+    if (s.mom) mg::dev_free(s.mom);
+    if (s.me) mg::dev_free(s.me);
+    if (s.host) mg::host_free(s.host);
+    if (s.host_nbad) mg::host_free(s.host_nbad);
     if (s.ev) cudaEventDestroy(s.ev);
     if (s.stream) cudaStreamDestroy(s.stream);
   }
@@ -241,10 +249,10 @@ mg_status mg_serve_create(const mg_serve_cfg* cfg_in, mg_server** out) {
     s.high = cfg.slots > 1 && i < srv->slots.size() / 2;
     if (cudaStreamCreateWithPriority(&s.stream, cudaStreamNonBlocking, s.high ? prio_high : prio_low) != cudaSuccess ||
         cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaMalloc(&s.mom, static_cast<size_t>(mg_mom_count(MG_GG_TTGGG, nmax)) * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&s.me, nmax * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&s.host, nmax * sizeof(double)) != cudaSuccess ||
-        cudaMallocHost(&s.host_nbad, sizeof(unsigned long long)) != cudaSuccess) {
+        mg::dev_alloc(&s.mom, static_cast<size_t>(mg_mom_count(MG_GG_TTGGG, nmax)) * sizeof(double)) != cudaSuccess ||
+        mg::dev_alloc(&s.me, nmax * sizeof(double)) != cudaSuccess ||
+        mg::host_alloc(&s.host, nmax * sizeof(double)) != cudaSuccess ||
+        mg::host_alloc(&s.host_nbad, sizeof(unsigned long long)) != cudaSuccess) {
       cudaGetLastError();
       st = MG_ENOMEM;
       break;
@@ -336,6 +344,27 @@ mg_status mg_serve_wait(mg_server* srv, uint64_t ticket, double* me_out_host, in
   if (!srv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [r] { return r->done; }))
     return MG_ETIMEOUT;
   return take_result(srv, r, me_out_host, latency_ms);
+}
+
+mg_status mg_serve_cancel(mg_server* srv, uint64_t ticket) {
+  if (!srv) return MG_EINVAL;
+  std::lock_guard<std::mutex> g(srv->mu);
+  auto it = srv->reqs.find(ticket);
+  if (it == srv->reqs.end()) return MG_EINVAL;
+  Request* r = it->second;
+  if (r->done) return MG_OK;
+  for (auto q = srv->queue.begin(); q != srv->queue.end(); ++q) {
+    if (*q != r) continue;
+    srv->queue.erase(q);   // not admitted yet: nothing of it ran
+    r->status = MG_ECANCELED;
+    r->done = true;
+    r->t_done = Clock::now();
+    srv->completed++;
+    srv->cv_done.notify_all();
+    return MG_OK;
+  }
+  r->cancel = true;        // in flight: the worker stops it at its next chunk boundary
+  return MG_OK;
 }
 
 mg_status mg_serve_stats(mg_server* srv, int64_t* completed, int64_t* events, int64_t* peak_bytes, int* peak_inflight) {

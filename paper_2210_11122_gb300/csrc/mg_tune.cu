@@ -18,6 +18,7 @@
 #include <string>
 #include <vector>
 
+#include "mg_alloc.h"
 #include "mg_ctx.h"
 #include "mg_internal.h"
 #include "mg_kernels.h"
@@ -97,8 +98,8 @@ extern "C" mg_status mg_autotune(mg_ctx* ctx, mg_precision precision, int64_t ne
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   mg_status rc = MG_OK;
   const mg::MeShape saved = ctx->shape[precision];
-  if (cudaMalloc(&mom, mg_mom_count(ctx->proc, nevt) * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&me, nevt * sizeof(double)) != cudaSuccess ||
+  if (mg::dev_alloc(&mom, mg_mom_count(ctx->proc, nevt) * sizeof(double)) != cudaSuccess ||
+      mg::dev_alloc(&me, nevt * sizeof(double)) != cudaSuccess ||
       cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
       cudaEventCreate(&e1) != cudaSuccess) {
     cudaGetLastError();
@@ -180,8 +181,8 @@ extern "C" mg_status mg_autotune(mg_ctx* ctx, mg_precision precision, int64_t ne
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   if (st) cudaStreamDestroy(st);
-  if (mom) cudaFree(mom);
-  if (me) cudaFree(me);
+  if (mom) mg::dev_free(mom);
+  if (me) mg::dev_free(me);
   ctx->last = nullptr;
   return rc;
 }

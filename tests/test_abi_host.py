@@ -41,6 +41,8 @@ def test_binding_constants_match_the_header(mg):
     for name in ("MG_FP64", "MG_FP32_AMP", "MG_FP64_TCCOLOR", "MG_MIXED", "MG_GG_TT", "MG_GG_TTG", "MG_GG_TTGG",
                  "MG_GG_TTGGG"):
         assert getattr(mg, name) == enums[name], name
+    status = {k: v for k, v in enums.items() if k == "MG_OK" or k.startswith("MG_E")}
+    assert {v: k for k, v in status.items()} == mg.STATUS
 
 
 def test_library_exports_every_declared_symbol(mg):
@@ -50,8 +52,9 @@ def test_library_exports_every_declared_symbol(mg):
 
 
 def test_strerror_and_defaults(mg):
-    for s in range(9):
+    for s in range(10):
         assert mg.lib().mg_strerror(s)
+    assert mg.lib().mg_strerror(9) != mg.lib().mg_strerror(99)
     p = mg.default_params()
     assert (p.mt, p.wt, p.alphas, p.hel_warmup, p.hel_tau) == (173.0, 0.0, 0.118, 1024, 1e-9)
 
@@ -185,3 +188,17 @@ def test_sde_channel_keys_equal_the_oracles(mg):
         keys = mg.sde_channels(proc)
         assert len(keys) == len(set(keys)) == [3, 15, 105, 945][ng]
         assert set(keys) == {sde.key(d) for d in sde.diagrams(ng)}
+
+
+def test_allocation_fault_injector_host(mg):
+    """The host-side allocation-failure injector: argument checks and the live count without a GPU."""
+    L = mg.lib()
+    assert L.mg_diag_fail_alloc(-1) == 1
+    assert L.mg_diag_fail_alloc(3) == 0
+    assert L.mg_diag_fail_alloc(0) == 0
+    assert mg.live_allocs() == 0              # nothing allocated in a process without a device
+    assert L.mg_serve_cancel(None, 1) == 1
+    r = ctypes.c_double()
+    assert L.mg_measure_mma_peak(0, ctypes.byref(r)) == 1 and L.mg_measure_mma_peak(1 << 17, ctypes.byref(r)) == 1
+    assert L.mg_measure_mma_peak(16, None) == 1
+    assert L.mg_set_fp32_tau(None, ctypes.c_double(1e-4)) == 1

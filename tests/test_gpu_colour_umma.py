@@ -98,3 +98,12 @@ def test_umma_bounded_wait_reports_timeout_and_context_recovers(env):
         ctx.sigmakin(mom, n, c, mg.MG_FP64_TCCOLOR)
         assert ctx.check() == 0
         assert torch.equal(a, c)
+
+
+def test_mma_peak_microbenchmark_is_exact_and_plausible(env):
+    """The tensor-core microbenchmark (tcgen05.mma kind::f16, the colour pass's instruction): the library
+    checks the accumulated integer products exactly; the rate lies between a tenth of and 1.5x the
+    nominal dense FP16 peak of 2.25 PFLOP/s."""
+    torch, mg, orc = env
+    r = mg.measure_mma_peak(4096)
+    assert 2.25e14 < r < 3.4e15, r
