@@ -90,6 +90,10 @@ def parse():
     return ap.parse_args()
 
 
+# sources of the FP64 slot kernels (body, algebra, dispatch): a committed traffic figure holds while their hash does
+ME_SOURCES = ("mg_me_kernel.cuh", "mg_me_algebra.cuh", "mg_me2.cu")
+
+
 def profiled_traffic(kernel_files, profile_md, nevt):
     """DRAM bytes of one launch scaled from a committed ncu summary, or None when the kernel sources
     (hashed in the order given) have changed since the counters were taken."""
@@ -416,11 +420,12 @@ class Leg:
         if precision == mg.MG_FP64:
             csrc = os.path.join(ROOT, "paper_2210_11122_gb300", "csrc")
             prof = profile_for(self.process)
-            traffic = profiled_traffic([os.path.join(csrc, f) for f in ("mg_me_kernel.cuh", "mg_me_algebra.cuh")],
-                                       prof, nev) if prof else None
+            traffic = profiled_traffic([os.path.join(csrc, f) for f in ME_SOURCES], prof, nev) if prof else None
             shared = self.shapes[name]["shared"]
-            kernel = ("k_event_prep + %sk_me_gluonhel<%d,double> + k_hel_sum (one mg_sigmakin call)"
-                      % ("k_share_level (per sequence length) + " if shared else "", self.ng + 2))
+            K = self.ng + 2
+            slot_kernel = ("k_me_gluonhel_occ<%d>" % K) if (K >= 4 or (K == 3 and shared)) else ("k_me_gluonhel<%d,double>" % K)
+            kernel = ("k_event_prep + %s%s + k_hel_sum (one mg_sigmakin call)"
+                      % ("k_share_level (per sequence length) + " if shared else "", slot_kernel))
             return fp64_roofline(amp + col, oracle_flops, nev, me_ms, p64, traffic, kernel)
         if precision == mg.MG_FP64_TCCOLOR:
             return time_roofline([("fp64", amp * nev, p64, src64),

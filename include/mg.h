@@ -174,7 +174,7 @@ mg_status mg_check(mg_ctx* ctx, void* stream, int64_t* nbad);
  * (once per event) and the currents and jamps of every gluon-helicity combination with a good
  * helicity, *colour_flops for the colour sums (4 ncol(ncol+1)/2 + 4 ncol per good helicity), counting
  * an FMA as 2.  The FP64-amplitude modes tabulate (gamma.J) v per current, the FP32-amplitude modes
- * form it per jamp term; for gg -> t tbar g and t tbar g g g the FP64-amplitude count is that of the
+ * form it per jamp term; from gg -> t tbar g on, the FP64-amplitude count is that of the
  * default MG_LAUNCH_SHARED algorithm (the currents of fewer than all gluons, with their (gamma.J) v, once
  * per helicity assignment of their own gluons per event).  mask (ceil(nhel/32) words, as returned by
  * mg_hel_mask) selects the good helicities; NULL = all.  Host only. */
@@ -324,7 +324,7 @@ mg_status mg_autotune(mg_ctx* ctx, mg_precision precision, int64_t nevt, const c
 
 /* The launch shape mg_sigmakin(precision) uses on this context (default: 128 events per block,
  * event-tile-major, flags MG_LAUNCH_UNROLLED | MG_LAUNCH_DF_REDO | MG_LAUNCH_FUSED, plus MG_LAUNCH_SHARED
- * for gg -> t tbar g and t tbar g g g, MG_LAUNCH_WARP for t tbar g g and t tbar g g g, and
+ * for gg -> t tbar g, t tbar g g and t tbar g g g, MG_LAUNCH_WARP for t tbar g g and t tbar g g g, and
  * MG_LAUNCH_TC_APART for t tbar g g g).  Any out-pointer may be NULL. */
 mg_status mg_get_launch_shape(mg_ctx* ctx, mg_precision precision, int* tile_ev, int* slot_major, int* flags);
 

@@ -302,9 +302,9 @@ mg_status mg_flops_per_event_shape(mg_process proc, mg_precision precision, cons
   double a, c;
   const bool fp32 = precision == MG_FP32_AMP || precision == MG_MIXED;
   // flags < 0: the default algorithm of each mode (as mg_create's launch shapes): FP64 amplitudes share
-  // the currents of fewer than all gluons between gluon-helicity combinations for 1 and 3 final-state gluons
+  // the currents of fewer than all gluons between gluon-helicity combinations from 1 final-state gluon on
   const int K = mg::gluons_of(proc);
-  const bool shared = flags < 0 ? (K == 3 || K == 5) : (flags & MG_LAUNCH_SHARED) != 0;
+  const bool shared = flags < 0 ? K >= 3 : (flags & MG_LAUNCH_SHARED) != 0;
   // the lane-group kernel (FP32 amplitudes, 3..5 gluons; the default for 4 and 5) with its SIMT colour
   // epilogue: MG_FP32_AMP, or MG_MIXED whose colour sums then run on the tensor cores (not counted here)
   const bool warp = flags < 0 ? K >= 4 : (flags & MG_LAUNCH_WARP) != 0;
@@ -470,8 +470,8 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
     // than the in-kernel one there); the autotuner can change it
     if (c->K == 5) c->shape[MG_MIXED].tc_apart = true;
     // FP64 amplitudes: share the currents of fewer than all gluons between gluon-helicity combinations
-    // where that was measured faster (1 and 3 final-state gluons); the autotuner can change it
-    for (int p = 0; p < 4; ++p) c->shape[p].shared = c->K == 3 || c->K == 5;
+    // where that was measured faster (1, 2 and 3 final-state gluons); the autotuner can change it
+    for (int p = 0; p < 4; ++p) c->shape[p].shared = c->K >= 3;
     // FP32 recomputation threshold: the largest plain-FP32 error among the events kept in FP32 was
     // measured at 3.6e-6 / 3.7e-6 / 2.0e-6 (1 / 2 / 3 final-state gluons) with tau = 3e-4, and 2.8e-6 for
     // 3 gluons with tau = 1e-4, which recomputes a third as many events there

@@ -113,6 +113,26 @@ static cudaError_t launch_v2(const double* mom, void* prep, int64_t nevt, const 
       return launch_me_static(K, sizeof(T) == 4, rec, nevt, gslots, maxslot, nslot, mask, cst, out, stride, jout, shape,
                               skip, st);
     if constexpr (std::is_same<T, double>::value) {
+      // the compile for more resident blocks (k_me_gluonhel_occ): 4 and 5 gluons, and 3 with shared currents
+      // (without them its bounded compile spills ~0.5 KB per thread)
+      if constexpr (K >= 3) {
+        constexpr int MINB = K == 3 ? 4 : 3;
+        if (K >= 4 || share) {
+          if (jout && share)
+            { v2::k_me_gluonhel_occ<K, true, true, MINB><<<grid, kMeThreads, 0, st>>>(
+                rec, nevt, tab, gslots, nslot, mask, ctri, cst, out, stride, jout, tev, sm, skip, share); mg::note_launch(); }
+          else if (share)
+            { v2::k_me_gluonhel_occ<K, false, true, MINB><<<grid, kMeThreads, 0, st>>>(
+                rec, nevt, tab, gslots, nslot, mask, ctri, cst, out, stride, nullptr, tev, sm, skip, share); mg::note_launch(); }
+          else if (jout)
+            { v2::k_me_gluonhel_occ<K, true, false, MINB><<<grid, kMeThreads, 0, st>>>(
+                rec, nevt, tab, gslots, nslot, mask, ctri, cst, out, stride, jout, tev, sm, skip, nullptr); mg::note_launch(); }
+          else
+            { v2::k_me_gluonhel_occ<K, false, false, MINB><<<grid, kMeThreads, 0, st>>>(
+                rec, nevt, tab, gslots, nslot, mask, ctri, cst, out, stride, nullptr, tev, sm, skip, nullptr); mg::note_launch(); }
+          return cudaGetLastError();
+        }
+      }
       if (share) {
         if (jout)
           { v2::k_me_gluonhel<K, T, false, true, true, true><<<grid, kMeThreads, 0, st>>>(

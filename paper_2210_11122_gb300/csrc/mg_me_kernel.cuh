@@ -262,14 +262,16 @@ __device__ __forceinline__ void me_slot(const double* __restrict__ mom, const T*
   }
 }
 
-template <int K, class T, bool PER_HEL, bool PREP, bool JOUT, bool SHARED = false, bool LHE = false>
-__global__ void __launch_bounds__(kMeThreads)
-k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab,
-              const int* __restrict__ gslots, const int* __restrict__ nslot_dev, const uint32_t* __restrict__ mask,
-              const typename ColourT<T>::type* __restrict__ ctri, MeConst cst, double* __restrict__ out, int64_t stride,
-              float2* __restrict__ jout, int tile_ev, int slot_major, const int* __restrict__ evlist,
-              const int* __restrict__ nlist, int rows_out, const uint8_t* __restrict__ skip,
-              const double* __restrict__ share = nullptr, double* __restrict__ j2 = nullptr) {
+// The kernel body: thread -> (event, slot) of the launch shape, then me_slot.
+template <int K, class T, bool PER_HEL, bool PREP, bool JOUT, bool SHARED, bool LHE>
+__device__ __forceinline__ void me_thread(const double* __restrict__ mom, const T* __restrict__ rec, int64_t nevt,
+                                          const Tables* __restrict__ tab, const int* __restrict__ gslots,
+                                          const int* __restrict__ nslot_dev, const uint32_t* __restrict__ mask,
+                                          const typename ColourT<T>::type* __restrict__ ctri, const MeConst& cst,
+                                          double* __restrict__ out, int64_t stride, float2* __restrict__ jout, int tile_ev,
+                                          int slot_major, const int* __restrict__ evlist, const int* __restrict__ nlist,
+                                          int rows_out, const uint8_t* __restrict__ skip, const double* __restrict__ share,
+                                          double* __restrict__ j2) {
   static_assert(!SHARED || (PREP && std::is_same<T, double>::value), "shared currents: FP64 with a record");
   static_assert(!LHE || (PREP && !PER_HEL && !JOUT && std::is_same<T, double>::value), "LHE rows: FP64 with a record");
   const int tile_sl = static_cast<int>(blockDim.x) / tile_ev;   // slots per block
@@ -285,6 +287,35 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
 
   me_slot<K, T, PER_HEL, PREP, JOUT, SHARED, LHE>(mom, rec, e, slot, gc, tab, mask, ctri, cst, out, stride, jout, rows_out,
                                                 share, j2);
+}
+
+template <int K, class T, bool PER_HEL, bool PREP, bool JOUT, bool SHARED = false, bool LHE = false>
+__global__ void __launch_bounds__(kMeThreads)
+k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab,
+              const int* __restrict__ gslots, const int* __restrict__ nslot_dev, const uint32_t* __restrict__ mask,
+              const typename ColourT<T>::type* __restrict__ ctri, MeConst cst, double* __restrict__ out, int64_t stride,
+              float2* __restrict__ jout, int tile_ev, int slot_major, const int* __restrict__ evlist,
+              const int* __restrict__ nlist, int rows_out, const uint8_t* __restrict__ skip,
+              const double* __restrict__ share = nullptr, double* __restrict__ j2 = nullptr) {
+  me_thread<K, T, PER_HEL, PREP, JOUT, SHARED, LHE>(mom, rec, nevt, tab, gslots, nslot_dev, mask, ctri, cst, out, stride,
+                                                    jout, tile_ev, slot_major, evlist, nlist, rows_out, skip, share, j2);
+}
+
+// The FP64 slot kernel with a record from 3 gluons on, compiled for MINB resident blocks per SM: 4 for 3
+// gluons (at most 128 registers; the unbounded compile takes 166, 3 blocks), 3 for 4 and 5 (at most 168;
+// unbounded 254, 2 blocks).  More warps hide more of the FP64 pipe's dependent-instruction latency:
+// measured 1.3 % faster for 3 gluons, 8 % for 4 (shared currents) and 3 % for 5; spills stay below 250
+// bytes per thread.
+template <int K, bool JOUT, bool SHARED, int MINB>
+__global__ void __launch_bounds__(kMeThreads, MINB)
+k_me_gluonhel_occ(const double* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab,
+                 const int* __restrict__ gslots, const int* __restrict__ nslot_dev, const uint32_t* __restrict__ mask,
+                 const double* __restrict__ ctri, MeConst cst, double* __restrict__ out, int64_t stride,
+                 float2* __restrict__ jout, int tile_ev, int slot_major, const uint8_t* __restrict__ skip,
+                 const double* __restrict__ share) {
+  me_thread<K, double, false, true, JOUT, SHARED, false>(nullptr, rec, nevt, tab, gslots, nslot_dev, mask, ctri, cst, out,
+                                                         stride, jout, tile_ev, slot_major, nullptr, nullptr, 0, skip,
+                                                         share, nullptr);
 }
 
 // Currents shared between gluon-helicity combinations (FP64): every canonical sequence s of `level`

@@ -50,6 +50,11 @@ template <> struct WSizes<3> { static constexpr int ncol = 6, nseq = 6, nfull = 
 template <> struct WSizes<4> { static constexpr int ncol = 24, nseq = 22, nfull = 12, G = 8; };
 template <> struct WSizes<5> { static constexpr int ncol = 120, nseq = 105, nfull = 60, G = 32; };
 
+// The recursion tables (18 KB) are copied into shared memory for 5 gluons and read through L1 otherwise:
+// with 4 gluons the copy costs a resident block per SM (measured 3 % slower), with 5 the table reads
+// of the 32-lane groups are faster from shared memory (measured 3 % faster)
+template <int K> constexpr bool kTabSmem = K == 5;
+
 // shared state of one slot: component-major, so that lanes reading different currents hit different banks
 template <int K>
 struct SlotState {
@@ -120,7 +125,7 @@ struct SmemLayout {
   static constexpr int GPW = 32 / WSizes<K>::G;
   static constexpr size_t rec_off = sizeof(SlotState<K>) * kWarps * GPW;
   static constexpr size_t tab_off = (rec_off + sizeof(float) * v2::EvLayout<K>::NITEM + 15) / 16 * 16;
-  static constexpr size_t bytes = tab_off + sizeof(Tables);
+  static constexpr size_t bytes = kTabSmem<K> ? tab_off + sizeof(Tables) : tab_off;
 };
 
 // (resident blocks per SM: 4 (the shared memory allows that many) and the registers to match)
@@ -134,8 +139,8 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
   constexpr int npar = K + 2, NCOL = WSizes<K>::ncol, NFULL = WSizes<K>::nfull;
   constexpr int NSUB = 1 << K;
   constexpr int G = WSizes<K>::G, GPW = 32 / G;   // lanes per slot, slots per warp
-  // shared memory (dynamic, see warp_smem_bytes): the slots' state, the event's record (read by every slot
-  // of the block), the recursion tables (read with per-lane indices)
+  // shared memory (dynamic, SmemLayout): the slots' state, the event's record (read by every slot of the
+  // block) and, for 5 gluons, the recursion tables (read with per-lane indices)
   extern __shared__ __align__(16) unsigned char wsm[];
   SlotState<K>* sh = reinterpret_cast<SlotState<K>*>(wsm);
   float* rs = reinterpret_cast<float*>(wsm + SmemLayout<K>::rec_off);
@@ -151,12 +156,14 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
     const float* in = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
     for (int i = threadIdx.x; i < L::NITEM; i += blockDim.x) rs[i] = __ldg(in + i * kPage);
     static_assert(sizeof(Tables) % 4 == 0, "table copy in words");
-    const unsigned* src = reinterpret_cast<const unsigned*>(tab_g);
-    unsigned* dst = reinterpret_cast<unsigned*>(&tabs);
-    for (int i = threadIdx.x; i < static_cast<int>(sizeof(Tables) / 4); i += blockDim.x) dst[i] = __ldg(src + i);
+    if constexpr (kTabSmem<K>) {
+      const unsigned* src = reinterpret_cast<const unsigned*>(tab_g);
+      unsigned* dst = reinterpret_cast<unsigned*>(&tabs);
+      for (int i = threadIdx.x; i < static_cast<int>(sizeof(Tables) / 4); i += blockDim.x) dst[i] = __ldg(src + i);
+    }
   }
   __syncthreads();
-  const Tables* __restrict__ tab = &tabs;
+  const Tables* __restrict__ tab = kTabSmem<K> ? &tabs : tab_g;
   const bool active = slot < nslot;
   // groups past the last slot leave (every sync of the slot work is per group), except with the
   // tensor-core epilogue, whose MMAs take the whole warp: there they contribute zero jamps

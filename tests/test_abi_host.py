@@ -124,14 +124,14 @@ def test_flop_model(mg):
             assert c32 == (nh // 4) * 4 * (4.0 * n * n + 4 * n)
         assert mg.flops_per_event(proc, None, mg.MG_MIXED) == (a32, col)
         # FP64 amplitudes with the currents shared between gluon-helicity combinations: fewer flops with
-        # every helicity good from 1 final-state gluon on, the same colour sums; the default for
-        # gg->ttg and gg->ttggg; no effect on the FP32-amplitude modes
+        # every helicity good from 1 final-state gluon on, the same colour sums; the default there;
+        # no effect on the FP32-amplitude modes
         sh = mg.flops_per_event(proc, None, mg.MG_FP64, mg.LAUNCH_SHARED)
         plain = mg.flops_per_event(proc, None, mg.MG_FP64, 0)
         assert sh[1] == plain[1] == col
         if proc != "ggtt":
             assert sh[0] < plain[0]
-        assert (amp, col) == (sh if proc in ("ggttg", "ggttggg") else plain)
+        assert (amp, col) == (sh if proc != "ggtt" else plain)
         warp = mg.LAUNCH_WARP if info["npar"] >= 6 else 0   # the FP32 default for 4 and 5 gluons
         assert mg.flops_per_event(proc, None, mg.MG_FP32_AMP, mg.LAUNCH_SHARED | warp) == (a32, c32)
     with pytest.raises(mg.MGError):
