@@ -577,7 +577,8 @@ static cudaError_t fork_repair(mg_ctx* ctx, const double* mom, int64_t nevt, con
   if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0);
   if (e == cudaSuccess && df)
     e = mg::launch_me_repair(ctx->K, mom, nevt, ctx->d_tab, ctx->d_gslots, 1 << ctx->K, ctx->d_ngslots, ctx->d_mask,
-                             ctx->d_ctri_f, cst, ctx->d_part, stride, ctx->d_repair, ctx->d_nrepair, rows_out, ctx->side);
+                             ctx->d_ctri_f, ctx->d_cfull, cst, ctx->d_part, stride, ctx->d_repair, ctx->d_nrepair, rows_out,
+                             ctx->side);
   else if (e == cudaSuccess)
     e = mg::launch_me_gluonhel(ctx->K, false, false, mom, nullptr, nevt, ctx->d_tab, ctx->d_gslots, 1 << ctx->K,
                                ctx->d_ngslots, ctx->d_mask, ctx->d_ctri, ctx->d_ctri_f, cst, ctx->d_part, stride,

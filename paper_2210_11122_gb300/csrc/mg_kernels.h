@@ -77,11 +77,17 @@ cudaError_t launch_share(int K, const void* rec, int64_t nevt, const Tables* tab
                          cudaStream_t st);
 int64_t event_record_bytes(int K, bool fp32);
 // The FP32 modes' recomputation of events evlist[0..*nlist) with double-float amplitudes (mg_me_dd.cu):
-// launch_me_gluonhel's contract for prep == NULL, per_hel false, FP32 colour table ctri32.
+// launch_me_gluonhel's contract for prep == NULL, per_hel false, FP32 colour table ctri32 (the per-thread
+// kernel) or full FP32 colour matrix cfull (the lane-group kernel, used for 4 and 5 gluons).
 cudaError_t launch_me_repair(int K, const double* mom, int64_t nevt, const Tables* tab, const int* gslots, int maxslot,
-                             const int* nslot, const uint32_t* mask, const float* ctri32, const MeConst& cst,
-                             double* out, int64_t stride, const int* evlist, const int* nlist, int rows_out,
-                             cudaStream_t st);
+                             const int* nslot, const uint32_t* mask, const float* ctri32, const float* cfull,
+                             const MeConst& cst, double* out, int64_t stride, const int* evlist, const int* nlist,
+                             int rows_out, cudaStream_t st);
+// The lane-group form of that recomputation (mg_me_warp.cu, K = 3..5).
+cudaError_t launch_me_warp_repair(int K, const double* mom, int64_t nevt, const Tables* tab, const int* gslots,
+                                  int maxslot, const int* nslot, const uint32_t* mask, const float* cfull,
+                                  const MeConst& cst, double* out, int64_t stride, const int* evlist, const int* nlist,
+                                  int rows_out, cudaStream_t st);
 // The compile-time-unrolled matrix-element kernel (mg_me3.cu): same contract as launch_me_gluonhel with
 // a per-event record rec (filled by k_event_prep), for the (K, precision) pairs me_static_available
 // lists.  me_static_upload_colour: its colour triangle (constant memory), once per device and K.

@@ -26,9 +26,14 @@ static cudaError_t launch_dd(const double* mom, int64_t nevt, const Tables* tab,
 }
 
 cudaError_t launch_me_repair(int K, const double* mom, int64_t nevt, const Tables* tab, const int* gslots, int maxslot,
-                             const int* nslot, const uint32_t* mask, const float* ctri32, const MeConst& cst,
-                             double* out, int64_t stride, const int* evlist, const int* nlist, int rows_out,
-                             cudaStream_t st) {
+                             const int* nslot, const uint32_t* mask, const float* ctri32, const float* cfull,
+                             const MeConst& cst, double* out, int64_t stride, const int* evlist, const int* nlist,
+                             int rows_out, cudaStream_t st) {
+  // 4 and 5 gluons: a group of lanes per (event, slot), the state in shared memory (the per-thread form
+  // keeps ~28 KB of double-float arrays per thread in local memory and runs as one long wave)
+  if (K >= 4)
+    return launch_me_warp_repair(K, mom, nevt, tab, gslots, maxslot, nslot, mask, cfull, cst, out, stride, evlist, nlist,
+                                 rows_out, st);
   switch (K) {
     case 2: return launch_dd<2>(mom, nevt, tab, gslots, maxslot, nslot, mask, ctri32, cst, out, stride, evlist, nlist, rows_out, st);
     case 3: return launch_dd<3>(mom, nevt, tab, gslots, maxslot, nslot, mask, ctri32, cst, out, stride, evlist, nlist, rows_out, st);

@@ -14,6 +14,7 @@
 //     rows and helicities), then sums over the group; or (jamp output) the jamps are written out for
 //     the tensor-core colour sum.
 #include <atomic>
+#include <type_traits>
 
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -50,21 +51,44 @@ template <> struct WSizes<3> { static constexpr int ncol = 6, nseq = 6, nfull = 
 template <> struct WSizes<4> { static constexpr int ncol = 24, nseq = 22, nfull = 12, G = 8; };
 template <> struct WSizes<5> { static constexpr int ncol = 120, nseq = 105, nfull = 60, G = 32; };
 
+// Shared-memory storage of a complex current component: float2 for FP32 amplitudes, float4 (hi and lo
+// of the real, then of the imaginary part) for double-float ones (the recomputation of flagged events)
+template <class T> struct WStore;
+template <> struct WStore<float> { using type = float2; };
+template <> struct WStore<dd::df> { using type = float4; };
+__device__ __forceinline__ cx<float> ldw(float2 v) { return {v.x, v.y}; }
+__device__ __forceinline__ cx<dd::df> ldw(float4 v) { return {dd::df(v.x, v.y), dd::df(v.z, v.w)}; }
+__device__ __forceinline__ float2 stw(cx<float> v) { return make_float2(v.r, v.i); }
+__device__ __forceinline__ float4 stw(cx<dd::df> v) { return make_float4(v.r.hi, v.r.lo, v.i.hi, v.i.lo); }
+// a jamp rounded to FP32 for the colour sum (FP32 arithmetic either way: C is exact, the quadratic form
+// is well conditioned)
+__device__ __forceinline__ float2 jamp32(cx<float> v) { return make_float2(v.r, v.i); }
+__device__ __forceinline__ float2 jamp32(cx<dd::df> v) {
+  return make_float2(__fadd_rn(v.r.hi, v.r.lo), __fadd_rn(v.i.hi, v.i.lo));
+}
+// the per-event record: FP32 values for FP32 amplitudes, FP64 for double-float ones
+template <class T> struct WRec { using type = float; };
+template <> struct WRec<dd::df> { using type = double; };
+__device__ __forceinline__ float rec_val(float v, float*) { return v; }
+__device__ __forceinline__ dd::df rec_val(double v, dd::df*) { return dd::df(v); }
+
 // The recursion tables (18 KB) are copied into shared memory for 5 gluons and read through L1 otherwise:
 // with 4 gluons the copy costs a resident block per SM (measured 3 % slower), with 5 the table reads
 // of the 32-lane groups are faster from shared memory (measured 3 % faster)
 template <int K> constexpr bool kTabSmem = K == 5;
 
 // shared state of one slot: component-major, so that lanes reading different currents hit different banks
-template <int K>
+template <int K, class T = float>
 struct SlotState {
-  float2 J[4][WSizes<K>::nseq];
-  float2 JF[4][WSizes<K>::nfull];
-  float2 A[4][WSizes<K>::ncol];   // jamps of helicity 2 * top + antitop
+  using W = typename WStore<T>::type;
+  W J[4][WSizes<K>::nseq];
+  W JF[4][WSizes<K>::nfull];
+  float2 A[4][WSizes<K>::ncol];   // jamps of helicity 2 * top + antitop (FP32)
 };
 
 __device__ __forceinline__ cx<float> c2(float2 v) { return {v.x, v.y}; }
 __device__ __forceinline__ float2 f2(cx<float> v) { return make_float2(v.r, v.i); }
+
 
 // first canonical sequence of length L (sequences are numbered by length: K singles, then L = 2, 3, ...)
 __host__ __device__ constexpr int seq_start(int K, int L) {
@@ -120,21 +144,31 @@ __device__ __forceinline__ float unsplit(uint32_t h, uint32_t l, int k) {
   return fmaf(__half2float(lh), 1.f / 2048.f, __half2float(hh));
 }
 
-template <int K>
+template <int K, class T = float>
 struct SmemLayout {
   static constexpr int GPW = 32 / WSizes<K>::G;
-  static constexpr size_t rec_off = sizeof(SlotState<K>) * kWarps * GPW;
-  static constexpr size_t tab_off = (rec_off + sizeof(float) * v2::EvLayout<K>::NITEM + 15) / 16 * 16;
+  static constexpr size_t rec_off = sizeof(SlotState<K, T>) * kWarps * GPW;
+  static constexpr size_t tab_off =
+      (rec_off + sizeof(typename WRec<T>::type) * v2::EvLayout<K>::NITEM + 15) / 16 * 16;
   static constexpr size_t bytes = kTabSmem<K> ? tab_off + sizeof(Tables) : tab_off;
 };
 
-// (resident blocks per SM: 4 (the shared memory allows that many) and the registers to match)
-template <int K, int EPI>
-__global__ void __launch_bounds__(kWarps * 32, 4)
-k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab_g, const int* __restrict__ gslots,
+// T = float: the FP32-amplitude kernel, one block per event (blockIdx.x), record from k_event_prep.
+// T = dd::df: the recomputation of the flagged events (evlist[0 .. *nlist)) with double-float amplitudes:
+// each block walks the list with a stride of gridDim.x, computes the event's FP64 record in shared memory
+// (four threads, one record part each) and runs the same slot work; SIMT colour epilogue only.
+// (resident blocks per SM: 4 for FP32 (the shared memory allows that many) and the registers to match;
+// 2 for double-float, whose state is twice as large)
+template <int K, int EPI, class T = float>
+__global__ void __launch_bounds__(kWarps * 32, std::is_same<T, float>::value ? 4 : 2)
+k_me_warp(const void* __restrict__ rec_any, int64_t nevt, const Tables* __restrict__ tab_g, const int* __restrict__ gslots,
           const int* __restrict__ nslot_dev, const uint32_t* __restrict__ mask, const float* __restrict__ cfull,
           const __half* __restrict__ cmat16, MeConst cst, double* __restrict__ out, int64_t stride,
-          float2* __restrict__ jout, const uint8_t* __restrict__ skip) {
+          float2* __restrict__ jout, const uint8_t* __restrict__ skip, const int* __restrict__ evlist = nullptr,
+          const int* __restrict__ nlist = nullptr, int rows_out = 0) {
+  constexpr bool DF = std::is_same<T, dd::df>::value;
+  static_assert(!DF || EPI == kSimt, "double-float: SIMT colour sums only");
+  using RecT = typename WRec<T>::type;
   using L = v2::EvLayout<K>;
   constexpr int npar = K + 2, NCOL = WSizes<K>::ncol, NFULL = WSizes<K>::nfull;
   constexpr int NSUB = 1 << K;
@@ -142,36 +176,35 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
   // shared memory (dynamic, SmemLayout): the slots' state, the event's record (read by every slot of the
   // block) and, for 5 gluons, the recursion tables (read with per-lane indices)
   extern __shared__ __align__(16) unsigned char wsm[];
-  SlotState<K>* sh = reinterpret_cast<SlotState<K>*>(wsm);
-  float* rs = reinterpret_cast<float*>(wsm + SmemLayout<K>::rec_off);
-  Tables& tabs = *reinterpret_cast<Tables*>(wsm + SmemLayout<K>::tab_off);
+  SlotState<K, T>* sh = reinterpret_cast<SlotState<K, T>*>(wsm);
+  RecT* rs = reinterpret_cast<RecT*>(wsm + SmemLayout<K, T>::rec_off);
+  Tables& tabs = *reinterpret_cast<Tables*>(wsm + SmemLayout<K, T>::tab_off);
   const int warp = threadIdx.x >> 5, grp = (threadIdx.x & 31) / G, lane = threadIdx.x % G;
   const unsigned gmask = (G == 32 ? 0xffffffffu : ((1u << (G & 31)) - 1u)) << (grp * G);   // this group's lanes
-  const int64_t e = blockIdx.x;   // one block per event: e < nevt
   const int slot0 = (blockIdx.y * kWarps + warp) * GPW;   // the warp's first slot
   const int slot = slot0 + grp;
   const int nslot = *nslot_dev;
-  if (skip && skip[e]) return;   // recomputed by another launch (the whole block: one event)
-  {
-    const float* in = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
-    for (int i = threadIdx.x; i < L::NITEM; i += blockDim.x) rs[i] = __ldg(in + i * kPage);
-    static_assert(sizeof(Tables) % 4 == 0, "table copy in words");
-    if constexpr (kTabSmem<K>) {
-      const unsigned* src = reinterpret_cast<const unsigned*>(tab_g);
-      unsigned* dst = reinterpret_cast<unsigned*>(&tabs);
-      for (int i = threadIdx.x; i < static_cast<int>(sizeof(Tables) / 4); i += blockDim.x) dst[i] = __ldg(src + i);
-    }
+  if constexpr (DF) {
+    if (static_cast<int>(blockIdx.x) >= *nlist) return;   // no listed event for this block
   }
-  __syncthreads();
+  if constexpr (kTabSmem<K>) {
+    static_assert(sizeof(Tables) % 4 == 0, "table copy in words");
+    const unsigned* src = reinterpret_cast<const unsigned*>(tab_g);
+    unsigned* dst = reinterpret_cast<unsigned*>(&tabs);
+    for (int i = threadIdx.x; i < static_cast<int>(sizeof(Tables) / 4); i += blockDim.x) dst[i] = __ldg(src + i);
+  }
   const Tables* __restrict__ tab = kTabSmem<K> ? &tabs : tab_g;
+  // the slot work of event e, its record already in rs (every thread of the block calls it)
+  auto run_event = [&](const int64_t e) {
+  __syncthreads();
   const bool active = slot < nslot;
   // groups past the last slot leave (every sync of the slot work is per group), except with the
   // tensor-core epilogue, whose MMAs take the whole warp: there they contribute zero jamps
   if (EPI != kMma && !active) return;
-  SlotState<K>& S = sh[warp * GPW + grp];
+  SlotState<K, T>& S = sh[warp * GPW + grp];
   const int gc = active ? gslots[slot] : 0;   // bit g = helicity (+1) of gluon g
-  auto ld = [&](int item) -> float { return rs[item]; };
-  const float gs = static_cast<float>(cst.gs);
+  auto ld = [&](int item) -> T { return rec_val(rs[item], static_cast<T*>(nullptr)); };
+  const T gs = rec_val(static_cast<RecT>(cst.gs), static_cast<T*>(nullptr));
   // helicity index of (gc, top helicity, antitop helicity), and which of the four are in the mask
   int hbase = 0;
 #pragma unroll
@@ -188,30 +221,30 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
 
     // ---- external gluon currents ----
     if (lane < K) {
-      float pol[5];
+      T pol[5];
 #pragma unroll
       for (int i = 0; i < 5; ++i) pol[i] = ld(L::EPS + 5 * lane + i);
-      cx<float> w[4];
+      cx<T> w[4];
       v2::ext_gluon(pol, (gc >> lane) & 1 ? 1 : -1, lane >= 2, w);
 #pragma unroll
-      for (int m = 0; m < 4; ++m) S.J[m][lane] = f2(w[m]);
+      for (int m = 0; m < 4; ++m) S.J[m][lane] = stw(w[m]);
     }
     __syncwarp(gmask);
-    auto getJ = [&](int slot_ref, cx<float>* j) {
+    auto getJ = [&](int slot_ref, cx<T>* j) {
 #pragma unroll
-      for (int m = 0; m < 4; ++m) j[m] = c2(S.J[m][slot_ref >> 1]);
+      for (int m = 0; m < 4; ++m) j[m] = ldw(S.J[m][slot_ref >> 1]);
     };
-    auto getP = [&](int seq, float* P) {
+    auto getP = [&](int seq, T* P) {
       const int msk = tab->seq_mask[seq];
 #pragma unroll
       for (int m = 0; m < 4; ++m) P[m] = ld(L::PT + 4 * msk + m);
     };
     // current of sequence s (splits from the tables) into acc
-    auto current = [&](int nv3, const int16_t (*v3)[2], int nv4, const int16_t (*v4)[3], cx<float>* acc) {
+    auto current = [&](int nv3, const int16_t (*v3)[2], int nv4, const int16_t (*v4)[3], cx<T>* acc) {
       for (int k = 0; k < nv3; ++k) {
         const int rl = v3[k][0], rr = v3[k][1];
-        cx<float> JL[4], JR[4];
-        float PL[4], PR[4];
+        cx<T> JL[4], JR[4];
+        T PL[4], PR[4];
         getJ(rl, JL);
         getJ(rr, JR);
         getP(rl >> 1, PL);
@@ -220,7 +253,7 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
       }
       for (int k = 0; k < nv4; ++k) {
         const int ra = v4[k][0], rb = v4[k][1], rc = v4[k][2];
-        cx<float> JA[4], JB[4], JC[4];
+        cx<T> JA[4], JB[4], JC[4];
         getJ(ra, JA);
         getJ(rb, JB);
         getJ(rc, JC);
@@ -232,22 +265,22 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
 #pragma unroll
     for (int len = 2; len < K; ++len) {
       for (int s = seq_start(K, len) + lane; s < seq_start(K, len + 1); s += G) {
-        cx<float> acc[4] = {};
+        cx<T> acc[4] = {};
         current(tab->seq_nv3[s], tab->seq_v3[s], tab->seq_nv4[s], tab->seq_v4[s], acc);
-        const float f = ld(L::GP + tab->seq_mask[s]);
+        const T f = ld(L::GP + tab->seq_mask[s]);
 #pragma unroll
-        for (int m = 0; m < 4; ++m) S.J[m][s] = f2(v2::cscale(f, acc[m]));
+        for (int m = 0; m < 4; ++m) S.J[m][s] = stw(v2::cscale(f, acc[m]));
       }
       __syncwarp(gmask);
     }
     // ---- all gluons on one current (canonical orderings) ----
     {
-      const float fz = ld(L::GP + NSUB - 1);
+      const T fz = ld(L::GP + NSUB - 1);
       for (int f = lane; f < NFULL; f += G) {
-        cx<float> acc[4] = {};
+        cx<T> acc[4] = {};
         current(tab->full_nv3[f], tab->full_v3[f], tab->full_nv4[f], tab->full_v4[f], acc);
 #pragma unroll
-        for (int m = 0; m < 4; ++m) S.JF[m][f] = f2(v2::cscale(fz, acc[m]));
+        for (int m = 0; m < 4; ++m) S.JF[m][f] = stw(v2::cscale(fz, acc[m]));
       }
     }
     __syncwarp(gmask);
@@ -258,7 +291,7 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
       const int a = lane / H, hl = lane % H;
       const int c0 = hl * NCOL / H, c1 = (hl + 1) * NCOL / H;
       if (good[2 * a] || good[2 * a + 1]) {
-        cx<float> vv[2][4], stk[K][4], Jq[2][4];
+        cx<T> vv[2][4], stk[K][4], Jq[2][4];
 #pragma unroll
         for (int b = 0; b < 2; ++b)
 #pragma unroll
@@ -272,16 +305,16 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
 #pragma unroll
           for (int m = 1; m < K; ++m) {
             if (m <= l) continue;
-            cx<float> acc[4] = {};
+            cx<T> acc[4] = {};
 #pragma unroll
             for (int j = 0; j < m; ++j) {
               const int r = tab->sub[c][j][m];
-              cx<float> Jr[4];
+              cx<T> Jr[4];
               getJ(r, Jr);
               v2::row_gamma_acc(acc, stk[j], Jr, (r & 1) != 0);
             }
             const int pm = tab->prefix_mask[c][m];
-            float q[5];
+            T q[5];
 #pragma unroll
             for (int k = 0; k < 5; ++k) q[k] = ld(L::QC + 5 * pm + k);
             v2::row_prop(acc, q, stk[m]);
@@ -289,10 +322,10 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
           const int fi = tab->full_idx[c];
           const int fj = fi >= 0 ? fi : -fi - 1;
           const bool fneg = fi < 0 && !(K & 1);   // reflection sign (-1)^(K+1)
-          cx<float> JFc[4];
+          cx<T> JFc[4];
 #pragma unroll
-          for (int m = 0; m < 4; ++m) JFc[m] = c2(S.JF[m][fj]);
-          cx<float> amp0 = v2::mdot(Jq[0], JFc), amp1 = v2::mdot(Jq[1], JFc);
+          for (int m = 0; m < 4; ++m) JFc[m] = ldw(S.JF[m][fj]);
+          cx<T> amp0 = v2::mdot(Jq[0], JFc), amp1 = v2::mdot(Jq[1], JFc);
           if (fneg) {
             amp0 = v2::cneg(amp0);
             amp1 = v2::cneg(amp1);
@@ -300,14 +333,14 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
 #pragma unroll
           for (int j = 1; j < K; ++j) {
             const int r = tab->sub[c][j][K];
-            cx<float> Jr[4], t[4] = {};
+            cx<T> Jr[4], t[4] = {};
             getJ(r, Jr);
             v2::row_gamma_acc(t, stk[j], Jr, (r & 1) != 0);
             v2::sdot_acc(amp0, t, vv[0], false);
             v2::sdot_acc(amp1, t, vv[1], false);
           }
-          S.A[2 * a][c] = good[2 * a] ? f2(amp0) : make_float2(0.f, 0.f);
-          S.A[2 * a + 1][c] = good[2 * a + 1] ? f2(amp1) : make_float2(0.f, 0.f);
+          S.A[2 * a][c] = good[2 * a] ? jamp32(amp0) : make_float2(0.f, 0.f);
+          S.A[2 * a + 1][c] = good[2 * a + 1] ? jamp32(amp1) : make_float2(0.f, 0.f);
         }
       } else {
         for (int c = c0; c < c1; ++c) {
@@ -363,7 +396,17 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
       for (int o = G / 2; o > 0; o >>= 1) s += __shfl_xor_sync(gmask, s, o, G);
       if (good[h]) total += s;
     }
-    if (lane == 0) out[slot * stride + e] = f32_times_pow2(total * static_cast<float>(cst.colour_scale), 0);
+    if (lane == 0) {
+      const double v = f32_times_pow2(total * static_cast<float>(cst.colour_scale), 0);
+      if (rows_out) {   // tensor-core row layout (slot * 4 + helicity pair): the slot total in the first row
+        out[(slot * 4) * stride + e] = v;
+        out[(slot * 4 + 1) * stride + e] = 0.0;
+        out[(slot * 4 + 2) * stride + e] = 0.0;
+        out[(slot * 4 + 3) * stride + e] = 0.0;
+      } else {
+        out[slot * stride + e] = v;
+      }
+    }
   } else if constexpr (GPW == 1) {
     // colour sums on the tensor cores, one slot per warp (5 gluons): Y = C a for the slot's 8 vectors
     // a_n (helicity n/2, real part for even n, imaginary for odd) as D = C B, MMA rows = colour index x
@@ -551,6 +594,37 @@ k_me_warp(const float* __restrict__ rec, int64_t nevt, const Tables* __restrict_
       }
     }
   }
+  };   // run_event
+
+  if constexpr (!DF) {
+    const int64_t e = blockIdx.x;   // one block per event: e < nevt
+    if (skip && skip[e]) return;    // recomputed by another launch (the whole block: one event)
+    const float* in = static_cast<const float*>(rec_any) + (e / kPage) * L::NITEM * kPage + (e % kPage);
+    for (int i = threadIdx.x; i < L::NITEM; i += blockDim.x) rs[i] = __ldg(in + i * kPage);
+    run_event(e);
+  } else {
+    const double* mom = static_cast<const double*>(rec_any);
+    const int n = *nlist;
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+      const int64_t e = evlist[i];
+      __syncthreads();   // the previous event's slot work has finished reading the record
+      if ((threadIdx.x & 31) == 0) {   // one part of the FP64 record per warp
+        double p[npar][4];
+        const double* base = mom + (e / kPage) * npar * 4 * kPage + (e % kPage);
+#pragma unroll
+        for (int q = 0; q < npar; ++q)
+#pragma unroll
+          for (int m = 0; m < 4; ++m) p[q][m] = __ldg(base + (q * 4 + m) * kPage);
+        auto put = [&](int item, double v) { rs[item] = v; };
+        if (warp == 0) v2::record_subsets<K, double, 0, NSUB / 2>(p, cst, put);
+        else if (warp == 1) v2::record_subsets<K, double, NSUB / 2, NSUB>(p, cst, put);
+        else if (warp == 2) v2::record_pols<K, double>(p, put);
+        else v2::record_tops<K, double>(p, cst, put);
+      }
+      run_event(e);
+    }
+  }
+
 }
 
 template <int K>
@@ -590,6 +664,33 @@ static cudaError_t launch_k(const void* rec, int64_t nevt, const Tables* tab, co
   return cudaGetLastError();
 }
 
+template <int K>
+static cudaError_t launch_dd_k(const double* mom, int64_t nevt, const Tables* tab, const int* gslots, int maxslot,
+                               const int* nslot, const uint32_t* mask, const float* cfull, const MeConst& cst,
+                               double* out, int64_t stride, const int* evlist, const int* nlist, int rows_out,
+                               cudaStream_t st) {
+  if (nevt <= 0 || maxslot <= 0) return cudaSuccess;
+  constexpr int per_block = kWarps * (32 / WSizes<K>::G);   // slots per block
+  // the blocks walk the list with a stride of gridDim.x (its length is known on the device only)
+  const unsigned gx = static_cast<unsigned>(nevt < 2048 ? nevt : 2048);
+  const dim3 grid(gx, static_cast<unsigned>((maxslot + per_block - 1) / per_block));
+  constexpr size_t smem = SmemLayout<K, dd::df>::bytes;
+  static std::atomic<unsigned long long> configured{0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (!(configured.load(std::memory_order_acquire) & bit)) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_me_warp<K, kSimt, dd::df>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (e != cudaSuccess) return e;
+    configured.fetch_or(bit, std::memory_order_release);
+  }
+  { k_me_warp<K, kSimt, dd::df><<<grid, kWarps * 32, smem, st>>>(mom, nevt, tab, gslots, nslot, mask, cfull, nullptr, cst,
+                                                                out, stride, nullptr, nullptr, evlist, nlist, rows_out);
+    mg::note_launch(); }
+  return cudaGetLastError();
+}
+
 }  // namespace wk
 
 bool me_warp_available(int K, bool fp32) { return fp32 && K >= 3 && K <= 5; }
@@ -602,6 +703,18 @@ cudaError_t launch_me_warp(int K, const void* rec, int64_t nevt, const Tables* t
     case 3: return wk::launch_k<3>(rec, nevt, tab, gslots, maxslot, nslot, mask, cfull, cmat16, epi, cst, out, stride, jout, skip, st);
     case 4: return wk::launch_k<4>(rec, nevt, tab, gslots, maxslot, nslot, mask, cfull, cmat16, epi, cst, out, stride, jout, skip, st);
     case 5: return wk::launch_k<5>(rec, nevt, tab, gslots, maxslot, nslot, mask, cfull, cmat16, epi, cst, out, stride, jout, skip, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_me_warp_repair(int K, const double* mom, int64_t nevt, const Tables* tab, const int* gslots,
+                                  int maxslot, const int* nslot, const uint32_t* mask, const float* cfull,
+                                  const MeConst& cst, double* out, int64_t stride, const int* evlist, const int* nlist,
+                                  int rows_out, cudaStream_t st) {
+  switch (K) {
+    case 3: return wk::launch_dd_k<3>(mom, nevt, tab, gslots, maxslot, nslot, mask, cfull, cst, out, stride, evlist, nlist, rows_out, st);
+    case 4: return wk::launch_dd_k<4>(mom, nevt, tab, gslots, maxslot, nslot, mask, cfull, cst, out, stride, evlist, nlist, rows_out, st);
+    case 5: return wk::launch_dd_k<5>(mom, nevt, tab, gslots, maxslot, nslot, mask, cfull, cst, out, stride, evlist, nlist, rows_out, st);
     default: return cudaErrorInvalidValue;
   }
 }
