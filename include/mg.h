@@ -334,8 +334,8 @@ mg_status mg_set_launch_shape(mg_ctx* ctx, mg_precision precision, int tile_ev, 
 
 /* FP32 modes (MG_FP32_AMP, MG_MIXED): the events whose smallest internal invariant -- |P^2| of a gluon
  * propagator or |Q^2 - m_t^2| of a top propagator, evaluated from the momenta -- is below tau * s are
- * recomputed with double-float (or FP64) amplitudes; default 3e-4, and 1e-4 for gg -> t tbar g g g, where
- * the plain FP32 error of the events kept was measured <= 3e-6; tau = 0 recomputes nothing (the plain
+ * recomputed with double-float (or FP64) amplitudes; default 3e-4, and 3e-5 for gg -> t tbar g g g, where
+ * the plain FP32 error of the events kept was measured <= 4e-6; tau = 0 recomputes nothing (the plain
  * FP32 error).  MG_EINVAL for tau < 0 or not finite. */
 mg_status mg_set_fp32_tau(mg_ctx* ctx, double tau);
 

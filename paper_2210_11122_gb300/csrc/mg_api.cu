@@ -51,21 +51,24 @@ mg_status grow(double** buf, int64_t* cap, int64_t need) {
 // the colour sum per good helicity.  mask == NULL means every helicity is good.
 // warp_simt: the FP32 lane-group kernel's SIMT colour epilogue, which multiplies the full ncol x ncol matrix
 // into the jamps of all four helicities of a slot (4 ncol^2 + 4 ncol each, good or not) instead of the
-// packed triangle per good helicity.
-void flop_model(const mg::Tables& t, const uint32_t* mask, bool fp32, bool shared, bool warp_simt, double* amp,
-                double* col) {
+// packed triangle per good helicity.  warp: the FP32 lane-group kernel (any epilogue), which for 5 gluons
+// takes the gluon-pair currents from the record; the FP32 record of 5 gluons computes them in FP64.
+void flop_model(const mg::Tables& t, const uint32_t* mask, bool fp32, bool shared, bool warp, bool warp_simt,
+                double* amp, double* col) {
   const int K = t.K, nsub = 1 << K, npar = K + 2;
   // three-gluon vertex in the current-conserving form: d (4) + JL.JR (30) + JL.PR, JR.PL (2 x 14) +
   // two scalings (4) + 4 x (real-complex and two complex multiply-adds) (80)
   const double v3 = 146.0, v4 = 192.0, row_gamma = 72.0, row_prop = 56.0, gamma_col = 64.0, sdot = 32.0,
                mdot = 30.0;
-  const double per_event = 25.0 * nsub + 30.0 * K + 100.0;        // subsets, propagators, wavefunctions (once)
+  const bool pairs = fp32 && K == 5;                              // gluon-pair currents in the FP32 record
+  const double per_event = 25.0 * nsub + 30.0 * K + 100.0 +      // subsets, propagators, wavefunctions (once)
+                           (pairs ? K * (K - 1) / 2 * (4.0 * (v3 + 8.0) + 20.0) : 0.0);
   double per_slot = 0.0;                                           // gluon currents of one helicity combination
   double shared_work = 0.0;                                        // (shared: once per event)
   for (int s = K; s < t.nseq; ++s) {
     const double c = v3 * t.seq_nv3[s] + v4 * t.seq_nv4[s] + 8.0;
     if (shared) shared_work += c * (1 << t.seq_len[s]);   // once per helicity assignment of its own gluons
-    else per_slot += c;
+    else if (!(pairs && warp && t.seq_len[s] == 2)) per_slot += c;
   }
   for (int f = 0; f < t.nfull; ++f) per_slot += v3 * t.full_nv3[f] + v4 * t.full_nv4[f] + 8.0;
   // FP64: (gamma.J) v tabulated for every current and both antitop helicities; FP32: formed per jamp term
@@ -308,8 +311,9 @@ mg_status mg_flops_per_event_shape(mg_process proc, mg_precision precision, cons
   // the lane-group kernel (FP32 amplitudes, 3..5 gluons; the default for 4 and 5) with its SIMT colour
   // epilogue: MG_FP32_AMP, or MG_MIXED whose colour sums then run on the tensor cores (not counted here)
   const bool warp = flags < 0 ? K >= 4 : (flags & MG_LAUNCH_WARP) != 0;
-  const bool warp_simt = precision == MG_FP32_AMP && warp && mg::me_warp_available(K, true);
-  flop_model(*t, mask, fp32, !fp32 && shared, warp_simt, &a, &c);
+  const bool warp_fp32 = fp32 && warp && mg::me_warp_available(K, true);
+  const bool warp_simt = precision == MG_FP32_AMP && warp_fp32;
+  flop_model(*t, mask, fp32, !fp32 && shared, warp_fp32, warp_simt, &a, &c);
   delete t;
   if (amp_flops) *amp_flops = a;
   if (colour_flops) *colour_flops = c;
@@ -473,9 +477,10 @@ mg_status mg_create(mg_process proc, const mg_params* params, mg_ctx** out) {
     // where that was measured faster (1, 2 and 3 final-state gluons); the autotuner can change it
     for (int p = 0; p < 4; ++p) c->shape[p].shared = c->K >= 3;
     // FP32 recomputation threshold: the largest plain-FP32 error among the events kept in FP32 was
-    // measured at 3.6e-6 / 3.7e-6 / 2.0e-6 (1 / 2 / 3 final-state gluons) with tau = 3e-4, and 2.8e-6 for
-    // 3 gluons with tau = 1e-4, which recomputes a third as many events there
-    c->fp32_tau = c->K == 5 ? 1e-4 : 3e-4;
+    // measured at 3.6e-6 / 3.7e-6 (1 / 2 final-state gluons) with tau = 3e-4, and for 3 gluons, whose
+    // lane-group kernel takes the gluon-pair currents from the FP64 record, at 3.9e-6 with tau = 3e-5,
+    // which recomputes a twelfth as many events as 3e-4
+    c->fp32_tau = c->K == 5 ? 3e-5 : 3e-4;
     // side stream of the FP32 modes' recomputation: highest priority, so that its few blocks are
     // dispatched ahead of the FP32 launch's
     int lo = 0, hi = 0;

@@ -41,6 +41,8 @@ __global__ void __launch_bounds__(128) k_event_prep(const double* __restrict__ m
     for (int m = 0; m < 4; ++m) p[i][m] = __ldg(base + (i * 4 + m) * kPage);
   T* out = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
   record_all<K, T>(p, cst, [&](int i, T v) { out[i * kPage] = v; });
+  if constexpr (std::is_same<T, float>::value && L::NPAIR > 0)
+    record_j2<K, T>(p, cst, [&](int i, T v) { out[i * kPage] = v; });
 }
 
 // FP32 modes: events whose smallest internal invariant |P^2| or |Q^2 - m^2| (over the gluon and quark

@@ -259,7 +259,7 @@ k_me_fused(const double* __restrict__ mom, int64_t nevt, const int* __restrict__
   static_assert(kMeThreads == 128, "four warps: four record parts");
   using L = v2::EvLayout<K>;
   constexpr int npar = K + 2, NSUB = 1 << K;
-  __shared__ T rec[L::NITEM * 32];
+  __shared__ T rec[L::NBASE * 32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t e = static_cast<int64_t>(blockIdx.x) * 32 + lane;
   if (e < nevt) {

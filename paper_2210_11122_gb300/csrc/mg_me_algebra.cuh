@@ -376,12 +376,19 @@ template <> struct ColourT<dd::df> { using type = float; };
 // ---- per-event data shared by every helicity of an event (FP64 arithmetic, stored as T) ----
 // Layout of one event's record (NITEM values of T): PT[S][4] (incoming gluon momentum of subset S),
 // gprop[S] (-g/P_S^2), qc[S][5] (quark propagator coefficients), pol[g][5] (gluon polarisation basis,
-// see gluon_pol), ubar[hel][4] complex, v[hel][4] complex.
+// see gluon_pol), ubar[hel][4] complex, v[hel][4] complex (the NBASE items every record holds); then, in
+// the FP32 record of 5 gluons, the currents of the gluon pairs (record_j2).  NITEM, the page stride.
 template <int K> struct EvLayout {
   static constexpr int NSUB = 1 << K;
   static constexpr int PT = 0, GP = 4 * NSUB, QC = 5 * NSUB, EPS = 10 * NSUB, UB = EPS + 5 * K, VV = UB + 16;
-  static constexpr int NITEM = VV + 16;
+  static constexpr int NBASE = VV + 16;
+  static constexpr int NPAIR = K == 5 ? K * (K - 1) / 2 : 0;
+  static constexpr int J2 = NBASE;
+  static constexpr int NITEM = J2 + 32 * NPAIR;
 };
+
+// index of the gluon pair a < b among the K (K - 1) / 2 pairs in lexicographic order
+__host__ __device__ constexpr int pair_index(int K, int a, int b) { return a * (2 * K - a - 1) / 2 + (b - a - 1); }
 
 // The record in parts, each written through put(item, value): subsets S in [S0, S1) (S0 = 0 or 2^(K-1),
 // so that every subset's momentum sum builds on one of the same range), the gluon polarisation bases,
@@ -473,6 +480,51 @@ __device__ __forceinline__ void record_tops(const double (*p)[4], const MeConst&
   }
 }
 
+// FP32 record, 5 gluons: the current of every gluon pair a < b for the four helicity assignments h
+// = h_a + 2 h_b (h = 1: helicity +1) of the pair, computed in FP64 and rounded once:
+// J_ab = (-g / P_ab^2) V3(J_a, J_b; P_a, P_b), the canonical split of the length-2 sequence (a, b), with
+// the incoming momenta of the pair's gluons.  Near a collinear pair the vertex numerator vanishes like
+// sqrt(P_ab^2) while its terms do not, so its FP32 rounding, amplified by 1/P_ab^2, is a large part of the
+// error of FP32 amplitudes near collinear pairs (measured: the FP32-kept events' largest error halves);
+// the lane-group FP32 kernel takes these currents from the record instead.  Only for 5 gluons: there the
+// 40 FP64 currents cost 0.3 % of an FP32 call; with 4 gluons their 24 cost 10 % (FP64 runs at 1/64 of the
+// FP32 rate), more than the recomputations they save.
+// Item J2 + ((pair_index(K, a, b) * 4 + h) * 4 + m) * 2 + (0: real, 1: imaginary part).
+template <int K, class T, class Put>
+__device__ __forceinline__ void record_j2(const double (*p)[4], const MeConst& cst, Put&& put) {
+  using L = EvLayout<K>;
+  double pol[K][5], P[K][4];
+#pragma unroll
+  for (int g = 0; g < K; ++g) {
+    const int part = g < 2 ? g : g + 2;
+    gluon_pol<double>(p[part], pol[g]);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) P[g][m] = g < 2 ? p[part][m] : -p[part][m];
+  }
+#pragma unroll
+  for (int a = 0; a < K; ++a)
+#pragma unroll
+    for (int b = a + 1; b < K; ++b) {
+      const double P0 = P[a][0] + P[b][0], P1 = P[a][1] + P[b][1], P2 = P[a][2] + P[b][2], P3 = P[a][3] + P[b][3];
+      const double gp = -cst.gs / (P0 * P0 - P1 * P1 - P2 * P2 - P3 * P3);
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        cx<double> Ja[4], Jb[4], acc[4];
+        ext_gluon(pol[a], (h & 1) ? 1 : -1, a >= 2, Ja);
+        ext_gluon(pol[b], (h >> 1) ? 1 : -1, b >= 2, Jb);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) acc[m] = {0.0, 0.0};
+        v3_acc(acc, Ja, Jb, P[a], P[b], false);
+        const int base = L::J2 + (pair_index(K, a, b) * 4 + h) * 8;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+          put(base + 2 * m, static_cast<T>(gp * acc[m].r));
+          put(base + 2 * m + 1, static_cast<T>(gp * acc[m].i));
+        }
+      }
+    }
+}
+
 template <int K, class T, class Put>
 __device__ __forceinline__ void record_all(const double (*p)[4], const MeConst& cst, Put&& put) {
   record_subsets<K, T, 0, (1 << K)>(p, cst, put);
@@ -485,7 +537,7 @@ template <int K, class T>
 __device__ __forceinline__ void event_data(const double (*p)[4], const MeConst& cst, T (*PT)[4], T* gprop, T (*qc)[5],
                                            T (*pol)[5], cx<T> (*ub)[4], cx<T> (*vv)[4]) {
   using L = EvLayout<K>;
-  T r[L::NITEM] = {};   // (the items no kernel reads stay zero)
+  T r[L::NBASE] = {};   // (the items no kernel reads stay zero)
   record_all<K, T>(p, cst, [&](int i, T v) { r[i] = v; });
   constexpr int NSUB = 1 << K;
 #pragma unroll

@@ -149,7 +149,7 @@ struct SmemLayout {
   static constexpr int GPW = 32 / WSizes<K>::G;
   static constexpr size_t rec_off = sizeof(SlotState<K, T>) * kWarps * GPW;
   static constexpr size_t tab_off =
-      (rec_off + sizeof(typename WRec<T>::type) * v2::EvLayout<K>::NITEM + 15) / 16 * 16;
+      (rec_off + sizeof(typename WRec<T>::type) * v2::EvLayout<K>::NBASE + 15) / 16 * 16;
   static constexpr size_t bytes = kTabSmem<K> ? tab_off + sizeof(Tables) : tab_off;
 };
 
@@ -265,6 +265,18 @@ k_me_warp(const void* __restrict__ rec_any, int64_t nevt, const Tables* __restri
 #pragma unroll
     for (int len = 2; len < K; ++len) {
       for (int s = seq_start(K, len) + lane; s < seq_start(K, len + 1); s += G) {
+        if constexpr (!DF && L::NPAIR > 0) {
+          if (len == 2) {   // the pair's current from the FP32 record (FP64 arithmetic, record_j2)
+            const int msk = tab->seq_mask[s];
+            const int ga = __ffs(msk) - 1, gb = 31 - __clz(msk);
+            const int h = ((gc >> ga) & 1) | (((gc >> gb) & 1) << 1);
+            const float* it = static_cast<const float*>(rec_any) + (e / kPage) * L::NITEM * kPage + (e % kPage) +
+                              (L::J2 + (v2::pair_index(K, ga, gb) * 4 + h) * 8) * kPage;
+#pragma unroll
+            for (int m = 0; m < 4; ++m) S.J[m][s] = stw(cx<T>{__ldg(it + 2 * m * kPage), __ldg(it + (2 * m + 1) * kPage)});
+            continue;
+          }
+        }
         cx<T> acc[4] = {};
         current(tab->seq_nv3[s], tab->seq_v3[s], tab->seq_nv4[s], tab->seq_v4[s], acc);
         const T f = ld(L::GP + tab->seq_mask[s]);
@@ -600,7 +612,7 @@ k_me_warp(const void* __restrict__ rec_any, int64_t nevt, const Tables* __restri
     const int64_t e = blockIdx.x;   // one block per event: e < nevt
     if (skip && skip[e]) return;    // recomputed by another launch (the whole block: one event)
     const float* in = static_cast<const float*>(rec_any) + (e / kPage) * L::NITEM * kPage + (e % kPage);
-    for (int i = threadIdx.x; i < L::NITEM; i += blockDim.x) rs[i] = __ldg(in + i * kPage);
+    for (int i = threadIdx.x; i < L::NBASE; i += blockDim.x) rs[i] = __ldg(in + i * kPage);
     run_event(e);
   } else {
     const double* mom = static_cast<const double*>(rec_any);
