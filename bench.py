@@ -425,7 +425,7 @@ class Leg:
             K = self.ng + 2
             slot_kernel = ("k_me_gluonhel_occ<%d>" % K) if (K >= 4 or (K == 3 and shared)) else ("k_me_gluonhel<%d,double>" % K)
             kernel = ("k_event_prep + %s%s + k_hel_sum (one mg_sigmakin call)"
-                      % ("k_share_level (per sequence length) + " if shared else "", slot_kernel))
+                      % ("k_share_level (per sequence length) + k_prefix_level (per prefix length) + " if shared else "", slot_kernel))
             return fp64_roofline(amp + col, oracle_flops, nev, me_ms, p64, traffic, kernel)
         if precision == mg.MG_FP64_TCCOLOR:
             return time_roofline([("fp64", amp * nev, p64, src64),

@@ -78,9 +78,17 @@ void flop_model(const mg::Tables& t, const uint32_t* mask, bool fp32, bool share
     else
       per_slot += 2.0 * gamma_col * t.nseq;
   }
+  // shared (FP64): the quark-line prefixes of lengths 1 .. pref_levels once per helicity assignment of
+  // their gluons and top helicity per event (k_prefix_level), the longer ones in the slot's walk
+  const int plev = shared ? t.pref_levels : 0;
+  for (int m = 1; m <= plev; ++m) {
+    int orderings = 1;
+    for (int i = 0; i < m; ++i) orderings *= K - i;
+    shared_work += static_cast<double>((orderings << m) * 2) * (row_gamma * m + row_prop);
+  }
   double walk = 50.0 + 2.0 * 72.0;                                 // ubar, two quark currents
   for (int c = 0; c < t.ncol; ++c) {
-    for (int m = t.lcp[c] + 1; m < K; ++m) walk += row_gamma * m + row_prop;
+    for (int m = t.lcp[c] + 1; m < K; ++m) walk += m <= plev ? 0.0 : row_gamma * m + row_prop;
     walk += fp32 ? 2.0 * mdot + (K - 1) * (row_gamma + 2.0 * sdot)  // jamps of both antitop helicities
                  : 2.0 * (mdot + sdot * (K - 1));
   }
@@ -159,7 +167,7 @@ cudaError_t free_raw(void* p, bool host) {
 }
 
 int64_t share_chunk(int K, int64_t stride) {
-  const int64_t per_event = static_cast<int64_t>(share_items(K)) * 24;   // doubles
+  const int64_t per_event = share_doubles(K);   // doubles
   int64_t chunk = (int64_t(1) << 28) / per_event / kPage * kPage;       // 2^28 doubles = 2 GiB
   if (chunk < kPage) chunk = kPage;
   return chunk < stride ? chunk : stride;
@@ -202,7 +210,7 @@ mg_status ctx_reserve(mg_ctx* ctx, int64_t nevt, mg_precision precision) {
   if (s == MG_OK && (precision == MG_FP64 || precision == MG_FP64_TCCOLOR) && ctx->shape[precision].shared &&
       ctx->prm.wt == 0.0) {
     const int64_t sc = share_chunk(ctx->K, stride);
-    s = grow(&ctx->d_share, &ctx->share_cap, (sc < chunk ? sc : chunk) * share_items(ctx->K) * 24);
+    s = grow(&ctx->d_share, &ctx->share_cap, (sc < chunk ? sc : chunk) * share_doubles(ctx->K));
   }
   return s;
 }
@@ -632,7 +640,7 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
     if (shared) {
       const int64_t sc = mg::share_chunk(ctx->K, stride);
       if (sc < chunk) chunk = sc;
-      s = grow(&ctx->d_share, &ctx->share_cap, chunk * mg::share_items(ctx->K) * 24);
+      s = grow(&ctx->d_share, &ctx->share_cap, chunk * mg::share_doubles(ctx->K));
       if (s != MG_OK) return s;
     }
     if (ctx->jamp_cap < chunk * per_event) {
@@ -709,7 +717,7 @@ mg_status mg_sigmakin(mg_ctx* ctx, const double* mom_dev, int64_t nevt, mg_preci
       // FP64: the currents of fewer than all gluons once per helicity assignment of their gluons, then
       // the matrix elements reading them; in chunks of events that bound the scratch
       const int64_t chunk = mg::share_chunk(ctx->K, stride);
-      s = grow(&ctx->d_share, &ctx->share_cap, chunk * mg::share_items(ctx->K) * 24);
+      s = grow(&ctx->d_share, &ctx->share_cap, chunk * mg::share_doubles(ctx->K));
       if (s != MG_OK) return s;
       const int64_t nitem = mg::event_record_bytes(ctx->K, false) / 8;
       for (int64_t e0 = 0; e0 < nevt; e0 += chunk) {

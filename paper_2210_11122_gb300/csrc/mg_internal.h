@@ -57,6 +57,14 @@ struct Tables {
   // own gluons h (2^len(s) of them) is item share_base[s] + h; share_n items per event
   int16_t share_base[kMaxSeq];
   int share_n;
+  // quark-line prefixes shared the same way: the row spinor after the first m gluons of a colour ordering
+  // (m = 1 .. pref_levels), for every helicity assignment of those gluons and both top helicities.
+  // Level m's node (p, h, a) -- p = ordering / (K - m)!, h = the prefix gluons' helicities in ordering
+  // order (bit j: gluon perm[.][j]), a = top helicity -- is item pref_off[m] + ((p << m | h) << 1 | a)
+  // (8 doubles) after the share_n current items (24 doubles each); share_stride doubles per event.
+  int pref_levels;
+  int pref_off[kMaxGluons];
+  int share_stride;
 };
 
 // helicity bits of the gluons in mask, packed (bit g of gc -> the rank of g among mask's bits), and back

@@ -73,6 +73,8 @@ cudaError_t launch_me_gluonhel(int K, bool fp32, bool per_hel, const double* mom
 // (layout in mg_me_kernel.cuh), computed from the FP64 records of nevt events by K - 1 launches (one per
 // sequence length); launch_me_gluonhel(..., share) then reads them instead of computing them per slot.
 int share_items(int K);
+// doubles per event of the shared buffer: the current items, then the quark-line prefixes (mg_internal.h)
+int64_t share_doubles(int K);
 cudaError_t launch_share(int K, const void* rec, int64_t nevt, const Tables* tab, const MeConst& cst, double* share,
                          cudaStream_t st);
 int64_t event_record_bytes(int K, bool fp32);

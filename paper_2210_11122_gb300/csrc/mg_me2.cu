@@ -205,7 +205,30 @@ static cudaError_t launch_share_k(const void* rec, int64_t nevt, const Tables* t
     if (e != cudaSuccess) return e;
     s0 += count;
   }
+  // then the quark-line prefixes, level by level (each reads the currents and the lower levels)
+  const int levels = K - 1 < 3 ? K - 1 : 3;
+  for (int m = 1; m <= levels; ++m) {
+    int orderings = 1;
+    for (int i = 0; i < m; ++i) orderings *= K - i;
+    const int64_t threads = nevt * (static_cast<int64_t>(orderings) << (m + 1));
+    if (threads > 0)
+      { v2::k_prefix_level<K><<<static_cast<unsigned>((threads + 127) / 128), 128, 0, st>>>(
+          static_cast<const double*>(rec), nevt, tab, m, share); mg::note_launch(); }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   return cudaSuccess;
+}
+
+int64_t share_doubles(int K) {
+  int64_t nodes = 0;
+  const int levels = K - 1 < 3 ? K - 1 : 3;
+  for (int m = 1; m <= levels; ++m) {
+    int orderings = 1;
+    for (int i = 0; i < m; ++i) orderings *= K - i;
+    nodes += static_cast<int64_t>(orderings << m) * 2;
+  }
+  return static_cast<int64_t>(share_items(K)) * 24 + nodes * 8;
 }
 
 int share_items(int K) {

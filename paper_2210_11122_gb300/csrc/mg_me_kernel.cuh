@@ -11,6 +11,8 @@
 namespace mg {
 namespace v2 {
 
+__device__ constexpr int kFactorial[6] = {1, 1, 2, 6, 24, 120};
+
 // JOUT: instead of colour sums, write the jamps of every helicity of the slot as FP32 complex
 // numbers to jout[((e * 4 * 2^K) + slot * 4 + 2 * top + antitop) * ncol + sigma] (zeros for helicities
 // outside the mask), for the tensor-core colour sum.
@@ -85,7 +87,7 @@ __device__ __forceinline__ void me_slot(const double* __restrict__ mom, const T*
   constexpr bool kTableX = std::is_same<T, double>::value;
   cx<T> X[kTableX ? 2 : 1][kTableX ? NSEQ : 1][4];
   if constexpr (SHARED) {
-    const double* sh = share + static_cast<int64_t>(e) * tab->share_n * 24;
+    const double* sh = share + static_cast<int64_t>(e) * tab->share_stride;
     for (int s = 0; s < NSEQ; ++s) {
       const double* it = sh + (tab->share_base[s] + pext_bits(gc, tab->seq_mask[s])) * 24;
 #pragma unroll
@@ -180,6 +182,18 @@ __device__ __forceinline__ void me_slot(const double* __restrict__ mom, const T*
     for (int c = 0; c < NCOL; ++c) {
       const int l = tab->lcp[c];
       for (int m = l + 1; m < K; ++m) {
+        if constexpr (SHARED) {
+          if (m <= tab->pref_levels) {   // the prefix spinor from k_prefix_level
+            int hm = 0;
+            for (int j = 0; j < m; ++j) hm |= ((gc >> tab->perm[c][j]) & 1) << j;
+            const int node = (((c / kFactorial[K - m]) << m | hm) << 1) | a;
+            const double* it = share + static_cast<int64_t>(e) * tab->share_stride + tab->share_n * 24 +
+                               (tab->pref_off[m] + node) * 8;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) stk[m][q] = {it[2 * q], it[2 * q + 1]};
+            continue;
+          }
+        }
         cx<T> acc[4] = {};
         for (int j = 0; j < m; ++j) {
           const int16_t r = tab->sub[c][j][m];
@@ -338,7 +352,7 @@ k_share_level(const double* __restrict__ rec, int64_t nevt, const Tables* __rest
   const int gc = pdep_bits(h, msk);
   const double* in = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
   auto ld = [&](int item) -> double { return __ldg(in + item * kPage); };
-  double* sh = share + e * tab->share_n * 24;
+  double* sh = share + e * tab->share_stride;
   auto getJ = [&](int slot, cx<double>* J) {
     const double* it = sh + (tab->share_base[slot] + pext_bits(gc, tab->seq_mask[slot])) * 24;
 #pragma unroll
@@ -398,6 +412,62 @@ k_share_level(const double* __restrict__ rec, int64_t nevt, const Tables* __rest
       out[8 + 8 * b + 2 * m] = X[m].r;
       out[8 + 8 * b + 2 * m + 1] = X[m].i;
     }
+  }
+}
+
+// Quark-line prefixes shared between gluon-helicity combinations (FP64): the row spinor after the first
+// `level` gluons of an ordering, for every helicity assignment of those gluons and both top helicities,
+// from the top spinor, the lower levels' nodes and the shared currents, by the same operations as the
+// slot kernel's walk (so the results are bit-identical).  One thread per (event, node of the level);
+// levels run in order 1 .. tab->pref_levels after the current levels.
+template <int K>
+__global__ void __launch_bounds__(128)
+k_prefix_level(const double* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab, int level,
+               double* __restrict__ share) {
+  using L = EvLayout<K>;
+  const int m = level;
+  const int per_ev = (kFactorial[K] / kFactorial[K - m]) << (m + 1);
+  const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= nevt * per_ev) return;
+  const int64_t e = t / per_ev;
+  const int node = static_cast<int>(t - e * per_ev);
+  const int a = node & 1, h = (node >> 1) & ((1 << m) - 1), p = node >> (m + 1);
+  const int c0 = p * kFactorial[K - m];   // the first ordering with this prefix
+  const double* in = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
+  double* sh = share + e * tab->share_stride;
+  double* pref = sh + tab->share_n * 24;
+  int gcp = 0;   // the prefix gluons' helicity bits, by gluon
+  for (int j = 0; j < m; ++j) gcp |= ((h >> j) & 1) << tab->perm[c0][j];
+  cx<double> stk[K][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    stk[0][q] = {__ldg(in + (L::UB + (a * 4 + q) * 2) * kPage), __ldg(in + (L::UB + (a * 4 + q) * 2 + 1) * kPage)};
+  for (int j = 1; j < m; ++j) {
+    const int nj = (((c0 / kFactorial[K - j]) << j | (h & ((1 << j) - 1))) << 1) | a;
+    const double* it = pref + (tab->pref_off[j] + nj) * 8;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) stk[j][q] = {it[2 * q], it[2 * q + 1]};
+  }
+  cx<double> acc[4] = {};
+  for (int j = 0; j < m; ++j) {
+    const int16_t r = tab->sub[c0][j][m];
+    const double* it = sh + (tab->share_base[rslot(r)] + pext_bits(gcp, tab->seq_mask[rslot(r)])) * 24;
+    cx<double> Jr[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) Jr[q] = {it[2 * q], it[2 * q + 1]};
+    row_gamma_acc(acc, stk[j], Jr, rneg(r));
+  }
+  double qc[5];
+  const int pm = tab->prefix_mask[c0][m];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) qc[i] = __ldg(in + (L::QC + 5 * pm + i) * kPage);
+  cx<double> o[4];
+  row_prop(acc, qc, o);
+  double* out = pref + (tab->pref_off[m] + node) * 8;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    out[2 * q] = o[q].r;
+    out[2 * q + 1] = o[q].i;
   }
 }
 

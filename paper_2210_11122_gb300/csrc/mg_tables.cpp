@@ -61,6 +61,16 @@ void build_tables(int K, Tables& t) {
     t.share_base[i] = static_cast<int16_t>(t.share_n);
     t.share_n += 1 << seqs[i].size();
   }
+  t.pref_levels = K - 1 < 3 ? K - 1 : 3;
+  int nodes = 0;
+  for (int m = 0; m < kMaxGluons; ++m) t.pref_off[m] = 0;
+  for (int m = 1; m <= t.pref_levels; ++m) {
+    int orderings = 1;   // ordered prefixes of m gluons: K! / (K - m)!
+    for (int i = 0; i < m; ++i) orderings *= K - i;
+    t.pref_off[m] = nodes;
+    nodes += (orderings << m) * 2;
+  }
+  t.share_stride = t.share_n * 24 + nodes * 8;
   auto ref = [&](const std::vector<int>& s) -> int16_t {
     if (s.size() == 1) return pack(s[0], false);
     if (s.front() < s.back()) return pack(slot_of.at(s), false);

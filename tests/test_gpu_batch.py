@@ -125,8 +125,8 @@ def test_graph_batch_fp32_modes(env, precision):
 
 def test_kernel_launch_counter(env):
     # mg_kernel_launches brackets the kernels of the calls between two reads: an FP64 gg->ttg call is
-    # the per-event record, the matrix elements and the helicity sum, plus one pass per sequence length
-    # (1 and 2 gluons) with the shared currents
+    # the per-event record, the matrix elements and the helicity sum, plus, with shared currents, one pass
+    # per sequence length (1 and 2 gluons) and one per quark-line prefix length (1 and 2 gluons)
     torch, mg = env
     n = 4096
     with mg.Context("ggttg") as ctx:
@@ -143,4 +143,4 @@ def test_kernel_launch_counter(env):
             ctx.sigmakin(mom, n, me, mg.MG_FP64)
             counts[flags] = mg.kernel_launches() - c0
         torch.cuda.synchronize()
-    assert list(counts.values()) == [5, 3]
+    assert list(counts.values()) == [7, 3]
