@@ -713,8 +713,6 @@ def batch_leg(mg, torch, stream, flush, nreq, reps=3):
         jobs = []
         for r in range(nreq):
             c = mg.Context(int(proc[r]), mt=MT, alphas=ALPHAS)
-            if persistent:
-                c.set_launch_shape(mg.MG_FP64, 128, 0, 7)
             n = int(nevt[r])
             mom = torch.zeros(c.mom_count(n), dtype=torch.float64, device="cuda")
             me = torch.zeros(n, dtype=torch.float64, device="cuda")

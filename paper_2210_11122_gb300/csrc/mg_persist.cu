@@ -7,8 +7,10 @@
 // (job, gluon-helicity slot, 128-event tile) triples, the jobs ordered by falling cost per tile (more
 // gluons first, so the longest tiles start first); each 128-thread block takes the next tile from an
 // atomic counter until the queue is empty, and runs the same per-thread FP64 work as k_me_gluonhel (the
-// currents of each slot built in the thread, the per-event record from k_event_prep).  The results are
-// bit-identical to mg_sigmakin(MG_FP64) with the unshared-current launch shape.
+// per-event record from k_event_prep; the currents and quark-line prefixes shared between a job's
+// gluon-helicity combinations from its k_share_level / k_prefix_level passes where its context's FP64
+// shape shares them and the job's buffer fits 2 GiB, else built in the thread).  The results are
+// bit-identical to mg_sigmakin(MG_FP64), with or without the shared currents.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -34,6 +36,7 @@ struct PJob {
   const int* nslot;
   const uint32_t* mask;
   const double* ctri;
+  const double* share;      // the job's shared currents and prefixes (k_share_level), or null: none
   double* part;             // part[slot * stride + e]
   int64_t nevt, stride, tile0;
   int K, ntile_ev;
@@ -46,7 +49,7 @@ struct PBatch {
   PJob job[kMaxJobs];
 };
 
-__global__ void __launch_bounds__(kMeThreads) k_me_persistent(const __grid_constant__ PBatch b,
+__global__ void __launch_bounds__(kMeThreads, 3) k_me_persistent(const __grid_constant__ PBatch b,
                                                               unsigned long long* __restrict__ next) {
   __shared__ long long s_tile;
   for (;;) {
@@ -67,6 +70,27 @@ __global__ void __launch_bounds__(kMeThreads) k_me_persistent(const __grid_const
     const int64_t e = (t - static_cast<int64_t>(slot) * J.ntile_ev) * kTileEv + threadIdx.x;
     if (e >= J.nevt || slot >= *J.nslot) continue;
     const int gc = J.gslots[slot];
+    if (J.share) {
+      switch (J.K) {
+        case 2:
+          v2::me_slot<2, double, false, true, false, true>(nullptr, J.rec, e, slot, gc, J.tab, J.mask, J.ctri, J.cst,
+                                                           J.part, J.stride, nullptr, 0, J.share, nullptr);
+          break;
+        case 3:
+          v2::me_slot<3, double, false, true, false, true>(nullptr, J.rec, e, slot, gc, J.tab, J.mask, J.ctri, J.cst,
+                                                           J.part, J.stride, nullptr, 0, J.share, nullptr);
+          break;
+        case 4:
+          v2::me_slot<4, double, false, true, false, true>(nullptr, J.rec, e, slot, gc, J.tab, J.mask, J.ctri, J.cst,
+                                                           J.part, J.stride, nullptr, 0, J.share, nullptr);
+          break;
+        default:
+          v2::me_slot<5, double, false, true, false, true>(nullptr, J.rec, e, slot, gc, J.tab, J.mask, J.ctri, J.cst,
+                                                           J.part, J.stride, nullptr, 0, J.share, nullptr);
+          break;
+      }
+      continue;
+    }
     switch (J.K) {
       case 2:
         v2::me_slot<2, double, false, true, false>(nullptr, J.rec, e, slot, gc, J.tab, J.mask, J.ctri, J.cst, J.part,
@@ -145,7 +169,18 @@ extern "C" mg_status mg_sigmakin_batch(const mg_batch_job* jobs, int njobs, void
     cst.wt = c->prm.wt;
     cst.colour_scale = cst.gs * cst.gs / static_cast<double>(c->colour_den);
     if (mg::launch_event_prep(c->K, false, j.mom_dev, j.nevt, cst, c->d_prep, st) != cudaSuccess) { s = MG_ECUDA; break; }
+    // the job's currents and quark-line prefixes shared between its gluon-helicity combinations, where its
+    // context's FP64 shape asks for them and the whole job's buffer stays within 2 GiB
+    const double* share = nullptr;
+    const int64_t sdoubles = stride * mg::share_doubles(c->K);
+    if (c->shape[MG_FP64].shared && sdoubles <= (int64_t(1) << 28)) {
+      s = grow_d(&c->d_share, &c->share_cap, sdoubles);
+      if (s != MG_OK) break;
+      if (mg::launch_share(c->K, c->d_prep, j.nevt, c->d_tab, cst, c->d_share, st) != cudaSuccess) { s = MG_ECUDA; break; }
+      share = c->d_share;
+    }
     mg::pers::PJob& p = batch->job[batch->njobs++];
+    p.share = share;
     p.rec = c->d_prep;
     p.tab = c->d_tab;
     p.gslots = c->d_gslots;
