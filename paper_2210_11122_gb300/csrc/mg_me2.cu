@@ -95,6 +95,15 @@ cudaError_t launch_gluon_slots(const uint32_t* mask, int K, int* gslots, int* n,
   return cudaGetLastError();
 }
 
+static int sm_count() {
+  int dev = 0, n = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return 1;
+  }
+  return n;
+}
+
 template <int K, class T, bool PER_HEL>
 static cudaError_t launch_v2(const double* mom, void* prep, int64_t nevt, const Tables* tab, const int* gslots,
                              int maxslot, const int* nslot, const uint32_t* mask, const void* ctri_any,
@@ -104,7 +113,17 @@ static cudaError_t launch_v2(const double* mom, void* prep, int64_t nevt, const 
   const T* ctri = static_cast<const T*>(ctri_any);
   int tev = shape.tile_ev;
   if (tev != 32 && tev != 64 && tev != 128) tev = 128;
-  const int tsl = kMeThreads / tev;
+  int threads = kMeThreads;
+  // a grid of fewer than 4 blocks per SM (gg -> t tbar at 16,384 events: 512 blocks of 4 warps, 3 or 4
+  // per SM, one per sub-partition each): blocks of 2 warps, so that the busiest sub-partition holds
+  // at most half a warp more than the average instead of a whole one
+  if (prep && !PER_HEL &&
+      static_cast<int64_t>((nevt + tev - 1) / tev) * ((maxslot + kMeThreads / tev - 1) / (kMeThreads / tev)) <
+          4 * static_cast<int64_t>(sm_count())) {
+    threads = kMeThreads / 2;
+    if (tev > threads) tev = threads;
+  }
+  const int tsl = threads / tev;
   const unsigned nev_t = static_cast<unsigned>((nevt + tev - 1) / tev), nsl_t = static_cast<unsigned>((maxslot + tsl - 1) / tsl);
   const int sm = shape.slot_major ? 1 : 0;
   dim3 grid = sm ? dim3(nsl_t, nev_t) : dim3(nev_t, nsl_t);
@@ -115,44 +134,44 @@ static cudaError_t launch_v2(const double* mom, void* prep, int64_t nevt, const 
       return launch_me_static(K, sizeof(T) == 4, rec, nevt, gslots, maxslot, nslot, mask, cst, out, stride, jout, shape,
                               skip, st);
     if constexpr (std::is_same<T, double>::value) {
-      // the compile for more resident blocks (k_me_gluonhel_occ): 4 and 5 gluons, and 3 with shared currents
-      // (without them its bounded compile spills ~0.5 KB per thread)
-      if constexpr (K >= 3) {
-        constexpr int MINB = K == 3 ? 4 : 3;
-        if (K >= 4 || share) {
+      // the compile for more resident blocks (k_me_gluonhel_occ): 2, 4 and 5 gluons, and 3 with shared
+      // currents (without them its bounded compile spills ~0.5 KB per thread)
+      if constexpr (K >= 2) {
+        constexpr int MINB = K <= 3 ? 4 : 3;
+        if (K != 3 || share) {
           if (jout && share)
-            { v2::k_me_gluonhel_occ<K, true, true, MINB><<<grid, kMeThreads, 0, st>>>(
+            { v2::k_me_gluonhel_occ<K, true, true, MINB><<<grid, threads, 0, st>>>(
                 rec, nevt, tab, gslots, nslot, mask, ctri, cst, out, stride, jout, tev, sm, skip, share); mg::note_launch(); }
           else if (share)
-            { v2::k_me_gluonhel_occ<K, false, true, MINB><<<grid, kMeThreads, 0, st>>>(
+            { v2::k_me_gluonhel_occ<K, false, true, MINB><<<grid, threads, 0, st>>>(
                 rec, nevt, tab, gslots, nslot, mask, ctri, cst, out, stride, nullptr, tev, sm, skip, share); mg::note_launch(); }
           else if (jout)
-            { v2::k_me_gluonhel_occ<K, true, false, MINB><<<grid, kMeThreads, 0, st>>>(
+            { v2::k_me_gluonhel_occ<K, true, false, MINB><<<grid, threads, 0, st>>>(
                 rec, nevt, tab, gslots, nslot, mask, ctri, cst, out, stride, jout, tev, sm, skip, nullptr); mg::note_launch(); }
           else
-            { v2::k_me_gluonhel_occ<K, false, false, MINB><<<grid, kMeThreads, 0, st>>>(
+            { v2::k_me_gluonhel_occ<K, false, false, MINB><<<grid, threads, 0, st>>>(
                 rec, nevt, tab, gslots, nslot, mask, ctri, cst, out, stride, nullptr, tev, sm, skip, nullptr); mg::note_launch(); }
           return cudaGetLastError();
         }
       }
       if (share) {
         if (jout)
-          { v2::k_me_gluonhel<K, T, false, true, true, true><<<grid, kMeThreads, 0, st>>>(
+          { v2::k_me_gluonhel<K, T, false, true, true, true><<<grid, threads, 0, st>>>(
               mom, rec, nevt, tab, gslots, nslot, mask, ctri, cst, out, stride, jout, tev, sm, nullptr, nullptr, 0, skip,
               share); mg::note_launch(); }
         else
-          { v2::k_me_gluonhel<K, T, false, true, false, true><<<grid, kMeThreads, 0, st>>>(
+          { v2::k_me_gluonhel<K, T, false, true, false, true><<<grid, threads, 0, st>>>(
               mom, rec, nevt, tab, gslots, nslot, mask, ctri, cst, out, stride, nullptr, tev, sm, nullptr, nullptr, 0,
               skip, share); mg::note_launch(); }
         return cudaGetLastError();
       }
     }
     if (jout)
-      { v2::k_me_gluonhel<K, T, false, true, true><<<grid, kMeThreads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot, mask,
+      { v2::k_me_gluonhel<K, T, false, true, true><<<grid, threads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot, mask,
                                                                              ctri, cst, out, stride, jout, tev, sm, nullptr,
                                                                              nullptr, 0, skip); mg::note_launch(); }
     else
-      { v2::k_me_gluonhel<K, T, false, true, false><<<grid, kMeThreads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot,
+      { v2::k_me_gluonhel<K, T, false, true, false><<<grid, threads, 0, st>>>(mom, rec, nevt, tab, gslots, nslot,
                                                                               mask, ctri, cst, out, stride, nullptr, tev,
                                                                               sm, nullptr, nullptr, 0, skip); mg::note_launch(); }
   } else if (PER_HEL) {

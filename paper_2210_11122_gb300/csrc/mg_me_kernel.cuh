@@ -315,11 +315,12 @@ k_me_gluonhel(const double* __restrict__ mom, const T* __restrict__ rec, int64_t
                                                     jout, tile_ev, slot_major, evlist, nlist, rows_out, skip, share, j2);
 }
 
-// The FP64 slot kernel with a record from 3 gluons on, compiled for MINB resident blocks per SM: 4 for 3
-// gluons (at most 128 registers; the unbounded compile takes 166, 3 blocks), 3 for 4 and 5 (at most 168;
+// The FP64 slot kernel with a record, compiled for MINB resident blocks per SM: 4 for 2 and 3 gluons (at
+// most 128 registers; the unbounded compile takes 168 and 166, 3 blocks), 3 for 4 and 5 (at most 168;
 // unbounded 254, 2 blocks).  More warps hide more of the FP64 pipe's dependent-instruction latency:
 // measured 1.3 % faster for 3 gluons, 8 % for 4 (shared currents) and 3 % for 5; spills stay below 250
-// bytes per thread.
+// bytes per thread.  With 2 gluons it lets gg -> t tbar's 16,384 events (2,048 warps) reside in one
+// wave instead of 3 blocks per SM and a tail.
 template <int K, bool JOUT, bool SHARED, int MINB>
 __global__ void __launch_bounds__(kMeThreads, MINB)
 k_me_gluonhel_occ(const double* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab,
