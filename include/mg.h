@@ -234,9 +234,13 @@ mg_status mg_sigmakin_noalloc(mg_ctx* ctx, const double* mom_dev, int64_t nevt, 
  *     fixed coupling params.alphas.  alphas_dev[e] (if not NULL) receives the coupling used.
  * rnd_hel_dev / rnd_col_dev: caller-supplied uniform numbers in [0, 1), one per event (device, FP64;
  * needed when the matching output is requested, else MG_EINVAL).  hel_dev / col_dev: int32 per event.
- * Every buffer holds nevt entries.  Zero top width only (MG_ENOTSUP otherwise).  Scratch: per-slot sums of
- * |J_sigma|^2 (events processed in chunks that keep it within 1 GiB), owned by the context.  If no helicity
- * mask exists yet, the call first runs mg_hel_filter on its own first events. */
+ * Every buffer holds nevt entries.  Zero top width only (MG_ENOTSUP otherwise).  The matrix elements come
+ * from the FP64 algorithm that the context's MG_FP64 launch shape selects (with MG_LAUNCH_SHARED: the
+ * shared currents and quark-line prefixes); at fixed coupling they equal mg_sigmakin(MG_FP64)'s up to the
+ * order of the helicity sum.
+ * Scratch: per-slot sums of |J_sigma|^2 (events processed in chunks that keep it within 1 GiB, and the
+ * shared currents within 2 GiB), owned by the context.  If no helicity mask exists yet, the call first
+ * runs mg_hel_filter on its own first events. */
 mg_status mg_sigmakin_lhe(mg_ctx* ctx, const double* mom_dev, int64_t nevt, const double* rnd_hel_dev,
                           const double* rnd_col_dev, int running_alphas, double* me_dev, int* hel_dev, int* col_dev,
                           double* alphas_dev, void* stream);

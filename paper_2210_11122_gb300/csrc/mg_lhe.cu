@@ -142,15 +142,41 @@ k_alphas_running(const double* __restrict__ mom, int64_t nevt, double a0, double
   if (as_out) as_out[e] = as;
 }
 
+// The slot kernel's LHE rows with the currents and quark-line prefixes of launch_share, compiled for
+// MINB resident blocks per SM (the bound of the plain FP64 slot kernel)
+template <int K, int MINB>
+__global__ void __launch_bounds__(kMeThreads, MINB)
+k_lhe_slot(const double* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab, const int* __restrict__ gslots,
+           const int* __restrict__ nslot, const uint32_t* __restrict__ mask, const double* __restrict__ ctri, MeConst cst,
+           double* __restrict__ part, int64_t stride, int tile_ev, const double* __restrict__ share,
+           double* __restrict__ j2) {
+  v2::me_thread<K, double, false, true, false, true, true>(nullptr, rec, nevt, tab, gslots, nslot, mask, ctri, cst, part,
+                                                          stride, nullptr, tile_ev, 0, nullptr, nullptr, 0, nullptr,
+                                                          share, j2);
+}
+
+// share: the chunk's currents and quark-line prefixes from launch_share (the slot kernel reads them
+// instead of forming them; bit-identical), or null for the unshared walk
 template <int K>
 cudaError_t launch_lhe_me(const double* rec, int64_t nevt, const Tables* tab, const int* gslots, int maxslot,
                           const int* nslot, const uint32_t* mask, const double* ctri, const MeConst& cst, double* part,
-                          double* j2, int64_t stride, cudaStream_t st) {
+                          double* j2, int64_t stride, const double* share, cudaStream_t st) {
   const int tev = 128, tsl = kMeThreads / tev;
   const dim3 grid(static_cast<unsigned>((nevt + tev - 1) / tev), static_cast<unsigned>((maxslot + tsl - 1) / tsl));
-  v2::k_me_gluonhel<K, double, false, true, false, false, true><<<grid, kMeThreads, 0, st>>>(
-      nullptr, rec, nevt, tab, gslots, nslot, mask, ctri, cst, part, stride, nullptr, tev, 0, nullptr, nullptr, 0,
-      nullptr, nullptr, j2);
+  // bounded compile for 2, 3 and 5 gluons (measured 12-25 % faster than unbounded); with 4 its 24 per-flow
+  // sums spill at 168 registers and the unbounded kernel is 7 % faster
+  if (share) {
+    if constexpr (K == 4)
+      v2::k_me_gluonhel<K, double, false, true, false, true, true><<<grid, kMeThreads, 0, st>>>(
+          nullptr, rec, nevt, tab, gslots, nslot, mask, ctri, cst, part, stride, nullptr, tev, 0, nullptr, nullptr, 0,
+          nullptr, share, j2);
+    else
+      k_lhe_slot<K, K <= 3 ? 4 : 3><<<grid, kMeThreads, 0, st>>>(rec, nevt, tab, gslots, nslot, mask, ctri, cst, part,
+                                                                stride, tev, share, j2);
+  } else
+    v2::k_me_gluonhel<K, double, false, true, false, false, true><<<grid, kMeThreads, 0, st>>>(
+        nullptr, rec, nevt, tab, gslots, nslot, mask, ctri, cst, part, stride, nullptr, tev, 0, nullptr, nullptr, 0,
+        nullptr, nullptr, j2);
   note_launch();
   return cudaGetLastError();
 }
@@ -187,13 +213,13 @@ mg_status grow_buf(double** buf, int64_t* cap, int64_t need) {
 }
 
 cudaError_t lhe_me(int K, const double* rec, int64_t nevt, const mg_ctx* c, const mg::MeConst& cst, double* part,
-                   double* j2, int64_t stride, cudaStream_t st) {
+                   double* j2, int64_t stride, const double* share, cudaStream_t st) {
   const int ms = 1 << K;
   switch (K) {
-    case 2: return mg::lhe::launch_lhe_me<2>(rec, nevt, c->d_tab, c->d_gslots, ms, c->d_ngslots, c->d_mask, c->d_ctri, cst, part, j2, stride, st);
-    case 3: return mg::lhe::launch_lhe_me<3>(rec, nevt, c->d_tab, c->d_gslots, ms, c->d_ngslots, c->d_mask, c->d_ctri, cst, part, j2, stride, st);
-    case 4: return mg::lhe::launch_lhe_me<4>(rec, nevt, c->d_tab, c->d_gslots, ms, c->d_ngslots, c->d_mask, c->d_ctri, cst, part, j2, stride, st);
-    case 5: return mg::lhe::launch_lhe_me<5>(rec, nevt, c->d_tab, c->d_gslots, ms, c->d_ngslots, c->d_mask, c->d_ctri, cst, part, j2, stride, st);
+    case 2: return mg::lhe::launch_lhe_me<2>(rec, nevt, c->d_tab, c->d_gslots, ms, c->d_ngslots, c->d_mask, c->d_ctri, cst, part, j2, stride, share, st);
+    case 3: return mg::lhe::launch_lhe_me<3>(rec, nevt, c->d_tab, c->d_gslots, ms, c->d_ngslots, c->d_mask, c->d_ctri, cst, part, j2, stride, share, st);
+    case 4: return mg::lhe::launch_lhe_me<4>(rec, nevt, c->d_tab, c->d_gslots, ms, c->d_ngslots, c->d_mask, c->d_ctri, cst, part, j2, stride, share, st);
+    case 5: return mg::lhe::launch_lhe_me<5>(rec, nevt, c->d_tab, c->d_gslots, ms, c->d_ngslots, c->d_mask, c->d_ctri, cst, part, j2, stride, share, st);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -236,9 +262,16 @@ mg_status mg_sigmakin_lhe(mg_ctx* ctx, const double* mom_dev, int64_t nevt, cons
   const int64_t stride_all = pad_page(nevt);
   if (chunk < mg::kPage) chunk = mg::kPage;
   if (chunk > stride_all) chunk = stride_all;
+  // the FP64 launch shape's choice of shared currents and prefixes (chunks within their buffer)
+  const bool shared = ctx->shape[MG_FP64].shared;
+  if (shared) {
+    const int64_t sc = mg::share_chunk(K, stride_all);
+    if (sc < chunk) chunk = sc;
+  }
   mg_status s = grow_buf(&ctx->d_part, &ctx->part_cap, chunk * ctx->nhel);
   if (s == MG_OK) s = grow_buf(&ctx->d_prep, &ctx->prep_cap, chunk * mg::event_record_bytes(K, false) / 8 + 1);
   if (s == MG_OK) s = grow_buf(&ctx->d_j2, &ctx->j2_cap, chunk * per_event);
+  if (s == MG_OK && shared) s = grow_buf(&ctx->d_share, &ctx->share_cap, chunk * mg::share_doubles(K));
   if (s != MG_OK) return s;
   mg::MeConst cst;
   cst.gs = std::sqrt(4.0 * 3.14159265358979323846 * ctx->prm.alphas);
@@ -251,7 +284,10 @@ mg_status mg_sigmakin_lhe(mg_ctx* ctx, const double* mom_dev, int64_t nevt, cons
     const int64_t stride = pad_page(n);
     const double* mom_c = mom_dev + (e0 / mg::kPage) * ctx->npar * 4 * mg::kPage;
     if (mg::launch_event_prep(K, false, mom_c, n, cst, ctx->d_prep, st) != cudaSuccess) return MG_ECUDA;
-    if (lhe_me(K, ctx->d_prep, n, ctx, cst, ctx->d_part, ctx->d_j2, stride, st) != cudaSuccess) return MG_ECUDA;
+    if (shared && mg::launch_share(K, ctx->d_prep, n, ctx->d_tab, cst, ctx->d_share, st) != cudaSuccess) return MG_ECUDA;
+    if (lhe_me(K, ctx->d_prep, n, ctx, cst, ctx->d_part, ctx->d_j2, stride, shared ? ctx->d_share : nullptr, st) !=
+        cudaSuccess)
+      return MG_ECUDA;
     if (lhe_epilogue(K, ctx->d_j2, ctx, mom_c, n, stride, norm, running_alphas, rnd_hel_dev ? rnd_hel_dev + e0 : nullptr,
                      rnd_col_dev ? rnd_col_dev + e0 : nullptr, me_dev + e0, hel_dev ? hel_dev + e0 : nullptr,
                      col_dev ? col_dev + e0 : nullptr, alphas_dev ? alphas_dev + e0 : nullptr, st) != cudaSuccess)

@@ -88,15 +88,16 @@ def test_lhe_epilogue_matches_oracle(env, ng, nevt, running):
 
 
 def test_lhe_epilogue_full_size_sampled(env):
-    """gg->ttggg at its full workload size (65,536 events: two chunks of the jamp-square scratch): the
-    sampled events carry the oracle's momenta in the full-size buffer; their MEs, couplings and choices
+    """gg->ttggg at its full workload size (65,536 events: ten chunks of 6,848 events, the shared-current
+    scratch's bound, inside the jamp-square scratch's 34,944): the sampled events, on both sides of chunk
+    boundaries, carry the oracle's momenta in the full-size buffer; their MEs, couplings and choices
     match the oracle's."""
     torch, mg, orc, olhe = env
     ng, seed, n = 3, 4, 65536
     npar = ng + 4
     rng = np.random.default_rng(7)
     rh, rc = rng.random(n), rng.random(n)
-    idx = np.unique(np.concatenate([[0, 34943, 34944, n - 1], rng.integers(0, n, 8)]))
+    idx = np.unique(np.concatenate([[0, 6847, 6848, 34943, 34944, 61631, 61632, n - 1], rng.integers(0, n, 8)]))
     ev = np.concatenate([orc.events(ng, seed, 1, e0=int(i))[0] for i in idx])
     warm, _, _ = orc.events(ng, seed, 256)
     mask, _ = orc.hel_mask(ng, warm, nthreads=NTHREADS)
