@@ -153,6 +153,11 @@ struct SmemLayout {
   static constexpr size_t bytes = kTabSmem<K> ? tab_off + sizeof(Tables) : tab_off;
 };
 
+// 4 resident blocks per SM for FP32 amplitudes: each block's shared memory plus the 1 KB the hardware
+// reserves per block within the SM's 228 KB
+static_assert(SmemLayout<4>::bytes + 1024 <= 233472 / 4 && SmemLayout<5>::bytes + 1024 <= 233472 / 4,
+              "FP32 lane-group kernel: shared memory for 4 blocks per SM");
+
 // T = float: the FP32-amplitude kernel, one block per event (blockIdx.x), record from k_event_prep.
 // T = dd::df: the recomputation of the flagged events (evlist[0 .. *nlist)) with double-float amplitudes:
 // each block walks the list with a stride of gridDim.x, computes the event's FP64 record in shared memory
