@@ -61,7 +61,9 @@ struct Tables {
   // (m = 1 .. pref_levels), for every helicity assignment of those gluons and both top helicities.
   // Level m's node (p, h, a) -- p = ordering / (K - m)!, h = the prefix gluons' helicities in ordering
   // order (bit j: gluon perm[.][j]), a = top helicity -- is item pref_off[m] + ((p << m | h) << 1 | a)
-  // (8 doubles) after the share_n current items (24 doubles each); share_stride doubles per event.
+  // (8 doubles) after the share_n current items (24 doubles each); share_stride doubles per event,
+  // interleaved by page of 32 events like the per-event record (double d of event e at
+  // (e / 32) * share_stride * 32 + d * 32 + e % 32).
   int pref_levels;
   int pref_off[kMaxGluons];
   int share_stride;

@@ -13,13 +13,22 @@ namespace v2 {
 
 __device__ constexpr int kFactorial[6] = {1, 1, 2, 6, 24, 120};
 
+// The shared currents and quark-line prefixes of event e (FP64, share_stride doubles per event) are
+// interleaved by page like the record: double d of the event sits at share_event(...)[d * kPage], so
+// the 32 events of a warp read or write one 256-byte line per double
+template <class P>
+__device__ __forceinline__ P* share_event(P* share, int64_t e, int stride) {
+  return share + (e / kPage) * static_cast<int64_t>(stride) * kPage + (e % kPage);
+}
+
 // JOUT: instead of colour sums, write the jamps of every helicity of the slot as FP32 complex
 // numbers to jout[((e * 4 * 2^K) + slot * 4 + 2 * top + antitop) * ncol + sigma] (zeros for helicities
 // outside the mask), for the tensor-core colour sum.
 // SHARED (FP64 with a per-event record): the gluon currents of fewer than all gluons and their (gamma.J) v
-// are not computed here but read from share, where k_share_level left them once per helicity
-// assignment of their own gluons (item tab->share_base[s] + helicity bits of s's gluons, 24 doubles:
-// J, then (gamma.J) v for both antitop helicities).
+// are not computed here but read from share where they are used (not copied into the thread's local
+// memory), where k_share_level left them once per helicity assignment of their own gluons (item
+// tab->share_base[s] + helicity bits of s's gluons, 24 doubles: J, then (gamma.J) v for both antitop
+// helicities; page-interleaved, share_event); likewise the quark-line prefixes of k_prefix_level.
 // LHE (FP64 with a per-event record, for the event-level epilogues): the colour sum of every helicity of
 // the slot in its own row, out[(slot * 4 + 2 top + antitop) * stride + e] (zero for helicities outside
 // the mask), and the slot's sum over its good helicities of every |jamp|^2,
@@ -41,7 +50,7 @@ __device__ __forceinline__ void me_slot(const double* __restrict__ mom, const T*
   T PT[NSUB][4];
   T gprop[NSUB];
   T qc[NSUB][5];
-  cx<T> J[NSEQ][4];
+  cx<T> J[SHARED ? 1 : NSEQ][4];   // SHARED: read from the shared buffer where used
   cx<T> ub[2][4], vv[2][4];
   if constexpr (PREP) {
     using L = EvLayout<K>;
@@ -85,20 +94,25 @@ __device__ __forceinline__ void me_slot(const double* __restrict__ mom, const T*
 
   // ---- gluon currents (helicities of gc) ----
   constexpr bool kTableX = std::is_same<T, double>::value;
-  cx<T> X[kTableX ? 2 : 1][kTableX ? NSEQ : 1][4];
-  if constexpr (SHARED) {
-    const double* sh = share + static_cast<int64_t>(e) * tab->share_stride;
-    for (int s = 0; s < NSEQ; ++s) {
-      const double* it = sh + (tab->share_base[s] + pext_bits(gc, tab->seq_mask[s])) * 24;
+  cx<T> X[kTableX && !SHARED ? 2 : 1][kTableX && !SHARED ? NSEQ : 1][4];
+  // SHARED: the item of sequence s for this slot's helicities: J (8 doubles), then (gamma.J) v of both
+  // antitop helicities (8 each), loaded where used instead of copied to local memory
+  const double* shp = SHARED ? share_event(share, e, tab->share_stride) : nullptr;
+  auto sitem = [&](int s) -> const double* {
+    return shp + static_cast<int64_t>(tab->share_base[s] + pext_bits(gc, tab->seq_mask[s])) * 24 * kPage;
+  };
+  auto ldJ = [&](int s, cx<T>* o) {   // (SHARED implies FP64)
+    const double* it = sitem(s);
 #pragma unroll
-      for (int m = 0; m < 4; ++m) J[s][m] = {it[2 * m], it[2 * m + 1]};
+    for (int m = 0; m < 4; ++m) o[m] = {static_cast<T>(it[(2 * m) * kPage]), static_cast<T>(it[(2 * m + 1) * kPage])};
+  };
+  auto ldX = [&](int b, int s, cx<T>* o) {
+    const double* it = sitem(s) + (8 + 8 * b) * kPage;
 #pragma unroll
-      for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int m = 0; m < 4; ++m) X[b][s][m] = {it[8 + 8 * b + 2 * m], it[8 + 8 * b + 2 * m + 1]};
-    }
-  }
-  for (int s = K; s < (SHARED ? 0 : NSEQ); ++s) {
+    for (int m = 0; m < 4; ++m) o[m] = {static_cast<T>(it[(2 * m) * kPage]), static_cast<T>(it[(2 * m + 1) * kPage])};
+  };
+  if constexpr (!SHARED)
+  for (int s = K; s < NSEQ; ++s) {
     cx<T> acc[4] = {};
     const int n3 = tab->seq_nv3[s];
     for (int k = 0; k < n3; ++k) {
@@ -123,12 +137,27 @@ __device__ __forceinline__ void me_slot(const double* __restrict__ mom, const T*
     for (int k = 0; k < n3; ++k) {
       const int16_t rl = tab->full_v3[f][k][0], rr = tab->full_v3[f][k][1];
       const int il = rslot(rl), ir = rslot(rr);
-      v3_acc(acc, J[il], J[ir], PT[tab->seq_mask[il]], PT[tab->seq_mask[ir]], rneg(rl) != rneg(rr));
+      if constexpr (SHARED) {
+        cx<T> jl[4], jr[4];
+        ldJ(il, jl);
+        ldJ(ir, jr);
+        v3_acc(acc, jl, jr, PT[tab->seq_mask[il]], PT[tab->seq_mask[ir]], rneg(rl) != rneg(rr));
+      } else {
+        v3_acc(acc, J[il], J[ir], PT[tab->seq_mask[il]], PT[tab->seq_mask[ir]], rneg(rl) != rneg(rr));
+      }
     }
     const int n4 = tab->full_nv4[f];
     for (int k = 0; k < n4; ++k) {
       const int16_t ra = tab->full_v4[f][k][0], rb = tab->full_v4[f][k][1], rc = tab->full_v4[f][k][2];
-      v4_acc(acc, J[rslot(ra)], J[rslot(rb)], J[rslot(rc)], gs, rneg(ra) ^ rneg(rb) ^ rneg(rc));
+      if constexpr (SHARED) {
+        cx<T> ja[4], jb[4], jc[4];
+        ldJ(rslot(ra), ja);
+        ldJ(rslot(rb), jb);
+        ldJ(rslot(rc), jc);
+        v4_acc(acc, ja, jb, jc, gs, rneg(ra) ^ rneg(rb) ^ rneg(rc));
+      } else {
+        v4_acc(acc, J[rslot(ra)], J[rslot(rb)], J[rslot(rc)], gs, rneg(ra) ^ rneg(rb) ^ rneg(rc));
+      }
     }
     const T fz = gprop[NSUB - 1];
 #pragma unroll
@@ -187,31 +216,42 @@ __device__ __forceinline__ void me_slot(const double* __restrict__ mom, const T*
             int hm = 0;
             for (int j = 0; j < m; ++j) hm |= ((gc >> tab->perm[c][j]) & 1) << j;
             const int node = (((c / kFactorial[K - m]) << m | hm) << 1) | a;
-            const double* it = share + static_cast<int64_t>(e) * tab->share_stride + tab->share_n * 24 +
-                               (tab->pref_off[m] + node) * 8;
+            const double* it = shp + static_cast<int64_t>(tab->share_n * 24 + (tab->pref_off[m] + node) * 8) * kPage;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) stk[m][q] = {it[2 * q], it[2 * q + 1]};
+            for (int q = 0; q < 4; ++q) stk[m][q] = {it[(2 * q) * kPage], it[(2 * q + 1) * kPage]};
             continue;
           }
         }
         cx<T> acc[4] = {};
         for (int j = 0; j < m; ++j) {
           const int16_t r = tab->sub[c][j][m];
-          row_gamma_acc(acc, stk[j], J[rslot(r)], rneg(r));
+          if constexpr (SHARED) {
+            cx<T> jr[4];
+            ldJ(rslot(r), jr);
+            row_gamma_acc(acc, stk[j], jr, rneg(r));
+          } else {
+            row_gamma_acc(acc, stk[j], J[rslot(r)], rneg(r));
+          }
         }
         row_prop(acc, qc[tab->prefix_mask[c][m]], stk[m]);
       }
       const int fi = tab->full_idx[c];
       const int fidx = fi >= 0 ? fi : -fi - 1;
       const bool fneg = fi < 0 && !(K & 1);   // reflection sign (-1)^(K+1)
-      if (kTableX) {
+      if constexpr (kTableX) {
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
           cx<T> amp = mdot(Jq[b], JF[fidx]);   // all gluons on one current: ubar gamma.J v = Jq.J
           if (fneg) amp = cneg(amp);
           for (int j = 1; j < K; ++j) {
             const int16_t r = tab->sub[c][j][K];
-            sdot_acc(amp, stk[j], X[b][rslot(r)], rneg(r));
+            if constexpr (SHARED) {
+              cx<T> x[4];
+              ldX(b, rslot(r), x);
+              sdot_acc(amp, stk[j], x, rneg(r));
+            } else {
+              sdot_acc(amp, stk[j], X[b][rslot(r)], rneg(r));
+            }
           }
           A[b][c] = amp;
         }
@@ -344,20 +384,24 @@ k_share_level(const double* __restrict__ rec, int64_t nevt, const Tables* __rest
               int s0, int s1, double* __restrict__ share) {
   using L = EvLayout<K>;
   const int per_ev = (s1 - s0) << level;
+  // thread -> (item of the level, page of 32 events, event in the page): a warp writes one item of 32
+  // consecutive events, one 256-byte line per double
+  const int64_t npage = (nevt + kPage - 1) / kPage;
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= nevt * per_ev) return;
-  const int64_t e = t / per_ev;
-  const int j = static_cast<int>(t - e * per_ev);
+  if (t >= npage * kPage * per_ev) return;
+  const int j = static_cast<int>(t / (npage * kPage));
+  const int64_t e = t - j * npage * kPage;
+  if (e >= nevt) return;
   const int s = s0 + (j >> level), h = j & ((1 << level) - 1);
   const int msk = tab->seq_mask[s];
   const int gc = pdep_bits(h, msk);
   const double* in = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
   auto ld = [&](int item) -> double { return __ldg(in + item * kPage); };
-  double* sh = share + e * tab->share_stride;
+  double* sh = share_event(share, e, tab->share_stride);
   auto getJ = [&](int slot, cx<double>* J) {
-    const double* it = sh + (tab->share_base[slot] + pext_bits(gc, tab->seq_mask[slot])) * 24;
+    const double* it = sh + static_cast<int64_t>(tab->share_base[slot] + pext_bits(gc, tab->seq_mask[slot])) * 24 * kPage;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) J[m] = {it[2 * m], it[2 * m + 1]};
+    for (int m = 0; m < 4; ++m) J[m] = {it[(2 * m) * kPage], it[(2 * m + 1) * kPage]};
   };
   auto getP = [&](int slot, double* P) {
 #pragma unroll
@@ -396,11 +440,11 @@ k_share_level(const double* __restrict__ rec, int64_t nevt, const Tables* __rest
 #pragma unroll
     for (int m = 0; m < 4; ++m) J[m] = cscale(f, acc[m]);
   }
-  double* out = sh + (tab->share_base[s] + h) * 24;
+  double* out = sh + static_cast<int64_t>(tab->share_base[s] + h) * 24 * kPage;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
-    out[2 * m] = J[m].r;
-    out[2 * m + 1] = J[m].i;
+    out[(2 * m) * kPage] = J[m].r;
+    out[(2 * m + 1) * kPage] = J[m].i;
   }
 #pragma unroll
   for (int b = 0; b < 2; ++b) {
@@ -410,8 +454,8 @@ k_share_level(const double* __restrict__ rec, int64_t nevt, const Tables* __rest
     gamma_col(J, v, X);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      out[8 + 8 * b + 2 * m] = X[m].r;
-      out[8 + 8 * b + 2 * m + 1] = X[m].i;
+      out[(8 + 8 * b + 2 * m) * kPage] = X[m].r;
+      out[(8 + 8 * b + 2 * m + 1) * kPage] = X[m].i;
     }
   }
 }
@@ -428,15 +472,18 @@ k_prefix_level(const double* __restrict__ rec, int64_t nevt, const Tables* __res
   using L = EvLayout<K>;
   const int m = level;
   const int per_ev = (kFactorial[K] / kFactorial[K - m]) << (m + 1);
+  // thread -> (node of the level, page, event in the page), as k_share_level
+  const int64_t npage = (nevt + kPage - 1) / kPage;
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (t >= nevt * per_ev) return;
-  const int64_t e = t / per_ev;
-  const int node = static_cast<int>(t - e * per_ev);
+  if (t >= npage * kPage * per_ev) return;
+  const int node = static_cast<int>(t / (npage * kPage));
+  const int64_t e = t - node * npage * kPage;
+  if (e >= nevt) return;
   const int a = node & 1, h = (node >> 1) & ((1 << m) - 1), p = node >> (m + 1);
   const int c0 = p * kFactorial[K - m];   // the first ordering with this prefix
   const double* in = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
-  double* sh = share + e * tab->share_stride;
-  double* pref = sh + tab->share_n * 24;
+  double* sh = share_event(share, e, tab->share_stride);
+  double* pref = sh + static_cast<int64_t>(tab->share_n) * 24 * kPage;
   int gcp = 0;   // the prefix gluons' helicity bits, by gluon
   for (int j = 0; j < m; ++j) gcp |= ((h >> j) & 1) << tab->perm[c0][j];
   cx<double> stk[K][4];
@@ -445,17 +492,18 @@ k_prefix_level(const double* __restrict__ rec, int64_t nevt, const Tables* __res
     stk[0][q] = {__ldg(in + (L::UB + (a * 4 + q) * 2) * kPage), __ldg(in + (L::UB + (a * 4 + q) * 2 + 1) * kPage)};
   for (int j = 1; j < m; ++j) {
     const int nj = (((c0 / kFactorial[K - j]) << j | (h & ((1 << j) - 1))) << 1) | a;
-    const double* it = pref + (tab->pref_off[j] + nj) * 8;
+    const double* it = pref + static_cast<int64_t>(tab->pref_off[j] + nj) * 8 * kPage;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) stk[j][q] = {it[2 * q], it[2 * q + 1]};
+    for (int q = 0; q < 4; ++q) stk[j][q] = {it[(2 * q) * kPage], it[(2 * q + 1) * kPage]};
   }
   cx<double> acc[4] = {};
   for (int j = 0; j < m; ++j) {
     const int16_t r = tab->sub[c0][j][m];
-    const double* it = sh + (tab->share_base[rslot(r)] + pext_bits(gcp, tab->seq_mask[rslot(r)])) * 24;
+    const double* it =
+        sh + static_cast<int64_t>(tab->share_base[rslot(r)] + pext_bits(gcp, tab->seq_mask[rslot(r)])) * 24 * kPage;
     cx<double> Jr[4];
 #pragma unroll
-    for (int q = 0; q < 4; ++q) Jr[q] = {it[2 * q], it[2 * q + 1]};
+    for (int q = 0; q < 4; ++q) Jr[q] = {it[(2 * q) * kPage], it[(2 * q + 1) * kPage]};
     row_gamma_acc(acc, stk[j], Jr, rneg(r));
   }
   double qc[5];
@@ -464,11 +512,11 @@ k_prefix_level(const double* __restrict__ rec, int64_t nevt, const Tables* __res
   for (int i = 0; i < 5; ++i) qc[i] = __ldg(in + (L::QC + 5 * pm + i) * kPage);
   cx<double> o[4];
   row_prop(acc, qc, o);
-  double* out = pref + (tab->pref_off[m] + node) * 8;
+  double* out = pref + static_cast<int64_t>(tab->pref_off[m] + node) * 8 * kPage;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    out[2 * q] = o[q].r;
-    out[2 * q + 1] = o[q].i;
+    out[(2 * q) * kPage] = o[q].r;
+    out[(2 * q + 1) * kPage] = o[q].i;
   }
 }
 
