@@ -47,21 +47,40 @@ __device__ __forceinline__ void me_slot(const double* __restrict__ mom, const T*
   constexpr int NFULL = Sizes<K>::nfull;
   constexpr int NSUB = 1 << K;
   const T gs = static_cast<T>(cst.gs);
-  T PT[NSUB][4];
-  T gprop[NSUB];
-  T qc[NSUB][5];
+  // SHARED: the record's subset momenta, gluon propagators and quark-propagator coefficients are read
+  // from the (page-interleaved) record where used, like the shared currents, not copied to local memory
+  T PT[SHARED ? 1 : NSUB][4];
+  T gprop[SHARED ? 1 : NSUB];
+  T qc[SHARED ? 1 : NSUB][5];
   cx<T> J[SHARED ? 1 : NSEQ][4];   // SHARED: read from the shared buffer where used
   cx<T> ub[2][4], vv[2][4];
+  const T* rin = PREP ? rec + (e / kPage) * EvLayout<K>::NITEM * kPage + (e % kPage) : nullptr;
+  auto getPT = [&](int S, T* P) {
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      if constexpr (SHARED) P[m] = __ldg(rin + (EvLayout<K>::PT + 4 * S + m) * kPage);
+      else P[m] = PT[S][m];
+    }
+  };
+  auto getQC = [&](int S, T* q) {
+#pragma unroll
+    for (int c = 0; c < 5; ++c) {
+      if constexpr (SHARED) q[c] = __ldg(rin + (EvLayout<K>::QC + 5 * S + c) * kPage);
+      else q[c] = qc[S][c];
+    }
+  };
   if constexpr (PREP) {
     using L = EvLayout<K>;
-    const T* in = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
+    const T* in = rin;
+    if constexpr (!SHARED) {
 #pragma unroll
-    for (int S = 0; S < NSUB; ++S) {
+      for (int S = 0; S < NSUB; ++S) {
 #pragma unroll
-      for (int m = 0; m < 4; ++m) PT[S][m] = __ldg(in + (L::PT + 4 * S + m) * kPage);
-      gprop[S] = __ldg(in + (L::GP + S) * kPage);
+        for (int m = 0; m < 4; ++m) PT[S][m] = __ldg(in + (L::PT + 4 * S + m) * kPage);
+        gprop[S] = __ldg(in + (L::GP + S) * kPage);
 #pragma unroll
-      for (int c = 0; c < 5; ++c) qc[S][c] = __ldg(in + (L::QC + 5 * S + c) * kPage);
+        for (int c = 0; c < 5; ++c) qc[S][c] = __ldg(in + (L::QC + 5 * S + c) * kPage);
+      }
     }
     if constexpr (!SHARED) {
 #pragma unroll
@@ -139,9 +158,12 @@ __device__ __forceinline__ void me_slot(const double* __restrict__ mom, const T*
       const int il = rslot(rl), ir = rslot(rr);
       if constexpr (SHARED) {
         cx<T> jl[4], jr[4];
+        T pl[4], pr[4];
         ldJ(il, jl);
         ldJ(ir, jr);
-        v3_acc(acc, jl, jr, PT[tab->seq_mask[il]], PT[tab->seq_mask[ir]], rneg(rl) != rneg(rr));
+        getPT(tab->seq_mask[il], pl);
+        getPT(tab->seq_mask[ir], pr);
+        v3_acc(acc, jl, jr, pl, pr, rneg(rl) != rneg(rr));
       } else {
         v3_acc(acc, J[il], J[ir], PT[tab->seq_mask[il]], PT[tab->seq_mask[ir]], rneg(rl) != rneg(rr));
       }
@@ -159,7 +181,9 @@ __device__ __forceinline__ void me_slot(const double* __restrict__ mom, const T*
         v4_acc(acc, J[rslot(ra)], J[rslot(rb)], J[rslot(rc)], gs, rneg(ra) ^ rneg(rb) ^ rneg(rc));
       }
     }
-    const T fz = gprop[NSUB - 1];
+    T fz;
+    if constexpr (SHARED) fz = __ldg(rin + (EvLayout<K>::GP + NSUB - 1) * kPage);
+    else fz = gprop[NSUB - 1];
 #pragma unroll
     for (int m = 0; m < 4; ++m) JF[f][m] = cscale(fz, acc[m]);
   }
@@ -233,7 +257,13 @@ __device__ __forceinline__ void me_slot(const double* __restrict__ mom, const T*
             row_gamma_acc(acc, stk[j], J[rslot(r)], rneg(r));
           }
         }
-        row_prop(acc, qc[tab->prefix_mask[c][m]], stk[m]);
+        if constexpr (SHARED) {
+          T q[5];
+          getQC(tab->prefix_mask[c][m], q);
+          row_prop(acc, q, stk[m]);
+        } else {
+          row_prop(acc, qc[tab->prefix_mask[c][m]], stk[m]);
+        }
       }
       const int fi = tab->full_idx[c];
       const int fidx = fi >= 0 ? fi : -fi - 1;
