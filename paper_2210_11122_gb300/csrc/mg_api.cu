@@ -79,12 +79,13 @@ void flop_model(const mg::Tables& t, const uint32_t* mask, bool fp32, bool share
       per_slot += 2.0 * gamma_col * t.nseq;
   }
   // shared (FP64): the quark-line prefixes of lengths 1 .. pref_levels once per helicity assignment of
-  // their gluons and top helicity per event (k_prefix_level), the longer ones in the slot's walk
+  // their gluons and top helicity per event (k_prefix_level: both top helicities share each current's
+  // gamma.J entries, the 8 additions of row_gamma), the longer ones in the slot's walk
   const int plev = shared ? t.pref_levels : 0;
   for (int m = 1; m <= plev; ++m) {
     int orderings = 1;
     for (int i = 0; i < m; ++i) orderings *= K - i;
-    shared_work += static_cast<double>((orderings << m) * 2) * (row_gamma * m + row_prop);
+    shared_work += static_cast<double>(orderings << m) * (8.0 * m + 2.0 * ((row_gamma - 8.0) * m + row_prop));
   }
   double walk = 50.0 + 2.0 * 72.0;                                 // ubar, two quark currents
   for (int c = 0; c < t.ncol; ++c) {

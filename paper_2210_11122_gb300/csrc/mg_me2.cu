@@ -229,7 +229,7 @@ static cudaError_t launch_share_k(const void* rec, int64_t nevt, const Tables* t
   for (int m = 1; m <= levels; ++m) {
     int orderings = 1;
     for (int i = 0; i < m; ++i) orderings *= K - i;
-    const int64_t threads = (nevt + kPage - 1) / kPage * kPage * (static_cast<int64_t>(orderings) << (m + 1));
+    const int64_t threads = (nevt + kPage - 1) / kPage * kPage * (static_cast<int64_t>(orderings) << m);
     if (threads > 0)
       { v2::k_prefix_level<K><<<static_cast<unsigned>((threads + 127) / 128), 128, 0, st>>>(
           static_cast<const double*>(rec), nevt, tab, m, share); mg::note_launch(); }

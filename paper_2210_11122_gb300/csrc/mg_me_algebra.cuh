@@ -277,17 +277,33 @@ __device__ __forceinline__ void v4_acc(cx<T>* acc, const cx<T>* JA, const cx<T>*
   }
 }
 
+// gamma.J in the chiral basis by its four distinct entries (sign (+/-) applied), so that several row
+// spinors can be multiplied into the same current
+template <class T> struct Slash { cx<T> a, b, jm, jp; };
+template <class T>
+__device__ __forceinline__ Slash<T> slash_of(const cx<T>* J, bool neg) {
+  Slash<T> g;
+  g.jm = {J[1].r + J[2].i, J[1].i - J[2].r};   // J1 - i J2
+  g.jp = {J[1].r - J[2].i, J[1].i + J[2].r};   // J1 + i J2
+  g.a = {J[0].r + J[3].r, J[0].i + J[3].i};
+  g.b = {J[0].r - J[3].r, J[0].i - J[3].i};
+  if (neg) { g.jm = cneg(g.jm); g.jp = cneg(g.jp); g.a = cneg(g.a); g.b = cneg(g.b); }
+  return g;
+}
+
+// acc += s g  (row spinor s times a current's gamma.J entries)
+template <class T>
+__device__ __forceinline__ void row_slash_acc(cx<T>* acc, const cx<T>* s, const Slash<T>& g) {
+  cmac(acc[0], s[2], g.a); cmac(acc[0], s[3], g.jp);
+  cmac(acc[1], s[2], g.jm); cmac(acc[1], s[3], g.b);
+  cmac(acc[2], s[0], g.b); cmsub(acc[2], s[1], g.jp);
+  cmac(acc[3], s[1], g.a); cmsub(acc[3], s[0], g.jm);
+}
+
 // acc (+/-)= s gamma.J  (row spinor s, gluon current J)
 template <class T>
 __device__ __forceinline__ void row_gamma_acc(cx<T>* acc, const cx<T>* s, const cx<T>* J, bool neg) {
-  cx<T> jm = {J[1].r + J[2].i, J[1].i - J[2].r};   // J1 - i J2
-  cx<T> jp = {J[1].r - J[2].i, J[1].i + J[2].r};   // J1 + i J2
-  cx<T> a = {J[0].r + J[3].r, J[0].i + J[3].i}, b = {J[0].r - J[3].r, J[0].i - J[3].i};
-  if (neg) { jm = cneg(jm); jp = cneg(jp); a = cneg(a); b = cneg(b); }
-  cmac(acc[0], s[2], a); cmac(acc[0], s[3], jp);
-  cmac(acc[1], s[2], jm); cmac(acc[1], s[3], b);
-  cmac(acc[2], s[0], b); cmsub(acc[2], s[1], jp);
-  cmac(acc[3], s[1], a); cmsub(acc[3], s[0], jm);
+  row_slash_acc(acc, s, slash_of(J, neg));
 }
 
 // (gamma.J) v

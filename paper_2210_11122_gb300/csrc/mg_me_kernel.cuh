@@ -493,40 +493,31 @@ k_share_level(const double* __restrict__ rec, int64_t nevt, const Tables* __rest
 // Quark-line prefixes shared between gluon-helicity combinations (FP64): the row spinor after the first
 // `level` gluons of an ordering, for every helicity assignment of those gluons and both top helicities,
 // from the top spinor, the lower levels' nodes and the shared currents, by the same operations as the
-// slot kernel's walk (so the results are bit-identical).  One thread per (event, node of the level);
-// levels run in order 1 .. tab->pref_levels after the current levels.
+// slot kernel's walk (so the results are bit-identical).  One thread per (event, node pair of the level):
+// the two top helicities of a node share its currents' gamma.J entries and propagator coefficients.
+// Levels run in order 1 .. tab->pref_levels after the current levels.
 template <int K>
 __global__ void __launch_bounds__(128)
 k_prefix_level(const double* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab, int level,
                double* __restrict__ share) {
   using L = EvLayout<K>;
   const int m = level;
-  const int per_ev = (kFactorial[K] / kFactorial[K - m]) << (m + 1);
-  // thread -> (node of the level, page, event in the page), as k_share_level
+  const int per_ev = (kFactorial[K] / kFactorial[K - m]) << m;   // node pairs (ordering prefix, helicities)
+  // thread -> (node pair of the level, page, event in the page), as k_share_level
   const int64_t npage = (nevt + kPage - 1) / kPage;
   const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= npage * kPage * per_ev) return;
-  const int node = static_cast<int>(t / (npage * kPage));
-  const int64_t e = t - node * npage * kPage;
+  const int pair = static_cast<int>(t / (npage * kPage));
+  const int64_t e = t - pair * npage * kPage;
   if (e >= nevt) return;
-  const int a = node & 1, h = (node >> 1) & ((1 << m) - 1), p = node >> (m + 1);
+  const int h = pair & ((1 << m) - 1), p = pair >> m;
   const int c0 = p * kFactorial[K - m];   // the first ordering with this prefix
   const double* in = rec + (e / kPage) * L::NITEM * kPage + (e % kPage);
   double* sh = share_event(share, e, tab->share_stride);
   double* pref = sh + static_cast<int64_t>(tab->share_n) * 24 * kPage;
   int gcp = 0;   // the prefix gluons' helicity bits, by gluon
   for (int j = 0; j < m; ++j) gcp |= ((h >> j) & 1) << tab->perm[c0][j];
-  cx<double> stk[K][4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    stk[0][q] = {__ldg(in + (L::UB + (a * 4 + q) * 2) * kPage), __ldg(in + (L::UB + (a * 4 + q) * 2 + 1) * kPage)};
-  for (int j = 1; j < m; ++j) {
-    const int nj = (((c0 / kFactorial[K - j]) << j | (h & ((1 << j) - 1))) << 1) | a;
-    const double* it = pref + static_cast<int64_t>(tab->pref_off[j] + nj) * 8 * kPage;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) stk[j][q] = {it[(2 * q) * kPage], it[(2 * q + 1) * kPage]};
-  }
-  cx<double> acc[4] = {};
+  Slash<double> g[K];
   for (int j = 0; j < m; ++j) {
     const int16_t r = tab->sub[c0][j][m];
     const double* it =
@@ -534,19 +525,34 @@ k_prefix_level(const double* __restrict__ rec, int64_t nevt, const Tables* __res
     cx<double> Jr[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) Jr[q] = {it[(2 * q) * kPage], it[(2 * q + 1) * kPage]};
-    row_gamma_acc(acc, stk[j], Jr, rneg(r));
+    g[j] = slash_of(Jr, rneg(r));
   }
   double qc[5];
   const int pm = tab->prefix_mask[c0][m];
 #pragma unroll
   for (int i = 0; i < 5; ++i) qc[i] = __ldg(in + (L::QC + 5 * pm + i) * kPage);
-  cx<double> o[4];
-  row_prop(acc, qc, o);
-  double* out = pref + static_cast<int64_t>(tab->pref_off[m] + node) * 8 * kPage;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    out[(2 * q) * kPage] = o[q].r;
-    out[(2 * q + 1) * kPage] = o[q].i;
+  for (int a = 0; a < 2; ++a) {
+    cx<double> stk[K][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      stk[0][q] = {__ldg(in + (L::UB + (a * 4 + q) * 2) * kPage), __ldg(in + (L::UB + (a * 4 + q) * 2 + 1) * kPage)};
+    for (int j = 1; j < m; ++j) {
+      const int nj = (((c0 / kFactorial[K - j]) << j | (h & ((1 << j) - 1))) << 1) | a;
+      const double* it = pref + static_cast<int64_t>(tab->pref_off[j] + nj) * 8 * kPage;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) stk[j][q] = {it[(2 * q) * kPage], it[(2 * q + 1) * kPage]};
+    }
+    cx<double> acc[4] = {};
+    for (int j = 0; j < m; ++j) row_slash_acc(acc, stk[j], g[j]);
+    cx<double> o[4];
+    row_prop(acc, qc, o);
+    double* out = pref + static_cast<int64_t>(tab->pref_off[m] + (pair << 1 | a)) * 8 * kPage;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      out[(2 * q) * kPage] = o[q].r;
+      out[(2 * q + 1) * kPage] = o[q].i;
+    }
   }
 }
 
