@@ -230,9 +230,14 @@ static cudaError_t launch_share_k(const void* rec, int64_t nevt, const Tables* t
     int orderings = 1;
     for (int i = 0; i < m; ++i) orderings *= K - i;
     const int64_t threads = (nevt + kPage - 1) / kPage * kPage * (static_cast<int64_t>(orderings) << m);
-    if (threads > 0)
-      { v2::k_prefix_level<K><<<static_cast<unsigned>((threads + 127) / 128), 128, 0, st>>>(
-          static_cast<const double*>(rec), nevt, tab, m, share); mg::note_launch(); }
+    const unsigned blocks = static_cast<unsigned>((threads + 127) / 128);
+    const double* r = static_cast<const double*>(rec);
+    if (threads > 0) {
+      if (m == 1) v2::k_prefix_level<K, 1><<<blocks, 128, 0, st>>>(r, nevt, tab, share);
+      if constexpr (K >= 3) if (m == 2) v2::k_prefix_level<K, 2><<<blocks, 128, 0, st>>>(r, nevt, tab, share);
+      if constexpr (K >= 4) if (m == 3) v2::k_prefix_level<K, 3><<<blocks, 128, 0, st>>>(r, nevt, tab, share);
+      mg::note_launch();
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -495,13 +495,14 @@ k_share_level(const double* __restrict__ rec, int64_t nevt, const Tables* __rest
 // from the top spinor, the lower levels' nodes and the shared currents, by the same operations as the
 // slot kernel's walk (so the results are bit-identical).  One thread per (event, node pair of the level):
 // the two top helicities of a node share its currents' gamma.J entries and propagator coefficients.
-// Levels run in order 1 .. tab->pref_levels after the current levels.
-template <int K>
+// Levels M run in order 1 .. tab->pref_levels after the current levels (M a template argument, so that
+// the per-level arrays stay in registers).
+template <int K, int M>
 __global__ void __launch_bounds__(128)
-k_prefix_level(const double* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab, int level,
+k_prefix_level(const double* __restrict__ rec, int64_t nevt, const Tables* __restrict__ tab,
                double* __restrict__ share) {
   using L = EvLayout<K>;
-  const int m = level;
+  constexpr int m = M;
   const int per_ev = (kFactorial[K] / kFactorial[K - m]) << m;   // node pairs (ordering prefix, helicities)
   // thread -> (node pair of the level, page, event in the page), as k_share_level
   const int64_t npage = (nevt + kPage - 1) / kPage;
@@ -516,8 +517,10 @@ k_prefix_level(const double* __restrict__ rec, int64_t nevt, const Tables* __res
   double* sh = share_event(share, e, tab->share_stride);
   double* pref = sh + static_cast<int64_t>(tab->share_n) * 24 * kPage;
   int gcp = 0;   // the prefix gluons' helicity bits, by gluon
+#pragma unroll
   for (int j = 0; j < m; ++j) gcp |= ((h >> j) & 1) << tab->perm[c0][j];
-  Slash<double> g[K];
+  Slash<double> g[m];
+#pragma unroll
   for (int j = 0; j < m; ++j) {
     const int16_t r = tab->sub[c0][j][m];
     const double* it =
@@ -533,10 +536,11 @@ k_prefix_level(const double* __restrict__ rec, int64_t nevt, const Tables* __res
   for (int i = 0; i < 5; ++i) qc[i] = __ldg(in + (L::QC + 5 * pm + i) * kPage);
 #pragma unroll
   for (int a = 0; a < 2; ++a) {
-    cx<double> stk[K][4];
+    cx<double> stk[m][4];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
       stk[0][q] = {__ldg(in + (L::UB + (a * 4 + q) * 2) * kPage), __ldg(in + (L::UB + (a * 4 + q) * 2 + 1) * kPage)};
+#pragma unroll
     for (int j = 1; j < m; ++j) {
       const int nj = (((c0 / kFactorial[K - j]) << j | (h & ((1 << j) - 1))) << 1) | a;
       const double* it = pref + static_cast<int64_t>(tab->pref_off[j] + nj) * 8 * kPage;
@@ -544,6 +548,7 @@ k_prefix_level(const double* __restrict__ rec, int64_t nevt, const Tables* __res
       for (int q = 0; q < 4; ++q) stk[j][q] = {it[(2 * q) * kPage], it[(2 * q + 1) * kPage]};
     }
     cx<double> acc[4] = {};
+#pragma unroll
     for (int j = 0; j < m; ++j) row_slash_acc(acc, stk[j], g[j]);
     cx<double> o[4];
     row_prop(acc, qc, o);
